@@ -1,0 +1,400 @@
+"""Benchmark: block simulation of a mixed-radix state vector on GB300.
+
+Workload: 12 qubits + 8 qutrits in a seeded wire order (26,873,856
+amplitudes), 500 gates of a Clifford+T-like hybrid mix (qubit H/S/T/CNOT,
+qutrit F_3/Z_3/X_3/controlled-X_3).  One step = reset to |0...0>, apply the
+500 gates, read the norm.  Metric: amplitude-gate updates per second
+(sum over gates of D / prod d_controls).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec c64|c128] [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the
+workload on its own GPU (the per-gate path has no exchange step when each
+GPU holds a whole state); time is the max over ranks and the value sums the
+ranks' updates ("weak" scaling).  ``--impl reference`` times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = "12 qubits + 8 qutrits (26,873,856 amplitudes), depth 500 hybrid Clifford+T-like mix, seed 1"
+METRIC = "amp-gate updates/s"
+UNIT = "updates/s"
+L2_BYTES = 129e6
+
+
+# ----------------------------------------------------------------------------------------------
+# Host logic (tested on CPU)
+# ----------------------------------------------------------------------------------------------
+def gate_updates(dims, gate) -> int:
+    """Logical amplitude updates of one gate: D / prod(d_controls)."""
+    D = int(np.prod(np.asarray(dims, dtype=np.int64)))
+    for c in gate.controls:
+        D //= dims[c]
+    return D
+
+
+def circuit_updates(circ) -> int:
+    return sum(gate_updates(circ.dims, g) for g in circ.gates)
+
+
+def algorithmic_bytes(plan: dict, amp_bytes: int) -> int:
+    """Bytes a gate must read and write: every touched row of every visited class, once each way."""
+    return 2 * amp_bytes * int(plan["classes"]) * int(plan["touched_rows"])
+
+
+def aggregate(units_per_rank, seconds_per_rank):
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    t = max(seconds_per_rank)
+    return sum(units_per_rank) / t, t
+
+
+def parse_clocks(lines):
+    """Summarise `nvidia-smi --query-gpu=...` CSV lines sampled during the timed region."""
+    sm, smax, power, reasons = [], [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 9 or not parts[1].split()[0].isdigit():
+            continue
+        try:
+            sm.append(float(parts[1].split()[0]))
+            smax.append(float(parts[2].split()[0]))
+            power.append(float(parts[3].split()[0]))
+        except ValueError:
+            continue
+        for nm, val in zip(names, parts[5:9]):
+            if val.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    loaded = [s for s, p in zip(sm, power) if p > 0.3 * max(power)] or sm
+    return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader", "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln)
+
+    def stop(self):
+        if self.proc is None:
+            return parse_clocks([])
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        return parse_clocks(self.lines)
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("qd_kernels.cu", "qd_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2410_17876_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec_name: str):
+    """DRAM bytes per launch of the gate kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "gate_kernel_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    ent = d.get(prec_name)
+    return None if ent is None else ent.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------------------------
+# Distributed set-up
+# ----------------------------------------------------------------------------------------------
+def dist_setup(n_gpus: int):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = os.environ.get("QD_BENCH_BACKEND", "nccl")
+        if backend == "nccl":
+            import torch
+
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle baseline
+# ----------------------------------------------------------------------------------------------
+def oracle_sample(circ, budget_s: float, nthreads: int):
+    """Time the oracle on the first gates of the circuit on the full state until
+    about ``budget_s`` seconds of work; returns (updates/s, gates run, seconds)."""
+    import oracle
+
+    psi = oracle.zero_state(circ.dims)
+    tmp = np.empty_like(psi)
+    done, upd, t0 = 0, 0, time.perf_counter()
+    for g in circ.gates:
+        oracle.apply_gate(circ.dims, psi, g, nthreads=nthreads, out=tmp)
+        psi, tmp = tmp, psi
+        done += 1
+        upd += gate_updates(circ.dims, g)
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return upd / dt, done, dt
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_2410_17876_gb300 import inputs as gen
+
+    oracle.build()
+    circ = gen.config1_circuit()
+    nthreads = oracle.max_threads()
+    per_step_budget = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_sample(circ, per_step_budget / 4, nthreads)
+    vals, gates_run, secs = [], [], []
+    for _ in range(args.steps):
+        v, n, dt = oracle_sample(circ, per_step_budget, nthreads)
+        vals.append(v)
+        gates_run.append(n)
+        secs.append(dt)
+    value = statistics.median(vals)
+    sample = (f"first {min(gates_run)}-{max(gates_run)} of the 500 gates per step on the full "
+              f"26,873,856-amplitude state, FP64, {nthreads} OpenMP threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "prec": "c128 (FP64 CPU oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthreads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------------------
+def run_gpu(args):
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    barrier(world)
+    from paper_2410_17876_gb300 import binding as qb
+    from paper_2410_17876_gb300 import inputs as gen
+
+    prec = qb.QD_C64 if args.prec == "c64" else qb.QD_C128
+    amp_bytes = 8 if prec == qb.QD_C64 else 16
+    circ = gen.config1_circuit()
+    upd = circuit_updates(circ)
+    stream = torch.cuda.current_stream(local)
+    st = qb.State(circ.dims, prec=prec, stream=stream, device=local)
+
+    def step():
+        st.reset()
+        st.run(circ)
+        return st.norm()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device time with CUDA events on the launching stream ----
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize()
+    n0 = qb.qd_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    launches = qb.qd_launch_count() - n0
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    t_max = max_over_ranks(dev_s, world)
+    value, _ = aggregate([upd * args.steps] * world, [t_max] * world)
+
+    # ---- per-launch durations of the gate kernel (one extra, untimed step) ----
+    plans = [qb.qd_plan_gate(circ.dims, prec, g.wires, g.U, g.controls or None, g.values or None)
+             for g in circ.gates]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(circ.gates) + 1)]
+    st.reset()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i, g in enumerate(circ.gates):
+        st.apply(g)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    k_time, k_bytes, k_n = 0.0, 0, 0
+    for i, p in enumerate(plans):
+        if p["family"] == 0 and p["touched_rows"] > 0:
+            k_time += evs[i].elapsed_time(evs[i + 1]) / 1e3
+            k_bytes += algorithmic_bytes(p, amp_bytes)
+            k_n += 1
+    peak, peak_kind = measured_peaks()
+    achieved = k_bytes / k_time / 1e9 if k_time > 0 else 0.0
+    traffic = ncu_traffic(args.prec)
+
+    # ---- end to end through the public API with host buffers ----
+    pinned = torch.empty(circ.D, dtype=torch.complex64 if prec == qb.QD_C64 else torch.complex128,
+                         pin_memory=True)
+    host_out = pinned.numpy()
+    h2d = sum(g.U.size * 16 + 8 * len(g.controls) for g in circ.gates)
+    d2h = host_out.nbytes + 8
+    e2e_steps = max(1, min(args.steps, 5))
+    qb.qd_state_get_raw(st.handle, host_out)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        st.reset()
+        st.run(circ)
+        st.norm()
+        qb.qd_state_get_raw(st.handle, host_out)
+    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+    e2e_value = world * upd / e2e_s
+
+    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        nthreads = oracle.max_threads()
+        v, n, dt = oracle_sample(circ, args.cpu_seconds, nthreads)
+        cpu = {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
+               "sample": f"first {n} of the 500 gates on the full 26,873,856-amplitude state, FP64, "
+                         f"{dt:.1f} s"}
+    st.close()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == qb.QD_C64 else "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "prec": args.prec, "amplitudes": circ.D, "gates": len(circ.gates),
+                       "state_bytes": circ.D * amp_bytes,
+                       "l2": f"state {circ.D * amp_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2, no flush",
+                       "parallelism": f"replicas x{world}"},
+            "hbm_gbs_effective": sum(algorithmic_bytes(p, amp_bytes) for p in plans) * args.steps / t_max / 1e9,
+            "roofline": {"kernel": "k_gate1 (per-class register kernel, all gates of the circuit)",
+                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
+                         "launches_measured": k_n},
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

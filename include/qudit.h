@@ -1,0 +1,212 @@
+/*
+ * qudit.h -- C ABI of libqudit.so: GB300 (sm_103a) block simulation of
+ * mixed-radix (qubit-qudit hybrid) state vectors.
+ *
+ * Method: Velmurugan et al., "Fast classical simulation of qubit-qudit hybrid
+ * systems" (arXiv 2410.17876).  A gate is applied directly to the state
+ * vector, never by building the circuit unitary (section "Proposed
+ * Methodology").  For a gate on wire q_i of dimension d_i, the amplitudes
+ * that differ only in digit i form an equivalence class of d_i members
+ * spaced b_i = d_0 * ... * d_{i-1} apart (section "Superposition gates",
+ * table of equivalent classes); each class is multiplied by the d_i x d_i
+ * matrix.  Phase gates scale blocks (section "Phase Gates"), permutation
+ * gates rotate them (section "Permutation Gates"), and controlled gates act
+ * only on classes whose control digits match (section "Controlled and
+ * Multi-Controlled Gates").
+ *
+ * Conventions shared by every call:
+ *   - Wire q_0 is the least significant digit of a basis index; the digit
+ *     of wire w in index j is floor(j / b_w) mod d_w.
+ *   - Amplitudes are complex; host arrays are interleaved (re, im) IEEE
+ *     binary64, so a state of D amplitudes is 2*D doubles.
+ *   - Gate matrices are host arrays of P*P complex binary64, row-major,
+ *     interleaved (2*P*P doubles); row index = output basis state.  For a
+ *     gate on several wires the local index lists the first wire as least
+ *     significant.  A complex64 state rounds the matrix to binary32 once.
+ *   - Every call returns a qd_status; on failure it writes nothing to its
+ *     out-parameters and qd_last_error() holds a message (per thread).
+ *     No C++ exception crosses this boundary.
+ *   - Apply calls are asynchronous on the state's CUDA stream; input arrays
+ *     are copied before the call returns, so the caller may reuse them at
+ *     once.  Readouts to host memory synchronise the stream.
+ *   - A state is used by one host thread at a time.
+ */
+#ifndef QUDIT_H
+#define QUDIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qd_state qd_state;
+
+typedef int32_t qd_status;
+#define QD_OK 0
+#define QD_ERR_ARG 1         /* invalid argument (range, duplicate wire, null pointer) */
+#define QD_ERR_OOM 2         /* device or host allocation failed */
+#define QD_ERR_CUDA 3        /* a CUDA runtime call or kernel launch failed */
+#define QD_ERR_TIMEOUT 4     /* a bounded device-side wait gave up */
+#define QD_ERR_UNSUPPORTED 5 /* valid request outside this build's limits */
+#define QD_ERR_DEVICE 6      /* a kernel reported an error through its status word */
+
+/* Precision of the stored amplitudes. */
+#define QD_C64 0  /* complex64: binary32 re/im, binary32 arithmetic */
+#define QD_C128 1 /* complex128: binary64 re/im, binary64 arithmetic */
+
+/* Limits of this build. */
+#define QD_MAX_WIRES 48      /* wires per state */
+#define QD_MAX_DIM 64        /* dimension of one wire */
+#define QD_MAX_GATE_DIM 64   /* P = product of a gate's wire dimensions */
+#define QD_MAX_CONTROLS 16   /* control wires per gate */
+
+/* ------------------------------------------------------------------------
+ * State lifetime (section "Proposed Methodology": the state is the vector
+ * of D = d_0 * ... * d_{n-1} amplitudes; only that vector is stored).
+ * --------------------------------------------------------------------- */
+
+/* Create a state of n wires with dimensions dims[0..n-1] (each 2..QD_MAX_DIM)
+ * in |0...0>, its amplitudes in device memory owned by the library.
+ * stream: a cudaStream_t the state's work is issued on (NULL = legacy
+ * default stream).  QD_ERR_ARG for a bad dimension or D overflow,
+ * QD_ERR_OOM if the allocation fails. */
+qd_status qd_state_create(const int32_t* dims, int32_t n, int32_t prec, void* stream,
+                          qd_state** out);
+
+/* Wrap caller-owned device memory (for example a torch tensor) as a state.
+ * dev_ptr must be 16-byte aligned and hold at least D amplitudes of the
+ * given precision (bytes >= D * 8 for QD_C64, D * 16 for QD_C128); its
+ * contents are left as they are.  The caller keeps the memory alive until
+ * qd_state_destroy.  The library still allocates a small reduction
+ * workspace for the state. */
+qd_status qd_state_wrap(void* dev_ptr, size_t bytes, const int32_t* dims, int32_t n,
+                        int32_t prec, void* stream, qd_state** out);
+
+/* Release the state (and its memory if the library owns it).  Waits for the
+ * state's stream.  NULL is accepted. */
+qd_status qd_state_destroy(qd_state* st);
+
+/* Set the state to the basis state |0...0>. */
+qd_status qd_state_reset(qd_state* st);
+
+/* Issue the state's later work on another cudaStream_t (NULL = default). */
+qd_status qd_state_set_stream(qd_state* st, void* stream);
+
+/* Number of amplitudes D, number of wires and precision. Any out pointer may be NULL. */
+qd_status qd_state_info(const qd_state* st, int64_t* num_amplitudes, int32_t* num_wires,
+                        int32_t* prec);
+
+/* Device pointer of the amplitudes (interleaved re/im in the state's precision). */
+qd_status qd_state_device_ptr(const qd_state* st, void** dev_ptr);
+
+/* Copy 2*D host doubles (interleaved) into the state (rounded once to
+ * binary32 for QD_C64).  Synchronous. */
+qd_status qd_state_set_amplitudes(qd_state* st, const double* host_interleaved);
+
+/* Copy the state to 2*D host doubles (widened exactly for QD_C64). Synchronous. */
+qd_status qd_state_get_amplitudes(qd_state* st, double* host_interleaved);
+
+/* Copy the raw amplitudes (2*D floats for QD_C64, 2*D doubles for QD_C128)
+ * to host memory of `bytes` bytes.  Synchronous. */
+qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes);
+
+/* ------------------------------------------------------------------------
+ * Gates.
+ * --------------------------------------------------------------------- */
+
+/* Apply a d x d matrix U (d = dims[target]) to wire `target`: every class
+ * of d amplitudes spaced b_target apart is multiplied by U (section
+ * "Superposition gates").  Diagonal matrices are applied as phase gates
+ * (section "Phase Gates"; rows with an entry of exactly 1 are not touched)
+ * and matrices with one non-zero per row and column as permutations
+ * (section "Permutation Gates"); the result is the same as the dense
+ * product.  The matrix is not checked for unitarity. */
+qd_status qd_apply_gate(qd_state* st, int32_t target, const double* U);
+
+/* Controlled form (section "Controlled and Multi-Controlled Gates"): the two
+ * lists ctrl_wires[0..n_ctrl-1] and ctrl_vals[0..n_ctrl-1]; U acts only on
+ * basis states whose digit on every control wire equals its value, all
+ * other amplitudes are left unchanged.  Control wires must be distinct,
+ * differ from the target, and each value must be < its wire's dimension.
+ * Only the D / (d_target * prod d_c) matching classes are visited: the
+ * control digits are inserted into the enumeration instead of testing
+ * every index. n_ctrl = 0 is qd_apply_gate. */
+qd_status qd_apply_controlled(qd_state* st, int32_t target, const double* U,
+                              const int32_t* ctrl_wires, const int32_t* ctrl_vals,
+                              int32_t n_ctrl);
+
+/* Multi-wire gate: a P x P matrix on k distinct wires wires[0..k-1]
+ * (P = prod dims[wires[m]] <= QD_MAX_GATE_DIM; local index with wires[0]
+ * least significant), optionally controlled as in qd_apply_controlled
+ * (ctrl_wires/ctrl_vals may be NULL when n_ctrl = 0).  The paper treats
+ * multi-qudit gates in its problem statement (section "Proposed
+ * Methodology") and through controls; the class structure generalises to
+ * the P amplitudes that differ only in the digits of the gate's wires. */
+qd_status qd_apply_multi(qd_state* st, const int32_t* wires, int32_t k, const double* U,
+                         const int32_t* ctrl_wires, const int32_t* ctrl_vals, int32_t n_ctrl);
+
+/* ------------------------------------------------------------------------
+ * Readouts.  Sums run in binary64 with compensated (Neumaier) summation in
+ * a fixed order, so results are deterministic for a given state size.
+ * The paper defines no readout; these are the standard Born-rule
+ * quantities of the state vector.
+ * --------------------------------------------------------------------- */
+
+/* sum_j |psi_j|^2 into *out (host).  Synchronous. */
+qd_status qd_norm(qd_state* st, double* out);
+
+/* |psi_j|^2 for all j into host_out[0..D-1].  Synchronous. */
+qd_status qd_probabilities(qd_state* st, double* host_out);
+
+/* |psi_j|^2 into device memory dev_out[0..D-1] (8-byte aligned).  Asynchronous. */
+qd_status qd_probabilities_device(qd_state* st, double* dev_out);
+
+/* Marginal of one wire: host_out[x] = sum over j with digit_wire(j) = x of
+ * |psi_j|^2, for x < dims[wire].  Synchronous. */
+qd_status qd_marginal(qd_state* st, int32_t wire, double* host_out);
+
+/* Wait for all work issued on the state's stream. */
+qd_status qd_synchronize(qd_state* st);
+
+/* ------------------------------------------------------------------------
+ * Introspection (host only; no GPU needed).
+ * --------------------------------------------------------------------- */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* qd_last_error(void);
+
+/* Number of kernels this library has launched in the process so far. */
+uint64_t qd_launch_count(void);
+
+/* Library version string. */
+const char* qd_version(void);
+
+/* Plan of a gate without a GPU: which kernel family would run it
+ * (0 = per-class register kernel, 1 = shared-memory tile kernel),
+ * the number of classes visited, the vector width in amplitudes and the
+ * kind the matrix was classified as (0 dense, 1 diagonal, 2 permutation).
+ * Arguments as in qd_apply_multi plus the state's dims/prec. */
+typedef struct qd_plan_info {
+    int32_t family;
+    int32_t kind;
+    int32_t vec;
+    int32_t touched_rows; /* rows of each class that are written */
+    int64_t classes;      /* classes visited */
+    int64_t run;          /* contiguous run of the class enumeration, in amplitudes */
+} qd_plan_info;
+qd_status qd_plan_gate(const int32_t* dims, int32_t n, int32_t prec, const int32_t* wires,
+                       int32_t k, const double* U, const int32_t* ctrl_wires,
+                       const int32_t* ctrl_vals, int32_t n_ctrl, qd_plan_info* out);
+
+/* Host self-test of the index arithmetic (division by invariant integers
+ * and the class enumeration) against plain integer division on
+ * `trials` random cases.  QD_OK if every case agrees. */
+qd_status qd_selftest_host(int32_t trials);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QUDIT_H */

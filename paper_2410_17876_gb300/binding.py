@@ -1,0 +1,315 @@
+"""ctypes binding of ``libqudit.so`` (C ABI in ``include/qudit.h``).
+
+Argument marshalling only: every step of a gate application, readout or
+reset runs in the library's CUDA kernels.  The module raises on import if
+the library has not been built -- there is no CPU fallback.  PyTorch is used
+for device memory (``State`` wraps a torch tensor) and streams.
+
+The ``qd_*`` functions keep the C names and raise :class:`QuditError` on a
+non-zero status instead of returning it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import build as _build
+
+QD_OK, QD_ERR_ARG, QD_ERR_OOM, QD_ERR_CUDA, QD_ERR_TIMEOUT, QD_ERR_UNSUPPORTED, QD_ERR_DEVICE = range(7)
+QD_C64, QD_C128 = 0, 1
+QD_MAX_WIRES, QD_MAX_DIM, QD_MAX_GATE_DIM, QD_MAX_CONTROLS = 48, 64, 64, 16
+
+LIB_PATH = _build.LIB
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libqudit.so is not built ({LIB_PATH}); run paper_2410_17876_gb300.build.build() "
+                      "or __graft_entry__.build() first -- there is no CPU fallback")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_vp = ctypes.c_void_p
+
+
+class qd_plan_info(ctypes.Structure):
+    _fields_ = [("family", ctypes.c_int32), ("kind", ctypes.c_int32), ("vec", ctypes.c_int32),
+                ("touched_rows", ctypes.c_int32), ("classes", ctypes.c_int64), ("run", ctypes.c_int64)]
+
+
+_SIGS = {
+    "qd_state_create": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
+    "qd_state_wrap": (ctypes.c_int32, [_vp, ctypes.c_size_t, _i32p, ctypes.c_int32, ctypes.c_int32, _vp,
+                                       ctypes.POINTER(_vp)]),
+    "qd_state_destroy": (ctypes.c_int32, [_vp]),
+    "qd_state_reset": (ctypes.c_int32, [_vp]),
+    "qd_state_set_stream": (ctypes.c_int32, [_vp, _vp]),
+    "qd_state_info": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int64), _i32p, _i32p]),
+    "qd_state_device_ptr": (ctypes.c_int32, [_vp, ctypes.POINTER(_vp)]),
+    "qd_state_set_amplitudes": (ctypes.c_int32, [_vp, _f64p]),
+    "qd_state_get_amplitudes": (ctypes.c_int32, [_vp, _f64p]),
+    "qd_state_get_raw": (ctypes.c_int32, [_vp, _vp, ctypes.c_size_t]),
+    "qd_apply_gate": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
+    "qd_apply_controlled": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p, _i32p, _i32p, ctypes.c_int32]),
+    "qd_apply_multi": (ctypes.c_int32, [_vp, _i32p, ctypes.c_int32, _f64p, _i32p, _i32p, ctypes.c_int32]),
+    "qd_norm": (ctypes.c_int32, [_vp, _f64p]),
+    "qd_probabilities": (ctypes.c_int32, [_vp, _f64p]),
+    "qd_probabilities_device": (ctypes.c_int32, [_vp, _vp]),
+    "qd_marginal": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
+    "qd_synchronize": (ctypes.c_int32, [_vp]),
+    "qd_last_error": (ctypes.c_char_p, []),
+    "qd_launch_count": (ctypes.c_uint64, []),
+    "qd_version": (ctypes.c_char_p, []),
+    "qd_plan_gate": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _f64p,
+                                      _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(qd_plan_info)]),
+    "qd_selftest_host": (ctypes.c_int32, [ctypes.c_int32]),
+}
+
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class QuditError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib.qd_last_error().decode(errors="replace")
+        super().__init__(f"{where} failed with status {status}: {msg}")
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != QD_OK:
+        raise QuditError(rc, where)
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
+
+
+def _mat(U) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(U, dtype=np.complex128)).view(np.float64)
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _opt_i32(a):
+    if a is None or len(a) == 0:
+        return None, np.zeros(1, np.int32)
+    arr = _i32(a)
+    return _p(arr, _i32p), arr
+
+
+# --- C-ABI functions, same names ---------------------------------------------------------------
+def qd_state_create(dims: Sequence[int], prec: int = QD_C128, stream: int = 0) -> int:
+    d = _i32(dims)
+    out = _vp()
+    _check(_lib.qd_state_create(_p(d, _i32p), len(d), prec, _vp(stream), ctypes.byref(out)), "qd_state_create")
+    return out.value
+
+
+def qd_state_wrap(dev_ptr: int, nbytes: int, dims: Sequence[int], prec: int, stream: int = 0) -> int:
+    d = _i32(dims)
+    out = _vp()
+    _check(_lib.qd_state_wrap(_vp(dev_ptr), nbytes, _p(d, _i32p), len(d), prec, _vp(stream), ctypes.byref(out)),
+           "qd_state_wrap")
+    return out.value
+
+
+def qd_state_destroy(st: int) -> None:
+    _check(_lib.qd_state_destroy(_vp(st)), "qd_state_destroy")
+
+
+def qd_state_reset(st: int) -> None:
+    _check(_lib.qd_state_reset(_vp(st)), "qd_state_reset")
+
+
+def qd_state_set_stream(st: int, stream: int) -> None:
+    _check(_lib.qd_state_set_stream(_vp(st), _vp(stream)), "qd_state_set_stream")
+
+
+def qd_state_info(st: int):
+    D = ctypes.c_int64()
+    n = ctypes.c_int32()
+    p = ctypes.c_int32()
+    _check(_lib.qd_state_info(_vp(st), ctypes.byref(D), ctypes.byref(n), ctypes.byref(p)), "qd_state_info")
+    return D.value, n.value, p.value
+
+
+def qd_state_device_ptr(st: int) -> int:
+    out = _vp()
+    _check(_lib.qd_state_device_ptr(_vp(st), ctypes.byref(out)), "qd_state_device_ptr")
+    return out.value
+
+
+def qd_state_set_amplitudes(st: int, psi: np.ndarray) -> None:
+    a = np.ascontiguousarray(psi, dtype=np.complex128).view(np.float64)
+    D, _, _ = qd_state_info(st)
+    if a.size != 2 * D:
+        raise ValueError(f"expected {D} amplitudes, got {a.size // 2}")
+    _check(_lib.qd_state_set_amplitudes(_vp(st), _p(a, _f64p)), "qd_state_set_amplitudes")
+
+
+def qd_state_get_amplitudes(st: int) -> np.ndarray:
+    D, _, _ = qd_state_info(st)
+    out = np.empty(D, dtype=np.complex128)
+    _check(_lib.qd_state_get_amplitudes(_vp(st), _p(out.view(np.float64), _f64p)), "qd_state_get_amplitudes")
+    return out
+
+
+def qd_state_get_raw(st: int, out: Optional[np.ndarray] = None) -> np.ndarray:
+    """Native-precision amplitudes (complex64 or complex128), no widening."""
+    D, _, prec = qd_state_info(st)
+    dt = np.complex64 if prec == QD_C64 else np.complex128
+    if out is None:
+        out = np.empty(D, dtype=dt)
+    _check(_lib.qd_state_get_raw(_vp(st), _vp(out.ctypes.data), out.nbytes), "qd_state_get_raw")
+    return out
+
+
+def qd_apply_gate(st: int, target: int, U) -> None:
+    _check(_lib.qd_apply_gate(_vp(st), int(target), _p(_mat(U), _f64p)), "qd_apply_gate")
+
+
+def qd_apply_controlled(st: int, target: int, U, ctrl_wires, ctrl_vals) -> None:
+    cw, cwa = _opt_i32(ctrl_wires)
+    cv, cva = _opt_i32(ctrl_vals)
+    n = 0 if ctrl_wires is None else len(ctrl_wires)
+    _check(_lib.qd_apply_controlled(_vp(st), int(target), _p(_mat(U), _f64p), cw, cv, n), "qd_apply_controlled")
+
+
+def qd_apply_multi(st: int, wires, U, ctrl_wires=None, ctrl_vals=None) -> None:
+    w = _i32(wires)
+    cw, cwa = _opt_i32(ctrl_wires)
+    cv, cva = _opt_i32(ctrl_vals)
+    n = 0 if ctrl_wires is None else len(ctrl_wires)
+    _check(_lib.qd_apply_multi(_vp(st), _p(w, _i32p), len(w), _p(_mat(U), _f64p), cw, cv, n), "qd_apply_multi")
+
+
+def qd_norm(st: int) -> float:
+    out = ctypes.c_double()
+    _check(_lib.qd_norm(_vp(st), ctypes.byref(out)), "qd_norm")
+    return out.value
+
+
+def qd_probabilities(st: int) -> np.ndarray:
+    D, _, _ = qd_state_info(st)
+    out = np.empty(D, dtype=np.float64)
+    _check(_lib.qd_probabilities(_vp(st), _p(out, _f64p)), "qd_probabilities")
+    return out
+
+
+def qd_probabilities_device(st: int, dev_out: int) -> None:
+    _check(_lib.qd_probabilities_device(_vp(st), _vp(dev_out)), "qd_probabilities_device")
+
+
+def qd_marginal(st: int, wire: int, d: int) -> np.ndarray:
+    out = np.empty(int(d), dtype=np.float64)
+    _check(_lib.qd_marginal(_vp(st), int(wire), _p(out, _f64p)), "qd_marginal")
+    return out
+
+
+def qd_synchronize(st: int) -> None:
+    _check(_lib.qd_synchronize(_vp(st)), "qd_synchronize")
+
+
+def qd_last_error() -> str:
+    return _lib.qd_last_error().decode(errors="replace")
+
+
+def qd_launch_count() -> int:
+    return int(_lib.qd_launch_count())
+
+
+def qd_version() -> str:
+    return _lib.qd_version().decode()
+
+
+def qd_plan_gate(dims, prec, wires, U, ctrl_wires=None, ctrl_vals=None) -> dict:
+    d = _i32(dims)
+    w = _i32(wires)
+    cw, cwa = _opt_i32(ctrl_wires)
+    cv, cva = _opt_i32(ctrl_vals)
+    n = 0 if ctrl_wires is None else len(ctrl_wires)
+    info = qd_plan_info()
+    _check(_lib.qd_plan_gate(_p(d, _i32p), len(d), prec, _p(w, _i32p), len(w), _p(_mat(U), _f64p), cw, cv, n,
+                             ctypes.byref(info)), "qd_plan_gate")
+    return {f: getattr(info, f) for f, _ in qd_plan_info._fields_}
+
+
+def qd_selftest_host(trials: int = 200) -> None:
+    _check(_lib.qd_selftest_host(int(trials)), "qd_selftest_host")
+
+
+# --- convenience ----------------------------------------------------------------------------------
+class State:
+    """A state vector in torch-allocated device memory, driven through the C ABI.
+
+    ``prec`` is ``QD_C64`` or ``QD_C128``.  Work is issued on ``stream``
+    (a ``torch.cuda.Stream``; default: the current stream at creation).
+    """
+
+    def __init__(self, dims: Sequence[int], prec: int = QD_C128, stream=None, device: int = 0):
+        import torch
+
+        self.dims = tuple(int(x) for x in dims)
+        self.prec = prec
+        self.D = int(np.prod(np.asarray(self.dims, dtype=np.int64)))
+        dt = torch.float32 if prec == QD_C64 else torch.float64
+        torch.cuda.set_device(device)
+        self.buf = torch.empty(2 * self.D, dtype=dt, device=f"cuda:{device}")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(device)
+        self.handle = qd_state_wrap(self.buf.data_ptr(), self.buf.numel() * self.buf.element_size(), self.dims,
+                                    prec, self.stream.cuda_stream)
+        qd_state_reset(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            qd_state_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self):
+        qd_state_reset(self.handle)
+
+    def apply(self, gate) -> None:
+        """Apply an ``inputs.Gate``."""
+        if len(gate.wires) == 1 and not gate.controls:
+            qd_apply_gate(self.handle, gate.wires[0], gate.U)
+        elif len(gate.wires) == 1:
+            qd_apply_controlled(self.handle, gate.wires[0], gate.U, gate.controls, gate.values)
+        else:
+            qd_apply_multi(self.handle, gate.wires, gate.U, gate.controls, gate.values)
+
+    def run(self, circuit) -> None:
+        for g in circuit.gates:
+            self.apply(g)
+
+    def amplitudes(self) -> np.ndarray:
+        return qd_state_get_amplitudes(self.handle)
+
+    def raw(self) -> np.ndarray:
+        return qd_state_get_raw(self.handle)
+
+    def set_amplitudes(self, psi) -> None:
+        qd_state_set_amplitudes(self.handle, psi)
+
+    def norm(self) -> float:
+        return qd_norm(self.handle)
+
+    def probabilities(self) -> np.ndarray:
+        return qd_probabilities(self.handle)
+
+    def marginal(self, wire: int) -> np.ndarray:
+        return qd_marginal(self.handle, wire, self.dims[wire])
+
+    def synchronize(self) -> None:
+        qd_synchronize(self.handle)

@@ -1,0 +1,718 @@
+// C ABI of libqudit.so (declared in include/qudit.h): state objects, exact
+// gate classification, planning of the class enumeration and kernel
+// dispatch.  Host code only; the kernels live in qd_kernels.cu.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "qd_internal.cuh"
+#include "qudit.h"
+
+namespace qd {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+static thread_local std::string g_err;
+
+static qd_status fail(qd_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+static qd_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(QD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define QD_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+static qd_status make_layout(const int32_t* dims, int32_t n, Layout& L) {
+    if (!dims) return fail(QD_ERR_ARG, "dims is NULL");
+    if (n < 1 || n > QD_MAX_WIRES) return fail(QD_ERR_ARG, "number of wires %d outside [1, %d]", n, QD_MAX_WIRES);
+    L.n = n;
+    int64_t D = 1;
+    for (int i = 0; i < n; ++i) {
+        if (dims[i] < 2 || dims[i] > QD_MAX_DIM)
+            return fail(QD_ERR_ARG, "dimension of wire %d is %d, outside [2, %d]", i, dims[i], QD_MAX_DIM);
+        L.dims[i] = dims[i];
+        L.b[i] = D;
+        if (D > ((int64_t)1 << 44) / dims[i])
+            return fail(QD_ERR_ARG, "state of more than 2^44 amplitudes");
+        D *= dims[i];
+    }
+    L.b[n] = D;
+    L.D = D;
+    return QD_OK;
+}
+
+static size_t amp_bytes(int32_t prec) { return prec == QD_C64 ? 8 : 16; }
+
+// ---------------------------------------------------------------------------
+// Planning
+// ---------------------------------------------------------------------------
+struct Plan {
+    int family;   // 0 = per-class register kernel, 1 = shared-memory tile kernel
+    int kind;
+    int vec;
+    int d;        // single-wire dimension (family 0)
+    int P;
+    uint32_t lmask, smask;
+    bool pure;
+    int perm[kMaxSmallD];
+    int64_t bt;
+    IndexMap map;
+    uint64_t classes;
+    int64_t run;
+    uint64_t off[kMaxGateDim];
+};
+
+static void build_map(const Layout& L, const int32_t* ins_w, const int64_t* ins_v, int m, IndexMap& map,
+                      uint64_t& classes) {
+    // sort inserted wires ascending (m <= kMaxInserted, insertion sort)
+    int w[kMaxInserted];
+    int64_t v[kMaxInserted];
+    for (int i = 0; i < m; ++i) { w[i] = ins_w[i]; v[i] = ins_v[i]; }
+    for (int i = 1; i < m; ++i)
+        for (int k = i; k > 0 && w[k - 1] > w[k]; --k) {
+            std::swap(w[k - 1], w[k]);
+            std::swap(v[k - 1], v[k]);
+        }
+    map.m = m;
+    map.fixed = 0;
+    uint64_t prod = 1;
+    for (int i = 0; i < m; ++i) {
+        map.fixed += (uint64_t)v[i] * (uint64_t)L.b[w[i]];
+        prod *= (uint64_t)L.dims[w[i]];
+        if (i == 0) {
+            map.seg[0].init((uint64_t)L.b[w[0]]);
+            map.off[0] = 1;
+        } else {
+            map.seg[i].init((uint64_t)(L.b[w[i]] / L.b[w[i - 1] + 1]));
+            map.off[i] = (uint64_t)L.b[w[i - 1] + 1];
+        }
+    }
+    map.off[m] = (uint64_t)L.b[w[m - 1] + 1];
+    classes = (uint64_t)L.D / prod;
+}
+
+static qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t k, const double* U,
+                           const int32_t* cw, const int32_t* cv, int32_t nc, Plan& p) {
+    if (prec != QD_C64 && prec != QD_C128) return fail(QD_ERR_ARG, "unknown precision %d", prec);
+    if (!wires || !U) return fail(QD_ERR_ARG, "wires or matrix is NULL");
+    if (k < 1 || k > L.n) return fail(QD_ERR_ARG, "gate acts on %d wires of %d", k, L.n);
+    if (nc < 0 || nc > QD_MAX_CONTROLS) return fail(QD_ERR_ARG, "%d controls outside [0, %d]", nc, QD_MAX_CONTROLS);
+    if (nc > 0 && (!cw || !cv)) return fail(QD_ERR_ARG, "control lists are NULL");
+    if (k + nc > L.n) return fail(QD_ERR_ARG, "gate wires plus controls exceed the wire count");
+    bool used[kMaxWires] = {false};
+    int64_t P = 1;
+    for (int i = 0; i < k; ++i) {
+        if (wires[i] < 0 || wires[i] >= L.n) return fail(QD_ERR_ARG, "gate wire %d out of range", wires[i]);
+        if (used[wires[i]]) return fail(QD_ERR_ARG, "gate wire %d listed twice", wires[i]);
+        used[wires[i]] = true;
+        P *= L.dims[wires[i]];
+        if (P > QD_MAX_GATE_DIM) return fail(QD_ERR_UNSUPPORTED, "gate dimension above %d", QD_MAX_GATE_DIM);
+    }
+    for (int i = 0; i < nc; ++i) {
+        if (cw[i] < 0 || cw[i] >= L.n) return fail(QD_ERR_ARG, "control wire %d out of range", cw[i]);
+        if (used[cw[i]]) return fail(QD_ERR_ARG, "control wire %d repeats a gate or control wire", cw[i]);
+        if (cv[i] < 0 || cv[i] >= L.dims[cw[i]])
+            return fail(QD_ERR_ARG, "control value %d of wire %d outside [0, %d)", cv[i], cw[i], L.dims[cw[i]]);
+        used[cw[i]] = true;
+    }
+    int32_t ins_w[kMaxInserted];
+    int64_t ins_v[kMaxInserted];
+    int m = 0;
+    for (int i = 0; i < k; ++i) { ins_w[m] = wires[i]; ins_v[m] = 0; ++m; }
+    for (int i = 0; i < nc; ++i) { ins_w[m] = cw[i]; ins_v[m] = cv[i]; ++m; }
+    build_map(L, ins_w, ins_v, m, p.map, p.classes);
+    int64_t run = L.D;
+    for (int i = 0; i < m; ++i) run = L.b[ins_w[i]] < run ? L.b[ins_w[i]] : run;
+    p.run = run;
+    p.P = (int)P;
+
+    if (k == 1 && P <= kMaxSmallD) {
+        const int d = (int)P;
+        p.family = 0;
+        p.d = d;
+        p.bt = L.b[wires[0]];
+        auto re = [&](int r, int c) { return U[2 * (r * d + c)]; };
+        auto im = [&](int r, int c) { return U[2 * (r * d + c) + 1]; };
+        auto nz = [&](int r, int c) { return re(r, c) != 0.0 || im(r, c) != 0.0; };
+        auto one = [&](int r, int c) { return re(r, c) == 1.0 && im(r, c) == 0.0; };
+        bool diag = true;
+        for (int r = 0; r < d; ++r)
+            for (int c = 0; c < d; ++c)
+                if (r != c && nz(r, c)) diag = false;
+        bool perm = true;
+        int src[kMaxSmallD];
+        bool col_used[kMaxSmallD] = {false};
+        for (int r = 0; r < d && perm; ++r) {
+            int cnt = 0;
+            for (int c = 0; c < d; ++c)
+                if (nz(r, c)) { ++cnt; src[r] = c; }
+            if (cnt != 1 || col_used[src[r]]) perm = false;
+            else col_used[src[r]] = true;
+        }
+        p.lmask = p.smask = 0;
+        p.pure = false;
+        for (int r = 0; r < kMaxSmallD; ++r) p.perm[r] = r < d ? r : 0;
+        if (diag) {
+            p.kind = kDiag;
+            for (int r = 0; r < d; ++r)
+                if (!one(r, r)) p.lmask |= 1u << r;
+            p.smask = p.lmask;
+        } else if (perm) {
+            p.kind = kPerm;
+            p.pure = true;
+            for (int r = 0; r < d; ++r) {
+                p.perm[r] = src[r];
+                if (!one(r, src[r])) p.pure = false;
+                if (src[r] != r || !one(r, src[r])) {
+                    p.smask |= 1u << r;
+                    p.lmask |= 1u << src[r];
+                }
+            }
+        } else {
+            p.kind = kDense;
+            p.lmask = p.smask = (1u << d) - 1u;
+        }
+        p.vec = (prec == QD_C64 && (run % 2) == 0) ? 2 : 1;
+    } else {
+        p.family = 1;
+        p.kind = kDense;
+        p.vec = 1;
+        p.d = 0;
+        p.bt = 0;
+        p.lmask = p.smask = 0;
+        p.pure = false;
+        for (int r = 0; r < P; ++r) {
+            uint64_t o = 0;
+            int rem = r;
+            for (int i = 0; i < k; ++i) {
+                o += (uint64_t)(rem % L.dims[wires[i]]) * (uint64_t)L.b[wires[i]];
+                rem /= L.dims[wires[i]];
+            }
+            p.off[r] = o;
+        }
+    }
+    return QD_OK;
+}
+
+}  // namespace qd
+
+using namespace qd;
+
+// ---------------------------------------------------------------------------
+// State object
+// ---------------------------------------------------------------------------
+static constexpr int kRingSlots = 8;
+
+struct qd_state {
+    Layout L;
+    int32_t prec;
+    void* psi;
+    bool owns;
+    size_t bytes;
+    cudaStream_t stream;
+    int device;
+    int nb;              // reduction blocks
+    double* partials;    // nb * 2 * max_dim doubles
+    double* dev_out;     // kMaxGateDim doubles
+    double* host_out;    // pinned, kMaxGateDim doubles
+    void* ring_dev;      // kRingSlots matrices of P*P complex (P <= 64)
+    void* ring_host;     // pinned staging
+    cudaEvent_t ring_ev[kRingSlots];
+    bool ring_ev_live[kRingSlots];
+    int ring_next;
+};
+
+static qd_status init_state_common(qd_state* st) {
+    QD_CUDA(cudaGetDevice(&st->device), "cudaGetDevice");
+    int maxd = 2;
+    for (int i = 0; i < st->L.n; ++i) maxd = st->L.dims[i] > maxd ? st->L.dims[i] : maxd;
+    st->nb = reduce_blocks(st->L.D);
+    cudaError_t e = cudaMalloc(&st->partials, sizeof(double) * 2 * (size_t)st->nb * maxd);
+    if (e != cudaSuccess) return fail(QD_ERR_OOM, "reduction workspace: %s", cudaGetErrorString(e));
+    e = cudaMalloc(&st->dev_out, sizeof(double) * kMaxGateDim);
+    if (e != cudaSuccess) return fail(QD_ERR_OOM, "readout buffer: %s", cudaGetErrorString(e));
+    e = cudaMallocHost(&st->host_out, sizeof(double) * kMaxGateDim);
+    if (e != cudaSuccess) return fail(QD_ERR_OOM, "pinned readout buffer: %s", cudaGetErrorString(e));
+    const size_t slot = amp_bytes(st->prec) * kMaxGateDim * kMaxGateDim;
+    e = cudaMalloc(&st->ring_dev, slot * kRingSlots);
+    if (e != cudaSuccess) return fail(QD_ERR_OOM, "matrix ring: %s", cudaGetErrorString(e));
+    e = cudaMallocHost(&st->ring_host, slot * kRingSlots);
+    if (e != cudaSuccess) return fail(QD_ERR_OOM, "pinned matrix ring: %s", cudaGetErrorString(e));
+    for (int i = 0; i < kRingSlots; ++i) {
+        QD_CUDA(cudaEventCreateWithFlags(&st->ring_ev[i], cudaEventDisableTiming), "cudaEventCreate");
+        st->ring_ev_live[i] = true;
+    }
+    return QD_OK;
+}
+
+static void free_state(qd_state* st) {
+    if (!st) return;
+    cudaStreamSynchronize(st->stream);
+    if (st->owns && st->psi) cudaFree(st->psi);
+    if (st->partials) cudaFree(st->partials);
+    if (st->dev_out) cudaFree(st->dev_out);
+    if (st->host_out) cudaFreeHost(st->host_out);
+    if (st->ring_dev) cudaFree(st->ring_dev);
+    if (st->ring_host) cudaFreeHost(st->ring_host);
+    for (int i = 0; i < kRingSlots; ++i)
+        if (st->ring_ev_live[i]) cudaEventDestroy(st->ring_ev[i]);
+    delete st;
+}
+
+static qd_state* new_state() {
+    qd_state* st = new (std::nothrow) qd_state;
+    if (!st) return nullptr;
+    std::memset(static_cast<void*>(st), 0, sizeof(qd_state));
+    return st;
+}
+
+template <typename R>
+static qd_status reset_impl(qd_state* st) {
+    cudaError_t e = launch_set_basis<R>(st->psi, st->L.D, 0, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "reset");
+    return QD_OK;
+}
+
+static qd_status reset_state(qd_state* st) {
+    return st->prec == QD_C64 ? reset_impl<float>(st) : reset_impl<double>(st);
+}
+
+// ---------------------------------------------------------------------------
+// Gate dispatch
+// ---------------------------------------------------------------------------
+template <typename R, int DT>
+static cudaError_t run_gate1(qd_state* st, const Plan& p, const double* U) {
+    using T2 = typename Cplx<R>::T2;
+    Gate1Args<R, DT> a;
+    std::memset(static_cast<void*>(&a), 0, sizeof a);
+    a.psi = reinterpret_cast<T2*>(st->psi);
+    a.n_elems = p.classes / (uint64_t)p.vec;
+    a.bt = (uint64_t)p.bt;
+    a.map = p.map;
+    a.kind = p.kind;
+    a.lmask = p.lmask;
+    a.smask = p.smask;
+    a.pure_perm = p.pure ? 1u : 0u;
+    for (int r = 0; r < DT; ++r) a.perm[r] = p.perm[r];
+    for (int i = 0; i < DT * DT; ++i) {
+        a.U[i].x = (R)U[2 * i];
+        a.U[i].y = (R)U[2 * i + 1];
+    }
+    if (p.vec == 2) {
+        if constexpr (sizeof(R) == 4) return launch_gate1<R, DT, 2>(a, st->stream);
+    }
+    return launch_gate1<R, DT, 1>(a, st->stream);
+}
+
+template <typename R>
+static cudaError_t dispatch_gate1(qd_state* st, const Plan& p, const double* U) {
+    switch (p.d) {
+        case 2: return run_gate1<R, 2>(st, p, U);
+        case 3: return run_gate1<R, 3>(st, p, U);
+        case 4: return run_gate1<R, 4>(st, p, U);
+        case 5: return run_gate1<R, 5>(st, p, U);
+        case 6: return run_gate1<R, 6>(st, p, U);
+        case 7: return run_gate1<R, 7>(st, p, U);
+        case 8: return run_gate1<R, 8>(st, p, U);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R>
+static qd_status run_tile(qd_state* st, const Plan& p, const double* U) {
+    using T2 = typename Cplx<R>::T2;
+    const int P = p.P;
+    const size_t slot_bytes = sizeof(T2) * kMaxGateDim * kMaxGateDim;
+    const int s = st->ring_next;
+    st->ring_next = (s + 1) % kRingSlots;
+    QD_CUDA(cudaEventSynchronize(st->ring_ev[s]), "matrix ring wait");
+    T2* h = reinterpret_cast<T2*>(static_cast<char*>(st->ring_host) + slot_bytes * s);
+    T2* dptr = reinterpret_cast<T2*>(static_cast<char*>(st->ring_dev) + slot_bytes * s);
+    for (int i = 0; i < P * P; ++i) {
+        h[i].x = (R)U[2 * i];
+        h[i].y = (R)U[2 * i + 1];
+    }
+    QD_CUDA(cudaMemcpyAsync(dptr, h, sizeof(T2) * P * P, cudaMemcpyHostToDevice, st->stream), "matrix upload");
+    QD_CUDA(cudaEventRecord(st->ring_ev[s], st->stream), "matrix ring record");
+    GateTileArgs<R> a;
+    std::memset(static_cast<void*>(&a), 0, sizeof a);
+    a.psi = reinterpret_cast<T2*>(st->psi);
+    a.U = dptr;
+    a.n_classes = p.classes;
+    a.map = p.map;
+    a.P = P;
+    a.Q = 64;
+    for (int r = 0; r < P; ++r) a.off[r] = p.off[r];
+    cudaError_t e = launch_gate_tile<R>(a, st->stream, (int)gate_tile_smem<R>(P, a.Q));
+    if (e != cudaSuccess) return cuda_fail(e, "tile gate kernel");
+    return QD_OK;
+}
+
+static qd_status apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
+                           const int32_t* cv, int32_t nc) {
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    Plan p;
+    qd_status rc = make_plan(st->L, st->prec, wires, k, U, cw, cv, nc, p);
+    if (rc != QD_OK) return rc;
+    if (p.classes == 0) return QD_OK;
+    if (p.family == 0) {
+        if (p.smask == 0) return QD_OK;  // identity
+        cudaError_t e = st->prec == QD_C64 ? dispatch_gate1<float>(st, p, U) : dispatch_gate1<double>(st, p, U);
+        if (e != cudaSuccess) return cuda_fail(e, "gate kernel");
+        return QD_OK;
+    }
+    return st->prec == QD_C64 ? run_tile<float>(st, p, U) : run_tile<double>(st, p, U);
+}
+
+// ---------------------------------------------------------------------------
+// Readout helpers
+// ---------------------------------------------------------------------------
+static qd_status read_out(qd_state* st, int count, double* host) {
+    QD_CUDA(cudaMemcpyAsync(st->host_out, st->dev_out, sizeof(double) * count, cudaMemcpyDeviceToHost, st->stream),
+            "readout copy");
+    QD_CUDA(cudaStreamSynchronize(st->stream), "readout sync");
+    std::memcpy(host, st->host_out, sizeof(double) * count);
+    return QD_OK;
+}
+
+#define QD_GUARD_BEGIN try {
+#define QD_GUARD_END                                                 \
+    }                                                                \
+    catch (const std::bad_alloc&) { return fail(QD_ERR_OOM, "host allocation failed"); } \
+    catch (...) { return fail(QD_ERR_ARG, "unexpected host exception"); }
+
+extern "C" {
+
+qd_status qd_state_create(const int32_t* dims, int32_t n, int32_t prec, void* stream, qd_state** out) {
+    QD_GUARD_BEGIN
+    if (!out) return fail(QD_ERR_ARG, "out is NULL");
+    if (prec != QD_C64 && prec != QD_C128) return fail(QD_ERR_ARG, "unknown precision %d", prec);
+    Layout L;
+    qd_status rc = make_layout(dims, n, L);
+    if (rc != QD_OK) return rc;
+    qd_state* st = new_state();
+    if (!st) return fail(QD_ERR_OOM, "host allocation failed");
+    st->L = L;
+    st->prec = prec;
+    st->stream = reinterpret_cast<cudaStream_t>(stream);
+    st->owns = true;
+    st->bytes = (size_t)L.D * amp_bytes(prec);
+    cudaError_t e = cudaMalloc(&st->psi, st->bytes);
+    if (e != cudaSuccess) {
+        st->psi = nullptr;
+        free_state(st);
+        return fail(QD_ERR_OOM, "state of %zu bytes: %s", (size_t)L.D * amp_bytes(prec), cudaGetErrorString(e));
+    }
+    rc = init_state_common(st);
+    if (rc == QD_OK) rc = reset_state(st);
+    if (rc != QD_OK) {
+        std::string msg = g_err;
+        free_state(st);
+        g_err = msg;
+        return rc;
+    }
+    *out = st;
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_wrap(void* dev_ptr, size_t bytes, const int32_t* dims, int32_t n, int32_t prec, void* stream,
+                        qd_state** out) {
+    QD_GUARD_BEGIN
+    if (!out || !dev_ptr) return fail(QD_ERR_ARG, "out or dev_ptr is NULL");
+    if (prec != QD_C64 && prec != QD_C128) return fail(QD_ERR_ARG, "unknown precision %d", prec);
+    if (reinterpret_cast<uintptr_t>(dev_ptr) % 16 != 0) return fail(QD_ERR_ARG, "dev_ptr is not 16-byte aligned");
+    Layout L;
+    qd_status rc = make_layout(dims, n, L);
+    if (rc != QD_OK) return rc;
+    if (bytes < (size_t)L.D * amp_bytes(prec))
+        return fail(QD_ERR_ARG, "buffer of %zu bytes is smaller than %lld amplitudes", bytes, (long long)L.D);
+    qd_state* st = new_state();
+    if (!st) return fail(QD_ERR_OOM, "host allocation failed");
+    st->L = L;
+    st->prec = prec;
+    st->stream = reinterpret_cast<cudaStream_t>(stream);
+    st->owns = false;
+    st->psi = dev_ptr;
+    st->bytes = (size_t)L.D * amp_bytes(prec);
+    rc = init_state_common(st);
+    if (rc != QD_OK) {
+        std::string msg = g_err;
+        free_state(st);
+        g_err = msg;
+        return rc;
+    }
+    *out = st;
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_destroy(qd_state* st) {
+    QD_GUARD_BEGIN
+    free_state(st);
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_reset(qd_state* st) {
+    QD_GUARD_BEGIN
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    return reset_state(st);
+    QD_GUARD_END
+}
+
+qd_status qd_state_set_stream(qd_state* st, void* stream) {
+    QD_GUARD_BEGIN
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    QD_CUDA(cudaStreamSynchronize(st->stream), "stream switch");
+    st->stream = reinterpret_cast<cudaStream_t>(stream);
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_info(const qd_state* st, int64_t* num_amplitudes, int32_t* num_wires, int32_t* prec) {
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    if (num_amplitudes) *num_amplitudes = st->L.D;
+    if (num_wires) *num_wires = st->L.n;
+    if (prec) *prec = st->prec;
+    return QD_OK;
+}
+
+qd_status qd_state_device_ptr(const qd_state* st, void** dev_ptr) {
+    if (!st || !dev_ptr) return fail(QD_ERR_ARG, "state or out is NULL");
+    *dev_ptr = st->psi;
+    return QD_OK;
+}
+
+qd_status qd_state_set_amplitudes(qd_state* st, const double* host) {
+    QD_GUARD_BEGIN
+    if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
+    const size_t D = (size_t)st->L.D;
+    if (st->prec == QD_C128) {
+        QD_CUDA(cudaMemcpyAsync(st->psi, host, D * 16, cudaMemcpyHostToDevice, st->stream), "upload");
+    } else {
+        std::vector<float> tmp(2 * D);
+        for (size_t i = 0; i < 2 * D; ++i) tmp[i] = (float)host[i];
+        QD_CUDA(cudaMemcpyAsync(st->psi, tmp.data(), D * 8, cudaMemcpyHostToDevice, st->stream), "upload");
+        QD_CUDA(cudaStreamSynchronize(st->stream), "upload sync");
+    }
+    QD_CUDA(cudaStreamSynchronize(st->stream), "upload sync");
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_get_amplitudes(qd_state* st, double* host) {
+    QD_GUARD_BEGIN
+    if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
+    const size_t D = (size_t)st->L.D;
+    if (st->prec == QD_C128) {
+        QD_CUDA(cudaMemcpyAsync(host, st->psi, D * 16, cudaMemcpyDeviceToHost, st->stream), "download");
+        QD_CUDA(cudaStreamSynchronize(st->stream), "download sync");
+    } else {
+        // raw binary32 pairs into the upper half of the caller's buffer, then
+        // widen front to back: element e is written at byte 8e and read from
+        // byte 8D + 4e, which is never behind the write position.
+        float* raw = reinterpret_cast<float*>(reinterpret_cast<char*>(host) + D * 8);
+        QD_CUDA(cudaMemcpyAsync(raw, st->psi, D * 8, cudaMemcpyDeviceToHost, st->stream), "download");
+        QD_CUDA(cudaStreamSynchronize(st->stream), "download sync");
+        for (size_t e = 0; e < 2 * D; ++e) host[e] = (double)raw[e];
+    }
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes) {
+    QD_GUARD_BEGIN
+    if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
+    if (bytes < st->bytes) return fail(QD_ERR_ARG, "host buffer of %zu bytes < %zu", bytes, st->bytes);
+    QD_CUDA(cudaMemcpyAsync(host, st->psi, st->bytes, cudaMemcpyDeviceToHost, st->stream), "download");
+    QD_CUDA(cudaStreamSynchronize(st->stream), "download sync");
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_apply_gate(qd_state* st, int32_t target, const double* U) {
+    QD_GUARD_BEGIN
+    return apply_any(st, &target, 1, U, nullptr, nullptr, 0);
+    QD_GUARD_END
+}
+
+qd_status qd_apply_controlled(qd_state* st, int32_t target, const double* U, const int32_t* cw,
+                              const int32_t* cv, int32_t nc) {
+    QD_GUARD_BEGIN
+    return apply_any(st, &target, 1, U, cw, cv, nc);
+    QD_GUARD_END
+}
+
+qd_status qd_apply_multi(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
+                         const int32_t* cv, int32_t nc) {
+    QD_GUARD_BEGIN
+    return apply_any(st, wires, k, U, cw, cv, nc);
+    QD_GUARD_END
+}
+
+qd_status qd_norm(qd_state* st, double* out) {
+    QD_GUARD_BEGIN
+    if (!st || !out) return fail(QD_ERR_ARG, "state or out is NULL");
+    cudaError_t e = st->prec == QD_C64
+                        ? launch_norm<float>(st->psi, st->L.D, st->partials, st->nb, st->dev_out, st->stream)
+                        : launch_norm<double>(st->psi, st->L.D, st->partials, st->nb, st->dev_out, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "norm kernel");
+    return read_out(st, 1, out);
+    QD_GUARD_END
+}
+
+qd_status qd_probabilities_device(qd_state* st, double* dev_out) {
+    QD_GUARD_BEGIN
+    if (!st || !dev_out) return fail(QD_ERR_ARG, "state or out is NULL");
+    if (reinterpret_cast<uintptr_t>(dev_out) % 8 != 0) return fail(QD_ERR_ARG, "dev_out is not 8-byte aligned");
+    cudaError_t e = st->prec == QD_C64 ? launch_probs<float>(st->psi, st->L.D, dev_out, st->stream)
+                                       : launch_probs<double>(st->psi, st->L.D, dev_out, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "probability kernel");
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_probabilities(qd_state* st, double* host_out) {
+    QD_GUARD_BEGIN
+    if (!st || !host_out) return fail(QD_ERR_ARG, "state or out is NULL");
+    double* tmp = nullptr;
+    const size_t bytes = sizeof(double) * (size_t)st->L.D;
+    cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, st->stream);
+    if (e != cudaSuccess) return fail(QD_ERR_OOM, "probability buffer: %s", cudaGetErrorString(e));
+    e = st->prec == QD_C64 ? launch_probs<float>(st->psi, st->L.D, tmp, st->stream)
+                           : launch_probs<double>(st->psi, st->L.D, tmp, st->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, tmp, bytes, cudaMemcpyDeviceToHost, st->stream);
+    cudaFreeAsync(tmp, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "probabilities");
+    QD_CUDA(cudaStreamSynchronize(st->stream), "probabilities sync");
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_marginal(qd_state* st, int32_t wire, double* host_out) {
+    QD_GUARD_BEGIN
+    if (!st || !host_out) return fail(QD_ERR_ARG, "state or out is NULL");
+    if (wire < 0 || wire >= st->L.n) return fail(QD_ERR_ARG, "wire %d out of range", wire);
+    IndexMap map;
+    uint64_t classes;
+    const int32_t w = wire;
+    const int64_t v = 0;
+    build_map(st->L, &w, &v, 1, map, classes);
+    const int d = st->L.dims[wire];
+    cudaError_t e = st->prec == QD_C64
+                        ? launch_marginal<float>(st->psi, map, classes, (uint64_t)st->L.b[wire], d, st->partials,
+                                                 st->nb, st->dev_out, st->stream)
+                        : launch_marginal<double>(st->psi, map, classes, (uint64_t)st->L.b[wire], d, st->partials,
+                                                  st->nb, st->dev_out, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "marginal kernel");
+    return read_out(st, d, host_out);
+    QD_GUARD_END
+}
+
+qd_status qd_synchronize(qd_state* st) {
+    QD_GUARD_BEGIN
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    QD_CUDA(cudaStreamSynchronize(st->stream), "synchronize");
+    return QD_OK;
+    QD_GUARD_END
+}
+
+const char* qd_last_error(void) { return g_err.c_str(); }
+
+uint64_t qd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char* qd_version(void) { return "qudit-gb300 0.1 (sm_103a)"; }
+
+qd_status qd_plan_gate(const int32_t* dims, int32_t n, int32_t prec, const int32_t* wires, int32_t k,
+                       const double* U, const int32_t* cw, const int32_t* cv, int32_t nc, qd_plan_info* out) {
+    QD_GUARD_BEGIN
+    if (!out) return fail(QD_ERR_ARG, "out is NULL");
+    Layout L;
+    qd_status rc = make_layout(dims, n, L);
+    if (rc != QD_OK) return rc;
+    Plan p;
+    rc = make_plan(L, prec, wires, k, U, cw, cv, nc, p);
+    if (rc != QD_OK) return rc;
+    out->family = p.family;
+    out->kind = p.kind;
+    out->vec = p.vec;
+    int rows = 0;
+    for (int r = 0; r < 32; ++r) rows += (p.smask >> r) & 1u;
+    out->touched_rows = p.family == 0 ? rows : p.P;
+    out->classes = (int64_t)p.classes;
+    out->run = p.run;
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_selftest_host(int32_t trials) {
+    QD_GUARD_BEGIN
+    uint64_t s = 0x9E3779B97F4A7C15ull;
+    auto rnd = [&]() {  // xorshift64*
+        s ^= s >> 12;
+        s ^= s << 25;
+        s ^= s >> 27;
+        return s * 0x2545F4914F6CDD1Dull;
+    };
+    // 1. division by invariant integers
+    for (int t = 0; t < trials; ++t) {
+        uint64_t d = 1 + rnd() % ((t % 3 == 0) ? 7 : (t % 3 == 1) ? 100000 : (1ull << 40));
+        FastDiv f(d);
+        const uint64_t ns[6] = {0, 1, d - 1, d, rnd() % (1ull << 45), (1ull << 45) - 1};
+        for (uint64_t n : ns)
+            if (f.div(n) != n / d)
+                return fail(QD_ERR_ARG, "fast division %llu / %llu wrong", (unsigned long long)n, (unsigned long long)d);
+    }
+    // 2. class enumeration: map(g) visits exactly the indices whose inserted
+    //    digits equal their fixed values, in increasing order.
+    for (int t = 0; t < trials; ++t) {
+        Layout L;
+        int32_t dims[6];
+        const int n = 2 + (int)(rnd() % 5);
+        for (int i = 0; i < n; ++i) dims[i] = 2 + (int)(rnd() % 4);
+        if (make_layout(dims, n, L) != QD_OK) return QD_ERR_ARG;
+        const int m = 1 + (int)(rnd() % (uint64_t)(n - 1));
+        int32_t w[6];
+        int64_t v[6];
+        int cnt = 0;
+        for (int i = 0; i < n && cnt < m; ++i)
+            if (rnd() % 2 == 0 || n - i == m - cnt) { w[cnt] = i; v[cnt] = (int64_t)(rnd() % (uint64_t)dims[i]); ++cnt; }
+        IndexMap map;
+        uint64_t classes;
+        build_map(L, w, v, cnt, map, classes);
+        uint64_t g = 0;
+        for (int64_t j = 0; j < L.D; ++j) {
+            bool match = true;
+            for (int i = 0; i < cnt; ++i)
+                if ((j / L.b[w[i]]) % L.dims[w[i]] != v[i]) match = false;
+            if (!match) continue;
+            if (g >= classes || map.map(g) != (uint64_t)j)
+                return fail(QD_ERR_ARG, "class enumeration wrong at g=%llu", (unsigned long long)g);
+            ++g;
+        }
+        if (g != classes) return fail(QD_ERR_ARG, "class count wrong");
+    }
+    return QD_OK;
+    QD_GUARD_END
+}
+
+}  // extern "C"

@@ -1,0 +1,165 @@
+// Internal declarations shared by the library's translation units.
+//
+// Index arithmetic.  A gate on wires W with controls C visits the classes
+// of amplitudes that differ only in the digits of W (section "Superposition
+// gates": block size b_i = prod_{t<i} d_t, repetitions prod_{t>i} d_t).
+// Instead of scanning all D indices for the control condition
+// floor(j / b_c) mod d_c = v_c (section "Controlled and Multi-Controlled
+// Gates"), the digits of W (set to 0) and of C (set to v_c) are *inserted*
+// into a free index g that counts only the visited classes:
+//
+//   inserted wires sorted p_0 < ... < p_{m-1};
+//   g = g_0 + seg_0 * (g_1 + seg_1 * (... g_m)),  seg_0 = b_{p_0},
+//       seg_i = b_{p_i} / b_{p_{i-1}+1};
+//   j(g) = fixed + g_0 + sum_{i>=1} g_i * b_{p_{i-1}+1},
+//       fixed = sum over controls of v_c * b_c.
+//
+// The divisions by the invariant seg_i use the round-up multiply-high method
+// of Granlund and Montgomery, "Division by invariant integers using
+// multiplication" (PLDI 1994), section 4.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#ifndef QD_HD
+#define QD_HD __host__ __device__ __forceinline__
+#endif
+
+namespace qd {
+
+constexpr int kMaxWires = 48;
+constexpr int kMaxInserted = 24;  // gate wires (<= 6 for P <= 64) + controls (<= 16)
+constexpr int kMaxGateDim = 64;
+constexpr int kMaxSmallD = 8;     // single-wire gates up to this dimension use the register kernel
+
+QD_HD uint64_t umulhi64(uint64_t a, uint64_t b) {
+#ifdef __CUDA_ARCH__
+    return __umul64hi(a, b);
+#else
+    return (uint64_t)(((unsigned __int128)a * (unsigned __int128)b) >> 64);
+#endif
+}
+
+// Unsigned 64-bit division by an invariant divisor d >= 1.
+struct FastDiv {
+    uint64_t d;
+    uint64_t mul;
+    uint32_t s1, s2;
+
+    FastDiv() = default;
+    __host__ explicit FastDiv(uint64_t div) { init(div); }
+    // Valid for 1 <= div <= 2^62 (indices here stay far below that).
+    __host__ void init(uint64_t div) {
+        d = div;
+        int l = 0;
+        while (((uint64_t)1 << l) < div) ++l;  // l = ceil(log2 d)
+        // mul = floor(2^64 (2^l - d) / d) + 1, which fits in 64 bits
+        const unsigned __int128 num = ((unsigned __int128)(((uint64_t)1 << l) - div)) << 64;
+        mul = (uint64_t)(num / div) + 1;
+        s1 = l < 1 ? l : 1;
+        s2 = l > 1 ? l - 1 : 0;
+    }
+    QD_HD uint64_t div(uint64_t n) const {
+        const uint64_t t = umulhi64(mul, n);
+        return (t + ((n - t) >> s1)) >> s2;
+    }
+    QD_HD void divmod(uint64_t n, uint64_t& q, uint64_t& r) const {
+        q = div(n);
+        r = n - q * d;
+    }
+};
+
+// Free class index -> basis index of the class's member with all gate digits 0.
+struct IndexMap {
+    int32_t m;                   // number of inserted wires
+    uint64_t fixed;              // sum of control values * strides
+    FastDiv seg[kMaxInserted];   // seg[0..m-1]
+    uint64_t off[kMaxInserted + 1];
+    QD_HD uint64_t map(uint64_t g) const {
+        uint64_t j = fixed;
+        uint64_t r = g;
+#pragma unroll 1
+        for (int i = 0; i < m; ++i) {
+            uint64_t q, rem;
+            seg[i].divmod(r, q, rem);
+            j += rem * off[i];
+            r = q;
+        }
+        return j + r * off[m];
+    }
+};
+
+// Host-side description of the state layout.
+struct Layout {
+    int32_t n;
+    int32_t dims[kMaxWires];
+    int64_t b[kMaxWires + 1];  // b[w] = prod_{t<w} d_t, b[n] = D
+    int64_t D;
+};
+
+// Kinds a gate matrix is classified into (exactly, in binary64).
+enum GateKind : int32_t { kDense = 0, kDiag = 1, kPerm = 2 };
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T2 = float2; };
+template <> struct Cplx<double> { using T2 = double2; };
+
+// Arguments of the per-class register kernel (single wire, d <= kMaxSmallD).
+template <typename R, int DT>
+struct Gate1Args {
+    using T2 = typename Cplx<R>::T2;
+    T2* psi;
+    uint64_t n_elems;     // classes / vec
+    uint64_t bt;          // stride of the target wire (distance between class members)
+    IndexMap map;
+    int32_t kind;
+    uint32_t lmask;       // rows loaded
+    uint32_t smask;       // rows stored
+    uint32_t pure_perm;   // permutation entries are all exactly 1
+    int32_t perm[DT];     // kPerm: source row of each output row
+    T2 U[DT * DT];
+};
+
+// Arguments of the shared-memory tile kernel (any gate with P <= 64).
+template <typename R>
+struct GateTileArgs {
+    using T2 = typename Cplx<R>::T2;
+    T2* psi;
+    const T2* U;          // device, P x P row-major
+    uint64_t n_classes;
+    IndexMap map;
+    int32_t P;
+    int32_t Q;            // classes per tile
+    uint64_t off[kMaxGateDim];  // member offsets of local row r
+};
+
+// Launchers (qd_kernels.cu).  All return a cudaError_t of the launch.
+template <typename R, int DT, int VEC>
+cudaError_t launch_gate1(const Gate1Args<R, DT>& a, cudaStream_t s);
+template <typename R>
+cudaError_t launch_gate_tile(const GateTileArgs<R>& a, cudaStream_t s, int smem_bytes);
+template <typename R>
+size_t gate_tile_smem(int P, int Q);
+
+template <typename R>
+cudaError_t launch_set_basis(void* psi, int64_t D, int64_t index, cudaStream_t s);
+template <typename R>
+cudaError_t launch_norm(const void* psi, int64_t D, double* partials, int nblocks, double* dev_out,
+                        cudaStream_t s);
+template <typename R>
+cudaError_t launch_probs(const void* psi, int64_t D, double* out, cudaStream_t s);
+template <typename R>
+cudaError_t launch_marginal(const void* psi, const IndexMap& map, uint64_t n_per_digit,
+                            uint64_t stride, int d, double* partials, int nblocks, double* dev_out,
+                            cudaStream_t s);
+template <typename R>
+cudaError_t launch_widen(const void* psi, int64_t D, double* out, cudaStream_t s);
+template <typename R>
+cudaError_t launch_narrow(const double* in, int64_t D, void* psi, cudaStream_t s);
+
+int reduce_blocks(int64_t D);
+
+void count_launch(int n = 1);
+
+}  // namespace qd
