@@ -381,16 +381,42 @@ def run_gpu(args):
     return 0
 
 
+def run_ncu_case(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2410_17876_gb300 import binding as qb
+    from paper_2410_17876_gb300 import inputs as gen
+
+    prec = qb.QD_C64 if args.prec == "c64" else qb.QD_C128
+    circ = gen.config1_circuit()
+    rng = np.random.Generator(np.random.PCG64(99))
+    st = qb.State(circ.dims, prec=prec)
+    for w in (0, 5, 10, 15, 19, 3):
+        st.apply(gen.Gate((w,), gen.haar(circ.dims[w], rng)))
+    st.synchronize()
+    st.close()
+    torch.cuda.synchronize()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", action="store_true",
+                    help="run only six dense single-wire gates (wires 0, 5, 10, 15, 19, 3) on the workload's "
+                         "state, for a profiler capture of launches 4-6; prints nothing")
     args = ap.parse_args(argv)
+    if args.ncu_case:
+        return run_ncu_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
