@@ -171,6 +171,45 @@ qd_status qd_marginal(qd_state* st, int32_t wire, double* host_out);
 qd_status qd_synchronize(qd_state* st);
 
 /* ------------------------------------------------------------------------
+ * Norm without allocation.  The paper has no counterpart to this call; it
+ * exists for callers that cannot allocate device memory: a thread that is
+ * capturing a CUDA graph (cudaMalloc is not allowed there), a framework
+ * whose caching allocator owns all device memory, or a latency-critical loop
+ * that must not stall on an allocation.  qd_norm needs a qd_state, and
+ * creating a state allocates its reduction workspace; this call allocates
+ * nothing (no cudaMalloc, cudaFree or allocating library routine).
+ *
+ * dev_amps: num_amplitudes interleaved amplitudes in device memory (float
+ *   pairs for QD_C64, 8-byte aligned; double pairs for QD_C128, 16-byte
+ *   aligned), owned by the caller and only read.
+ * dev_out: one double in device memory (8-byte aligned) that receives
+ *   sum_j |psi_j|^2, computed exactly as qd_norm does (binary64, Neumaier
+ *   compensation, fixed order), so the two agree bit for bit on the same
+ *   amplitudes.
+ * stream: the cudaStream_t the two kernels are issued on (NULL = default);
+ *   the call is asynchronous, read dev_out after synchronising the stream.
+ *
+ * Scratch: the partial sums live in a fixed device array inside the library,
+ * QD_NORM_NOALLOC_BLOCKS pairs of doubles (16 KiB), which every GPU that
+ * loads the library keeps until the process exits.  The first call on each
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Calls share the array and it keeps the last call's contents (each call
+ * writes every entry it reads before reading it, so nothing needs
+ * clearing); calls whose kernels overlap on the GPU -- on different streams
+ * or different host threads without ordering -- race on it and give wrong
+ * results.  Order them on one stream or with events.
+ *
+ * Errors: QD_ERR_ARG for NULL or misaligned pointers, an unknown precision,
+ * or num_amplitudes outside [1, QD_NORM_NOALLOC_MAX_AMPLITUDES];
+ * QD_ERR_CUDA if the set-up or a launch fails.
+ * --------------------------------------------------------------------- */
+#define QD_NORM_NOALLOC_BLOCKS 1024
+#define QD_NORM_NOALLOC_MAX_AMPLITUDES ((int64_t)1 << 44)
+qd_status qd_norm_noalloc(const void* dev_amps, int64_t num_amplitudes, int32_t prec, void* stream,
+                          double* dev_out);
+
+/* ------------------------------------------------------------------------
  * Introspection (host only; no GPU needed).
  * --------------------------------------------------------------------- */
 

@@ -58,6 +58,7 @@ _SIGS = {
     "qd_probabilities_device": (ctypes.c_int32, [_vp, _vp]),
     "qd_marginal": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
     "qd_synchronize": (ctypes.c_int32, [_vp]),
+    "qd_norm_noalloc": (ctypes.c_int32, [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]),
     "qd_last_error": (ctypes.c_char_p, []),
     "qd_launch_count": (ctypes.c_uint64, []),
     "qd_version": (ctypes.c_char_p, []),
@@ -214,6 +215,14 @@ def qd_marginal(st: int, wire: int, d: int) -> np.ndarray:
 
 def qd_synchronize(st: int) -> None:
     _check(_lib.qd_synchronize(_vp(st)), "qd_synchronize")
+
+
+def qd_norm_noalloc(dev_amps: int, num_amplitudes: int, prec: int, stream: int, dev_out: int) -> None:
+    """Squared norm of caller-owned device amplitudes into the device double at
+    ``dev_out``, allocating nothing (for callers that cannot allocate, such as
+    code under CUDA-graph capture); asynchronous on ``stream``."""
+    _check(_lib.qd_norm_noalloc(_vp(dev_amps), int(num_amplitudes), int(prec), _vp(stream), _vp(dev_out)),
+           "qd_norm_noalloc")
 
 
 def qd_last_error() -> str:

@@ -30,6 +30,8 @@ static qd_status fail(qd_status st, const char* fmt, ...) {
     return st;
 }
 
+void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
+
 static qd_status cuda_fail(cudaError_t e, const char* what) {
     return fail(QD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
