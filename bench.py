@@ -270,9 +270,12 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(local)
     st = qb.State(circ.dims, prec=prec, stream=stream, device=local)
 
+    fuse = args.fuse == "tile"
+    fopts = {"max_tile_amps": args.tile} if fuse and args.tile else {}
+
     def step():
         st.reset()
-        st.run(circ)
+        st.run(circ, fuse=fuse, **fopts)
         return st.norm()
 
     for _ in range(max(3, args.warmup)):
@@ -300,26 +303,50 @@ def run_gpu(args):
     t_max = max_over_ranks(dev_s, world)
     value, _ = aggregate([upd * args.steps] * world, [t_max] * world)
 
-    # ---- per-launch durations of the gate kernel (one extra, untimed step) ----
+    # ---- per-launch durations of the dominant kernel (one extra, untimed step) ----
     plans = [qb.qd_plan_gate(circ.dims, prec, g.wires, g.U, g.controls or None, g.values or None)
              for g in circ.gates]
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(circ.gates) + 1)]
-    st.reset()
-    torch.cuda.synchronize()
-    evs[0].record(stream)
-    for i, g in enumerate(circ.gates):
-        st.apply(g)
-        evs[i + 1].record(stream)
-    torch.cuda.synchronize()
-    k_time, k_bytes, k_n = 0.0, 0, 0
-    for i, p in enumerate(plans):
-        if p["family"] == 0 and p["touched_rows"] > 0:
-            k_time += evs[i].elapsed_time(evs[i + 1]) / 1e3
-            k_bytes += algorithmic_bytes(p, amp_bytes)
-            k_n += 1
+    if fuse:
+        # one qd_apply_circuit call per planned pass, CUDA events around each
+        order, pass_of, tiles = qb.qd_plan_circuit(circ.dims, prec, circ, **fopts)
+        groups = [[] for _ in range(len(tiles))]
+        for g_idx, p_idx in zip(order, pass_of):
+            groups[p_idx].append(circ.gates[g_idx])
+        subs = [gen.Circuit(circ.dims, gl) for gl in groups]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(subs) + 1)]
+        st.reset()
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for i, sc in enumerate(subs):
+            st.run(sc, fuse=True, **fopts)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        k_time, k_bytes, k_n = 0.0, 0, 0
+        for i, t in enumerate(tiles):
+            if t > 0:
+                k_time += evs[i].elapsed_time(evs[i + 1]) / 1e3
+                k_bytes += 2 * amp_bytes * circ.D
+                k_n += 1
+        kname = "k_fused_tile (shared-memory tile pass, all tile passes of the circuit)"
+    else:
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(circ.gates) + 1)]
+        st.reset()
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        for i, g in enumerate(circ.gates):
+            st.apply(g)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        k_time, k_bytes, k_n = 0.0, 0, 0
+        for i, p in enumerate(plans):
+            if p["family"] == 0 and p["touched_rows"] > 0:
+                k_time += evs[i].elapsed_time(evs[i + 1]) / 1e3
+                k_bytes += algorithmic_bytes(p, amp_bytes)
+                k_n += 1
+        kname = "k_gate1 (per-class register kernel, all gates of the circuit)"
     peak, peak_kind = measured_peaks()
     achieved = k_bytes / k_time / 1e9 if k_time > 0 else 0.0
-    traffic = ncu_traffic(args.prec)
+    traffic = None if fuse else ncu_traffic(args.prec)
 
     # ---- end to end through the public API with host buffers ----
     pinned = torch.empty(circ.D, dtype=torch.complex64 if prec == qb.QD_C64 else torch.complex128,
@@ -333,7 +360,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         st.reset()
-        st.run(circ)
+        st.run(circ, fuse=fuse, **fopts)
         st.norm()
         qb.qd_state_get_raw(st.handle, host_out)
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
@@ -358,12 +385,13 @@ def run_gpu(args):
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == qb.QD_C64 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prec": args.prec, "amplitudes": circ.D, "gates": len(circ.gates),
+            "config": {"workload": WORKLOAD, "prec": args.prec, "fusion": args.fuse, "tile_amps": args.tile or None,
+                       "amplitudes": circ.D, "gates": len(circ.gates),
                        "state_bytes": circ.D * amp_bytes,
                        "l2": f"state {circ.D * amp_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs_effective": sum(algorithmic_bytes(p, amp_bytes) for p in plans) * args.steps / t_max / 1e9,
-            "roofline": {"kernel": "k_gate1 (per-class register kernel, all gates of the circuit)",
+            "roofline": {"kernel": kname,
                          "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
                          "launches_measured": k_n},
@@ -408,6 +436,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--fuse", choices=["tile", "off"], default="tile",
+                    help="tile: consecutive gates share one shared-memory pass over the state; off: one pass per gate")
+    ap.add_argument("--tile", type=int, default=0, help="amplitudes per fused tile (0 = library default)")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -148,6 +148,62 @@ qd_status qd_apply_multi(qd_state* st, const int32_t* wires, int32_t k, const do
                          const int32_t* ctrl_wires, const int32_t* ctrl_vals, int32_t n_ctrl);
 
 /* ------------------------------------------------------------------------
+ * Circuits and gate fusion.  The paper executes gates one after another
+ * (section "Experimental Analysis": runtime grows with the N gates executed
+ * sequentially) and leaves parallelism across blocks as future scope
+ * (end of section "Example Circuit").  A circuit call may run several
+ * consecutive gates per pass over the state: a tile holds every amplitude
+ * whose digits outside a cached wire set S are fixed (S = the lowest wires,
+ * for contiguous rows, plus the high wires the pass's gates act on); each
+ * tile is read once, all the pass's gates are applied to it in on-chip
+ * memory, and it is written back once.  Gates are reordered only across
+ * gates they commute with (disjoint written wires; controls and diagonal
+ * gates commute with each other), so the result equals the sequential one
+ * up to rounding.
+ * --------------------------------------------------------------------- */
+#define QD_MAX_GATE_WIRES 6
+
+/* One gate of a circuit: n_wires target wires (local index with wires[0]
+ * least significant), n_ctrl controls with values, and the offset, in
+ * complex entries, of its P x P row-major matrix inside the `matrices`
+ * array passed with the circuit (2 doubles per entry). */
+typedef struct qd_gate_desc {
+    int32_t n_wires;
+    int32_t n_ctrl;
+    int32_t wires[QD_MAX_GATE_WIRES];
+    int32_t ctrl_wires[QD_MAX_CONTROLS];
+    int32_t ctrl_vals[QD_MAX_CONTROLS];
+    int64_t matrix_offset;
+} qd_gate_desc;
+
+#define QD_FUSE_OFF 0  /* one kernel pass per gate */
+#define QD_FUSE_TILE 1 /* shared-memory tile passes over cached wire sets */
+
+typedef struct qd_fusion_opts {
+    int32_t mode;          /* QD_FUSE_OFF or QD_FUSE_TILE */
+    int32_t max_tile_amps; /* amplitudes per tile, 0 = default (8192 complex64, 4096 complex128) */
+    int32_t min_gates;     /* passes with fewer gates run gate by gate; 0 = default (2) */
+    int32_t min_row;       /* contiguous amplitudes per tile row, 0 = default (16 c64, 8 c128) */
+} qd_fusion_opts;
+
+/* Apply n_gates gates in order.  Each gate is validated as in
+ * qd_apply_multi before anything is launched (QD_ERR_ARG / UNSUPPORTED:
+ * nothing applied).  opts = NULL means QD_FUSE_OFF.  Asynchronous; the
+ * arrays may be reused when the call returns. */
+qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates,
+                           const double* matrices, const qd_fusion_opts* opts);
+
+/* The execution plan of qd_apply_circuit without a GPU: exec_order[i] is the
+ * index of the i-th gate executed, pass_of[i] its pass, pass_tile_amps[p]
+ * the tile size of pass p (0 = a per-gate kernel pass); *n_passes receives
+ * the number of passes.  Every array has n_gates entries; pass_tile_amps
+ * may be NULL. */
+qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd_gate_desc* gates,
+                          int32_t n_gates, const double* matrices, const qd_fusion_opts* opts,
+                          int32_t* exec_order, int32_t* pass_of, int64_t* pass_tile_amps,
+                          int32_t* n_passes);
+
+/* ------------------------------------------------------------------------
  * Readouts.  Sums run in binary64 with compensated (Neumaier) summation in
  * a fixed order, so results are deterministic for a given state size.
  * The paper defines no readout; these are the standard Born-rule

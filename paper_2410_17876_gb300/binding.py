@@ -38,6 +38,22 @@ class qd_plan_info(ctypes.Structure):
                 ("touched_rows", ctypes.c_int32), ("classes", ctypes.c_int64), ("run", ctypes.c_int64)]
 
 
+QD_MAX_GATE_WIRES = 6
+QD_FUSE_OFF, QD_FUSE_TILE = 0, 1
+
+
+class qd_gate_desc(ctypes.Structure):
+    _fields_ = [("n_wires", ctypes.c_int32), ("n_ctrl", ctypes.c_int32),
+                ("wires", ctypes.c_int32 * QD_MAX_GATE_WIRES),
+                ("ctrl_wires", ctypes.c_int32 * QD_MAX_CONTROLS),
+                ("ctrl_vals", ctypes.c_int32 * QD_MAX_CONTROLS), ("matrix_offset", ctypes.c_int64)]
+
+
+class qd_fusion_opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("max_tile_amps", ctypes.c_int32), ("min_gates", ctypes.c_int32),
+                ("min_row", ctypes.c_int32)]
+
+
 _SIGS = {
     "qd_state_create": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
     "qd_state_wrap": (ctypes.c_int32, [_vp, ctypes.c_size_t, _i32p, ctypes.c_int32, ctypes.c_int32, _vp,
@@ -65,6 +81,11 @@ _SIGS = {
     "qd_plan_gate": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _f64p,
                                       _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(qd_plan_info)]),
     "qd_selftest_host": (ctypes.c_int32, [ctypes.c_int32]),
+    "qd_apply_circuit": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_gate_desc), ctypes.c_int32, _f64p,
+                                          ctypes.POINTER(qd_fusion_opts)]),
+    "qd_plan_circuit": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(qd_gate_desc),
+                                         ctypes.c_int32, _f64p, ctypes.POINTER(qd_fusion_opts), _i32p, _i32p,
+                                         ctypes.POINTER(ctypes.c_int64), _i32p]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -253,6 +274,64 @@ def qd_selftest_host(trials: int = 200) -> None:
     _check(_lib.qd_selftest_host(int(trials)), "qd_selftest_host")
 
 
+def circuit_arrays(circuit):
+    """(qd_gate_desc array, concatenated matrices) for a circuit; cached on the circuit object."""
+    cache = getattr(circuit, "_qd_arrays", None)
+    if cache is not None and cache[0] == len(circuit.gates):
+        return cache[1], cache[2]
+    n = len(circuit.gates)
+    descs = (qd_gate_desc * max(1, n))()
+    mats = []
+    off = 0
+    for i, g in enumerate(circuit.gates):
+        d = descs[i]
+        d.n_wires = len(g.wires)
+        d.n_ctrl = len(g.controls)
+        for m, w in enumerate(g.wires):
+            d.wires[m] = w
+        for m, (c, v) in enumerate(zip(g.controls, g.values)):
+            d.ctrl_wires[m] = c
+            d.ctrl_vals[m] = v
+        d.matrix_offset = off
+        U = np.ascontiguousarray(g.U, dtype=np.complex128).reshape(-1)
+        mats.append(U)
+        off += U.size
+    m = np.ascontiguousarray(np.concatenate(mats) if mats else np.zeros(1, np.complex128)).view(np.float64)
+    try:
+        circuit._qd_arrays = (n, descs, m)
+    except AttributeError:
+        pass
+    return descs, m
+
+
+def _opts(mode, max_tile_amps=0, min_gates=0, min_row=0):
+    if mode is None:
+        return None
+    return ctypes.byref(qd_fusion_opts(int(mode), int(max_tile_amps), int(min_gates), int(min_row)))
+
+
+def qd_apply_circuit(st: int, circuit, mode=QD_FUSE_OFF, max_tile_amps=0, min_gates=0, min_row=0) -> None:
+    descs, m = circuit_arrays(circuit)
+    _check(_lib.qd_apply_circuit(_vp(st), descs, len(circuit.gates), _p(m, _f64p),
+                                 _opts(mode, max_tile_amps, min_gates, min_row)), "qd_apply_circuit")
+
+
+def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min_gates=0, min_row=0):
+    """(exec_order, pass_of, pass_tile_amps[:n_passes]) of the circuit's execution plan."""
+    d = _i32(dims)
+    descs, m = circuit_arrays(circuit)
+    n = len(circuit.gates)
+    order = np.zeros(max(1, n), np.int32)
+    pass_of = np.zeros(max(1, n), np.int32)
+    tiles = np.zeros(max(1, n), np.int64)
+    npass = ctypes.c_int32()
+    _check(_lib.qd_plan_circuit(_p(d, _i32p), len(d), prec, descs, n, _p(m, _f64p),
+                                _opts(mode, max_tile_amps, min_gates, min_row), _p(order, _i32p),
+                                _p(pass_of, _i32p), tiles.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                ctypes.byref(npass)), "qd_plan_circuit")
+    return order[:n], pass_of[:n], tiles[:npass.value]
+
+
 # --- convenience ----------------------------------------------------------------------------------
 class State:
     """A state vector in torch-allocated device memory, driven through the C ABI.
@@ -298,7 +377,11 @@ class State:
         else:
             qd_apply_multi(self.handle, gate.wires, gate.U, gate.controls, gate.values)
 
-    def run(self, circuit) -> None:
+    def run(self, circuit, fuse: bool = False, **opts) -> None:
+        """Apply the circuit's gates through one qd_apply_circuit call (tile fusion if ``fuse``)."""
+        qd_apply_circuit(self.handle, circuit, QD_FUSE_TILE if fuse else QD_FUSE_OFF, **opts)
+
+    def run_gate_by_gate(self, circuit) -> None:
         for g in circuit.gates:
             self.apply(g)
 

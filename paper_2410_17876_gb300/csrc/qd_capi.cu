@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "qd_internal.cuh"
+#include "qd_runtime.h"
 #include "qudit.h"
 
 namespace qd {
@@ -20,7 +21,7 @@ void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_r
 
 static thread_local std::string g_err;
 
-static qd_status fail(qd_status st, const char* fmt, ...) {
+qd_status fail(qd_status st, const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -32,17 +33,12 @@ static qd_status fail(qd_status st, const char* fmt, ...) {
 
 void set_last_error(const char* msg) { g_err = msg ? msg : ""; }
 
-static qd_status cuda_fail(cudaError_t e, const char* what) {
+qd_status cuda_fail(cudaError_t e, const char* what) {
     return fail(QD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define QD_CUDA(call, what)                          \
-    do {                                             \
-        cudaError_t e_ = (call);                     \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
 
-static qd_status make_layout(const int32_t* dims, int32_t n, Layout& L) {
+qd_status make_layout(const int32_t* dims, int32_t n, Layout& L) {
     if (!dims) return fail(QD_ERR_ARG, "dims is NULL");
     if (n < 1 || n > QD_MAX_WIRES) return fail(QD_ERR_ARG, "number of wires %d outside [1, %d]", n, QD_MAX_WIRES);
     L.n = n;
@@ -61,28 +57,13 @@ static qd_status make_layout(const int32_t* dims, int32_t n, Layout& L) {
     return QD_OK;
 }
 
-static size_t amp_bytes(int32_t prec) { return prec == QD_C64 ? 8 : 16; }
+size_t amp_bytes(int32_t prec) { return prec == QD_C64 ? 8 : 16; }
 
 // ---------------------------------------------------------------------------
 // Planning
 // ---------------------------------------------------------------------------
-struct Plan {
-    int family;   // 0 = per-class register kernel, 1 = shared-memory tile kernel
-    int kind;
-    int vec;
-    int d;        // single-wire dimension (family 0)
-    int P;
-    uint32_t lmask, smask;
-    bool pure;
-    int perm[kMaxSmallD];
-    int64_t bt;
-    IndexMap map;
-    uint64_t classes;
-    int64_t run;
-    uint64_t off[kMaxGateDim];
-};
 
-static void build_map(const Layout& L, const int32_t* ins_w, const int64_t* ins_v, int m, IndexMap& map,
+void build_map(const Layout& L, const int32_t* ins_w, const int64_t* ins_v, int m, IndexMap& map,
                       uint64_t& classes) {
     // sort inserted wires ascending (m <= kMaxInserted, insertion sort)
     int w[kMaxInserted];
@@ -111,7 +92,7 @@ static void build_map(const Layout& L, const int32_t* ins_w, const int64_t* ins_
     classes = (uint64_t)L.D / prod;
 }
 
-static qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t k, const double* U,
+qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t k, const double* U,
                            const int32_t* cw, const int32_t* cv, int32_t nc, Plan& p) {
     if (prec != QD_C64 && prec != QD_C128) return fail(QD_ERR_ARG, "unknown precision %d", prec);
     if (!wires || !U) return fail(QD_ERR_ARG, "wires or matrix is NULL");
@@ -221,26 +202,6 @@ using namespace qd;
 // ---------------------------------------------------------------------------
 // State object
 // ---------------------------------------------------------------------------
-static constexpr int kRingSlots = 8;
-
-struct qd_state {
-    Layout L;
-    int32_t prec;
-    void* psi;
-    bool owns;
-    size_t bytes;
-    cudaStream_t stream;
-    int device;
-    int nb;              // reduction blocks
-    double* partials;    // nb * 2 * max_dim doubles
-    double* dev_out;     // kMaxGateDim doubles
-    double* host_out;    // pinned, kMaxGateDim doubles
-    void* ring_dev;      // kRingSlots matrices of P*P complex (P <= 64)
-    void* ring_host;     // pinned staging
-    cudaEvent_t ring_ev[kRingSlots];
-    bool ring_ev_live[kRingSlots];
-    int ring_next;
-};
 
 static qd_status init_state_common(qd_state* st) {
     QD_CUDA(cudaGetDevice(&st->device), "cudaGetDevice");
@@ -276,6 +237,9 @@ static void free_state(qd_state* st) {
     if (st->ring_host) cudaFreeHost(st->ring_host);
     for (int i = 0; i < kRingSlots; ++i)
         if (st->ring_ev_live[i]) cudaEventDestroy(st->ring_ev[i]);
+    if (st->fuse_dev) cudaFree(st->fuse_dev);
+    if (st->fuse_host) cudaFreeHost(st->fuse_host);
+    if (st->fuse_ev_live) cudaEventDestroy(st->fuse_ev);
     delete st;
 }
 
@@ -368,7 +332,7 @@ static qd_status run_tile(qd_state* st, const Plan& p, const double* U) {
     return QD_OK;
 }
 
-static qd_status apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
+qd_status qd::apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
                            const int32_t* cv, int32_t nc) {
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
     Plan p;
@@ -387,7 +351,7 @@ static qd_status apply_any(qd_state* st, const int32_t* wires, int32_t k, const 
 // ---------------------------------------------------------------------------
 // Readout helpers
 // ---------------------------------------------------------------------------
-static qd_status read_out(qd_state* st, int count, double* host) {
+qd_status qd::read_out(qd_state* st, int count, double* host) {
     QD_CUDA(cudaMemcpyAsync(st->host_out, st->dev_out, sizeof(double) * count, cudaMemcpyDeviceToHost, st->stream),
             "readout copy");
     QD_CUDA(cudaStreamSynchronize(st->stream), "readout sync");

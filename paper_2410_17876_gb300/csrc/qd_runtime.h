@@ -1,0 +1,80 @@
+// Host-side internals shared by the runtime translation units (C ABI,
+// fusion planner): error reporting, layout and gate planning, the state
+// object and the per-gate dispatcher.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "qd_internal.cuh"
+#include "qudit.h"
+
+namespace qd {
+
+qd_status fail(qd_status st, const char* fmt, ...);
+qd_status cuda_fail(cudaError_t e, const char* what);
+void set_last_error(const char* msg);
+
+#define QD_CUDA(call, what)                                     \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return ::qd::cuda_fail(e_, what); \
+    } while (0)
+
+qd_status make_layout(const int32_t* dims, int32_t n, Layout& L);
+size_t amp_bytes(int32_t prec);
+
+// Plan of one gate for the per-gate kernels.
+struct Plan {
+    int family;   // 0 = per-class register kernel, 1 = shared-memory tile kernel
+    int kind;
+    int vec;
+    int d;        // single-wire dimension (family 0)
+    int P;
+    uint32_t lmask, smask;
+    bool pure;
+    int perm[kMaxSmallD];
+    int64_t bt;
+    IndexMap map;
+    uint64_t classes;
+    int64_t run;
+    uint64_t off[kMaxGateDim];
+};
+
+void build_map(const Layout& L, const int32_t* ins_w, const int64_t* ins_v, int m, IndexMap& map,
+               uint64_t& classes);
+qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t k, const double* U,
+                    const int32_t* cw, const int32_t* cv, int32_t nc, Plan& p);
+
+}  // namespace qd
+
+static constexpr int kRingSlots = 8;
+
+struct qd_state {
+    qd::Layout L;
+    int32_t prec;
+    void* psi;
+    bool owns;
+    size_t bytes;
+    cudaStream_t stream;
+    int device;
+    int nb;              // reduction blocks
+    double* partials;    // nb * 2 * max_dim doubles
+    double* dev_out;     // kMaxGateDim doubles
+    double* host_out;    // pinned, kMaxGateDim doubles
+    void* ring_dev;      // kRingSlots matrices of P*P complex (P <= 64)
+    void* ring_host;     // pinned staging
+    cudaEvent_t ring_ev[kRingSlots];
+    bool ring_ev_live[kRingSlots];
+    int ring_next;
+    void* fuse_dev;      // fused-pass descriptors (device)
+    void* fuse_host;     // pinned staging of the same
+    size_t fuse_bytes;   // capacity of both
+    cudaEvent_t fuse_ev; // upload of the staging buffer finished
+    bool fuse_ev_live;
+};
+
+namespace qd {
+qd_status apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
+                    const int32_t* cv, int32_t nc);
+qd_status read_out(qd_state* st, int count, double* host);
+}  // namespace qd

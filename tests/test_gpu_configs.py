@@ -35,13 +35,14 @@ def config1_ref(gen):
     return circ, oracle.run_circuit(circ, nthreads=max(1, oracle.max_threads()))
 
 
+@pytest.mark.parametrize("fuse", [False, True])
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-def test_config1_full_depth_500(qb, config1_ref, prec):
-    """12 qubits + 8 qutrits (26,873,856 amplitudes), 500 gates."""
+def test_config1_full_depth_500(qb, config1_ref, prec, fuse):
+    """12 qubits + 8 qutrits (26,873,856 amplitudes), 500 gates, gate by gate and fused."""
     circ, ref = config1_ref
     p = qb.QD_C128 if prec == "c128" else qb.QD_C64
     st = qb.State(circ.dims, prec=p)
-    st.run(circ)
+    st.run(circ, fuse=fuse)
     got = st.raw()
     nrm = st.norm()
     st.close()
@@ -49,29 +50,32 @@ def test_config1_full_depth_500(qb, config1_ref, prec):
     assert abs(nrm - 1.0) < (1e-12 if p == qb.QD_C128 else 1e-5)
 
 
-def test_config2_prefix_against_oracle(qb, gen):
+@pytest.mark.parametrize("fuse", [False, True])
+def test_config2_prefix_against_oracle(qb, gen, fuse):
     """The lowest 20 wires of the 18-qubit + 8-qutrit workload with the gates that stay inside them."""
     full = gen.config2_circuit()
     pre = gen.prefix_circuit(full, 20)
     ref = oracle.run_circuit(pre, nthreads=max(1, oracle.max_threads()))
     st = qb.State(pre.dims, prec=qb.QD_C64)
-    st.run(pre)
+    st.run(pre, fuse=fuse)
     got = st.raw()
     st.close()
     assert_close(got, ref, qb.QD_C64, "config2 prefix")
 
 
-def test_config2_full_size_inverse_returns_to_zero(qb, gen):
+@pytest.mark.parametrize("fuse", [False, True])
+def test_config2_full_size_inverse_returns_to_zero(qb, gen, fuse):
     """1.72e9 amplitudes, complex64: the circuit followed by its inverse gives
     back |0...0> (|psi_0|^2 = 1 and norm 1 pin every other amplitude to ~0)."""
     import torch
 
     circ = gen.config2_circuit()
+    inv = gen.Circuit(circ.dims, [gen.Gate(g.wires, g.U.conj().T, g.controls, g.values)
+                                  for g in reversed(circ.gates)])
     st = qb.State(circ.dims, prec=qb.QD_C64)
-    st.run(circ)
+    st.run(circ, fuse=fuse)
     mid = st.norm()
-    for g in reversed(circ.gates):
-        st.apply(gen.Gate(g.wires, g.U.conj().T, g.controls, g.values))
+    st.run(inv, fuse=fuse)
     nrm = st.norm()
     amp0 = st.buf[:2].double().cpu().numpy()
     st.close()

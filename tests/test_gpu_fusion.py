@@ -1,0 +1,105 @@
+"""GPU parity of fused circuits (shared-memory tile passes) against the oracle,
+across tile sizes, odd and even row lengths, in-tile and outside controls,
+and non-fusable gates interleaved."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+from tests.gpu_util import assert_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qb():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    __graft_entry__.build()
+    from paper_2410_17876_gb300 import binding
+
+    return binding
+
+
+@pytest.fixture(scope="module")
+def gen():
+    from paper_2410_17876_gb300 import inputs
+
+    return inputs
+
+
+def _run(qb, circ, prec, psi0=None, **opts):
+    st = qb.State(circ.dims, prec=prec)
+    if psi0 is not None:
+        st.set_amplitudes(psi0)
+    st.run(circ, fuse=True, **opts)
+    out = st.amplitudes()
+    st.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_config0_fused_single_tile(qb, gen, prec):
+    p = qb.QD_C128 if prec == "c128" else qb.QD_C64
+    circ = gen.config0_circuit(seed=0, depth=200)
+    order, pass_of, tiles = qb.qd_plan_circuit(circ.dims, p, circ)
+    assert len(tiles) == 1 and tiles[0] == circ.D  # the whole state is one tile
+    assert_close(_run(qb, circ, p), oracle.run_circuit(circ), p, "config0 fused")
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("max_tile", [64, 256, 2048, 8192])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_random_mixed_circuits_fused(qb, gen, prec, max_tile, seed):
+    p = qb.QD_C128 if prec == "c128" else qb.QD_C64
+    if p == qb.QD_C128 and max_tile > 4096:
+        max_tile = 4096
+    rng = np.random.Generator(np.random.PCG64(100 + seed))
+    dims = tuple(int(x) for x in rng.choice([2, 3, 4, 5], size=int(rng.integers(7, 11))))
+    if seed == 2:
+        dims = (3, 3, 5, 3) + dims[4:]  # odd row lengths (no 16-byte path)
+    circ = gen.random_mixed_circuit(dims, 160, rng)
+    # interleave multi-controlled, diagonal and non-fusable gates
+    extra = []
+    n = len(dims)
+    for _ in range(25):
+        t = int(rng.integers(n))
+        cw = tuple(int(x) for x in rng.permutation([w for w in range(n) if w != t])[:3])
+        extra.append(gen.Gate((t,), gen.haar(dims[t], rng), cw, tuple(int(rng.integers(dims[c])) for c in cw)))
+        extra.append(gen.Gate((t,), gen.z_gen(dims[t])))
+    extra.append(gen.Gate((1, 0), gen.haar(dims[0] * dims[1], rng)))
+    gates = circ.gates[:80] + extra + circ.gates[80:]
+    circ = gen.Circuit(dims, gates)
+    psi0 = gen.random_state(circ.D, rng)
+    got = _run(qb, circ, p, psi0, max_tile_amps=max_tile)
+    ref = oracle.run_circuit(circ, psi0)
+    assert_close(got, ref, p, f"fused dims={dims} tile={max_tile}")
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_fused_equals_unfused_on_wide_state(qb, gen, prec):
+    """A 2^22-amplitude state: many tiles per pass; fused within tolerance of per-gate."""
+    p = qb.QD_C128 if prec == "c128" else qb.QD_C64
+    rng = np.random.Generator(np.random.PCG64(7))
+    dims = (2,) * 10 + (3, 2, 2, 3) + (2,) * 6
+    circ = gen.random_mixed_circuit(dims, 300, rng)
+    st = qb.State(dims, prec=p)
+    st.run(circ, fuse=True)
+    a = st.amplitudes()
+    st.reset()
+    st.run(circ, fuse=False)
+    b = st.amplitudes()
+    st.close()
+    tol = 1e-12 if p == qb.QD_C128 else 1e-5
+    assert np.max(np.abs(a - b)) < tol
+    assert abs(np.vdot(a, a).real - 1.0) < tol
+
+
+def test_tile_too_large_is_rejected(qb, gen):
+    circ = gen.config0_circuit(depth=5)
+    st = qb.State(circ.dims, prec=qb.QD_C128)
+    with pytest.raises(qb.QuditError) as ei:
+        st.run(circ, fuse=True, max_tile_amps=1 << 20)
+    assert ei.value.status == qb.QD_ERR_UNSUPPORTED
+    st.close()
