@@ -430,6 +430,25 @@ def run_ncu_case(args):
     return 0
 
 
+def run_ncu_fused_case(args):
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2410_17876_gb300 import binding as qb
+    from paper_2410_17876_gb300 import inputs as gen
+
+    prec = qb.QD_C64 if args.prec == "c64" else qb.QD_C128
+    circ = gen.config1_circuit()
+    st = qb.State(circ.dims, prec=prec)
+    st.run(circ, fuse=True, **({"max_tile_amps": args.tile} if args.tile else {}))
+    st.synchronize()
+    st.close()
+    torch.cuda.synchronize()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -445,9 +464,14 @@ def main(argv=None):
     ap.add_argument("--ncu-case", action="store_true",
                     help="run only six dense single-wire gates (wires 0, 5, 10, 15, 19, 3) on the workload's "
                          "state, for a profiler capture of launches 4-6; prints nothing")
+    ap.add_argument("--ncu-fused-case", action="store_true",
+                    help="run only the workload circuit once with tile fusion (reset + passes), for a profiler "
+                         "capture of one k_fused_tile launch; prints nothing")
     args = ap.parse_args(argv)
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.ncu_fused_case:
+        return run_ncu_fused_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

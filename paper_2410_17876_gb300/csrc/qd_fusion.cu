@@ -40,16 +40,19 @@ struct FastDiv32 {
     }
 };
 
-constexpr int kMaxLocalIns = 1 + QD_MAX_CONTROLS;
-constexpr int kMaxFusedD = 5;  // single-wire gates up to this dimension join fused passes
+constexpr int kMaxFusedD = 5;      // single-wire gates up to this dimension join fused passes
+constexpr int kMaxTileCtrl = 7;    // controls of a fused gate (inside or outside the tile)
+constexpr int kMaxLocalIns = 1 + kMaxTileCtrl;
+constexpr int kMaxPassGates = 64;  // gates per fused pass (their descriptors live in shared memory)
 constexpr int kMaxRows = 2048;
 
 // Class enumeration inside a tile (local index space of S), 32-bit.
-struct LocalMap {
+struct __align__(16) LocalMap {
     int32_t m;
     uint32_t fixed;
+    uint32_t pad_[2];
     FastDiv32 seg[kMaxLocalIns];
-    uint32_t off[kMaxLocalIns + 1];
+    uint32_t off[kMaxLocalIns + 4];
     __device__ __forceinline__ uint32_t map(uint32_t g) const {
         uint32_t j = fixed, r = g;
         for (int i = 0; i < m; ++i) {
@@ -61,19 +64,20 @@ struct LocalMap {
     }
 };
 
-// One gate of a pass (device memory).
+// One gate of a pass.  Built on the host, copied to shared memory by every CTA.
 template <typename R>
-struct FGate {
+struct __align__(16) FGate {
     using T2 = typename Cplx<R>::T2;
-    int32_t d, kind;
-    uint32_t lmask, smask, pure;
-    int32_t perm[kMaxSmallD];
-    uint32_t nclasses, lst;  // classes in a tile; local stride of the target
-    int32_t n_out;           // controls outside S
-    int32_t out_w[QD_MAX_CONTROLS];
-    int32_t out_v[QD_MAX_CONTROLS];
+    T2 U[kMaxFusedD * kMaxFusedD];
     LocalMap map;
-    T2 U[kMaxSmallD * kMaxSmallD];
+    uint32_t nclasses;  // classes in a tile
+    uint32_t lst;       // local stride of the target
+    uint32_t step;      // lst * d (class base step when the target is the only inserted wire)
+    uint32_t pad_;
+    uint8_t d, kind, lmask, smask, pure, n_out, pad2_[2];
+    uint8_t perm[8];
+    uint8_t out_w[kMaxTileCtrl + 1];  // controls outside S: global wire, value
+    uint8_t out_v[kMaxTileCtrl + 1];
 };
 
 template <typename R>
@@ -92,7 +96,7 @@ struct FusedArgs {
     int32_t free_w[kMaxWires];
     uint32_t free_d[kMaxWires];
     uint64_t free_b[kMaxWires];
-    const uint64_t* rowoff;  // device, R entries: offset of each row from the tile base
+    const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
 };
 
 namespace {
@@ -110,75 +114,164 @@ template <typename T2> __device__ __forceinline__ void fcmac(T2& acc, const T2& 
     acc.y = fma(u.y, x.x, acc.y);
 }
 
+// Small fixed-size arrays passed by value, so that they stay in registers.
+template <typename T, int N>
+struct Arr {
+    T v[N];
+};
+
+// y = G x for one class held in registers (dense, diagonal or permutation).
+template <typename T2, int DT>
+__device__ __forceinline__ Arr<T2, DT> class_math(const Arr<T2, DT> x, int kind, bool pure, const Arr<int, DT> perm,
+                                                  const Arr<T2, DT * DT> u) {
+    Arr<T2, DT> y;
+    if (kind == kDense) {
+#pragma unroll
+        for (int r = 0; r < DT; ++r) {
+            T2 acc = fcmul(u.v[r * DT], x.v[0]);
+#pragma unroll
+            for (int k = 1; k < DT; ++k) fcmac(acc, u.v[r * DT + k], x.v[k]);
+            y.v[r] = acc;
+        }
+    } else if (kind == kDiag) {
+#pragma unroll
+        for (int r = 0; r < DT; ++r) y.v[r] = fcmul(u.v[r * DT + r], x.v[r]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < DT; ++r) {
+            T2 v = x.v[0], w = u.v[r * DT];
+#pragma unroll
+            for (int k = 1; k < DT; ++k)
+                if (perm.v[r] == k) {
+                    v = x.v[k];
+                    w = u.v[r * DT + k];
+                }
+            y.v[r] = pure ? v : fcmul(w, v);
+        }
+    }
+    return y;
+}
+
 // Apply one single-wire gate of dimension DT to the tile in shared memory.
-// The gate's matrix (sU) and class enumeration (map) were staged in shared
-// memory by the caller; every thread reads the same entries (broadcast).
+// Matrix, permutation and masks are loop invariants read once per gate from
+// the shared-memory descriptor.  With no control inside the tile (m == 1) a
+// class index c = hi * lst + lo has base hi * lst * d + lo (one division);
+// complex64 with an even local stride processes two adjacent classes with
+// 16-byte accesses.
 template <typename R, int DT>
-__device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGate<R>& G, const LocalMap& map,
-                                          const typename Cplx<R>::T2* sU) {
+__device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGate<R>& G) {
     using T2 = typename Cplx<R>::T2;
     const int kind = G.kind;
     const uint32_t lmask = G.lmask, smask = G.smask, lst = G.lst, nc = G.nclasses;
-    int perm[DT];
-#pragma unroll
-    for (int r = 0; r < DT; ++r) perm[r] = G.perm[r];
     const bool pure = G.pure != 0;
-    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
-        const uint32_t b = map.map(c);
-        T2 x[DT];
+    Arr<int, DT> perm;
 #pragma unroll
-        for (int k = 0; k < DT; ++k)
-            if (lmask >> k & 1u) x[k] = tile[b + k * lst];
-        if (kind == kDense) {
-            T2 y[DT];
+    for (int r = 0; r < DT; ++r) perm.v[r] = G.perm[r];
+    Arr<T2, DT * DT> u;
 #pragma unroll
-            for (int r = 0; r < DT; ++r) {
-                T2 acc = fcmul(sU[r * DT], x[0]);
+    for (int i = 0; i < DT * DT; ++i) u.v[i] = G.U[i];
+    if (G.map.m == 1) {
+        const FastDiv32 f = G.map.seg[0];
+        const uint32_t step = G.step;
+        if constexpr (sizeof(R) == 4) {
+            if ((lst & 1u) == 0) {
+                for (uint32_t c = 2 * threadIdx.x; c < nc; c += 2 * blockDim.x) {
+                    const uint32_t hi = f.div(c);
+                    const uint32_t b = hi * step + (c - hi * lst);
+                    Arr<T2, DT> x0, x1;
 #pragma unroll
-                for (int k = 1; k < DT; ++k) fcmac(acc, sU[r * DT + k], x[k]);
-                y[r] = acc;
-            }
-#pragma unroll
-            for (int r = 0; r < DT; ++r) tile[b + r * lst] = y[r];
-        } else if (kind == kDiag) {
-#pragma unroll
-            for (int r = 0; r < DT; ++r)
-                if (smask >> r & 1u) tile[b + r * lst] = fcmul(sU[r * DT + r], x[r]);
-        } else {
-            T2 y[DT];
-#pragma unroll
-            for (int r = 0; r < DT; ++r) {
-                T2 v = x[0];
-                int src = 0;
-#pragma unroll
-                for (int k = 1; k < DT; ++k)
-                    if (perm[r] == k) {
-                        v = x[k];
-                        src = k;
+                    for (int k = 0; k < DT; ++k) {
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (lmask >> k & 1u) v = *reinterpret_cast<const float4*>(tile + b + k * lst);
+                        x0.v[k] = make_float2(v.x, v.y);
+                        x1.v[k] = make_float2(v.z, v.w);
                     }
-                y[r] = pure ? v : fcmul(sU[r * DT + src], v);
+                    const Arr<T2, DT> y0 = class_math<T2, DT>(x0, kind, pure, perm, u);
+                    const Arr<T2, DT> y1 = class_math<T2, DT>(x1, kind, pure, perm, u);
+#pragma unroll
+                    for (int r = 0; r < DT; ++r)
+                        if (smask >> r & 1u)
+                            *reinterpret_cast<float4*>(tile + b + r * lst) =
+                                make_float4(y0.v[r].x, y0.v[r].y, y1.v[r].x, y1.v[r].y);
+                }
+                return;
             }
+            if (DT == 2 && lst == 1) {  // the class is two adjacent amplitudes
+                for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+                    const float4 v = *reinterpret_cast<const float4*>(tile + 2 * c);
+                    Arr<T2, DT> x;
+                    x.v[0] = make_float2(v.x, v.y);
+                    x.v[DT - 1] = make_float2(v.z, v.w);
+                    const Arr<T2, DT> y = class_math<T2, DT>(x, kind, pure, perm, u);
+                    if (smask == 3u)
+                        *reinterpret_cast<float4*>(tile + 2 * c) = make_float4(y.v[0].x, y.v[0].y, y.v[DT - 1].x,
+                                                                               y.v[DT - 1].y);
+                    else
+#pragma unroll
+                        for (int r = 0; r < DT; ++r)
+                            if (smask >> r & 1u) tile[2 * c + r] = y.v[r];
+                }
+                return;
+            }
+        }
+        for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+            const uint32_t hi = f.div(c);
+            const uint32_t b = hi * step + (c - hi * lst);
+            Arr<T2, DT> x;
+#pragma unroll
+            for (int k = 0; k < DT; ++k) {
+                x.v[k].x = 0;
+                x.v[k].y = 0;
+                if (lmask >> k & 1u) x.v[k] = tile[b + k * lst];
+            }
+            const Arr<T2, DT> y = class_math<T2, DT>(x, kind, pure, perm, u);
 #pragma unroll
             for (int r = 0; r < DT; ++r)
-                if (smask >> r & 1u) tile[b + r * lst] = y[r];
+                if (smask >> r & 1u) tile[b + r * lst] = y.v[r];
+        }
+    } else {
+        for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+            const uint32_t b = G.map.map(c);
+            Arr<T2, DT> x;
+#pragma unroll
+            for (int k = 0; k < DT; ++k) {
+                x.v[k].x = 0;
+                x.v[k].y = 0;
+                if (lmask >> k & 1u) x.v[k] = tile[b + k * lst];
+            }
+            const Arr<T2, DT> y = class_math<T2, DT>(x, kind, pure, perm, u);
+#pragma unroll
+            for (int r = 0; r < DT; ++r)
+                if (smask >> r & 1u) tile[b + r * lst] = y.v[r];
         }
     }
 }
 
+// Shared memory of a CTA: [pass descriptors][row offsets][tile], each 16-byte aligned.
 template <typename R>
+__host__ __device__ inline size_t fused_desc_bytes(int ngates) {
+    return sizeof(FGate<R>) * (size_t)ngates;
+}
+__host__ __device__ inline size_t fused_rows_bytes(uint32_t rows) { return ((size_t)rows * 8 + 15) & ~(size_t)15; }
+
+template <typename R, int DMAX>
 __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ FusedArgs<R> a) {
     using T2 = typename Cplx<R>::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2* tile = reinterpret_cast<T2*>(smem_raw);
-    uint64_t* srow = reinterpret_cast<uint64_t*>(tile + a.T);
+    FGate<R>* sg = reinterpret_cast<FGate<R>*>(smem_raw);
+    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + fused_desc_bytes<R>(a.ngates));
+    T2* tile = reinterpret_cast<T2*>(smem_raw + fused_desc_bytes<R>(a.ngates) + fused_rows_bytes(a.rows));
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
-    __shared__ LocalMap smap;
-    __shared__ T2 sU[kMaxFusedD * kMaxFusedD];
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.gates);
+        uint4* dst = reinterpret_cast<uint4*>(sg);
+        const uint32_t n16 = (uint32_t)(fused_desc_bytes<R>(a.ngates) / 16);
+        for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+    }
     for (uint32_t r = threadIdx.x; r < a.rows; r += blockDim.x) srow[r] = a.rowoff[r];
-    const uint64_t t = blockIdx.x;
     if (threadIdx.x == 0) {
-        uint64_t rem = t, base = 0;
+        uint64_t rem = blockIdx.x, base = 0;
         for (int i = 0; i < a.nfree; ++i) {
             const uint64_t q = rem / a.free_d[i];
             const uint32_t dig = (uint32_t)(rem - q * a.free_d[i]);
@@ -193,8 +286,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
     if (a.vec2) {
         for (uint32_t e = 2 * threadIdx.x; e < a.T; e += 2 * blockDim.x) {
             const uint32_t r = a.bLdiv.div(e);
-            const float4 v = *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(g) + srow[r] + (e - r * a.bL));
-            reinterpret_cast<float4*>(tile)[e >> 1] = v;
+            reinterpret_cast<float4*>(tile)[e >> 1] =
+                *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(g) + srow[r] + (e - r * a.bL));
         }
     } else {
         for (uint32_t e = threadIdx.x; e < a.T; e += blockDim.x) {
@@ -204,24 +297,14 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
     }
     __syncthreads();
     for (int gi = 0; gi < a.ngates; ++gi) {
-        const FGate<R>& G = a.gates[gi];
+        const FGate<R>& G = sg[gi];
         bool ok = true;
-        for (int c = 0; c < G.n_out; ++c) ok = ok && (odig[G.out_w[c]] == G.out_v[c]);
+        for (int c = 0; c < G.n_out; ++c) ok = ok && (odig[G.out_w[c]] == (int32_t)G.out_v[c]);
         if (!ok) continue;  // uniform across the CTA
-        {   // enumeration and matrix are read once per class: stage them in shared memory
-            const uint32_t* src = reinterpret_cast<const uint32_t*>(&G.map);
-            uint32_t* dst = reinterpret_cast<uint32_t*>(&smap);
-            for (uint32_t i = threadIdx.x; i < sizeof(LocalMap) / 4; i += blockDim.x) dst[i] = src[i];
-            const int dd = G.d * G.d;
-            for (int i = threadIdx.x; i < dd; i += blockDim.x) sU[i] = G.U[i];
-        }
-        __syncthreads();
-        switch (G.d) {
-            case 2: tile_gate<R, 2>(tile, G, smap, sU); break;
-            case 3: tile_gate<R, 3>(tile, G, smap, sU); break;
-            case 4: tile_gate<R, 4>(tile, G, smap, sU); break;
-            default: tile_gate<R, 5>(tile, G, smap, sU); break;
-        }
+        if (G.d == 2) tile_gate<R, 2>(tile, G);
+        else if (DMAX == 3 || G.d == 3) tile_gate<R, 3>(tile, G);
+        else if (G.d == 4) tile_gate<R, (DMAX > 3 ? 4 : 3)>(tile, G);
+        else tile_gate<R, DMAX>(tile, G);
         __syncthreads();
     }
     if (a.vec2) {
@@ -239,22 +322,29 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
 }
 
 template <typename R>
-size_t fused_smem(uint32_t tile_amps, uint32_t rows) {
-    return sizeof(typename Cplx<R>::T2) * (size_t)tile_amps + sizeof(uint64_t) * (size_t)rows;
+size_t fused_smem(const FusedArgs<R>& a) {
+    return fused_desc_bytes<R>(a.ngates) + fused_rows_bytes(a.rows) + sizeof(typename Cplx<R>::T2) * (size_t)a.T;
 }
 
+// dmax: largest wire dimension among the pass's gates (selects the kernel
+// instance, so passes of qubits and qutrits do not pay for d = 5 registers).
 template <typename R>
-cudaError_t launch_fused(const FusedArgs<R>& a, cudaStream_t s) {
+cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
     static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused_tile<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             200 * 1024);
+        cudaError_t e = cudaFuncSetAttribute(k_fused_tile<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_tile<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    k_fused_tile<R><<<(unsigned)a.ntiles, 256, fused_smem<R>(a.T, a.rows), s>>>(a);
+    if (dmax <= 3)
+        k_fused_tile<R, 3><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
+    else
+        k_fused_tile<R, 5><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -330,7 +420,7 @@ static qd_status load_gates(const Layout& L, int32_t prec, const qd_gate_desc* g
         }
         h.P = h.plan.P;
         h.diag = h.plan.family == 0 && h.plan.kind == kDiag;
-        h.fusable = h.plan.family == 0 && h.plan.d <= kMaxFusedD;
+        h.fusable = h.plan.family == 0 && h.plan.d <= kMaxFusedD && h.nc <= kMaxTileCtrl;
         h.tmask = 0;
         h.cmask = 0;
         for (int m = 0; m < h.k; ++m) h.tmask |= 1ull << h.wires[m];
@@ -367,7 +457,7 @@ static void plan_passes(const Layout& L, const std::vector<HGate>& G, const Fuse
                 const uint64_t W = g.diag ? 0 : g.tmask;
                 const uint64_t Rd = g.cmask | (g.diag ? g.tmask : 0);
                 const bool blocked = (W & (BW | BR)) || (Rd & BW);
-                bool ok = !blocked && g.fusable;
+                bool ok = !blocked && g.fusable && (int)sched.size() < kMaxPassGates;
                 if (ok) {
                     const uint64_t need = g.tmask & ~S;
                     int64_t T2 = T;
@@ -461,29 +551,24 @@ static void tile_geometry(const Layout& L, uint64_t S, int64_t min_row, TileGeom
     }
 }
 
-static void to_local32(const IndexMap& m, LocalMap& o) {
-    o.m = m.m;
-    o.fixed = (uint32_t)m.fixed;
-    for (int i = 0; i < m.m; ++i) o.seg[i].init((uint32_t)m.seg[i].d);
-    for (int i = 0; i <= m.m; ++i) o.off[i] = (uint32_t)m.off[i];
-}
 
 template <typename R>
-static void build_fgate(const Layout& L, const TileGeom& geo, const HGate& h, FGate<R>& f) {
+static void build_fgate(const TileGeom& geo, const HGate& h, FGate<R>& f) {
     std::memset(static_cast<void*>(&f), 0, sizeof f);
     const Plan& p = h.plan;
-    f.d = p.d;
-    f.kind = p.kind;
-    f.lmask = p.lmask;
-    f.smask = p.smask;
-    f.pure = p.pure ? 1u : 0u;
-    for (int r = 0; r < kMaxSmallD; ++r) f.perm[r] = p.perm[r];
+    f.d = (uint8_t)p.d;
+    f.kind = (uint8_t)p.kind;
+    f.lmask = (uint8_t)p.lmask;
+    f.smask = (uint8_t)p.smask;
+    f.pure = p.pure ? 1 : 0;
+    for (int r = 0; r < 8; ++r) f.perm[r] = (uint8_t)(r < kMaxSmallD ? p.perm[r] : 0);
     for (int i = 0; i < p.d * p.d; ++i) {
         f.U[i].x = (R)h.U[2 * i];
         f.U[i].y = (R)h.U[2 * i + 1];
     }
     const int t = geo.loc[h.wires[0]];
     f.lst = (uint32_t)geo.local.b[t];
+    f.step = f.lst * (uint32_t)p.d;
     int32_t ins_w[kMaxLocalIns];
     int64_t ins_v[kMaxLocalIns];
     int m = 0;
@@ -498,15 +583,18 @@ static void build_fgate(const Layout& L, const TileGeom& geo, const HGate& h, FG
             ins_v[m] = h.cv[c];
             ++m;
         } else {
-            f.out_w[f.n_out] = h.cw[c];
-            f.out_v[f.n_out] = h.cv[c];
+            f.out_w[f.n_out] = (uint8_t)h.cw[c];
+            f.out_v[f.n_out] = (uint8_t)h.cv[c];
             ++f.n_out;
         }
     }
     IndexMap im;
     uint64_t classes;
     build_map(geo.local, ins_w, ins_v, m, im, classes);
-    to_local32(im, f.map);
+    f.map.m = im.m;
+    f.map.fixed = (uint32_t)im.fixed;
+    for (int i = 0; i < im.m; ++i) f.map.seg[i].init((uint32_t)im.seg[i].d);
+    for (int i = 0; i <= im.m; ++i) f.map.off[i] = (uint32_t)im.off[i];
     f.nclasses = (uint32_t)classes;
 }
 
@@ -547,6 +635,7 @@ static qd_status run_circuit_impl(qd_state* st, std::vector<HGate>& G, const Fus
     // fill the staging buffer
     struct Launch {
         FusedArgs<R> a;
+        int dmax;
     };
     std::vector<Launch> launches;
     size_t off = 0;
@@ -558,7 +647,7 @@ static qd_status run_circuit_impl(qd_state* st, std::vector<HGate>& G, const Fus
         tile_geometry(st->L, p.smask, cfg.min_row, geo);
         FGate<R>* hg = reinterpret_cast<FGate<R>*>(hb + off);
         const FGate<R>* dg = reinterpret_cast<const FGate<R>*>(db + off);
-        for (size_t i = 0; i < p.gates.size(); ++i) build_fgate<R>(st->L, geo, G[p.gates[i]], hg[i]);
+        for (size_t i = 0; i < p.gates.size(); ++i) build_fgate<R>(geo, G[p.gates[i]], hg[i]);
         off += sizeof(FGate<R>) * p.gates.size();
         off = (off + 255) & ~(size_t)255;
         uint64_t* hr = reinterpret_cast<uint64_t*>(hb + off);
@@ -584,6 +673,8 @@ static qd_status run_circuit_impl(qd_state* st, std::vector<HGate>& G, const Fus
             L.a.free_b[i] = geo.free_b[i];
         }
         L.a.rowoff = dr;
+        L.dmax = 2;
+        for (int idx : p.gates) L.dmax = G[idx].plan.d > L.dmax ? G[idx].plan.d : L.dmax;
         launches.push_back(L);
     }
     if (bytes > 0) {
@@ -594,7 +685,8 @@ static qd_status run_circuit_impl(qd_state* st, std::vector<HGate>& G, const Fus
     size_t li = 0;
     for (const PassPlan& p : passes) {
         if (p.tile) {
-            cudaError_t e = launch_fused<R>(launches[li++].a, st->stream);
+            const Launch& ln = launches[li++];
+            cudaError_t e = launch_fused<R>(ln.a, ln.dmax, st->stream);
             if (e != cudaSuccess) return cuda_fail(e, "fused tile kernel");
         } else {
             const HGate& h = G[p.gates[0]];
