@@ -204,6 +204,66 @@ qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd
                           int32_t* n_passes);
 
 /* ------------------------------------------------------------------------
+ * Batches of independent circuits.  Each circuit starts from its own
+ * |0...0> state; the states of one run live side by side in one device
+ * buffer owned by the batch.  The paper simulates one circuit at a time;
+ * independent circuits share nothing, so they run concurrently:
+ *   - a circuit whose state fits one CTA's shared memory (D <=
+ *     small_max_amps) and whose gates are all single-wire with d <= 5 and
+ *     at most 7 controls runs whole inside one CTA -- all such circuits in
+ *     one launch, the state written to HBM once at the end;
+ *   - every other circuit runs as a (fused) circuit program, round-robin on
+ *     n_streams auxiliary streams joined back to the batch stream;
+ *   - with use_graph, the whole run is captured in a CUDA graph, launched,
+ *     and kept for qd_batch_relaunch.
+ * Every circuit's squared norm is reduced on the GPU after its last gate.
+ * --------------------------------------------------------------------- */
+typedef struct qd_batch qd_batch;
+
+typedef struct qd_circuit {
+    int32_t n_wires;
+    const int32_t* dims;        /* n_wires dimensions, q_0 first */
+    int32_t n_gates;
+    const qd_gate_desc* gates;  /* as for qd_apply_circuit */
+    const double* matrices;
+} qd_circuit;
+
+typedef struct qd_batch_opts {
+    int32_t small_max_amps;  /* 0 = default (8192 complex64, 4096 complex128) */
+    int32_t n_streams;       /* 0 = default (8), at most 64 */
+    int32_t use_graph;       /* capture the run in a CUDA graph */
+    int32_t reserved;
+    qd_fusion_opts fusion;   /* for circuits outside the one-CTA path */
+} qd_batch_opts;
+
+/* Create an empty batch whose work is issued on `stream` (NULL = default). */
+qd_status qd_batch_create(int32_t prec, void* stream, qd_batch** out);
+
+/* Validate all n circuits (nothing runs if one is invalid: QD_ERR_ARG or
+ * QD_ERR_UNSUPPORTED naming the circuit), lay out their states, and issue
+ * the run asynchronously.  opts = NULL: defaults with tile fusion.  The
+ * arrays may be reused when the call returns.  A batch is used by one host
+ * thread at a time; a new run replaces the previous run's states. */
+qd_status qd_batch_run(qd_batch* b, const qd_circuit* circuits, int32_t n, const qd_batch_opts* opts);
+
+/* Launch the graph captured by the last qd_batch_run again (same circuits,
+ * recomputed from |0...0>).  QD_ERR_ARG if that run was not captured. */
+qd_status qd_batch_relaunch(qd_batch* b);
+
+/* Device pointer and amplitude count of circuit i's state after the run. */
+qd_status qd_batch_state(qd_batch* b, int32_t i, void** dev_ptr, int64_t* num_amplitudes);
+
+/* Circuit i's final state as 2*D host doubles (widened exactly for
+ * QD_C64).  Synchronous. */
+qd_status qd_batch_get_amplitudes(qd_batch* b, int32_t i, double* host_interleaved);
+
+/* The n squared norms of the last run into host_out.  Synchronous. */
+qd_status qd_batch_norms(qd_batch* b, double* host_out);
+
+qd_status qd_batch_synchronize(qd_batch* b);
+qd_status qd_batch_destroy(qd_batch* b);
+
+/* ------------------------------------------------------------------------
  * Readouts.  Sums run in binary64 with compensated (Neumaier) summation in
  * a fixed order, so results are deterministic for a given state size.
  * The paper defines no readout; these are the standard Born-rule

@@ -54,6 +54,16 @@ class qd_fusion_opts(ctypes.Structure):
                 ("min_row", ctypes.c_int32)]
 
 
+class qd_circuit(ctypes.Structure):
+    _fields_ = [("n_wires", ctypes.c_int32), ("dims", ctypes.POINTER(ctypes.c_int32)), ("n_gates", ctypes.c_int32),
+                ("gates", ctypes.POINTER(qd_gate_desc)), ("matrices", ctypes.POINTER(ctypes.c_double))]
+
+
+class qd_batch_opts(ctypes.Structure):
+    _fields_ = [("small_max_amps", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("fusion", qd_fusion_opts)]
+
+
 _SIGS = {
     "qd_state_create": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
     "qd_state_wrap": (ctypes.c_int32, [_vp, ctypes.c_size_t, _i32p, ctypes.c_int32, ctypes.c_int32, _vp,
@@ -81,6 +91,14 @@ _SIGS = {
     "qd_plan_gate": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _f64p,
                                       _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(qd_plan_info)]),
     "qd_selftest_host": (ctypes.c_int32, [ctypes.c_int32]),
+    "qd_batch_create": (ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
+    "qd_batch_run": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_circuit), ctypes.c_int32, ctypes.POINTER(qd_batch_opts)]),
+    "qd_batch_relaunch": (ctypes.c_int32, [_vp]),
+    "qd_batch_state": (ctypes.c_int32, [_vp, ctypes.c_int32, ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int64)]),
+    "qd_batch_get_amplitudes": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
+    "qd_batch_norms": (ctypes.c_int32, [_vp, _f64p]),
+    "qd_batch_synchronize": (ctypes.c_int32, [_vp]),
+    "qd_batch_destroy": (ctypes.c_int32, [_vp]),
     "qd_apply_circuit": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_gate_desc), ctypes.c_int32, _f64p,
                                           ctypes.POINTER(qd_fusion_opts)]),
     "qd_plan_circuit": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(qd_gate_desc),
@@ -330,6 +348,65 @@ def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min
                                 _p(pass_of, _i32p), tiles.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                 ctypes.byref(npass)), "qd_plan_circuit")
     return order[:n], pass_of[:n], tiles[:npass.value]
+
+
+def qd_batch_create(prec: int = QD_C64, stream: int = 0) -> int:
+    out = _vp()
+    _check(_lib.qd_batch_create(int(prec), _vp(stream), ctypes.byref(out)), "qd_batch_create")
+    return out.value
+
+
+def qd_batch_run(b: int, circuits, small_max_amps=0, n_streams=0, use_graph=False, fuse=True,
+                 max_tile_amps=0, min_gates=0, min_row=0) -> None:
+    """Run independent circuits (each from |0...0>) as one batch; asynchronous."""
+    n = len(circuits)
+    arr = (qd_circuit * max(1, n))()
+    keep = []
+    for i, c in enumerate(circuits):
+        dims = _i32(c.dims)
+        descs, m = circuit_arrays(c)
+        keep.append((dims, descs, m))
+        arr[i].n_wires = len(dims)
+        arr[i].dims = _p(dims, _i32p)
+        arr[i].n_gates = len(c.gates)
+        arr[i].gates = ctypes.cast(descs, ctypes.POINTER(qd_gate_desc))
+        arr[i].matrices = _p(m, _f64p)
+    opts = qd_batch_opts(int(small_max_amps), int(n_streams), 1 if use_graph else 0, 0,
+                         qd_fusion_opts(QD_FUSE_TILE if fuse else QD_FUSE_OFF, int(max_tile_amps), int(min_gates),
+                                        int(min_row)))
+    _check(_lib.qd_batch_run(_vp(b), arr, n, ctypes.byref(opts)), "qd_batch_run")
+
+
+def qd_batch_relaunch(b: int) -> None:
+    _check(_lib.qd_batch_relaunch(_vp(b)), "qd_batch_relaunch")
+
+
+def qd_batch_state(b: int, i: int):
+    ptr = _vp()
+    D = ctypes.c_int64()
+    _check(_lib.qd_batch_state(_vp(b), int(i), ctypes.byref(ptr), ctypes.byref(D)), "qd_batch_state")
+    return ptr.value, D.value
+
+
+def qd_batch_get_amplitudes(b: int, i: int) -> np.ndarray:
+    _, D = qd_batch_state(b, i)
+    out = np.empty(D, dtype=np.complex128)
+    _check(_lib.qd_batch_get_amplitudes(_vp(b), int(i), _p(out.view(np.float64), _f64p)), "qd_batch_get_amplitudes")
+    return out
+
+
+def qd_batch_norms(b: int, n: int) -> np.ndarray:
+    out = np.empty(max(1, n), dtype=np.float64)
+    _check(_lib.qd_batch_norms(_vp(b), _p(out, _f64p)), "qd_batch_norms")
+    return out[:n]
+
+
+def qd_batch_synchronize(b: int) -> None:
+    _check(_lib.qd_batch_synchronize(_vp(b)), "qd_batch_synchronize")
+
+
+def qd_batch_destroy(b: int) -> None:
+    _check(_lib.qd_batch_destroy(_vp(b)), "qd_batch_destroy")
 
 
 # --- convenience ----------------------------------------------------------------------------------

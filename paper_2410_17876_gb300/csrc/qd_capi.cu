@@ -237,9 +237,10 @@ static void free_state(qd_state* st) {
     if (st->ring_host) cudaFreeHost(st->ring_host);
     for (int i = 0; i < kRingSlots; ++i)
         if (st->ring_ev_live[i]) cudaEventDestroy(st->ring_ev[i]);
-    if (st->fuse_dev) cudaFree(st->fuse_dev);
-    if (st->fuse_host) cudaFreeHost(st->fuse_host);
-    if (st->fuse_ev_live) cudaEventDestroy(st->fuse_ev);
+    if (st->arena) {
+        st->arena->release();
+        delete st->arena;
+    }
     delete st;
 }
 

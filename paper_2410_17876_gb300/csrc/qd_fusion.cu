@@ -13,6 +13,8 @@
 // pass instead of one per gate.
 #include <algorithm>
 #include <cstring>
+#include <functional>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -97,6 +99,16 @@ struct FusedArgs {
     uint32_t free_d[kMaxWires];
     uint64_t free_b[kMaxWires];
     const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
+};
+
+// One small circuit of a batch (whole state in one CTA).
+struct SmallTask {
+    uint64_t psi_off;     // byte offset of the state in the batch's state arena
+    uint64_t gate_off;    // byte offset of its FGate descriptors in the descriptor arena
+    uint32_t D;           // amplitudes
+    uint32_t ngates;
+    uint32_t norm_index;  // slot of its squared norm
+    uint32_t pad_;
 };
 
 namespace {
@@ -345,6 +357,102 @@ cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
         k_fused_tile<R, 3><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
     else
         k_fused_tile<R, 5><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Whole circuits of small states, one CTA per circuit: the state starts as
+// |0...0> in shared memory, every gate of the circuit is applied there
+// (descriptors streamed through shared memory in chunks of kMaxPassGates),
+// then the state is written to HBM once and its squared norm is reduced.
+template <typename R, int DMAX>
+__global__ void __launch_bounds__(256, 2) k_batch_small(const SmallTask* tasks, char* state_base,
+                                                         const char* desc_base, double* norms) {
+    using T2 = typename Cplx<R>::T2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    FGate<R>* sg = reinterpret_cast<FGate<R>*>(smem_raw);
+    T2* tile = reinterpret_cast<T2*>(smem_raw + fused_desc_bytes<R>(kMaxPassGates));
+    __shared__ double red_s[8], red_c[8];
+    const SmallTask tk = tasks[blockIdx.x];
+    for (uint32_t e = threadIdx.x; e < tk.D; e += blockDim.x) {
+        T2 z;
+        z.x = e == 0 ? (R)1 : (R)0;
+        z.y = 0;
+        tile[e] = z;
+    }
+    const FGate<R>* gates = reinterpret_cast<const FGate<R>*>(desc_base + tk.gate_off);
+    for (uint32_t g0 = 0; g0 < tk.ngates; g0 += kMaxPassGates) {
+        const uint32_t ng = tk.ngates - g0 < (uint32_t)kMaxPassGates ? tk.ngates - g0 : (uint32_t)kMaxPassGates;
+        __syncthreads();  // previous chunk done with the descriptors
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(gates + g0);
+            uint4* dst = reinterpret_cast<uint4*>(sg);
+            const uint32_t n16 = (uint32_t)(fused_desc_bytes<R>((int)ng) / 16);
+            for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        for (uint32_t gi = 0; gi < ng; ++gi) {
+            const FGate<R>& G = sg[gi];
+            if (G.d == 2) tile_gate<R, 2>(tile, G);
+            else if (DMAX == 3 || G.d == 3) tile_gate<R, 3>(tile, G);
+            else if (G.d == 4) tile_gate<R, (DMAX > 3 ? 4 : 3)>(tile, G);
+            else tile_gate<R, DMAX>(tile, G);
+            __syncthreads();
+        }
+    }
+    T2* psi = reinterpret_cast<T2*>(state_base + tk.psi_off);
+    double s = 0.0, c = 0.0;  // Neumaier per thread, then a fixed-order tree
+    for (uint32_t e = threadIdx.x; e < tk.D; e += blockDim.x) {
+        const T2 v = tile[e];
+        psi[e] = v;
+        const double p = fma((double)v.x, (double)v.x, (double)v.y * (double)v.y);
+        const double t = s + p;
+        c += fabs(s) >= fabs(p) ? (s - t) + p : (p - t) + s;
+        s = t;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const double s2 = __shfl_down_sync(0xffffffffu, s, o);
+        const double c2 = __shfl_down_sync(0xffffffffu, c, o);
+        const double t = s + s2, bb = t - s;
+        c = c + c2 + ((s - (t - bb)) + (s2 - bb));
+        s = t;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        red_s[threadIdx.x >> 5] = s;
+        red_c[threadIdx.x >> 5] = c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0, C = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            const double t = S + red_s[w], bb = t - S;
+            C += red_c[w] + ((S - (t - bb)) + (red_s[w] - bb));
+            S = t;
+        }
+        norms[tk.norm_index] = S + C;
+    }
+}
+
+template <typename R>
+cudaError_t launch_batch_small(const SmallTask* tasks, int ntasks, int dmax, uint32_t max_d, char* state_base,
+                               const char* desc_base, double* norms, cudaStream_t s) {
+    if (ntasks <= 0) return cudaSuccess;
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_batch_small<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_batch_small<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const size_t smem = fused_desc_bytes<R>(kMaxPassGates) + sizeof(typename Cplx<R>::T2) * (size_t)max_d;
+    if (dmax <= 3)
+        k_batch_small<R, 3><<<ntasks, 256, smem, s>>>(tasks, state_base, desc_base, norms);
+    else
+        k_batch_small<R, 5><<<ntasks, 256, smem, s>>>(tasks, state_base, desc_base, norms);
     count_launch();
     return cudaGetLastError();
 }
@@ -598,108 +706,420 @@ static void build_fgate(const TileGeom& geo, const HGate& h, FGate<R>& f) {
     f.nclasses = (uint32_t)classes;
 }
 
+// ---------------------------------------------------------------------------
+// Programs: the launches of a circuit with their descriptors.  Building a
+// program makes no CUDA call; running it uploads the descriptors once and
+// issues the launches, so many programs can share one upload and be issued
+// on several streams or inside a CUDA graph capture.
+// ---------------------------------------------------------------------------
+using Op = std::function<cudaError_t(cudaStream_t, const char*)>;
+
+struct Program {
+    std::vector<char> desc;
+    std::vector<Op> ops;
+    size_t reserve(size_t n) {
+        const size_t o = (desc.size() + 255) & ~(size_t)255;
+        desc.resize(o + n);
+        return o;
+    }
+    size_t put(const void* p, size_t n) {
+        const size_t o = reserve(n);
+        std::memcpy(desc.data() + o, p, n);
+        return o;
+    }
+};
+
+qd_status Arena::upload(const void* bytes, size_t n, cudaStream_t s) {
+    if (n == 0) return QD_OK;
+    if (n > cap) {
+        QD_CUDA(cudaStreamSynchronize(s), "descriptor arena resize");
+        if (ev_live) cudaEventSynchronize(ev);
+        if (dev) cudaFree(dev);
+        if (host) cudaFreeHost(host);
+        dev = host = nullptr;
+        cap = 0;
+        const size_t want = n + n / 2;
+        cudaError_t e = cudaMalloc(&dev, want);
+        if (e != cudaSuccess) return fail(QD_ERR_OOM, "descriptor arena: %s", cudaGetErrorString(e));
+        e = cudaMallocHost(&host, want);
+        if (e != cudaSuccess) return fail(QD_ERR_OOM, "pinned descriptor arena: %s", cudaGetErrorString(e));
+        cap = want;
+        if (!ev_live) {
+            QD_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "cudaEventCreate");
+            ev_live = true;
+        }
+    } else if (ev_live) {
+        QD_CUDA(cudaEventSynchronize(ev), "descriptor staging wait");
+    }
+    std::memcpy(host, bytes, n);
+    QD_CUDA(cudaMemcpyAsync(dev, host, n, cudaMemcpyHostToDevice, s), "descriptor upload");
+    QD_CUDA(cudaEventRecord(ev, s), "descriptor event");
+    return QD_OK;
+}
+
+void Arena::release() {
+    if (ev_live) {
+        cudaEventSynchronize(ev);
+        cudaEventDestroy(ev);
+    }
+    if (dev) cudaFree(dev);
+    if (host) cudaFreeHost(host);
+    dev = host = nullptr;
+    cap = 0;
+    ev_live = false;
+}
+
+template <typename R, int DT>
+static Op gate1_op(void* psi, const Plan& p, const double* U) {
+    using T2 = typename Cplx<R>::T2;
+    Gate1Args<R, DT> a;
+    std::memset(static_cast<void*>(&a), 0, sizeof a);
+    a.psi = reinterpret_cast<T2*>(psi);
+    a.n_elems = p.classes / (uint64_t)p.vec;
+    a.bt = (uint64_t)p.bt;
+    a.map = p.map;
+    a.kind = p.kind;
+    a.lmask = p.lmask;
+    a.smask = p.smask;
+    a.pure_perm = p.pure ? 1u : 0u;
+    for (int r = 0; r < DT; ++r) a.perm[r] = p.perm[r];
+    for (int i = 0; i < DT * DT; ++i) {
+        a.U[i].x = (R)U[2 * i];
+        a.U[i].y = (R)U[2 * i + 1];
+    }
+    if (sizeof(R) == 4 && p.vec == 2)
+        return [a](cudaStream_t s, const char*) { return launch_gate1<R, DT, (sizeof(R) == 4 ? 2 : 1)>(a, s); };
+    return [a](cudaStream_t s, const char*) { return launch_gate1<R, DT, 1>(a, s); };
+}
+
+// The op of one gate for the per-gate kernels (no fusion).
 template <typename R>
-static qd_status run_circuit_impl(qd_state* st, std::vector<HGate>& G, const FuseCfg& cfg) {
-    std::vector<PassPlan> passes;
-    plan_passes(st->L, G, cfg, passes);
-    // descriptors of all tile passes of this call, uploaded once
-    size_t bytes = 0;
-    for (const PassPlan& p : passes)
-        if (p.tile) {
-            bytes += sizeof(FGate<R>) * p.gates.size();
-            bytes = (bytes + 255) & ~(size_t)255;
-            bytes += sizeof(uint64_t) * kMaxRows;
-            bytes = (bytes + 255) & ~(size_t)255;
-        }
-    if (bytes > 0) {
-        if (bytes > st->fuse_bytes) {
-            QD_CUDA(cudaStreamSynchronize(st->stream), "fusion arena resize");
-            if (st->fuse_dev) cudaFree(st->fuse_dev);
-            if (st->fuse_host) cudaFreeHost(st->fuse_host);
-            st->fuse_dev = st->fuse_host = nullptr;
-            st->fuse_bytes = 0;
-            size_t cap = bytes + bytes / 2;
-            cudaError_t e = cudaMalloc(&st->fuse_dev, cap);
-            if (e != cudaSuccess) return fail(QD_ERR_OOM, "fusion arena: %s", cudaGetErrorString(e));
-            e = cudaMallocHost(&st->fuse_host, cap);
-            if (e != cudaSuccess) return fail(QD_ERR_OOM, "pinned fusion arena: %s", cudaGetErrorString(e));
-            st->fuse_bytes = cap;
-            if (!st->fuse_ev_live) {
-                QD_CUDA(cudaEventCreateWithFlags(&st->fuse_ev, cudaEventDisableTiming), "cudaEventCreate");
-                st->fuse_ev_live = true;
-            }
-        } else if (st->fuse_ev_live) {
-            QD_CUDA(cudaEventSynchronize(st->fuse_ev), "fusion staging wait");
+static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog) {
+    using T2 = typename Cplx<R>::T2;
+    if (p.family == 0) {
+        switch (p.d) {
+            case 2: return gate1_op<R, 2>(psi, p, U);
+            case 3: return gate1_op<R, 3>(psi, p, U);
+            case 4: return gate1_op<R, 4>(psi, p, U);
+            case 5: return gate1_op<R, 5>(psi, p, U);
+            case 6: return gate1_op<R, 6>(psi, p, U);
+            case 7: return gate1_op<R, 7>(psi, p, U);
+            default: return gate1_op<R, 8>(psi, p, U);
         }
     }
-    // fill the staging buffer
-    struct Launch {
-        FusedArgs<R> a;
-        int dmax;
+    const int P = p.P;
+    std::vector<T2> m((size_t)P * P);
+    for (int i = 0; i < P * P; ++i) {
+        m[i].x = (R)U[2 * i];
+        m[i].y = (R)U[2 * i + 1];
+    }
+    const size_t uoff = prog.put(m.data(), sizeof(T2) * m.size());
+    GateTileArgs<R> a;
+    std::memset(static_cast<void*>(&a), 0, sizeof a);
+    a.psi = reinterpret_cast<T2*>(psi);
+    a.n_classes = p.classes;
+    a.map = p.map;
+    a.P = P;
+    a.Q = 64;
+    for (int r = 0; r < P; ++r) a.off[r] = p.off[r];
+    const int smem = (int)gate_tile_smem<R>(P, a.Q);
+    return [a, uoff, smem](cudaStream_t s, const char* base) {
+        GateTileArgs<R> b = a;
+        b.U = reinterpret_cast<const T2*>(base + uoff);
+        return launch_gate_tile<R>(b, s, smem);
     };
-    std::vector<Launch> launches;
-    size_t off = 0;
-    char* hb = static_cast<char*>(st->fuse_host);
-    char* db = static_cast<char*>(st->fuse_dev);
-    for (const PassPlan& p : passes) {
-        if (!p.tile) continue;
-        TileGeom geo;
-        tile_geometry(st->L, p.smask, cfg.min_row, geo);
-        FGate<R>* hg = reinterpret_cast<FGate<R>*>(hb + off);
-        const FGate<R>* dg = reinterpret_cast<const FGate<R>*>(db + off);
-        for (size_t i = 0; i < p.gates.size(); ++i) build_fgate<R>(geo, G[p.gates[i]], hg[i]);
-        off += sizeof(FGate<R>) * p.gates.size();
-        off = (off + 255) & ~(size_t)255;
-        uint64_t* hr = reinterpret_cast<uint64_t*>(hb + off);
-        const uint64_t* dr = reinterpret_cast<const uint64_t*>(db + off);
-        std::memcpy(hr, geo.rowoff.data(), sizeof(uint64_t) * geo.R);
-        off += sizeof(uint64_t) * kMaxRows;
-        off = (off + 255) & ~(size_t)255;
-        Launch L;
-        std::memset(static_cast<void*>(&L.a), 0, sizeof L.a);
-        L.a.psi = reinterpret_cast<typename Cplx<R>::T2*>(st->psi);
-        L.a.gates = dg;
-        L.a.ngates = (int32_t)p.gates.size();
-        L.a.T = (uint32_t)p.T;
-        L.a.bL = geo.bL;
-        L.a.rows = geo.R;
-        L.a.vec2 = (sizeof(R) == 4 && geo.bL % 2 == 0) ? 1 : 0;
-        L.a.bLdiv.init(geo.bL);
-        L.a.ntiles = (uint64_t)(st->L.D / p.T);
-        L.a.nfree = geo.nfree;
-        for (int i = 0; i < geo.nfree; ++i) {
-            L.a.free_w[i] = geo.free_w[i];
-            L.a.free_d[i] = geo.free_d[i];
-            L.a.free_b[i] = geo.free_b[i];
-        }
-        L.a.rowoff = dr;
-        L.dmax = 2;
-        for (int idx : p.gates) L.dmax = G[idx].plan.d > L.dmax ? G[idx].plan.d : L.dmax;
-        launches.push_back(L);
+}
+
+// Ops of a whole circuit on the state at psi (layout L): optional reset to
+// |0...0>, then the planned passes in order.
+template <typename R>
+static void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
+                          bool reset_first, Program& prog) {
+    using T2 = typename Cplx<R>::T2;
+    if (reset_first) {
+        const int64_t D = L.D;
+        prog.ops.push_back([psi, D](cudaStream_t s, const char*) { return launch_set_basis<R>(psi, D, 0, s); });
     }
-    if (bytes > 0) {
-        QD_CUDA(cudaMemcpyAsync(st->fuse_dev, st->fuse_host, off, cudaMemcpyHostToDevice, st->stream),
-                "fusion descriptor upload");
-        QD_CUDA(cudaEventRecord(st->fuse_ev, st->stream), "fusion event");
-    }
-    size_t li = 0;
+    std::vector<PassPlan> passes;
+    plan_passes(L, G, cfg, passes);
     for (const PassPlan& p : passes) {
-        if (p.tile) {
-            const Launch& ln = launches[li++];
-            cudaError_t e = launch_fused<R>(ln.a, ln.dmax, st->stream);
-            if (e != cudaSuccess) return cuda_fail(e, "fused tile kernel");
-        } else {
+        if (!p.tile) {
             const HGate& h = G[p.gates[0]];
-            qd_status rc = apply_any(st, h.wires, h.k, h.U, h.cw, h.cv, h.nc);
-            if (rc != QD_OK) return rc;
+            if (h.plan.family == 0 && h.plan.smask == 0) continue;  // identity
+            if (h.plan.classes == 0) continue;
+            prog.ops.push_back(gate_op<R>(psi, h.plan, h.U, prog));
+            continue;
         }
+        TileGeom geo;
+        tile_geometry(L, p.smask, cfg.min_row, geo);
+        const size_t offF = prog.reserve(sizeof(FGate<R>) * p.gates.size());
+        for (size_t i = 0; i < p.gates.size(); ++i)
+            build_fgate<R>(geo, G[p.gates[i]], reinterpret_cast<FGate<R>*>(prog.desc.data() + offF)[i]);
+        const size_t offR = prog.put(geo.rowoff.data(), sizeof(uint64_t) * geo.R);
+        FusedArgs<R> a;
+        std::memset(static_cast<void*>(&a), 0, sizeof a);
+        a.psi = reinterpret_cast<T2*>(psi);
+        a.ngates = (int32_t)p.gates.size();
+        a.T = (uint32_t)p.T;
+        a.bL = geo.bL;
+        a.rows = geo.R;
+        a.vec2 = (sizeof(R) == 4 && geo.bL % 2 == 0) ? 1 : 0;
+        a.bLdiv.init(geo.bL);
+        a.ntiles = (uint64_t)(L.D / p.T);
+        a.nfree = geo.nfree;
+        for (int i = 0; i < geo.nfree; ++i) {
+            a.free_w[i] = geo.free_w[i];
+            a.free_d[i] = geo.free_d[i];
+            a.free_b[i] = geo.free_b[i];
+        }
+        int dmax = 2;
+        for (int idx : p.gates) dmax = G[idx].plan.d > dmax ? G[idx].plan.d : dmax;
+        prog.ops.push_back([a, offF, offR, dmax](cudaStream_t s, const char* base) {
+            FusedArgs<R> b = a;
+            b.gates = reinterpret_cast<const FGate<R>*>(base + offF);
+            b.rowoff = reinterpret_cast<const uint64_t*>(base + offR);
+            return launch_fused<R>(b, dmax, s);
+        });
     }
+}
+
+static qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
+    for (const Op& op : prog.ops) {
+        cudaError_t e = op(s, base);
+        if (e != cudaSuccess) return cuda_fail(e, "circuit kernel launch");
+    }
+    return QD_OK;
+}
+
+static qd_status check_cfg(const FuseCfg& cfg, int32_t prec) {
+    if (cfg.mode != QD_FUSE_OFF && cfg.mode != QD_FUSE_TILE) return fail(QD_ERR_ARG, "unknown fusion mode");
+    if (cfg.mode == QD_FUSE_TILE && cfg.Tmax > tile_limit(prec))
+        return fail(QD_ERR_UNSUPPORTED, "tile of %lld amplitudes exceeds shared memory (limit %lld)",
+                    (long long)cfg.Tmax, (long long)tile_limit(prec));
     return QD_OK;
 }
 
 }  // namespace qd
 
 using namespace qd;
+
+// ---------------------------------------------------------------------------
+// Batches of independent circuits.
+// ---------------------------------------------------------------------------
+struct qd_batch {
+    int32_t prec;
+    cudaStream_t main;
+    std::vector<cudaStream_t> aux;
+    std::vector<cudaEvent_t> aux_ev;
+    cudaEvent_t fork_ev;
+    bool fork_live;
+    char* states;          // all states of the last run
+    size_t states_cap;
+    std::vector<uint64_t> psi_off;
+    std::vector<int64_t> D;
+    double* norms;         // device, one per circuit
+    double* host_norms;    // pinned
+    size_t norms_cap;
+    double* partials;      // reduction scratch, one block per aux stream
+    size_t partials_stride;
+    Arena arena;
+    cudaGraph_t graph;
+    cudaGraphExec_t graph_exec;
+    bool graph_live;
+};
+
+static void batch_free(qd_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->main);
+    for (size_t i = 0; i < b->aux.size(); ++i) {
+        cudaStreamDestroy(b->aux[i]);
+        cudaEventDestroy(b->aux_ev[i]);
+    }
+    if (b->fork_live) cudaEventDestroy(b->fork_ev);
+    if (b->graph_live) {
+        cudaGraphExecDestroy(b->graph_exec);
+        cudaGraphDestroy(b->graph);
+    }
+    if (b->states) cudaFree(b->states);
+    if (b->norms) cudaFree(b->norms);
+    if (b->host_norms) cudaFreeHost(b->host_norms);
+    if (b->partials) cudaFree(b->partials);
+    b->arena.release();
+    delete b;
+}
+
+template <typename R>
+static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t n, const qd_batch_opts* opts) {
+    using T2 = typename Cplx<R>::T2;
+    const size_t ab = sizeof(T2);
+    qd_fusion_opts fo{};
+    if (opts) fo = opts->fusion;
+    FuseCfg cfg = fuse_cfg(opts ? &fo : nullptr, b->prec);
+    if (!opts) cfg.mode = QD_FUSE_TILE;
+    qd_status rc = check_cfg(cfg, b->prec);
+    if (rc != QD_OK) return rc;
+    const int64_t small_max = (opts && opts->small_max_amps > 0) ? opts->small_max_amps : (b->prec == QD_C64 ? 8192 : 4096);
+    if (small_max > tile_limit(b->prec)) return fail(QD_ERR_UNSUPPORTED, "small-circuit tile above shared memory");
+    int nstreams = (opts && opts->n_streams > 0) ? opts->n_streams : 8;
+    if (nstreams > 64) nstreams = 64;
+    const bool use_graph = opts && opts->use_graph;
+
+    // 1. validate every circuit and lay out the states
+    std::vector<Layout> Ls((size_t)n);
+    std::vector<std::vector<HGate>> Gs((size_t)n);
+    b->psi_off.assign((size_t)n, 0);
+    b->D.assign((size_t)n, 0);
+    size_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        const qd_circuit& c = circuits[i];
+        rc = make_layout(c.dims, c.n_wires, Ls[i]);
+        if (rc == QD_OK) rc = load_gates(Ls[i], b->prec, c.gates, c.n_gates, c.matrices, Gs[i]);
+        if (rc != QD_OK) {
+            std::string msg = qd_last_error();
+            return fail(rc, "circuit %d: %s", i, msg.c_str());
+        }
+        b->psi_off[i] = total;
+        b->D[i] = Ls[i].D;
+        total += ((size_t)Ls[i].D * ab + 255) & ~(size_t)255;
+    }
+    // 2. device buffers (grown when needed)
+    QD_CUDA(cudaStreamSynchronize(b->main), "batch sync");
+    if (b->graph_live) {
+        cudaGraphExecDestroy(b->graph_exec);
+        cudaGraphDestroy(b->graph);
+        b->graph_live = false;
+    }
+    if (total > b->states_cap) {
+        if (b->states) cudaFree(b->states);
+        b->states = nullptr;
+        b->states_cap = 0;
+        cudaError_t e = cudaMalloc(&b->states, total);
+        if (e != cudaSuccess) return fail(QD_ERR_OOM, "batch states (%zu bytes): %s", total, cudaGetErrorString(e));
+        b->states_cap = total;
+    }
+    if ((size_t)n > b->norms_cap) {
+        if (b->norms) cudaFree(b->norms);
+        if (b->host_norms) cudaFreeHost(b->host_norms);
+        b->norms = nullptr;
+        b->host_norms = nullptr;
+        b->norms_cap = 0;
+        const size_t cap = (size_t)n + 16;
+        cudaError_t e = cudaMalloc(&b->norms, sizeof(double) * cap);
+        if (e == cudaSuccess) e = cudaMallocHost(&b->host_norms, sizeof(double) * cap);
+        if (e != cudaSuccess) return fail(QD_ERR_OOM, "batch norms: %s", cudaGetErrorString(e));
+        b->norms_cap = cap;
+    }
+    while ((int)b->aux.size() < nstreams) {
+        cudaStream_t s;
+        cudaEvent_t e;
+        QD_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "batch stream");
+        QD_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "batch event");
+        b->aux.push_back(s);
+        b->aux_ev.push_back(e);
+    }
+    if (!b->partials) {
+        b->partials_stride = 2 * 1024;
+        cudaError_t e = cudaMalloc(&b->partials, sizeof(double) * b->partials_stride * 64);
+        if (e != cudaSuccess) return fail(QD_ERR_OOM, "batch reduction scratch: %s", cudaGetErrorString(e));
+    }
+    // 3. programs: small circuits whole in one CTA; the rest through the planner
+    Program prog;
+    std::vector<SmallTask> small3, small5;
+    uint32_t maxd3 = 1, maxd5 = 1;
+    std::vector<Program> big;
+    std::vector<int> big_idx;
+    for (int i = 0; i < n; ++i) {
+        const Layout& L = Ls[i];
+        bool fits = L.D <= small_max && (int)Gs[i].size() > 0;
+        int dmax = 2;
+        for (const HGate& h : Gs[i]) {
+            if (!h.fusable) fits = false;
+            dmax = h.plan.d > dmax ? h.plan.d : dmax;
+        }
+        if (fits) {
+            TileGeom geo;
+            tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo);
+            SmallTask t{};
+            t.psi_off = b->psi_off[i];
+            t.D = (uint32_t)L.D;
+            t.ngates = (uint32_t)Gs[i].size();
+            t.norm_index = (uint32_t)i;
+            t.gate_off = prog.reserve(sizeof(FGate<R>) * Gs[i].size());
+            for (size_t g = 0; g < Gs[i].size(); ++g)
+                build_fgate<R>(geo, Gs[i][g], reinterpret_cast<FGate<R>*>(prog.desc.data() + t.gate_off)[g]);
+            if (dmax <= 3) {
+                small3.push_back(t);
+                maxd3 = t.D > maxd3 ? t.D : maxd3;
+            } else {
+                small5.push_back(t);
+                maxd5 = t.D > maxd5 ? t.D : maxd5;
+            }
+        } else {
+            Program pg;
+            pg.desc.swap(prog.desc);  // share one descriptor buffer: offsets stay global
+            build_program<R>(L, b->states + b->psi_off[i], Gs[i], cfg, true, pg);
+            prog.desc.swap(pg.desc);
+            big.push_back(std::move(pg));
+            big_idx.push_back(i);
+        }
+    }
+    const size_t off3 = small3.empty() ? 0 : prog.put(small3.data(), sizeof(SmallTask) * small3.size());
+    const size_t off5 = small5.empty() ? 0 : prog.put(small5.data(), sizeof(SmallTask) * small5.size());
+    rc = b->arena.upload(prog.desc.data(), prog.desc.size(), b->main);
+    if (rc != QD_OK) return rc;
+    const char* base = static_cast<const char*>(b->arena.dev);
+
+    // 4. issue: small circuits on the main stream, the others round-robin on
+    //    the auxiliary streams (joined back to the main stream at the end)
+    if (use_graph) QD_CUDA(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal), "graph capture");
+    if (!b->fork_live) {
+        QD_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming), "fork event");
+        b->fork_live = true;
+    }
+    QD_CUDA(cudaEventRecord(b->fork_ev, b->main), "fork record");
+    for (int k = 0; k < nstreams; ++k) QD_CUDA(cudaStreamWaitEvent(b->aux[k], b->fork_ev, 0), "fork wait");
+    cudaError_t e = launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + off3), (int)small3.size(), 3,
+                                          maxd3, b->states, base, b->norms, b->main);
+    if (e == cudaSuccess)
+        e = launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + off5), (int)small5.size(), 5, maxd5,
+                                  b->states, base, b->norms, b->main);
+    if (e != cudaSuccess) {
+        if (use_graph) {
+            cudaGraph_t g;
+            cudaStreamEndCapture(b->main, &g);
+        }
+        return cuda_fail(e, "small-circuit batch kernel");
+    }
+    for (size_t j = 0; j < big.size(); ++j) {
+        const int k = (int)(j % (size_t)nstreams);
+        const int i = big_idx[j];
+        rc = issue(big[j], base, b->aux[k]);
+        if (rc == QD_OK) {
+            const int nb = reduce_blocks(b->D[i]);
+            e = launch_norm<R>(b->states + b->psi_off[i], b->D[i], b->partials + b->partials_stride * k, nb,
+                               b->norms + i, b->aux[k]);
+            if (e != cudaSuccess) rc = cuda_fail(e, "batch norm");
+        }
+        if (rc != QD_OK) {
+            if (use_graph) {
+                cudaGraph_t g;
+                cudaStreamEndCapture(b->main, &g);
+            }
+            return rc;
+        }
+    }
+    for (int k = 0; k < nstreams; ++k) {
+        QD_CUDA(cudaEventRecord(b->aux_ev[k], b->aux[k]), "join record");
+        QD_CUDA(cudaStreamWaitEvent(b->main, b->aux_ev[k], 0), "join wait");
+    }
+    if (use_graph) {
+        QD_CUDA(cudaStreamEndCapture(b->main, &b->graph), "graph end capture");
+        QD_CUDA(cudaGraphInstantiate(&b->graph_exec, b->graph, 0), "graph instantiate");
+        b->graph_live = true;
+        QD_CUDA(cudaGraphLaunch(b->graph_exec, b->main), "graph launch");
+    }
+    return QD_OK;
+}
 
 extern "C" {
 
@@ -711,11 +1131,17 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
         qd_status rc = load_gates(st->L, st->prec, gates, n_gates, matrices, G);
         if (rc != QD_OK) return rc;
         const FuseCfg cfg = fuse_cfg(opts, st->prec);
-        if (cfg.mode != QD_FUSE_OFF && cfg.mode != QD_FUSE_TILE) return fail(QD_ERR_ARG, "unknown fusion mode");
-        if (cfg.Tmax > tile_limit(st->prec))
-            return fail(QD_ERR_UNSUPPORTED, "tile of %lld amplitudes exceeds shared memory (limit %lld)",
-                        (long long)cfg.Tmax, (long long)tile_limit(st->prec));
-        return st->prec == QD_C64 ? run_circuit_impl<float>(st, G, cfg) : run_circuit_impl<double>(st, G, cfg);
+        rc = check_cfg(cfg, st->prec);
+        if (rc != QD_OK) return rc;
+        Program prog;
+        if (st->prec == QD_C64)
+            build_program<float>(st->L, st->psi, G, cfg, false, prog);
+        else
+            build_program<double>(st->L, st->psi, G, cfg, false, prog);
+        if (!st->arena) st->arena = new Arena();
+        rc = st->arena->upload(prog.desc.data(), prog.desc.size(), st->stream);
+        if (rc != QD_OK) return rc;
+        return issue(prog, static_cast<const char*>(st->arena->dev), st->stream);
     } catch (...) {
         return fail(QD_ERR_OOM, "host exception in qd_apply_circuit");
     }
@@ -749,6 +1175,92 @@ qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd
     } catch (...) {
         return fail(QD_ERR_OOM, "host exception in qd_plan_circuit");
     }
+}
+
+qd_status qd_batch_create(int32_t prec, void* stream, qd_batch** out) {
+    if (!out) return fail(QD_ERR_ARG, "out is NULL");
+    if (prec != QD_C64 && prec != QD_C128) return fail(QD_ERR_ARG, "unknown precision %d", prec);
+    qd_batch* b = new (std::nothrow) qd_batch();
+    if (!b) return fail(QD_ERR_OOM, "host allocation failed");
+    b->prec = prec;
+    b->main = reinterpret_cast<cudaStream_t>(stream);
+    b->fork_live = false;
+    b->states = nullptr;
+    b->states_cap = 0;
+    b->norms = nullptr;
+    b->host_norms = nullptr;
+    b->norms_cap = 0;
+    b->partials = nullptr;
+    b->partials_stride = 0;
+    b->graph_live = false;
+    *out = b;
+    return QD_OK;
+}
+
+qd_status qd_batch_run(qd_batch* b, const qd_circuit* circuits, int32_t n, const qd_batch_opts* opts) {
+    try {
+        if (!b) return fail(QD_ERR_ARG, "batch is NULL");
+        if (n < 0 || (n > 0 && !circuits)) return fail(QD_ERR_ARG, "bad circuit list");
+        return b->prec == QD_C64 ? batch_run_impl<float>(b, circuits, n, opts)
+                                 : batch_run_impl<double>(b, circuits, n, opts);
+    } catch (...) {
+        return fail(QD_ERR_OOM, "host exception in qd_batch_run");
+    }
+}
+
+qd_status qd_batch_relaunch(qd_batch* b) {
+    if (!b) return fail(QD_ERR_ARG, "batch is NULL");
+    if (!b->graph_live) return fail(QD_ERR_ARG, "the last qd_batch_run was not captured in a graph");
+    QD_CUDA(cudaGraphLaunch(b->graph_exec, b->main), "graph launch");
+    return QD_OK;
+}
+
+qd_status qd_batch_state(qd_batch* b, int32_t i, void** dev_ptr, int64_t* num_amplitudes) {
+    if (!b || !dev_ptr) return fail(QD_ERR_ARG, "batch or out is NULL");
+    if (i < 0 || (size_t)i >= b->D.size()) return fail(QD_ERR_ARG, "circuit index %d out of range", i);
+    *dev_ptr = b->states + b->psi_off[i];
+    if (num_amplitudes) *num_amplitudes = b->D[i];
+    return QD_OK;
+}
+
+qd_status qd_batch_get_amplitudes(qd_batch* b, int32_t i, double* host) {
+    if (!b || !host) return fail(QD_ERR_ARG, "batch or out is NULL");
+    if (i < 0 || (size_t)i >= b->D.size()) return fail(QD_ERR_ARG, "circuit index %d out of range", i);
+    const size_t D = (size_t)b->D[i];
+    const char* src = b->states + b->psi_off[i];
+    if (b->prec == QD_C128) {
+        QD_CUDA(cudaMemcpyAsync(host, src, D * 16, cudaMemcpyDeviceToHost, b->main), "batch download");
+        QD_CUDA(cudaStreamSynchronize(b->main), "batch download sync");
+    } else {
+        // binary32 pairs into the upper half of the caller's buffer, widened front to back
+        float* raw = reinterpret_cast<float*>(reinterpret_cast<char*>(host) + D * 8);
+        QD_CUDA(cudaMemcpyAsync(raw, src, D * 8, cudaMemcpyDeviceToHost, b->main), "batch download");
+        QD_CUDA(cudaStreamSynchronize(b->main), "batch download sync");
+        for (size_t e = 0; e < 2 * D; ++e) host[e] = (double)raw[e];
+    }
+    return QD_OK;
+}
+
+qd_status qd_batch_norms(qd_batch* b, double* host_out) {
+    if (!b || !host_out) return fail(QD_ERR_ARG, "batch or out is NULL");
+    const size_t n = b->D.size();
+    if (n == 0) return QD_OK;
+    QD_CUDA(cudaMemcpyAsync(b->host_norms, b->norms, sizeof(double) * n, cudaMemcpyDeviceToHost, b->main),
+            "norm copy");
+    QD_CUDA(cudaStreamSynchronize(b->main), "norm sync");
+    std::memcpy(host_out, b->host_norms, sizeof(double) * n);
+    return QD_OK;
+}
+
+qd_status qd_batch_synchronize(qd_batch* b) {
+    if (!b) return fail(QD_ERR_ARG, "batch is NULL");
+    QD_CUDA(cudaStreamSynchronize(b->main), "batch synchronize");
+    return QD_OK;
+}
+
+qd_status qd_batch_destroy(qd_batch* b) {
+    batch_free(b);
+    return QD_OK;
 }
 
 }  // extern "C"

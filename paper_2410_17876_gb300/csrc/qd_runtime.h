@@ -21,6 +21,20 @@ void set_last_error(const char* msg);
     } while (0)
 
 qd_status make_layout(const int32_t* dims, int32_t n, Layout& L);
+
+// Device buffer plus pinned staging for kernel descriptors.  upload() waits
+// until the previous upload from the staging buffer has completed before
+// overwriting it, grows both buffers when needed (after synchronising the
+// stream), and issues one asynchronous copy on the stream.
+struct Arena {
+    void* dev = nullptr;
+    void* host = nullptr;
+    size_t cap = 0;
+    cudaEvent_t ev{};
+    bool ev_live = false;
+    qd_status upload(const void* bytes, size_t n, cudaStream_t s);
+    void release();
+};
 size_t amp_bytes(int32_t prec);
 
 // Plan of one gate for the per-gate kernels.
@@ -66,11 +80,7 @@ struct qd_state {
     cudaEvent_t ring_ev[kRingSlots];
     bool ring_ev_live[kRingSlots];
     int ring_next;
-    void* fuse_dev;      // fused-pass descriptors (device)
-    void* fuse_host;     // pinned staging of the same
-    size_t fuse_bytes;   // capacity of both
-    cudaEvent_t fuse_ev; // upload of the staging buffer finished
-    bool fuse_ev_live;
+    qd::Arena* arena;    // descriptors of circuit calls (device + pinned staging)
 };
 
 namespace qd {

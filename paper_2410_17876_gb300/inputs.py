@@ -35,7 +35,7 @@ from typing import List, Sequence, Tuple
 import numpy as np
 
 __all__ = [
-    "Gate", "Circuit", "haar", "x_plus", "z_gen", "fourier", "qubit_s",
+    "Gate", "Circuit", "haar", "haar_batch", "x_plus", "z_gen", "fourier", "qubit_s",
     "qubit_t", "random_state", "config0_circuit", "config1_circuit",
     "config2_circuit", "prefix_circuit", "config3_batch", "config4_trace",
     "random_mixed_circuit", "ghz_circuit", "amp_gate_updates",
@@ -147,38 +147,66 @@ def random_state(D: int, rng: np.random.Generator) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # Circuit generators (one per workload shape)
 # ----------------------------------------------------------------------------
-def _mixed_gate(dims: Sequence[int], rng: np.random.Generator) -> Gate:
-    """The 50/20/30 gate mix: Haar single / {X_{+1}, Z_d, F_d} / controlled.
-
-    Controlled gates draw a control wire different from the target, a
-    control value uniform in ``[0, d_c)`` and a target matrix that is either
-    ``X_{+1}`` or Haar with equal probability.
-    """
-    n = len(dims)
-    u = rng.random()
-    t = int(rng.integers(n))
-    d = dims[t]
-    if u < 0.5 or n == 1:
-        return Gate((t,), haar(d, rng), name="haar")
-    if u < 0.7:
-        k = int(rng.integers(3))
-        if k == 0:
-            return Gate((t,), x_plus(d, 1), name="X")
-        if k == 1:
-            return Gate((t,), z_gen(d), name="Z")
-        return Gate((t,), fourier(d), name="F")
-    c = int(rng.integers(n - 1))
-    if c >= t:
-        c += 1
-    v = int(rng.integers(dims[c]))
-    if rng.random() < 0.5:
-        return Gate((t,), x_plus(d, 1), (c,), (v,), name="CX")
-    return Gate((t,), haar(d, rng), (c,), (v,), name="CU")
+def haar_batch(d: int, m: int, rng: np.random.Generator) -> np.ndarray:
+    """``m`` Haar-random ``d x d`` unitaries (the same construction as :func:`haar`, batched)."""
+    if m == 0:
+        return np.zeros((0, d, d), dtype=np.complex128)
+    z = (rng.standard_normal((m, d, d)) + 1j * rng.standard_normal((m, d, d))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(z)
+    diag = np.diagonal(r, axis1=1, axis2=2)
+    ph = diag / np.abs(diag)
+    return np.ascontiguousarray(q * ph[:, np.newaxis, :])
 
 
 def random_mixed_circuit(dims: Sequence[int], depth: int, rng: np.random.Generator) -> Circuit:
+    """``depth`` gates of the 50/20/30 mix: Haar single-wire / one of
+    {X_{+1}, Z_d, F_d} / controlled (a control wire different from the
+    target, a control value uniform in ``[0, d_c)``, and a target matrix
+    that is X_{+1} or Haar with equal probability).  Wires are uniform.
+
+    The gate skeleton is drawn first (fixed order of vectorised draws), then
+    the Haar matrices, batched per dimension in gate order.
+    """
     dims = tuple(int(x) for x in dims)
-    return Circuit(dims, [_mixed_gate(dims, rng) for _ in range(depth)])
+    n = len(dims)
+    u = rng.random(depth)
+    t = rng.integers(n, size=depth)
+    k3 = rng.integers(3, size=depth)
+    craw = rng.integers(max(n - 1, 1), size=depth)
+    vu = rng.random(depth)
+    xhalf = rng.random(depth) < 0.5
+    kind = np.where((u < 0.5) | (n == 1), 0, np.where(u < 0.7, 1, 2))
+    need_haar = (kind == 0) | ((kind == 2) & ~xhalf)
+    tdims = np.asarray(dims)[t]
+    mats = {}
+    for d in sorted(set(int(x) for x in tdims[need_haar])):
+        idx = np.flatnonzero(need_haar & (tdims == d))
+        mats.update(zip(idx.tolist(), haar_batch(d, len(idx), rng)))
+    gates: List[Gate] = []
+    fixed = {}
+    for i in range(depth):
+        ti = int(t[i])
+        d = dims[ti]
+        if kind[i] == 0:
+            gates.append(Gate((ti,), mats[i], name="haar"))
+        elif kind[i] == 1:
+            key = (d, int(k3[i]))
+            if key not in fixed:
+                fixed[key] = (x_plus(d, 1), z_gen(d), fourier(d))[key[1]]
+            gates.append(Gate((ti,), fixed[key], name=("X", "Z", "F")[key[1]]))
+        else:
+            c = int(craw[i])
+            if c >= ti:
+                c += 1
+            v = int(vu[i] * dims[c])
+            if xhalf[i]:
+                key = (d, "x")
+                if key not in fixed:
+                    fixed[key] = x_plus(d, 1)
+                gates.append(Gate((ti,), fixed[key], (c,), (v,), name="CX"))
+            else:
+                gates.append(Gate((ti,), mats[i], (c,), (v,), name="CU"))
+    return Circuit(dims, gates)
 
 
 def config0_circuit(seed: int = 0, depth: int = 200) -> Circuit:

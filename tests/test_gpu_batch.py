@@ -1,0 +1,118 @@
+"""GPU parity of batched independent circuits against the oracle: one-CTA
+small circuits, fused programs on auxiliary streams, CUDA-graph capture and
+relaunch, and the 8192-circuit batched workload (sampled against the oracle,
+norms checked for every circuit)."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+from tests.gpu_util import assert_close
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def qb():
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    __graft_entry__.build()
+    from paper_2410_17876_gb300 import binding
+
+    return binding
+
+
+@pytest.fixture(scope="module")
+def gen():
+    from paper_2410_17876_gb300 import inputs
+
+    return inputs
+
+
+def _mixed_batch(gen, seed, n=40):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    circs = []
+    for i in range(n):
+        w = int(rng.integers(2, 9)) if i % 4 else int(rng.integers(9, 12))
+        dims = tuple(int(x) for x in rng.choice([2, 3, 4, 5], size=w))
+        c = gen.random_mixed_circuit(dims, int(rng.integers(5, 120)), rng)
+        if i % 7 == 3 and len(dims) >= 2:  # a multi-wire gate: not eligible for the one-CTA path
+            P = dims[0] * dims[1]
+            if P <= 64:
+                c.gates.insert(len(c.gates) // 2, gen.Gate((1, 0), gen.haar(P, rng)))
+        circs.append(c)
+    return circs
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_mixed_batch_against_oracle(qb, gen, prec, use_graph):
+    p = qb.QD_C128 if prec == "c128" else qb.QD_C64
+    circs = _mixed_batch(gen, 11)
+    b = qb.qd_batch_create(p)
+    qb.qd_batch_run(b, circs, use_graph=use_graph)
+    norms = qb.qd_batch_norms(b, len(circs))
+    for i, c in enumerate(circs):
+        got = qb.qd_batch_get_amplitudes(b, i)
+        ref = oracle.run_circuit(c)
+        assert_close(got, ref, p, f"batch circuit {i} dims={c.dims}")
+        tol = 1e-12 if p == qb.QD_C128 else 1e-5
+        assert abs(norms[i] - oracle.norm(ref)) < tol
+    qb.qd_batch_destroy(b)
+
+
+def test_batch_modes_agree_bitwise(qb, gen):
+    """Each circuit's kernels depend only on its own shape: streams, graph
+    capture and relaunch give bit-identical states."""
+    circs = _mixed_batch(gen, 12, n=24)
+    outs = []
+    for kw in (dict(n_streams=1), dict(n_streams=8), dict(n_streams=4, use_graph=True)):
+        b = qb.qd_batch_create(qb.QD_C64)
+        qb.qd_batch_run(b, circs, **kw)
+        outs.append([qb.qd_batch_get_amplitudes(b, i) for i in range(len(circs))])
+        if kw.get("use_graph"):
+            qb.qd_batch_relaunch(b)
+            outs.append([qb.qd_batch_get_amplitudes(b, i) for i in range(len(circs))])
+        qb.qd_batch_destroy(b)
+    for o in outs[1:]:
+        for a, c in zip(outs[0], o):
+            assert np.array_equal(a, c)
+
+
+def test_batch_alone_equals_in_batch(qb, gen):
+    """A circuit gives the same state alone and among others."""
+    circs = _mixed_batch(gen, 13, n=16)
+    b = qb.qd_batch_create(qb.QD_C64)
+    qb.qd_batch_run(b, circs)
+    together = [qb.qd_batch_get_amplitudes(b, i) for i in range(len(circs))]
+    for i in (0, 5, 9):
+        qb.qd_batch_run(b, [circs[i]])
+        assert np.array_equal(qb.qd_batch_get_amplitudes(b, 0), together[i])
+    qb.qd_batch_destroy(b)
+
+
+def test_invalid_circuit_rejects_the_batch(qb, gen):
+    circs = _mixed_batch(gen, 14, n=4)
+    bad = gen.Circuit((2, 3), [gen.Gate((0,), gen.x_plus(2), (1,), (5,))])  # control value 5 >= 3
+    b = qb.qd_batch_create(qb.QD_C64)
+    with pytest.raises(qb.QuditError) as ei:
+        qb.qd_batch_run(b, circs + [bad])
+    assert ei.value.status == qb.QD_ERR_ARG and "circuit 4" in str(ei.value)
+    qb.qd_batch_destroy(b)
+
+
+def test_batched_workload_8192_circuits(qb, gen):
+    """8192 circuits (widths 4-12, dims from {2,3,4,5}, depths 20-300), complex64:
+    every norm within 1e-5 of 1; every circuit with D <= 20,000 against the oracle."""
+    circs = gen.config3_batch()
+    b = qb.qd_batch_create(qb.QD_C64)
+    qb.qd_batch_run(b, circs, use_graph=True)
+    norms = qb.qd_batch_norms(b, len(circs))
+    assert np.all(np.abs(norms - 1.0) < 1e-5), np.max(np.abs(norms - 1.0))
+    rng = np.random.Generator(np.random.PCG64(5))
+    small = [i for i, c in enumerate(circs) if c.D <= 20000]
+    for i in rng.permutation(small)[:40]:
+        got = qb.qd_batch_get_amplitudes(b, int(i))
+        assert_close(got, oracle.run_circuit(circs[int(i)]), qb.QD_C64, f"workload circuit {i}")
+    qb.qd_batch_destroy(b)
