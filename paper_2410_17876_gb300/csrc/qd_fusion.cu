@@ -908,7 +908,10 @@ using namespace qd;
 // ---------------------------------------------------------------------------
 struct qd_batch {
     int32_t prec;
-    cudaStream_t main;
+    cudaStream_t main;     // the caller's stream
+    cudaStream_t work;     // private stream the run is issued (or captured) on
+    cudaEvent_t in_ev, out_ev;
+    bool work_live;
     std::vector<cudaStream_t> aux;
     std::vector<cudaEvent_t> aux_ev;
     cudaEvent_t fork_ev;
@@ -931,6 +934,12 @@ struct qd_batch {
 static void batch_free(qd_batch* b) {
     if (!b) return;
     cudaStreamSynchronize(b->main);
+    if (b->work_live) {
+        cudaStreamSynchronize(b->work);
+        cudaStreamDestroy(b->work);
+        cudaEventDestroy(b->in_ev);
+        cudaEventDestroy(b->out_ev);
+    }
     for (size_t i = 0; i < b->aux.size(); ++i) {
         cudaStreamDestroy(b->aux[i]);
         cudaEventDestroy(b->aux_ev[i]);
@@ -1069,24 +1078,40 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
     if (rc != QD_OK) return rc;
     const char* base = static_cast<const char*>(b->arena.dev);
 
-    // 4. issue: small circuits on the main stream, the others round-robin on
-    //    the auxiliary streams (joined back to the main stream at the end)
-    if (use_graph) QD_CUDA(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal), "graph capture");
+    // 4. issue on the private work stream: small circuits first, the others
+    //    round-robin on the auxiliary streams, joined back at the end.  The
+    //    work stream follows the caller's stream and the caller's stream
+    //    follows it; with use_graph the work stream is captured and the
+    //    graph is launched on the caller's stream instead.
+    if (!b->work_live) {
+        QD_CUDA(cudaStreamCreateWithFlags(&b->work, cudaStreamNonBlocking), "batch work stream");
+        QD_CUDA(cudaEventCreateWithFlags(&b->in_ev, cudaEventDisableTiming), "batch event");
+        QD_CUDA(cudaEventCreateWithFlags(&b->out_ev, cudaEventDisableTiming), "batch event");
+        b->work_live = true;
+    }
     if (!b->fork_live) {
         QD_CUDA(cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming), "fork event");
         b->fork_live = true;
     }
-    QD_CUDA(cudaEventRecord(b->fork_ev, b->main), "fork record");
+    // the descriptor upload was issued on the caller's stream
+    QD_CUDA(cudaEventRecord(b->in_ev, b->main), "batch order");
+    QD_CUDA(cudaStreamWaitEvent(b->work, b->in_ev, 0), "batch order");
+    if (use_graph) {
+        QD_CUDA(cudaStreamSynchronize(b->work), "batch pre-capture sync");
+        QD_CUDA(cudaStreamBeginCapture(b->work, cudaStreamCaptureModeRelaxed), "graph capture");
+    }
+    cudaStream_t ws = b->work;
+    QD_CUDA(cudaEventRecord(b->fork_ev, ws), "fork record");
     for (int k = 0; k < nstreams; ++k) QD_CUDA(cudaStreamWaitEvent(b->aux[k], b->fork_ev, 0), "fork wait");
     cudaError_t e = launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + off3), (int)small3.size(), 3,
-                                          maxd3, b->states, base, b->norms, b->main);
+                                          maxd3, b->states, base, b->norms, ws);
     if (e == cudaSuccess)
         e = launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + off5), (int)small5.size(), 5, maxd5,
-                                  b->states, base, b->norms, b->main);
+                                  b->states, base, b->norms, ws);
     if (e != cudaSuccess) {
         if (use_graph) {
             cudaGraph_t g;
-            cudaStreamEndCapture(b->main, &g);
+            if (cudaStreamEndCapture(ws, &g) == cudaSuccess && g) cudaGraphDestroy(g);
         }
         return cuda_fail(e, "small-circuit batch kernel");
     }
@@ -1103,20 +1128,23 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
         if (rc != QD_OK) {
             if (use_graph) {
                 cudaGraph_t g;
-                cudaStreamEndCapture(b->main, &g);
+                if (cudaStreamEndCapture(ws, &g) == cudaSuccess && g) cudaGraphDestroy(g);
             }
             return rc;
         }
     }
     for (int k = 0; k < nstreams; ++k) {
         QD_CUDA(cudaEventRecord(b->aux_ev[k], b->aux[k]), "join record");
-        QD_CUDA(cudaStreamWaitEvent(b->main, b->aux_ev[k], 0), "join wait");
+        QD_CUDA(cudaStreamWaitEvent(ws, b->aux_ev[k], 0), "join wait");
     }
     if (use_graph) {
-        QD_CUDA(cudaStreamEndCapture(b->main, &b->graph), "graph end capture");
+        QD_CUDA(cudaStreamEndCapture(ws, &b->graph), "graph end capture");
         QD_CUDA(cudaGraphInstantiate(&b->graph_exec, b->graph, 0), "graph instantiate");
         b->graph_live = true;
         QD_CUDA(cudaGraphLaunch(b->graph_exec, b->main), "graph launch");
+    } else {
+        QD_CUDA(cudaEventRecord(b->out_ev, ws), "batch order");
+        QD_CUDA(cudaStreamWaitEvent(b->main, b->out_ev, 0), "batch order");
     }
     return QD_OK;
 }
@@ -1184,6 +1212,7 @@ qd_status qd_batch_create(int32_t prec, void* stream, qd_batch** out) {
     if (!b) return fail(QD_ERR_OOM, "host allocation failed");
     b->prec = prec;
     b->main = reinterpret_cast<cudaStream_t>(stream);
+    b->work_live = false;
     b->fork_live = false;
     b->states = nullptr;
     b->states_cap = 0;
