@@ -250,6 +250,69 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------------
+def measure_large(qb, gen, torch, stream, amp_bytes_c64=8):
+    """18 qubits + 8 qutrits (1,719,926,784 amplitudes, 13.76 GB complex64), 200 gates:
+    one timed run per path; the per-gate kernel's HBM fraction on its dense gates."""
+    circ = gen.config2_circuit()
+    upd = circuit_updates(circ)
+    st = qb.State(circ.dims, prec=qb.QD_C64, stream=stream)
+    out = {"workload": "18 qubits + 8 qutrits (1,719,926,784 amplitudes), 200 gates, complex64",
+           "updates_per_circuit": upd}
+    peak, _ = measured_peaks()
+    for name, fuse in (("per_gate", False), ("fused", True)):
+        st.reset()
+        st.run(circ, fuse=fuse)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        st.reset()
+        e0.record(stream)
+        st.run(circ, fuse=fuse)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        out[name] = {"seconds": t, "value": upd / t, "unit": UNIT}
+    # per-launch roofline of the dense single-wire gates (uncontrolled Haar)
+    dense = [g for g in circ.gates if not g.controls][:12]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(dense) + 1)]
+    evs[0].record(stream)
+    for i, g in enumerate(dense):
+        st.apply(g)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    tt = sum(evs[i].elapsed_time(evs[i + 1]) for i in range(len(dense))) / 1e3
+    gbs = len(dense) * 2 * amp_bytes_c64 * circ.D / tt / 1e9
+    out["dense_gate_kernel"] = {"achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak, "launches": len(dense)}
+    st.close()
+    return out
+
+
+def measure_batched(qb, gen, torch, stream):
+    """8192 independent circuits (widths 4-12, dims {2,3,4,5}, depths 20-300), complex64,
+    captured in a CUDA graph: build+first run wall time, then relaunches timed with events."""
+    t0 = time.perf_counter()
+    circs = gen.config3_batch()
+    t_gen = time.perf_counter() - t0
+    upd = sum(circuit_updates(c) for c in circs)
+    b = qb.qd_batch_create(qb.QD_C64, stream.cuda_stream)
+    t0 = time.perf_counter()
+    qb.qd_batch_run(b, circs, use_graph=True)
+    qb.qd_batch_synchronize(b)
+    t_first = time.perf_counter() - t0
+    reps = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        qb.qd_batch_relaunch(b)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / reps
+    norms = qb.qd_batch_norms(b, len(circs))
+    qb.qd_batch_destroy(b)
+    return {"workload": "8192 circuits, widths 4-12, dims {2,3,4,5}, depths 20-300, complex64",
+            "circuits_per_s": len(circs) / t, "value": upd / t, "unit": UNIT, "seconds_per_batch": t,
+            "first_run_wall_s": t_first, "generate_s": t_gen, "max_norm_error": float(np.max(np.abs(norms - 1.0)))}
+
+
 def run_gpu(args):
     import torch
 
@@ -366,6 +429,17 @@ def run_gpu(args):
     e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
     e2e_value = world * upd / e2e_s
 
+    # ---- the other workloads of the path, each one timed run (rank 0 reports its own) ----
+    extra = {}
+    if not args.no_extra:
+        st.close()
+        torch.cuda.empty_cache()
+        extra["large_state"] = measure_large(qb, gen, torch, stream, amp_bytes_c64=8)
+        torch.cuda.empty_cache()
+        extra["batched"] = measure_batched(qb, gen, torch, stream)
+        torch.cuda.empty_cache()
+        st = qb.State(circ.dims, prec=prec, stream=stream, device=local)
+
     # ---- CPU oracle baseline (rank 0, N = 1 only) ----
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -401,6 +475,7 @@ def run_gpu(args):
             "gpu_launches": launches,
             "clocks": clocks,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
@@ -461,6 +536,7 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the large-state and batched measurements")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run only six dense single-wire gates (wires 0, 5, 10, 15, 19, 3) on the workload's "
                          "state, for a profiler capture of launches 4-6; prints nothing")

@@ -264,6 +264,69 @@ qd_status qd_batch_synchronize(qd_batch* b);
 qd_status qd_batch_destroy(qd_batch* b);
 
 /* ------------------------------------------------------------------------
+ * Serving.  Requests (circuits, each from |0...0>) arrive over time; a
+ * worker thread admits them in arrival order while the state bytes fit the
+ * server's device-memory budget and an execution slot is free, runs them
+ * concurrently with the requests already on the GPU (continuous batching:
+ * small states admitted in the same step share one one-CTA-per-circuit
+ * launch, larger ones run as fused circuit programs on their own streams),
+ * reduces each final state's squared norm, frees its memory (unless kept)
+ * and publishes the result with arrival / admission / completion times on
+ * the server's clock (seconds since creation).  A request's kernels depend
+ * only on its own circuit: its result is the same alone and in any mix.
+ * --------------------------------------------------------------------- */
+typedef struct qd_server qd_server;
+
+typedef struct qd_server_opts {
+    uint64_t hbm_budget_bytes; /* device memory for resident states, 0 = 8 GiB */
+    int32_t max_slots;         /* concurrent larger requests, 0 = 16 */
+    int32_t small_max_amps;    /* one-CTA path threshold, 0 = default */
+    int32_t max_group;         /* small requests per launch, 0 = 1024 */
+    int32_t reserved;
+    qd_fusion_opts fusion;     /* for larger requests (mode QD_FUSE_OFF = per gate) */
+} qd_server_opts;
+
+typedef struct qd_request_result {
+    uint64_t id;
+    int32_t status;          /* QD_OK or the error of this request */
+    int32_t kept;            /* state kept until qd_server_release */
+    int64_t num_amplitudes;
+    double norm;             /* squared norm of the final state */
+    double t_arrival, t_admit, t_done;
+} qd_request_result;
+
+/* Create a server (allocates the state budget, starts the worker thread). */
+qd_status qd_server_create(int32_t prec, const qd_server_opts* opts, qd_server** out);
+
+/* Submit a circuit now (copied before return).  keep_state: keep the final
+ * state on the device until qd_server_release.  QD_ERR_ARG for an invalid
+ * circuit, QD_ERR_UNSUPPORTED if its state exceeds the whole budget. */
+qd_status qd_server_submit(qd_server* s, const qd_circuit* c, int32_t keep_state, uint64_t* id_out);
+
+/* Submit a circuit that arrives at server time release_time (an open-loop
+ * load generator can submit a whole trace ahead of time). */
+qd_status qd_server_submit_at(qd_server* s, const qd_circuit* c, int32_t keep_state, double release_time,
+                              uint64_t* id_out);
+
+/* Move up to max finished results into out (oldest first); *n_out = count. */
+qd_status qd_server_poll(qd_server* s, qd_request_result* out, int32_t max, int32_t* n_out);
+
+/* Wait until every submitted request has finished (QD_ERR_TIMEOUT otherwise). */
+qd_status qd_server_drain(qd_server* s, double timeout_s);
+
+/* Current server time in seconds. */
+qd_status qd_server_now(qd_server* s, double* t);
+
+/* A finished, kept request's state as 2*D host doubles.  Synchronous. */
+qd_status qd_server_get_amplitudes(qd_server* s, uint64_t id, double* host_interleaved);
+
+/* Return a kept state's memory to the budget. */
+qd_status qd_server_release(qd_server* s, uint64_t id);
+
+/* Stop the worker after all submitted requests finished, free everything. */
+qd_status qd_server_destroy(qd_server* s);
+
+/* ------------------------------------------------------------------------
  * Readouts.  Sums run in binary64 with compensated (Neumaier) summation in
  * a fixed order, so results are deterministic for a given state size.
  * The paper defines no readout; these are the standard Born-rule

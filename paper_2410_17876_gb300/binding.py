@@ -64,6 +64,18 @@ class qd_batch_opts(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("fusion", qd_fusion_opts)]
 
 
+class qd_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_int32),
+                ("small_max_amps", ctypes.c_int32), ("max_group", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("fusion", qd_fusion_opts)]
+
+
+class qd_request_result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("kept", ctypes.c_int32),
+                ("num_amplitudes", ctypes.c_int64), ("norm", ctypes.c_double), ("t_arrival", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
 _SIGS = {
     "qd_state_create": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
     "qd_state_wrap": (ctypes.c_int32, [_vp, ctypes.c_size_t, _i32p, ctypes.c_int32, ctypes.c_int32, _vp,
@@ -99,6 +111,17 @@ _SIGS = {
     "qd_batch_norms": (ctypes.c_int32, [_vp, _f64p]),
     "qd_batch_synchronize": (ctypes.c_int32, [_vp]),
     "qd_batch_destroy": (ctypes.c_int32, [_vp]),
+    "qd_server_create": (ctypes.c_int32, [ctypes.c_int32, ctypes.POINTER(qd_server_opts), ctypes.POINTER(_vp)]),
+    "qd_server_submit": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_circuit), ctypes.c_int32,
+                                          ctypes.POINTER(ctypes.c_uint64)]),
+    "qd_server_submit_at": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_circuit), ctypes.c_int32, ctypes.c_double,
+                                             ctypes.POINTER(ctypes.c_uint64)]),
+    "qd_server_poll": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_request_result), ctypes.c_int32, _i32p]),
+    "qd_server_drain": (ctypes.c_int32, [_vp, ctypes.c_double]),
+    "qd_server_now": (ctypes.c_int32, [_vp, _f64p]),
+    "qd_server_get_amplitudes": (ctypes.c_int32, [_vp, ctypes.c_uint64, _f64p]),
+    "qd_server_release": (ctypes.c_int32, [_vp, ctypes.c_uint64]),
+    "qd_server_destroy": (ctypes.c_int32, [_vp]),
     "qd_apply_circuit": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_gate_desc), ctypes.c_int32, _f64p,
                                           ctypes.POINTER(qd_fusion_opts)]),
     "qd_plan_circuit": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(qd_gate_desc),
@@ -407,6 +430,71 @@ def qd_batch_synchronize(b: int) -> None:
 
 def qd_batch_destroy(b: int) -> None:
     _check(_lib.qd_batch_destroy(_vp(b)), "qd_batch_destroy")
+
+
+def _circuit_struct(c):
+    dims = _i32(c.dims)
+    descs, m = circuit_arrays(c)
+    cs = qd_circuit(len(dims), _p(dims, _i32p), len(c.gates), ctypes.cast(descs, ctypes.POINTER(qd_gate_desc)),
+                    _p(m, _f64p))
+    return cs, (dims, descs, m)
+
+
+def qd_server_create(prec: int = QD_C64, hbm_budget_bytes: int = 0, max_slots: int = 0, small_max_amps: int = 0,
+                     max_group: int = 0, fuse: bool = True, max_tile_amps: int = 0) -> int:
+    opts = qd_server_opts(int(hbm_budget_bytes), int(max_slots), int(small_max_amps), int(max_group), 0,
+                          qd_fusion_opts(QD_FUSE_TILE if fuse else QD_FUSE_OFF, int(max_tile_amps), 0, 0))
+    out = _vp()
+    _check(_lib.qd_server_create(int(prec), ctypes.byref(opts), ctypes.byref(out)), "qd_server_create")
+    return out.value
+
+
+def qd_server_submit(s: int, circuit, keep_state: bool = False) -> int:
+    cs, keep = _circuit_struct(circuit)
+    rid = ctypes.c_uint64()
+    _check(_lib.qd_server_submit(_vp(s), ctypes.byref(cs), 1 if keep_state else 0, ctypes.byref(rid)),
+           "qd_server_submit")
+    return rid.value
+
+
+def qd_server_submit_at(s: int, circuit, release_time: float, keep_state: bool = False) -> int:
+    cs, keep = _circuit_struct(circuit)
+    rid = ctypes.c_uint64()
+    _check(_lib.qd_server_submit_at(_vp(s), ctypes.byref(cs), 1 if keep_state else 0, float(release_time),
+                                    ctypes.byref(rid)), "qd_server_submit_at")
+    return rid.value
+
+
+def qd_server_poll(s: int, max_results: int = 4096):
+    buf = (qd_request_result * max(1, max_results))()
+    n = ctypes.c_int32()
+    _check(_lib.qd_server_poll(_vp(s), buf, int(max_results), ctypes.byref(n)), "qd_server_poll")
+    return [{f: getattr(buf[i], f) for f, _ in qd_request_result._fields_} for i in range(n.value)]
+
+
+def qd_server_drain(s: int, timeout_s: float = 600.0) -> None:
+    _check(_lib.qd_server_drain(_vp(s), float(timeout_s)), "qd_server_drain")
+
+
+def qd_server_now(s: int) -> float:
+    t = ctypes.c_double()
+    _check(_lib.qd_server_now(_vp(s), ctypes.byref(t)), "qd_server_now")
+    return t.value
+
+
+def qd_server_get_amplitudes(s: int, rid: int, num_amplitudes: int) -> np.ndarray:
+    out = np.empty(int(num_amplitudes), dtype=np.complex128)
+    _check(_lib.qd_server_get_amplitudes(_vp(s), int(rid), _p(out.view(np.float64), _f64p)),
+           "qd_server_get_amplitudes")
+    return out
+
+
+def qd_server_release(s: int, rid: int) -> None:
+    _check(_lib.qd_server_release(_vp(s), int(rid)), "qd_server_release")
+
+
+def qd_server_destroy(s: int) -> None:
+    _check(_lib.qd_server_destroy(_vp(s)), "qd_server_destroy")
 
 
 # --- convenience ----------------------------------------------------------------------------------

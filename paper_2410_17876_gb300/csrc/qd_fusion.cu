@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "qd_internal.cuh"
+#include "qd_program.h"
 #include "qd_runtime.h"
 
 namespace qd {
@@ -99,16 +100,6 @@ struct FusedArgs {
     uint32_t free_d[kMaxWires];
     uint64_t free_b[kMaxWires];
     const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
-};
-
-// One small circuit of a batch (whole state in one CTA).
-struct SmallTask {
-    uint64_t psi_off;     // byte offset of the state in the batch's state arena
-    uint64_t gate_off;    // byte offset of its FGate descriptors in the descriptor arena
-    uint32_t D;           // amplitudes
-    uint32_t ngates;
-    uint32_t norm_index;  // slot of its squared norm
-    uint32_t pad_;
 };
 
 namespace {
@@ -433,6 +424,8 @@ __global__ void __launch_bounds__(256, 2) k_batch_small(const SmallTask* tasks, 
     }
 }
 
+}  // namespace
+
 template <typename R>
 cudaError_t launch_batch_small(const SmallTask* tasks, int ntasks, int dmax, uint32_t max_d, char* state_base,
                                const char* desc_base, double* norms, cudaStream_t s) {
@@ -457,21 +450,9 @@ cudaError_t launch_batch_small(const SmallTask* tasks, int ntasks, int dmax, uin
     return cudaGetLastError();
 }
 
-}  // namespace
-
 // ---------------------------------------------------------------------------
 // Planner
 // ---------------------------------------------------------------------------
-struct HGate {
-    int k, nc, P;
-    int wires[QD_MAX_GATE_WIRES];
-    int cw[QD_MAX_CONTROLS], cv[QD_MAX_CONTROLS];
-    const double* U;
-    Plan plan;
-    bool diag, fusable;
-    uint64_t tmask, cmask;
-};
-
 struct PassPlan {
     bool tile;
     std::vector<int> gates;
@@ -479,17 +460,10 @@ struct PassPlan {
     int64_t T;
 };
 
-struct FuseCfg {
-    int mode;
-    int64_t Tmax;
-    int min_gates;
-    int64_t min_row;
-};
-
 // Largest tile that fits the shared memory of one CTA (tile + row table).
-static int64_t tile_limit(int32_t prec) { return prec == QD_C64 ? 16384 : 8192; }
+int64_t tile_limit(int32_t prec) { return prec == QD_C64 ? 16384 : 8192; }
 
-static FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
+FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     FuseCfg c;
     c.mode = o ? o->mode : QD_FUSE_OFF;
     c.Tmax = (o && o->max_tile_amps > 0) ? o->max_tile_amps : (prec == QD_C64 ? 8192 : 4096);
@@ -501,7 +475,7 @@ static FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     return c;
 }
 
-static qd_status load_gates(const Layout& L, int32_t prec, const qd_gate_desc* gates, int32_t n,
+qd_status load_gates(const Layout& L, int32_t prec, const qd_gate_desc* gates, int32_t n,
                             const double* matrices, std::vector<HGate>& out) {
     if (n < 0) return fail(QD_ERR_ARG, "negative gate count");
     if (n > 0 && (!gates || !matrices)) return fail(QD_ERR_ARG, "gates or matrices is NULL");
@@ -712,23 +686,6 @@ static void build_fgate(const TileGeom& geo, const HGate& h, FGate<R>& f) {
 // issues the launches, so many programs can share one upload and be issued
 // on several streams or inside a CUDA graph capture.
 // ---------------------------------------------------------------------------
-using Op = std::function<cudaError_t(cudaStream_t, const char*)>;
-
-struct Program {
-    std::vector<char> desc;
-    std::vector<Op> ops;
-    size_t reserve(size_t n) {
-        const size_t o = (desc.size() + 255) & ~(size_t)255;
-        desc.resize(o + n);
-        return o;
-    }
-    size_t put(const void* p, size_t n) {
-        const size_t o = reserve(n);
-        std::memcpy(desc.data() + o, p, n);
-        return o;
-    }
-};
-
 qd_status Arena::upload(const void* bytes, size_t n, cudaStream_t s) {
     if (n == 0) return QD_OK;
     if (n > cap) {
@@ -833,7 +790,7 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog) {
 // Ops of a whole circuit on the state at psi (layout L): optional reset to
 // |0...0>, then the planned passes in order.
 template <typename R>
-static void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
+void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
                           bool reset_first, Program& prog) {
     using T2 = typename Cplx<R>::T2;
     if (reset_first) {
@@ -883,7 +840,7 @@ static void build_program(const Layout& L, void* psi, const std::vector<HGate>& 
     }
 }
 
-static qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
+qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
     for (const Op& op : prog.ops) {
         cudaError_t e = op(s, base);
         if (e != cudaSuccess) return cuda_fail(e, "circuit kernel launch");
@@ -891,13 +848,46 @@ static qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
     return QD_OK;
 }
 
-static qd_status check_cfg(const FuseCfg& cfg, int32_t prec) {
+qd_status check_cfg(const FuseCfg& cfg, int32_t prec) {
     if (cfg.mode != QD_FUSE_OFF && cfg.mode != QD_FUSE_TILE) return fail(QD_ERR_ARG, "unknown fusion mode");
     if (cfg.mode == QD_FUSE_TILE && cfg.Tmax > tile_limit(prec))
         return fail(QD_ERR_UNSUPPORTED, "tile of %lld amplitudes exceeds shared memory (limit %lld)",
                     (long long)cfg.Tmax, (long long)tile_limit(prec));
     return QD_OK;
 }
+
+bool small_eligible(const Layout& L, const std::vector<HGate>& G, int64_t small_max, int* dmax) {
+    if (L.D > small_max || G.empty()) return false;
+    int dm = 2;
+    for (const HGate& h : G) {
+        if (!h.fusable) return false;
+        dm = h.plan.d > dm ? h.plan.d : dm;
+    }
+    if (dmax) *dmax = dm;
+    return true;
+}
+
+template <typename R>
+size_t put_small_gates(const Layout& L, const std::vector<HGate>& G, Program& prog) {
+    TileGeom geo;
+    tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo);
+    const size_t off = prog.reserve(sizeof(FGate<R>) * G.size());
+    for (size_t g = 0; g < G.size(); ++g)
+        build_fgate<R>(geo, G[g], reinterpret_cast<FGate<R>*>(prog.desc.data() + off)[g]);
+    return off;
+}
+
+template size_t put_small_gates<float>(const Layout&, const std::vector<HGate>&, Program&);
+template size_t put_small_gates<double>(const Layout&, const std::vector<HGate>&, Program&);
+
+template void build_program<float>(const Layout&, void*, const std::vector<HGate>&, const FuseCfg&, bool,
+                                   Program&);
+template void build_program<double>(const Layout&, void*, const std::vector<HGate>&, const FuseCfg&, bool,
+                                    Program&);
+template cudaError_t launch_batch_small<float>(const SmallTask*, int, int, uint32_t, char*, const char*, double*,
+                                               cudaStream_t);
+template cudaError_t launch_batch_small<double>(const SmallTask*, int, int, uint32_t, char*, const char*, double*,
+                                                cudaStream_t);
 
 }  // namespace qd
 
