@@ -313,6 +313,78 @@ def measure_batched(qb, gen, torch, stream):
             "first_run_wall_s": t_first, "generate_s": t_gen, "max_norm_error": float(np.max(np.abs(norms - 1.0)))}
 
 
+def measure_serving(qb, gen, torch, duration=3.0, plain_budget_s=6.0, oracle_budget_s=20.0):
+    """Open-loop serving: Poisson arrivals (mean 2000/s) for ``duration`` seconds of circuits
+    with widths 4-16, dims {2,3,4}, 16 <= D <= 1.6e7, depths 50-500, complex64 states with
+    FP64 norms.  All requests are submitted ahead with their arrival times on the server
+    clock.  p50/p99 latency = done - arrival.  1% of the requests (those with D <= 2^20)
+    are kept and compared with the FP64 oracle.  The plain path -- one circuit at a time,
+    complex128, one kernel per gate, state created and destroyed per request -- is timed
+    on the same circuits in arrival order for about ``plain_budget_s`` seconds."""
+    import oracle
+
+    trace = gen.config4_trace(duration=duration)
+    circs = [c for _, c in trace]
+    arr = np.array([t for t, _ in trace])
+    upd = np.array([circuit_updates(c) for c in circs], dtype=np.float64)
+    for c in circs:
+        qb.circuit_arrays(c)
+    rng = np.random.Generator(np.random.PCG64(44))
+    eligible = [i for i, c in enumerate(circs) if c.D <= (1 << 20)]
+    sample = sorted(int(i) for i in rng.permutation(eligible)[:max(1, len(circs) // 100)])
+    keep = set(sample)
+    srv = qb.qd_server_create(qb.QD_C64, hbm_budget_bytes=48 << 30, max_slots=32)
+    base = qb.qd_server_now(srv) + 1.0 + 4e-4 * len(circs)
+    ids = [qb.qd_server_submit_at(srv, c, base + float(t), keep_state=(i in keep)) for i, (c, t) in
+           enumerate(zip(circs, arr))]
+    late = qb.qd_server_now(srv) > base
+    qb.qd_server_drain(srv, 600)
+    res = {}
+    while len(res) < len(ids):
+        for r in qb.qd_server_poll(srv):
+            res[r["id"]] = r
+    lat = np.array([res[i]["t_done"] - res[i]["t_arrival"] for i in ids])
+    done = np.array([res[i]["t_done"] for i in ids])
+    ok = all(res[i]["status"] == 0 for i in ids)
+    span = float(done.max() - (base + arr.min()))
+    errs, infs = [], []
+    t0 = time.perf_counter()
+    for i in sample:
+        if time.perf_counter() - t0 > oracle_budget_s:
+            break
+        got = qb.qd_server_get_amplitudes(srv, ids[i], circs[i].D)
+        ref = oracle.run_circuit(circs[i], nthreads=oracle.max_threads())
+        errs.append(float(np.max(np.abs(got - ref))))
+        ov = np.vdot(ref, got)
+        infs.append(float(1 - abs(ov) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)))
+    qb.qd_server_destroy(srv)
+    # plain path: complex128, one circuit at a time, one kernel per gate
+    n_plain, t_plain = 0, 0.0
+    t0 = time.perf_counter()
+    for c in circs:
+        h = qb.qd_state_create(c.dims, qb.QD_C128)
+        qb.qd_apply_circuit(h, c, qb.QD_FUSE_OFF)
+        qb.qd_norm(h)
+        qb.qd_state_destroy(h)
+        n_plain += 1
+        t_plain = time.perf_counter() - t0
+        if t_plain > plain_budget_s:
+            break
+    served_cps = len(circs) / span
+    plain_cps = n_plain / t_plain
+    return {"workload": f"Poisson arrivals at 2000/s for {duration:g} s ({len(circs)} requests), widths 4-16, "
+                        "dims {2,3,4}, 16 <= D <= 1.6e7, depths 50-500, complex64 with FP64 norms",
+            "circuits_per_s": served_cps, "p50_latency_s": float(np.percentile(lat, 50)),
+            "p99_latency_s": float(np.percentile(lat, 99)), "offered_updates_per_s": float(upd.sum() / duration),
+            "served_updates_per_s": float(upd.sum() / span), "all_ok": ok, "submission_late": bool(late),
+            "oracle_sample": {"requests": len(errs), "max_abs_err": max(errs) if errs else None,
+                              "max_infidelity": max(infs) if infs else None,
+                              "rule": "1% of requests drawn among those with D <= 2^20"},
+            "plain_c128_one_at_a_time": {"circuits_per_s": plain_cps, "requests_timed": n_plain,
+                                         "seconds": t_plain},
+            "served_over_plain": served_cps / plain_cps}
+
+
 def run_gpu(args):
     import torch
 
@@ -437,6 +509,8 @@ def run_gpu(args):
         extra["large_state"] = measure_large(qb, gen, torch, stream, amp_bytes_c64=8)
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(qb, gen, torch, stream)
+        torch.cuda.empty_cache()
+        extra["serving"] = measure_serving(qb, gen, torch)
         torch.cuda.empty_cache()
         st = qb.State(circ.dims, prec=prec, stream=stream, device=local)
 

@@ -315,34 +315,47 @@ def qd_selftest_host(trials: int = 200) -> None:
     _check(_lib.qd_selftest_host(int(trials)), "qd_selftest_host")
 
 
+_DESC_DTYPE = np.dtype([("n_wires", np.int32), ("n_ctrl", np.int32), ("wires", np.int32, QD_MAX_GATE_WIRES),
+                        ("ctrl_wires", np.int32, QD_MAX_CONTROLS), ("ctrl_vals", np.int32, QD_MAX_CONTROLS),
+                        ("matrix_offset", np.int64)], align=True)
+assert _DESC_DTYPE.itemsize == ctypes.sizeof(qd_gate_desc)
+
+
 def circuit_arrays(circuit):
-    """(qd_gate_desc array, concatenated matrices) for a circuit; cached on the circuit object."""
+    """(qd_gate_desc array, concatenated matrices) for a circuit; cached on the circuit object.
+
+    The descriptors are a numpy structured array with the C layout of
+    qd_gate_desc, so building them is a handful of vectorised assignments.
+    """
     cache = getattr(circuit, "_qd_arrays", None)
     if cache is not None and cache[0] == len(circuit.gates):
         return cache[1], cache[2]
-    n = len(circuit.gates)
-    descs = (qd_gate_desc * max(1, n))()
-    mats = []
-    off = 0
-    for i, g in enumerate(circuit.gates):
-        d = descs[i]
-        d.n_wires = len(g.wires)
-        d.n_ctrl = len(g.controls)
-        for m, w in enumerate(g.wires):
-            d.wires[m] = w
-        for m, (c, v) in enumerate(zip(g.controls, g.values)):
-            d.ctrl_wires[m] = c
-            d.ctrl_vals[m] = v
-        d.matrix_offset = off
-        U = np.ascontiguousarray(g.U, dtype=np.complex128).reshape(-1)
-        mats.append(U)
-        off += U.size
-    m = np.ascontiguousarray(np.concatenate(mats) if mats else np.zeros(1, np.complex128)).view(np.float64)
+    gates = circuit.gates
+    n = len(gates)
+    d = np.zeros(max(1, n), dtype=_DESC_DTYPE)
+    sizes = np.fromiter((g.U.size for g in gates), dtype=np.int64, count=n)
+    if n:
+        d["n_wires"][:n] = [len(g.wires) for g in gates]
+        d["n_ctrl"][:n] = [len(g.controls) for g in gates]
+        for i, g in enumerate(gates):
+            k = len(g.wires)
+            d["wires"][i, :k] = g.wires
+            if g.controls:
+                m = len(g.controls)
+                d["ctrl_wires"][i, :m] = g.controls
+                d["ctrl_vals"][i, :m] = g.values
+        d["matrix_offset"][:n] = np.concatenate(([0], np.cumsum(sizes)[:-1]))
+        m = np.concatenate([g.U.reshape(-1) for g in gates]).astype(np.complex128, copy=False)
+    else:
+        m = np.zeros(1, np.complex128)
+    mats = np.ascontiguousarray(m).view(np.float64)
+    descs = d.ctypes.data_as(ctypes.POINTER(qd_gate_desc))
+    descs._keep = d  # the pointer keeps its buffer alive
     try:
-        circuit._qd_arrays = (n, descs, m)
+        circuit._qd_arrays = (n, descs, mats)
     except AttributeError:
         pass
-    return descs, m
+    return descs, mats
 
 
 def _opts(mode, max_tile_amps=0, min_gates=0, min_row=0):
@@ -392,7 +405,7 @@ def qd_batch_run(b: int, circuits, small_max_amps=0, n_streams=0, use_graph=Fals
         arr[i].n_wires = len(dims)
         arr[i].dims = _p(dims, _i32p)
         arr[i].n_gates = len(c.gates)
-        arr[i].gates = ctypes.cast(descs, ctypes.POINTER(qd_gate_desc))
+        arr[i].gates = descs
         arr[i].matrices = _p(m, _f64p)
     opts = qd_batch_opts(int(small_max_amps), int(n_streams), 1 if use_graph else 0, 0,
                          qd_fusion_opts(QD_FUSE_TILE if fuse else QD_FUSE_OFF, int(max_tile_amps), int(min_gates),
@@ -435,8 +448,7 @@ def qd_batch_destroy(b: int) -> None:
 def _circuit_struct(c):
     dims = _i32(c.dims)
     descs, m = circuit_arrays(c)
-    cs = qd_circuit(len(dims), _p(dims, _i32p), len(c.gates), ctypes.cast(descs, ctypes.POINTER(qd_gate_desc)),
-                    _p(m, _f64p))
+    cs = qd_circuit(len(dims), _p(dims, _i32p), len(c.gates), descs, _p(m, _f64p))
     return cs, (dims, descs, m)
 
 
