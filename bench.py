@@ -604,7 +604,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
-    ap.add_argument("--fuse", choices=["tile", "off"], default="tile",
+    ap.add_argument("--fuse", choices=["tile", "off"], default="off",
                     help="tile: consecutive gates share one shared-memory pass over the state; off: one pass per gate")
     ap.add_argument("--tile", type=int, default=0, help="amplitudes per fused tile (0 = library default)")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
