@@ -184,6 +184,10 @@ typedef struct qd_fusion_opts {
     int32_t max_tile_amps; /* amplitudes per tile, 0 = default (8192 complex64, 4096 complex128) */
     int32_t min_gates;     /* passes with fewer gates run gate by gate; 0 = default (2) */
     int32_t min_row;       /* contiguous amplitudes per tile row, 0 = default (16 c64, 8 c128) */
+    int32_t block_dim;     /* inside a pass, runs of gates on a few wires are composed (binary64,
+                              on the host) into one P x P block with P <= block_dim (at most 16);
+                              0 = default (16), 1 = no composition */
+    int32_t reserved;
 } qd_fusion_opts;
 
 /* Apply n_gates gates in order.  Each gate is validated as in

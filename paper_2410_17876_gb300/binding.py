@@ -51,7 +51,7 @@ class qd_gate_desc(ctypes.Structure):
 
 class qd_fusion_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_tile_amps", ctypes.c_int32), ("min_gates", ctypes.c_int32),
-                ("min_row", ctypes.c_int32)]
+                ("min_row", ctypes.c_int32), ("block_dim", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class qd_circuit(ctypes.Structure):
@@ -358,19 +358,21 @@ def circuit_arrays(circuit):
     return descs, mats
 
 
-def _opts(mode, max_tile_amps=0, min_gates=0, min_row=0):
+def _opts(mode, max_tile_amps=0, min_gates=0, min_row=0, block_dim=0):
     if mode is None:
         return None
-    return ctypes.byref(qd_fusion_opts(int(mode), int(max_tile_amps), int(min_gates), int(min_row)))
+    return ctypes.byref(qd_fusion_opts(int(mode), int(max_tile_amps), int(min_gates), int(min_row), int(block_dim),
+                                       0))
 
 
-def qd_apply_circuit(st: int, circuit, mode=QD_FUSE_OFF, max_tile_amps=0, min_gates=0, min_row=0) -> None:
+def qd_apply_circuit(st: int, circuit, mode=QD_FUSE_OFF, max_tile_amps=0, min_gates=0, min_row=0,
+                     block_dim=0) -> None:
     descs, m = circuit_arrays(circuit)
     _check(_lib.qd_apply_circuit(_vp(st), descs, len(circuit.gates), _p(m, _f64p),
-                                 _opts(mode, max_tile_amps, min_gates, min_row)), "qd_apply_circuit")
+                                 _opts(mode, max_tile_amps, min_gates, min_row, block_dim)), "qd_apply_circuit")
 
 
-def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min_gates=0, min_row=0):
+def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min_gates=0, min_row=0, block_dim=0):
     """(exec_order, pass_of, pass_tile_amps[:n_passes]) of the circuit's execution plan."""
     d = _i32(dims)
     descs, m = circuit_arrays(circuit)
@@ -380,7 +382,7 @@ def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min
     tiles = np.zeros(max(1, n), np.int64)
     npass = ctypes.c_int32()
     _check(_lib.qd_plan_circuit(_p(d, _i32p), len(d), prec, descs, n, _p(m, _f64p),
-                                _opts(mode, max_tile_amps, min_gates, min_row), _p(order, _i32p),
+                                _opts(mode, max_tile_amps, min_gates, min_row, block_dim), _p(order, _i32p),
                                 _p(pass_of, _i32p), tiles.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                 ctypes.byref(npass)), "qd_plan_circuit")
     return order[:n], pass_of[:n], tiles[:npass.value]
@@ -393,7 +395,7 @@ def qd_batch_create(prec: int = QD_C64, stream: int = 0) -> int:
 
 
 def qd_batch_run(b: int, circuits, small_max_amps=0, n_streams=0, use_graph=False, fuse=True,
-                 max_tile_amps=0, min_gates=0, min_row=0) -> None:
+                 max_tile_amps=0, min_gates=0, min_row=0, block_dim=0) -> None:
     """Run independent circuits (each from |0...0>) as one batch; asynchronous."""
     n = len(circuits)
     arr = (qd_circuit * max(1, n))()
@@ -409,7 +411,7 @@ def qd_batch_run(b: int, circuits, small_max_amps=0, n_streams=0, use_graph=Fals
         arr[i].matrices = _p(m, _f64p)
     opts = qd_batch_opts(int(small_max_amps), int(n_streams), 1 if use_graph else 0, 0,
                          qd_fusion_opts(QD_FUSE_TILE if fuse else QD_FUSE_OFF, int(max_tile_amps), int(min_gates),
-                                        int(min_row)))
+                                        int(min_row), int(block_dim), 0))
     _check(_lib.qd_batch_run(_vp(b), arr, n, ctypes.byref(opts)), "qd_batch_run")
 
 
@@ -453,9 +455,10 @@ def _circuit_struct(c):
 
 
 def qd_server_create(prec: int = QD_C64, hbm_budget_bytes: int = 0, max_slots: int = 0, small_max_amps: int = 0,
-                     max_group: int = 0, fuse: bool = True, max_tile_amps: int = 0) -> int:
+                     max_group: int = 0, fuse: bool = True, max_tile_amps: int = 0, block_dim: int = 0) -> int:
     opts = qd_server_opts(int(hbm_budget_bytes), int(max_slots), int(small_max_amps), int(max_group), 0,
-                          qd_fusion_opts(QD_FUSE_TILE if fuse else QD_FUSE_OFF, int(max_tile_amps), 0, 0))
+                          qd_fusion_opts(QD_FUSE_TILE if fuse else QD_FUSE_OFF, int(max_tile_amps), 0, 0,
+                                         int(block_dim), 0))
     out = _vp()
     _check(_lib.qd_server_create(int(prec), ctypes.byref(opts), ctypes.byref(out)), "qd_server_create")
     return out.value

@@ -67,28 +67,50 @@ struct __align__(16) LocalMap {
     }
 };
 
-// One gate of a pass.  Built on the host, copied to shared memory by every CTA.
-template <typename R>
+constexpr int kMaxBlock = 16;       // largest composed block (product of its wires' dimensions)
+constexpr int kMaxChunkGates = 64;  // gate records per chunk
+constexpr int kPoolEntries = 2048;  // matrix entries per chunk (complex, in the state's precision)
+
+// One gate or composed block inside a chunk.  Built on the host, staged in
+// shared memory by every CTA that applies the chunk.
+//   single = 1: one wire of dimension P = d (in-tile controls inserted in map;
+//               lst/step give the one-division enumeration when m == 1);
+//   single = 0: a dense / diagonal / monomial P x P block over several wires,
+//               members of a class at base + off[r].
 struct __align__(16) FGate {
-    using T2 = typename Cplx<R>::T2;
-    T2 U[kMaxFusedD * kMaxFusedD];
     LocalMap map;
-    uint32_t nclasses;  // classes in a tile
-    uint32_t lst;       // local stride of the target
-    uint32_t step;      // lst * d (class base step when the target is the only inserted wire)
-    uint32_t pad_;
-    uint8_t d, kind, lmask, smask, pure, n_out, pad2_[2];
-    uint8_t perm[8];
-    uint8_t out_w[kMaxTileCtrl + 1];  // controls outside S: global wire, value
-    uint8_t out_v[kMaxTileCtrl + 1];
+    uint32_t nclasses;
+    uint32_t lst, step;
+    uint32_t u_off;  // matrix: entries [u_off, u_off + PP * PP) of the chunk pool, row-major, PP columns
+    uint8_t P, PP, kind, single;
+    uint8_t n_out, pure, pad0[2];
+    uint16_t lmask, smask;
+    uint8_t pad1[4];
+    uint8_t perm[kMaxBlock];
+    uint8_t out_w[8], out_v[8];  // controls outside the tile: global wire, value
+    uint16_t off[kMaxBlock];
 };
+
+// Chunk header; the chunk is [header][ngates FGate][npool matrix entries], 16-byte aligned.
+struct __align__(16) ChunkHdr {
+    uint32_t ngates, npool, bytes, pad;
+};
+
+template <typename R>
+__host__ __device__ inline size_t chunk_bytes(uint32_t ngates, uint32_t npool) {
+    return sizeof(ChunkHdr) + sizeof(FGate) * (size_t)ngates + sizeof(typename Cplx<R>::T2) * (size_t)npool;
+}
+template <typename R>
+__host__ __device__ inline size_t chunk_smem_max() {
+    return (chunk_bytes<R>(kMaxChunkGates, kPoolEntries) + 15) & ~(size_t)15;
+}
 
 template <typename R>
 struct FusedArgs {
     using T2 = typename Cplx<R>::T2;
     T2* psi;
-    const FGate<R>* gates;
-    int32_t ngates;
+    const char* chunks;  // first chunk (device)
+    int32_t nchunks;
     uint32_t T;      // tile amplitudes
     uint32_t bL;     // contiguous run (row) length
     uint32_t rows;   // rows per tile
@@ -101,6 +123,7 @@ struct FusedArgs {
     uint64_t free_b[kMaxWires];
     const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
 };
+
 
 namespace {
 
@@ -157,12 +180,12 @@ __device__ __forceinline__ Arr<T2, DT> class_math(const Arr<T2, DT> x, int kind,
 
 // Apply one single-wire gate of dimension DT to the tile in shared memory.
 // Matrix, permutation and masks are loop invariants read once per gate from
-// the shared-memory descriptor.  With no control inside the tile (m == 1) a
-// class index c = hi * lst + lo has base hi * lst * d + lo (one division);
-// complex64 with an even local stride processes two adjacent classes with
-// 16-byte accesses.
+// the staged chunk.  With no control inside the tile (m == 1) a class index
+// c = hi * lst + lo has base hi * lst * d + lo (one division); complex64 with
+// an even local stride processes two adjacent classes with 16-byte accesses.
 template <typename R, int DT>
-__device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGate<R>& G) {
+__device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGate& G,
+                                          const typename Cplx<R>::T2* pool) {
     using T2 = typename Cplx<R>::T2;
     const int kind = G.kind;
     const uint32_t lmask = G.lmask, smask = G.smask, lst = G.lst, nc = G.nclasses;
@@ -171,8 +194,11 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
 #pragma unroll
     for (int r = 0; r < DT; ++r) perm.v[r] = G.perm[r];
     Arr<T2, DT * DT> u;
+    const T2* gu = pool + G.u_off;
 #pragma unroll
-    for (int i = 0; i < DT * DT; ++i) u.v[i] = G.U[i];
+    for (int r = 0; r < DT; ++r)
+#pragma unroll
+        for (int k = 0; k < DT; ++k) u.v[r * DT + k] = gu[r * G.PP + k];
     if (G.map.m == 1) {
         const FastDiv32 f = G.map.seg[0];
         const uint32_t step = G.step;
@@ -250,28 +276,116 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
     }
 }
 
-// Shared memory of a CTA: [pass descriptors][row offsets][tile], each 16-byte aligned.
-template <typename R>
-__host__ __device__ inline size_t fused_desc_bytes(int ngates) {
-    return sizeof(FGate<R>) * (size_t)ngates;
+// Apply one composed block (P <= PP) to the tile.  A class's P members are
+// gathered into registers (padded rows are masked out), each output row is
+// accumulated from the matrix row in the staged pool (every thread reads the
+// same entries: broadcast), and stored at once -- all inputs are in
+// registers before the first store.
+template <typename R, int PP>
+__device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGate& G,
+                                           const typename Cplx<R>::T2* pool) {
+    using T2 = typename Cplx<R>::T2;
+    const uint32_t nc = G.nclasses, lmask = G.lmask, smask = G.smask;
+    const int kind = G.kind;
+    const bool pure = G.pure != 0;
+    uint32_t off[PP];
+#pragma unroll
+    for (int r = 0; r < PP; ++r) off[r] = G.off[r];
+    const T2* M = pool + G.u_off;
+    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+        const uint32_t b = G.map.map(c);
+        T2 x[PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            x[k].x = 0;
+            x[k].y = 0;
+            if (lmask >> k & 1u) x[k] = tile[b + off[k]];
+        }
+        if (kind == kDense) {
+#pragma unroll
+            for (int r = 0; r < PP; ++r) {
+                if (!(smask >> r & 1u)) continue;
+                const T2* Mr = M + r * PP;
+                T2 acc = fcmul(Mr[0], x[0]);
+#pragma unroll
+                for (int k = 1; k < PP; ++k) fcmac(acc, Mr[k], x[k]);
+                tile[b + off[r]] = acc;
+            }
+        } else if (kind == kDiag) {
+#pragma unroll
+            for (int r = 0; r < PP; ++r)
+                if (smask >> r & 1u) tile[b + off[r]] = fcmul(M[r * PP + r], x[r]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < PP; ++r) {
+                if (!(smask >> r & 1u)) continue;
+                const int src = G.perm[r];
+                T2 v = x[0];
+#pragma unroll
+                for (int k = 1; k < PP; ++k)
+                    if (src == k) v = x[k];
+                tile[b + off[r]] = pure ? v : fcmul(M[r * PP + src], v);
+            }
+        }
+    }
 }
+
+// Apply a list of chunks to a tile in shared memory.  stage: shared memory
+// for one chunk; odig: digits of the wires outside the tile (fused passes).
+template <typename R, int DMAX>
+__device__ __forceinline__ void apply_chunks(typename Cplx<R>::T2* tile, const char* chunk, int nchunks,
+                                             unsigned char* stage, const int32_t* odig) {
+    using T2 = typename Cplx<R>::T2;
+    for (int ci = 0; ci < nchunks; ++ci) {
+        const ChunkHdr h = *reinterpret_cast<const ChunkHdr*>(chunk);
+        __syncthreads();  // the previous chunk is done with the stage
+        {
+            const uint4* src = reinterpret_cast<const uint4*>(chunk);
+            uint4* dst = reinterpret_cast<uint4*>(stage);
+            for (uint32_t i = threadIdx.x; i < h.bytes / 16; i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        const FGate* gates = reinterpret_cast<const FGate*>(stage + sizeof(ChunkHdr));
+        const T2* pool = reinterpret_cast<const T2*>(stage + sizeof(ChunkHdr) + sizeof(FGate) * h.ngates);
+        for (uint32_t gi = 0; gi < h.ngates; ++gi) {
+            const FGate& G = gates[gi];
+            if (odig) {
+                bool ok = true;
+                for (int c = 0; c < G.n_out; ++c) ok = ok && (odig[G.out_w[c]] == (int32_t)G.out_v[c]);
+                if (!ok) continue;  // uniform across the CTA
+            }
+            if (G.single) {
+                if (G.P == 2) tile_gate<R, 2>(tile, G, pool);
+                else if (DMAX == 3 || G.P == 3) tile_gate<R, 3>(tile, G, pool);
+                else if (G.P == 4) tile_gate<R, (DMAX > 3 ? 4 : 3)>(tile, G, pool);
+                else tile_gate<R, DMAX>(tile, G, pool);
+            } else {
+                switch (G.PP) {
+                    case 4: block_gate<R, 4>(tile, G, pool); break;
+                    case 6: block_gate<R, 6>(tile, G, pool); break;
+                    case 8: block_gate<R, 8>(tile, G, pool); break;
+                    case 9: block_gate<R, 9>(tile, G, pool); break;
+                    case 12: block_gate<R, 12>(tile, G, pool); break;
+                    default: block_gate<R, 16>(tile, G, pool); break;
+                }
+            }
+            __syncthreads();
+        }
+        chunk += h.bytes;
+    }
+}
+
 __host__ __device__ inline size_t fused_rows_bytes(uint32_t rows) { return ((size_t)rows * 8 + 15) & ~(size_t)15; }
 
 template <typename R, int DMAX>
 __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ FusedArgs<R> a) {
     using T2 = typename Cplx<R>::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FGate<R>* sg = reinterpret_cast<FGate<R>*>(smem_raw);
-    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + fused_desc_bytes<R>(a.ngates));
-    T2* tile = reinterpret_cast<T2*>(smem_raw + fused_desc_bytes<R>(a.ngates) + fused_rows_bytes(a.rows));
+    unsigned char* stage = smem_raw;
+    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + chunk_smem_max<R>());
+    T2* tile = reinterpret_cast<T2*>(smem_raw + chunk_smem_max<R>() + fused_rows_bytes(a.rows));
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(a.gates);
-        uint4* dst = reinterpret_cast<uint4*>(sg);
-        const uint32_t n16 = (uint32_t)(fused_desc_bytes<R>(a.ngates) / 16);
-        for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
-    }
     for (uint32_t r = threadIdx.x; r < a.rows; r += blockDim.x) srow[r] = a.rowoff[r];
     if (threadIdx.x == 0) {
         uint64_t rem = blockIdx.x, base = 0;
@@ -298,18 +412,8 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
             tile[e] = g[srow[r] + (e - r * a.bL)];
         }
     }
+    apply_chunks<R, DMAX>(tile, a.chunks, a.nchunks, stage, odig);
     __syncthreads();
-    for (int gi = 0; gi < a.ngates; ++gi) {
-        const FGate<R>& G = sg[gi];
-        bool ok = true;
-        for (int c = 0; c < G.n_out; ++c) ok = ok && (odig[G.out_w[c]] == (int32_t)G.out_v[c]);
-        if (!ok) continue;  // uniform across the CTA
-        if (G.d == 2) tile_gate<R, 2>(tile, G);
-        else if (DMAX == 3 || G.d == 3) tile_gate<R, 3>(tile, G);
-        else if (G.d == 4) tile_gate<R, (DMAX > 3 ? 4 : 3)>(tile, G);
-        else tile_gate<R, DMAX>(tile, G);
-        __syncthreads();
-    }
     if (a.vec2) {
         for (uint32_t e = 2 * threadIdx.x; e < a.T; e += 2 * blockDim.x) {
             const uint32_t r = a.bLdiv.div(e);
@@ -326,11 +430,11 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
 
 template <typename R>
 size_t fused_smem(const FusedArgs<R>& a) {
-    return fused_desc_bytes<R>(a.ngates) + fused_rows_bytes(a.rows) + sizeof(typename Cplx<R>::T2) * (size_t)a.T;
+    return chunk_smem_max<R>() + fused_rows_bytes(a.rows) + sizeof(typename Cplx<R>::T2) * (size_t)a.T;
 }
 
-// dmax: largest wire dimension among the pass's gates (selects the kernel
-// instance, so passes of qubits and qutrits do not pay for d = 5 registers).
+// dmax: largest single-wire dimension among the pass's gates (selects the
+// kernel instance, so qubit/qutrit passes do not pay for d = 5 registers).
 template <typename R>
 cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
     static int attr_dev = -1;
@@ -353,16 +457,15 @@ cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
 }
 
 // Whole circuits of small states, one CTA per circuit: the state starts as
-// |0...0> in shared memory, every gate of the circuit is applied there
-// (descriptors streamed through shared memory in chunks of kMaxPassGates),
+// |0...0> in shared memory, every chunk of the circuit is applied there,
 // then the state is written to HBM once and its squared norm is reduced.
 template <typename R, int DMAX>
 __global__ void __launch_bounds__(256, 2) k_batch_small(const SmallTask* tasks, char* state_base,
                                                          const char* desc_base, double* norms) {
     using T2 = typename Cplx<R>::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    FGate<R>* sg = reinterpret_cast<FGate<R>*>(smem_raw);
-    T2* tile = reinterpret_cast<T2*>(smem_raw + fused_desc_bytes<R>(kMaxPassGates));
+    unsigned char* stage = smem_raw;
+    T2* tile = reinterpret_cast<T2*>(smem_raw + chunk_smem_max<R>());
     __shared__ double red_s[8], red_c[8];
     const SmallTask tk = tasks[blockIdx.x];
     for (uint32_t e = threadIdx.x; e < tk.D; e += blockDim.x) {
@@ -371,26 +474,8 @@ __global__ void __launch_bounds__(256, 2) k_batch_small(const SmallTask* tasks, 
         z.y = 0;
         tile[e] = z;
     }
-    const FGate<R>* gates = reinterpret_cast<const FGate<R>*>(desc_base + tk.gate_off);
-    for (uint32_t g0 = 0; g0 < tk.ngates; g0 += kMaxPassGates) {
-        const uint32_t ng = tk.ngates - g0 < (uint32_t)kMaxPassGates ? tk.ngates - g0 : (uint32_t)kMaxPassGates;
-        __syncthreads();  // previous chunk done with the descriptors
-        {
-            const uint4* src = reinterpret_cast<const uint4*>(gates + g0);
-            uint4* dst = reinterpret_cast<uint4*>(sg);
-            const uint32_t n16 = (uint32_t)(fused_desc_bytes<R>((int)ng) / 16);
-            for (uint32_t i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = src[i];
-        }
-        __syncthreads();
-        for (uint32_t gi = 0; gi < ng; ++gi) {
-            const FGate<R>& G = sg[gi];
-            if (G.d == 2) tile_gate<R, 2>(tile, G);
-            else if (DMAX == 3 || G.d == 3) tile_gate<R, 3>(tile, G);
-            else if (G.d == 4) tile_gate<R, (DMAX > 3 ? 4 : 3)>(tile, G);
-            else tile_gate<R, DMAX>(tile, G);
-            __syncthreads();
-        }
-    }
+    apply_chunks<R, DMAX>(tile, desc_base + tk.chunk_off, (int)tk.nchunks, stage, nullptr);
+    __syncthreads();
     T2* psi = reinterpret_cast<T2*>(state_base + tk.psi_off);
     double s = 0.0, c = 0.0;  // Neumaier per thread, then a fixed-order tree
     for (uint32_t e = threadIdx.x; e < tk.D; e += blockDim.x) {
@@ -441,7 +526,7 @@ cudaError_t launch_batch_small(const SmallTask* tasks, int ntasks, int dmax, uin
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    const size_t smem = fused_desc_bytes<R>(kMaxPassGates) + sizeof(typename Cplx<R>::T2) * (size_t)max_d;
+    const size_t smem = chunk_smem_max<R>() + sizeof(typename Cplx<R>::T2) * (size_t)max_d;
     if (dmax <= 3)
         k_batch_small<R, 3><<<ntasks, 256, smem, s>>>(tasks, state_base, desc_base, norms);
     else
@@ -469,6 +554,8 @@ FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     c.Tmax = (o && o->max_tile_amps > 0) ? o->max_tile_amps : (prec == QD_C64 ? 8192 : 4096);
     c.min_gates = (o && o->min_gates > 0) ? o->min_gates : 2;
     c.min_row = (o && o->min_row > 0) ? o->min_row : (prec == QD_C64 ? 16 : 8);
+    c.block_dim = (o && o->block_dim > 0) ? o->block_dim : kMaxBlock;
+    if (c.block_dim > kMaxBlock) c.block_dim = kMaxBlock;
     // rows per tile are bounded by the row table
     const int64_t need = (c.Tmax + kMaxRows - 1) / kMaxRows;
     if (c.min_row < need) c.min_row = need;
@@ -634,19 +721,177 @@ static void tile_geometry(const Layout& L, uint64_t S, int64_t min_row, TileGeom
 }
 
 
+// ---------------------------------------------------------------------------
+// Blocks inside a pass: runs of gates on a few wires composed into one matrix.
+// ---------------------------------------------------------------------------
+struct BlockPlan {
+    std::vector<int> gates;  // in application order
+    uint64_t lw;             // local wires (bit i = local wire i)
+    bool single;
+};
+
+static int padded_dim(int P) {
+    static const int sizes[] = {4, 6, 8, 9, 12, 16};
+    for (int q : sizes)
+        if (P <= q) return q;
+    return 16;
+}
+
+static uint64_t local_mask(const TileGeom& geo, uint64_t global) {
+    uint64_t m = 0;
+    for (int w = 0; w < 64; ++w)
+        if ((global >> w & 1) && geo.loc[w] >= 0) m |= 1ull << geo.loc[w];
+    return m;
+}
+
+static int64_t local_prod(const TileGeom& geo, uint64_t lw) {
+    int64_t p = 1;
+    for (int i = 0; i < geo.ns; ++i)
+        if (lw >> i & 1) p *= geo.local.dims[i];
+    return p;
+}
+
+// Arithmetic per amplitude of a gate or block, in complex MACs plus a fixed
+// cost for the shared-memory sweep and the class enumeration.
+static double sweep_cost(int kind, int64_t P) { return 4.0 + (kind == kDense ? (double)P : 1.0); }
+
+static void form_blocks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<int>& pg, int Pmax,
+                        std::vector<BlockPlan>& out) {
+    out.clear();
+    std::vector<int> rem = pg;
+    auto outside = [&](const HGate& h) {
+        for (int c = 0; c < h.nc; ++c)
+            if (geo.loc[h.cw[c]] < 0) return true;
+        return h.k != 1;
+    };
+    while (!rem.empty()) {
+        const HGate& g0 = G[rem[0]];
+        BlockPlan bp;
+        bp.single = true;
+        bp.gates = {rem[0]};
+        bp.lw = local_mask(geo, g0.tmask | g0.cmask);
+        if (Pmax >= 4 && !outside(g0) && local_prod(geo, bp.lw) <= Pmax) {
+            uint64_t W = bp.lw, BW = 0, BR = 0;
+            std::vector<int> sel = {rem[0]};
+            double cost_single = sweep_cost(g0.plan.kind, g0.plan.d);
+            for (size_t j = 1; j < rem.size(); ++j) {
+                const HGate& g = G[rem[j]];
+                const uint64_t Wg = g.diag ? 0 : g.tmask;
+                const uint64_t Rg = g.cmask | (g.diag ? g.tmask : 0);
+                const bool blocked = (Wg & (BW | BR)) || (Rg & BW);
+                bool ok = !blocked && !outside(g);
+                if (ok) {
+                    const uint64_t W2 = W | local_mask(geo, g.tmask | g.cmask);
+                    if (local_prod(geo, W2) <= Pmax) {
+                        W = W2;
+                        sel.push_back(rem[j]);
+                        cost_single += sweep_cost(g.plan.kind, g.plan.d);
+                        continue;
+                    }
+                }
+                BW |= Wg;
+                BR |= Rg;
+            }
+            bool all_diag = true;
+            for (int idx : sel) all_diag = all_diag && G[idx].diag;
+            const double cost_block = sweep_cost(all_diag ? kDiag : kDense, local_prod(geo, W));
+            if (sel.size() > 1 && cost_block <= cost_single) {
+                bp.single = false;
+                bp.gates = sel;
+                bp.lw = W;
+            }
+        }
+        out.push_back(bp);
+        std::vector<int> rest;
+        for (int idx : rem)
+            if (std::find(bp.gates.begin(), bp.gates.end(), idx) == bp.gates.end()) rest.push_back(idx);
+        rem.swap(rest);
+    }
+}
+
+// Compose a block in binary64: M = G_k ... G_1 on the P-dimensional space of
+// the block's wires (local wires ascending, first least significant).  Each
+// gate acts on every column of M as on a state: classes of d entries spaced
+// by the target's stride, controls checked on the class's digits.
+static void compose_block(const TileGeom& geo, const std::vector<HGate>& G, const BlockPlan& bp,
+                          std::vector<double>& M, int& P, std::vector<int>& wl) {
+    wl.clear();
+    for (int i = 0; i < geo.ns; ++i)
+        if (bp.lw >> i & 1) wl.push_back(i);
+    std::vector<int> wd(wl.size()), ws(wl.size());
+    P = 1;
+    for (size_t i = 0; i < wl.size(); ++i) {
+        wd[i] = geo.local.dims[wl[i]];
+        ws[i] = P;
+        P *= wd[i];
+    }
+    auto pos = [&](int local) {
+        for (size_t i = 0; i < wl.size(); ++i)
+            if (wl[i] == local) return (int)i;
+        return -1;
+    };
+    M.assign((size_t)2 * P * P, 0.0);
+    for (int i = 0; i < P; ++i) M[2 * ((size_t)i * P + i)] = 1.0;
+    std::vector<double> col(2 * (size_t)P), nxt(2 * (size_t)P);
+    for (int idx : bp.gates) {
+        const HGate& h = G[idx];
+        const int pt = pos(geo.loc[h.wires[0]]);
+        const int d = wd[pt], st = ws[pt];
+        std::vector<int> cp, cv;
+        for (int c = 0; c < h.nc; ++c) {
+            cp.push_back(pos(geo.loc[h.cw[c]]));
+            cv.push_back(h.cv[c]);
+        }
+        for (int j = 0; j < P; ++j) {  // column j of M
+            for (int r = 0; r < P; ++r) {
+                col[2 * r] = M[2 * ((size_t)r * P + j)];
+                col[2 * r + 1] = M[2 * ((size_t)r * P + j) + 1];
+            }
+            nxt = col;
+            for (int base = 0; base < P; ++base) {
+                if ((base / st) % d != 0) continue;  // class representatives: target digit 0
+                bool ok = true;
+                for (size_t c = 0; c < cp.size(); ++c)
+                    if ((base / ws[cp[c]]) % wd[cp[c]] != cv[c]) ok = false;
+                if (!ok) continue;
+                for (int r = 0; r < d; ++r) {
+                    double re = 0.0, im = 0.0;
+                    for (int k = 0; k < d; ++k) {
+                        const double ur = h.U[2 * (r * d + k)], ui = h.U[2 * (r * d + k) + 1];
+                        const double xr = col[2 * (base + k * st)], xi = col[2 * (base + k * st) + 1];
+                        re += ur * xr - ui * xi;
+                        im += ur * xi + ui * xr;
+                    }
+                    nxt[2 * (base + r * st)] = re;
+                    nxt[2 * (base + r * st) + 1] = im;
+                }
+            }
+            for (int r = 0; r < P; ++r) {
+                M[2 * ((size_t)r * P + j)] = nxt[2 * r];
+                M[2 * ((size_t)r * P + j) + 1] = nxt[2 * r + 1];
+            }
+        }
+    }
+}
+
 template <typename R>
-static void build_fgate(const TileGeom& geo, const HGate& h, FGate<R>& f) {
+static void fill_single(const TileGeom& geo, const HGate& h, FGate& f, std::vector<typename Cplx<R>::T2>& pool) {
     std::memset(static_cast<void*>(&f), 0, sizeof f);
     const Plan& p = h.plan;
-    f.d = (uint8_t)p.d;
+    f.single = 1;
+    f.P = (uint8_t)p.d;
+    f.PP = (uint8_t)p.d;
     f.kind = (uint8_t)p.kind;
-    f.lmask = (uint8_t)p.lmask;
-    f.smask = (uint8_t)p.smask;
+    f.lmask = (uint16_t)p.lmask;
+    f.smask = (uint16_t)p.smask;
     f.pure = p.pure ? 1 : 0;
-    for (int r = 0; r < 8; ++r) f.perm[r] = (uint8_t)(r < kMaxSmallD ? p.perm[r] : 0);
+    for (int r = 0; r < kMaxSmallD && r < kMaxBlock; ++r) f.perm[r] = (uint8_t)p.perm[r];
+    f.u_off = (uint32_t)pool.size();
     for (int i = 0; i < p.d * p.d; ++i) {
-        f.U[i].x = (R)h.U[2 * i];
-        f.U[i].y = (R)h.U[2 * i + 1];
+        typename Cplx<R>::T2 v;
+        v.x = (R)h.U[2 * i];
+        v.y = (R)h.U[2 * i + 1];
+        pool.push_back(v);
     }
     const int t = geo.loc[h.wires[0]];
     f.lst = (uint32_t)geo.local.b[t];
@@ -680,12 +925,141 @@ static void build_fgate(const TileGeom& geo, const HGate& h, FGate<R>& f) {
     f.nclasses = (uint32_t)classes;
 }
 
-// ---------------------------------------------------------------------------
-// Programs: the launches of a circuit with their descriptors.  Building a
-// program makes no CUDA call; running it uploads the descriptors once and
-// issues the launches, so many programs can share one upload and be issued
-// on several streams or inside a CUDA graph capture.
-// ---------------------------------------------------------------------------
+template <typename R>
+static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const BlockPlan& bp, FGate& f,
+                       std::vector<typename Cplx<R>::T2>& pool) {
+    std::memset(static_cast<void*>(&f), 0, sizeof f);
+    std::vector<double> M;
+    std::vector<int> wl;
+    int P = 0;
+    compose_block(geo, G, bp, M, P, wl);
+    const int PP = padded_dim(P);
+    auto re = [&](int r, int c) { return M[2 * ((size_t)r * P + c)]; };
+    auto im = [&](int r, int c) { return M[2 * ((size_t)r * P + c) + 1]; };
+    auto nz = [&](int r, int c) { return re(r, c) != 0.0 || im(r, c) != 0.0; };
+    auto one = [&](int r, int c) { return re(r, c) == 1.0 && im(r, c) == 0.0; };
+    bool diag = true, mono = true;
+    int src[kMaxBlock];
+    bool used[kMaxBlock] = {false};
+    for (int r = 0; r < P; ++r) {
+        int cnt = 0;
+        for (int c = 0; c < P; ++c)
+            if (nz(r, c)) {
+                ++cnt;
+                src[r] = c;
+                if (c != r) diag = false;
+            }
+        if (cnt != 1 || used[src[r]]) mono = false;
+        else used[src[r]] = true;
+    }
+    f.single = 0;
+    f.P = (uint8_t)P;
+    f.PP = (uint8_t)PP;
+    f.lmask = f.smask = 0;
+    f.pure = 0;
+    if (diag) {
+        f.kind = kDiag;
+        for (int r = 0; r < P; ++r)
+            if (!one(r, r)) f.lmask |= (uint16_t)(1u << r);
+        f.smask = f.lmask;
+    } else if (mono) {
+        f.kind = kPerm;
+        f.pure = 1;
+        for (int r = 0; r < P; ++r) {
+            f.perm[r] = (uint8_t)src[r];
+            if (!one(r, src[r])) f.pure = 0;
+            if (src[r] != r || !one(r, src[r])) {
+                f.smask |= (uint16_t)(1u << r);
+                f.lmask |= (uint16_t)(1u << src[r]);
+            }
+        }
+    } else {
+        f.kind = kDense;
+        f.lmask = f.smask = (uint16_t)((1u << P) - 1u);
+    }
+    f.u_off = (uint32_t)pool.size();
+    for (int r = 0; r < PP; ++r)
+        for (int c = 0; c < PP; ++c) {
+            typename Cplx<R>::T2 v;
+            v.x = (r < P && c < P) ? (R)re(r, c) : (R)0;
+            v.y = (r < P && c < P) ? (R)im(r, c) : (R)0;
+            pool.push_back(v);
+        }
+    for (int r = 0; r < P; ++r) {
+        uint32_t o = 0;
+        int rem = r;
+        for (int lw : wl) {
+            const int d = geo.local.dims[lw];
+            o += (uint32_t)(rem % d) * (uint32_t)geo.local.b[lw];
+            rem /= d;
+        }
+        f.off[r] = (uint16_t)o;
+    }
+    int32_t ins_w[kMaxLocalIns];
+    int64_t ins_v[kMaxLocalIns];
+    int m = 0;
+    for (int lw : wl) {
+        ins_w[m] = lw;
+        ins_v[m] = 0;
+        ++m;
+    }
+    IndexMap imap;
+    uint64_t classes;
+    build_map(geo.local, ins_w, ins_v, m, imap, classes);
+    f.map.m = imap.m;
+    f.map.fixed = (uint32_t)imap.fixed;
+    for (int i = 0; i < imap.m; ++i) f.map.seg[i].init((uint32_t)imap.seg[i].d);
+    for (int i = 0; i <= imap.m; ++i) f.map.off[i] = (uint32_t)imap.off[i];
+    f.nclasses = (uint32_t)classes;
+    f.n_out = 0;
+}
+
+// Chunks of a list of blocks, contiguous, appended to prog.desc (256-aligned
+// start).  Returns the first chunk's offset; *nchunks the count; *dmax the
+// largest single-wire dimension (kernel instance).
+template <typename R>
+static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<BlockPlan>& blocks,
+                          Program& prog, uint32_t* nchunks, int* dmax) {
+    using T2 = typename Cplx<R>::T2;
+    std::vector<char> buf;
+    uint32_t n = 0;
+    int dm = 2;
+    size_t i = 0;
+    while (i < blocks.size()) {
+        std::vector<FGate> fg;
+        std::vector<T2> pool;
+        while (i < blocks.size() && fg.size() < (size_t)kMaxChunkGates) {
+            const BlockPlan& bp = blocks[i];
+            const size_t need = bp.single ? (size_t)G[bp.gates[0]].plan.d * G[bp.gates[0]].plan.d
+                                          : (size_t)padded_dim((int)local_prod(geo, bp.lw)) *
+                                                padded_dim((int)local_prod(geo, bp.lw));
+            if (pool.size() + need > (size_t)kPoolEntries && !fg.empty()) break;
+            FGate f;
+            if (bp.single) {
+                fill_single<R>(geo, G[bp.gates[0]], f, pool);
+                dm = G[bp.gates[0]].plan.d > dm ? G[bp.gates[0]].plan.d : dm;
+            } else {
+                fill_block<R>(geo, G, bp, f, pool);
+            }
+            fg.push_back(f);
+            ++i;
+        }
+        ChunkHdr h{};
+        h.ngates = (uint32_t)fg.size();
+        h.npool = (uint32_t)pool.size();
+        h.bytes = (uint32_t)((chunk_bytes<R>(h.ngates, h.npool) + 15) & ~(size_t)15);
+        const size_t o = buf.size();
+        buf.resize(o + h.bytes, 0);
+        std::memcpy(buf.data() + o, &h, sizeof h);
+        std::memcpy(buf.data() + o + sizeof h, fg.data(), sizeof(FGate) * fg.size());
+        std::memcpy(buf.data() + o + sizeof h + sizeof(FGate) * fg.size(), pool.data(), sizeof(T2) * pool.size());
+        ++n;
+    }
+    *nchunks = n;
+    if (dmax) *dmax = dm;
+    return prog.put(buf.data(), buf.size());
+}
+
 qd_status Arena::upload(const void* bytes, size_t n, cudaStream_t s) {
     if (n == 0) return QD_OK;
     if (n > cap) {
@@ -809,14 +1183,16 @@ void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, cons
         }
         TileGeom geo;
         tile_geometry(L, p.smask, cfg.min_row, geo);
-        const size_t offF = prog.reserve(sizeof(FGate<R>) * p.gates.size());
-        for (size_t i = 0; i < p.gates.size(); ++i)
-            build_fgate<R>(geo, G[p.gates[i]], reinterpret_cast<FGate<R>*>(prog.desc.data() + offF)[i]);
+        std::vector<BlockPlan> blocks;
+        form_blocks(geo, G, p.gates, cfg.block_dim, blocks);
+        uint32_t nchunks = 0;
+        int dmax = 2;
+        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax);
         const size_t offR = prog.put(geo.rowoff.data(), sizeof(uint64_t) * geo.R);
         FusedArgs<R> a;
         std::memset(static_cast<void*>(&a), 0, sizeof a);
         a.psi = reinterpret_cast<T2*>(psi);
-        a.ngates = (int32_t)p.gates.size();
+        a.nchunks = (int32_t)nchunks;
         a.T = (uint32_t)p.T;
         a.bL = geo.bL;
         a.rows = geo.R;
@@ -829,11 +1205,9 @@ void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, cons
             a.free_d[i] = geo.free_d[i];
             a.free_b[i] = geo.free_b[i];
         }
-        int dmax = 2;
-        for (int idx : p.gates) dmax = G[idx].plan.d > dmax ? G[idx].plan.d : dmax;
-        prog.ops.push_back([a, offF, offR, dmax](cudaStream_t s, const char* base) {
+        prog.ops.push_back([a, offC, offR, dmax](cudaStream_t s, const char* base) {
             FusedArgs<R> b = a;
-            b.gates = reinterpret_cast<const FGate<R>*>(base + offF);
+            b.chunks = base + offC;
             b.rowoff = reinterpret_cast<const uint64_t*>(base + offR);
             return launch_fused<R>(b, dmax, s);
         });
@@ -868,17 +1242,21 @@ bool small_eligible(const Layout& L, const std::vector<HGate>& G, int64_t small_
 }
 
 template <typename R>
-size_t put_small_gates(const Layout& L, const std::vector<HGate>& G, Program& prog) {
+size_t put_small_chunks(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg, Program& prog,
+                        uint32_t* nchunks) {
     TileGeom geo;
     tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo);
-    const size_t off = prog.reserve(sizeof(FGate<R>) * G.size());
-    for (size_t g = 0; g < G.size(); ++g)
-        build_fgate<R>(geo, G[g], reinterpret_cast<FGate<R>*>(prog.desc.data() + off)[g]);
-    return off;
+    std::vector<int> all(G.size());
+    for (size_t i = 0; i < G.size(); ++i) all[i] = (int)i;
+    std::vector<BlockPlan> blocks;
+    form_blocks(geo, G, all, cfg.block_dim, blocks);
+    return emit_chunks<R>(geo, G, blocks, prog, nchunks, nullptr);
 }
 
-template size_t put_small_gates<float>(const Layout&, const std::vector<HGate>&, Program&);
-template size_t put_small_gates<double>(const Layout&, const std::vector<HGate>&, Program&);
+template size_t put_small_chunks<float>(const Layout&, const std::vector<HGate>&, const FuseCfg&, Program&,
+                                        uint32_t*);
+template size_t put_small_chunks<double>(const Layout&, const std::vector<HGate>&, const FuseCfg&, Program&,
+                                         uint32_t*);
 
 template void build_program<float>(const Layout&, void*, const std::vector<HGate>&, const FuseCfg&, bool,
                                    Program&);
@@ -1036,16 +1414,11 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
             dmax = h.plan.d > dmax ? h.plan.d : dmax;
         }
         if (fits) {
-            TileGeom geo;
-            tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo);
             SmallTask t{};
             t.psi_off = b->psi_off[i];
             t.D = (uint32_t)L.D;
-            t.ngates = (uint32_t)Gs[i].size();
             t.norm_index = (uint32_t)i;
-            t.gate_off = prog.reserve(sizeof(FGate<R>) * Gs[i].size());
-            for (size_t g = 0; g < Gs[i].size(); ++g)
-                build_fgate<R>(geo, Gs[i][g], reinterpret_cast<FGate<R>*>(prog.desc.data() + t.gate_off)[g]);
+            t.chunk_off = put_small_chunks<R>(L, Gs[i], cfg, prog, &t.nchunks);
             if (dmax <= 3) {
                 small3.push_back(t);
                 maxd3 = t.D > maxd3 ? t.D : maxd3;

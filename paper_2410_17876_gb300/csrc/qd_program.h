@@ -27,6 +27,7 @@ struct FuseCfg {
     int64_t Tmax;
     int min_gates;
     int64_t min_row;
+    int block_dim;  // largest composed block inside a pass (< 4: no composition)
 };
 
 int64_t tile_limit(int32_t prec);
@@ -66,9 +67,9 @@ qd_status issue(const Program& prog, const char* base, cudaStream_t s);
 // One small circuit of a batch (whole state in one CTA).
 struct SmallTask {
     uint64_t psi_off;     // byte offset of the state in the batch's state arena
-    uint64_t gate_off;    // byte offset of its FGate descriptors in the descriptor arena
+    uint64_t chunk_off;   // byte offset of its first chunk in the descriptor arena
     uint32_t D;           // amplitudes
-    uint32_t ngates;
+    uint32_t nchunks;
     uint32_t norm_index;  // slot of its squared norm
     uint32_t pad_;
 };
@@ -77,9 +78,11 @@ struct SmallTask {
 // every gate can join a fused pass; *dmax receives its largest wire dimension.
 bool small_eligible(const Layout& L, const std::vector<HGate>& G, int64_t small_max, int* dmax);
 
-// Append the circuit's one-CTA gate descriptors to prog; returns their offset.
+// Append the circuit's one-CTA chunks to prog; returns the first chunk's
+// offset and sets *nchunks.
 template <typename R>
-size_t put_small_gates(const Layout& L, const std::vector<HGate>& G, Program& prog);
+size_t put_small_chunks(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg, Program& prog,
+                        uint32_t* nchunks);
 
 // Launch the one-CTA kernel over ntasks small circuits (tasks in device memory).
 template <typename R>

@@ -187,9 +187,8 @@ bool issue_small(qd_server* s, Lane& ln) {
         SmallTask t{};
         t.psi_off = r.off;
         t.D = (uint32_t)r.L.D;
-        t.ngates = (uint32_t)r.G.size();
         t.norm_index = (uint32_t)i;
-        t.gate_off = put_small_gates<R>(r.L, r.G, prog);
+        t.chunk_off = put_small_chunks<R>(r.L, r.G, s->cfg, prog, &t.nchunks);
         if (r.dmax <= 3) {
             t3.push_back(t);
             m3 = std::max(m3, t.D);

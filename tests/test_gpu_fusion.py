@@ -51,9 +51,9 @@ def test_config0_fused_single_tile(qb, gen, prec):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-@pytest.mark.parametrize("max_tile", [64, 256, 2048, 8192])
+@pytest.mark.parametrize("max_tile,block_dim", [(64, 16), (256, 4), (2048, 8), (8192, 16), (8192, 1), (2048, 9)])
 @pytest.mark.parametrize("seed", [0, 1, 2])
-def test_random_mixed_circuits_fused(qb, gen, prec, max_tile, seed):
+def test_random_mixed_circuits_fused(qb, gen, prec, max_tile, block_dim, seed):
     p = qb.QD_C128 if prec == "c128" else qb.QD_C64
     if p == qb.QD_C128 and max_tile > 4096:
         max_tile = 4096
@@ -74,9 +74,9 @@ def test_random_mixed_circuits_fused(qb, gen, prec, max_tile, seed):
     gates = circ.gates[:80] + extra + circ.gates[80:]
     circ = gen.Circuit(dims, gates)
     psi0 = gen.random_state(circ.D, rng)
-    got = _run(qb, circ, p, psi0, max_tile_amps=max_tile)
+    got = _run(qb, circ, p, psi0, max_tile_amps=max_tile, block_dim=block_dim)
     ref = oracle.run_circuit(circ, psi0)
-    assert_close(got, ref, p, f"fused dims={dims} tile={max_tile}")
+    assert_close(got, ref, p, f"fused dims={dims} tile={max_tile} block={block_dim}")
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
