@@ -199,13 +199,16 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
 
 /* The execution plan of qd_apply_circuit without a GPU: exec_order[i] is the
  * index of the i-th gate executed, pass_of[i] its pass, pass_tile_amps[p]
- * the tile size of pass p (0 = a per-gate kernel pass); *n_passes receives
- * the number of passes.  Every array has n_gates entries; pass_tile_amps
- * may be NULL. */
+ * the tile size of pass p (0 = a per-gate kernel pass), pass_flops[p] the
+ * arithmetic of pass p over the whole state (real floating-point operations:
+ * 8 P per amplitude for a dense P x P block or gate, 6 per changed amplitude
+ * for a diagonal or phased-permutation one, 0 for a pure permutation), and
+ * *n_passes the number of passes.  Every array has n_gates entries;
+ * pass_tile_amps and pass_flops may be NULL. */
 qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd_gate_desc* gates,
                           int32_t n_gates, const double* matrices, const qd_fusion_opts* opts,
                           int32_t* exec_order, int32_t* pass_of, int64_t* pass_tile_amps,
-                          int32_t* n_passes);
+                          double* pass_flops, int32_t* n_passes);
 
 /* ------------------------------------------------------------------------
  * Batches of independent circuits.  Each circuit starts from its own

@@ -126,7 +126,7 @@ _SIGS = {
                                           ctypes.POINTER(qd_fusion_opts)]),
     "qd_plan_circuit": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(qd_gate_desc),
                                          ctypes.c_int32, _f64p, ctypes.POINTER(qd_fusion_opts), _i32p, _i32p,
-                                         ctypes.POINTER(ctypes.c_int64), _i32p]),
+                                         ctypes.POINTER(ctypes.c_int64), _f64p, _i32p]),
 }
 
 for _name, (_res, _args) in _SIGS.items():
@@ -372,19 +372,24 @@ def qd_apply_circuit(st: int, circuit, mode=QD_FUSE_OFF, max_tile_amps=0, min_ga
                                  _opts(mode, max_tile_amps, min_gates, min_row, block_dim)), "qd_apply_circuit")
 
 
-def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min_gates=0, min_row=0, block_dim=0):
-    """(exec_order, pass_of, pass_tile_amps[:n_passes]) of the circuit's execution plan."""
+def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min_gates=0, min_row=0, block_dim=0,
+                    with_flops=False):
+    """(exec_order, pass_of, pass_tile_amps[:n_passes]) of the circuit's execution plan,
+    plus pass_flops[:n_passes] when ``with_flops``."""
     d = _i32(dims)
     descs, m = circuit_arrays(circuit)
     n = len(circuit.gates)
     order = np.zeros(max(1, n), np.int32)
     pass_of = np.zeros(max(1, n), np.int32)
     tiles = np.zeros(max(1, n), np.int64)
+    flops = np.zeros(max(1, n), np.float64)
     npass = ctypes.c_int32()
     _check(_lib.qd_plan_circuit(_p(d, _i32p), len(d), prec, descs, n, _p(m, _f64p),
                                 _opts(mode, max_tile_amps, min_gates, min_row, block_dim), _p(order, _i32p),
                                 _p(pass_of, _i32p), tiles.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
-                                ctypes.byref(npass)), "qd_plan_circuit")
+                                _p(flops, _f64p), ctypes.byref(npass)), "qd_plan_circuit")
+    if with_flops:
+        return order[:n], pass_of[:n], tiles[:npass.value], flops[:npass.value]
     return order[:n], pass_of[:n], tiles[:npass.value]
 
 

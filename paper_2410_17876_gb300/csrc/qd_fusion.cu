@@ -1258,6 +1258,38 @@ template size_t put_small_chunks<float>(const Layout&, const std::vector<HGate>&
 template size_t put_small_chunks<double>(const Layout&, const std::vector<HGate>&, const FuseCfg&, Program&,
                                          uint32_t*);
 
+// Arithmetic of one gate or block over the whole state (real flops): 8 P per
+// amplitude of each visited class when dense, 6 per changed amplitude when
+// diagonal or a phased permutation, nothing for a pure permutation.
+static double unit_flops(int kind, bool pure, int P, int changed_rows, double classes) {
+    if (kind == kDense) return 8.0 * P * P * classes;
+    if (kind == kPerm && pure) return 0.0;
+    return 6.0 * changed_rows * classes;
+}
+
+static double pass_arith(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg, const PassPlan& p) {
+    auto popc = [](uint32_t m) { int c = 0; while (m) { c += m & 1u; m >>= 1; } return c; };
+    if (!p.tile) {
+        const Plan& q = G[p.gates[0]].plan;
+        if (q.family == 1) return 8.0 * q.P * q.P * (double)q.classes;
+        return unit_flops(q.kind, q.pure, q.d, popc(q.smask), (double)q.classes);
+    }
+    TileGeom geo;
+    tile_geometry(L, p.smask, cfg.min_row, geo);
+    std::vector<BlockPlan> blocks;
+    form_blocks(geo, G, p.gates, cfg.block_dim, blocks);
+    const double tiles = (double)(L.D / p.T);
+    double f = 0.0;
+    std::vector<typename Cplx<double>::T2> pool;
+    for (const BlockPlan& bp : blocks) {
+        FGate fg;
+        if (bp.single) fill_single<double>(geo, G[bp.gates[0]], fg, pool);
+        else fill_block<double>(geo, G, bp, fg, pool);
+        f += tiles * unit_flops(fg.kind, fg.pure != 0, fg.P, popc(fg.smask), (double)fg.nclasses);
+    }
+    return f;
+}
+
 template void build_program<float>(const Layout&, void*, const std::vector<HGate>&, const FuseCfg&, bool,
                                    Program&);
 template void build_program<double>(const Layout&, void*, const std::vector<HGate>&, const FuseCfg&, bool,
@@ -1540,7 +1572,7 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
 
 qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd_gate_desc* gates, int32_t n_gates,
                           const double* matrices, const qd_fusion_opts* opts, int32_t* exec_order, int32_t* pass_of,
-                          int64_t* pass_tile_amps, int32_t* n_passes) {
+                          int64_t* pass_tile_amps, double* pass_flops, int32_t* n_passes) {
     try {
         if (!exec_order || !pass_of || !n_passes) return fail(QD_ERR_ARG, "output array is NULL");
         Layout L;
@@ -1560,6 +1592,7 @@ qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd
                 ++pos;
             }
             if (pass_tile_amps) pass_tile_amps[p] = passes[p].tile ? passes[p].T : 0;
+            if (pass_flops) pass_flops[p] = pass_arith(L, G, cfg, passes[p]);
         }
         *n_passes = (int32_t)passes.size();
         return QD_OK;
