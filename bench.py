@@ -36,6 +36,11 @@ WORKLOAD = "12 qubits + 8 qutrits (26,873,856 amplitudes), depth 500 hybrid Clif
 METRIC = "amp-gate updates/s"
 UNIT = "updates/s"
 L2_BYTES = 129e6
+# FP32 / FP64 vector peaks of GB300 from unit counts and the maximum SM clock:
+# 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 from NVIDIA's 1.25 TFLOP/s figure.
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP64_TFLOPS = 1.25
+ALU_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s (FP64: 1.25 TFLOP/s nominal)"
 
 
 # ----------------------------------------------------------------------------------------------
@@ -133,23 +138,30 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {
+    "gate": ("qd_kernels.cu", "qd_internal.cuh"),
+    "fused": ("qd_fusion.cu", "qd_internal.cuh", "qd_program.h"),
+}
+TRAFFIC_FILES = {"gate": "gate_kernel_traffic.json", "fused": "fused_kernel_traffic.json"}
+
+
+def kernel_source_hash(kind: str = "gate") -> str:
     h = hashlib.sha256()
-    for fn in ("qd_kernels.cu", "qd_internal.cuh"):
+    for fn in KERNEL_SOURCES[kind]:
         with open(os.path.join(ROOT, "paper_2410_17876_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(prec_name: str):
-    """DRAM bytes per launch of the gate kernel from the committed ncu summary, if it
+def ncu_traffic(prec_name: str, kind: str = "gate"):
+    """DRAM bytes per launch of the kernel from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "gate_kernel_traffic.json")
+    p = os.path.join(ROOT, "profiles", TRAFFIC_FILES[kind])
     if not os.path.exists(p):
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash(kind):
         return None
     ent = d.get(prec_name)
     return None if ent is None else ent.get("dram_bytes_per_launch")
@@ -405,8 +417,16 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(local)
     st = qb.State(circ.dims, prec=prec, stream=stream, device=local)
 
-    fuse = args.fuse == "tile"
-    fopts = {"max_tile_amps": args.tile} if fuse and args.tile else {}
+    tuned = None
+    if args.fuse == "auto":
+        from paper_2410_17876_gb300 import autotune
+
+        tuned = autotune.tune_circuit(st, circ)
+        fuse = bool(tuned["fuse"])
+        fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"]} if fuse else {}
+    else:
+        fuse = args.fuse == "tile"
+        fopts = {"max_tile_amps": args.tile} if fuse and args.tile else {}
 
     def step():
         st.reset()
@@ -443,7 +463,7 @@ def run_gpu(args):
              for g in circ.gates]
     if fuse:
         # one qd_apply_circuit call per planned pass, CUDA events around each
-        order, pass_of, tiles = qb.qd_plan_circuit(circ.dims, prec, circ, **fopts)
+        order, pass_of, tiles, pflops = qb.qd_plan_circuit(circ.dims, prec, circ, with_flops=True, **fopts)
         groups = [[] for _ in range(len(tiles))]
         for g_idx, p_idx in zip(order, pass_of):
             groups[p_idx].append(circ.gates[g_idx])
@@ -456,10 +476,11 @@ def run_gpu(args):
             st.run(sc, fuse=True, **fopts)
             evs[i + 1].record(stream)
         torch.cuda.synchronize()
-        k_time, k_bytes, k_n = 0.0, 0, 0
+        k_time, k_flops, k_bytes, k_n = 0.0, 0.0, 0, 0
         for i, t in enumerate(tiles):
             if t > 0:
                 k_time += evs[i].elapsed_time(evs[i + 1]) / 1e3
+                k_flops += float(pflops[i])
                 k_bytes += 2 * amp_bytes * circ.D
                 k_n += 1
         kname = "k_fused_tile (shared-memory tile pass, all tile passes of the circuit)"
@@ -480,8 +501,20 @@ def run_gpu(args):
                 k_n += 1
         kname = "k_gate1 (per-class register kernel, all gates of the circuit)"
     peak, peak_kind = measured_peaks()
-    achieved = k_bytes / k_time / 1e9 if k_time > 0 else 0.0
-    traffic = None if fuse else ncu_traffic(args.prec)
+    if fuse:
+        # a fused pass is bound by its on-chip arithmetic (composed blocks), not by HBM:
+        # FP32 (complex64) or FP64 (complex128) pipe peak from unit counts and clocks
+        alu_peak = FP32_TFLOPS if prec == qb.QD_C64 else FP64_TFLOPS
+        roof = {"kernel": kname, "bound": "alu", "achieved": k_flops / k_time / 1e12 if k_time > 0 else 0.0,
+                "peak": alu_peak, "unit": "TFLOP/s", "peak_source": "derived: " + ALU_PEAK_NOTE,
+                "traffic": ncu_traffic(args.prec, "fused"), "launches_measured": k_n,
+                "hbm_view": {"achieved_gbs": k_bytes / k_time / 1e9 if k_time > 0 else 0.0, "peak_gbs": peak}}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        achieved = k_bytes / k_time / 1e9 if k_time > 0 else 0.0
+        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": ncu_traffic(args.prec),
+                "launches_measured": k_n}
 
     # ---- end to end through the public API with host buffers ----
     pinned = torch.empty(circ.D, dtype=torch.complex64 if prec == qb.QD_C64 else torch.complex128,
@@ -533,16 +566,14 @@ def run_gpu(args):
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == qb.QD_C64 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prec": args.prec, "fusion": args.fuse, "tile_amps": args.tile or None,
+            "config": {"workload": WORKLOAD, "prec": args.prec, "fusion": "tile" if fuse else "off",
+                       "fusion_opts": fopts, "autotuned": tuned is not None,
                        "amplitudes": circ.D, "gates": len(circ.gates),
                        "state_bytes": circ.D * amp_bytes,
                        "l2": f"state {circ.D * amp_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2, no flush",
                        "parallelism": f"replicas x{world}"},
             "hbm_gbs_effective": sum(algorithmic_bytes(p, amp_bytes) for p in plans) * args.steps / t_max / 1e9,
-            "roofline": {"kernel": kname,
-                         "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "peak_source": peak_kind, "traffic": traffic,
-                         "launches_measured": k_n},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
@@ -604,8 +635,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
-    ap.add_argument("--fuse", choices=["tile", "off"], default="off",
-                    help="tile: consecutive gates share one shared-memory pass over the state; off: one pass per gate")
+    ap.add_argument("--fuse", choices=["auto", "tile", "off"], default="auto",
+                    help="tile: consecutive gates share one shared-memory pass over the state; off: one pass per "
+                         "gate; auto: the autotuner's choice of the two (and of tile size and block width)")
     ap.add_argument("--tile", type=int, default=0, help="amplitudes per fused tile (0 = library default)")
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

@@ -276,11 +276,12 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
     }
 }
 
-// Apply one composed block (P <= PP) to the tile.  A class's P members are
-// gathered into registers (padded rows are masked out), each output row is
-// accumulated from the matrix row in the staged pool (every thread reads the
-// same entries: broadcast), and stored at once -- all inputs are in
-// registers before the first store.
+// Apply one composed block (P <= PP) to the tile.  Each thread takes two
+// classes per iteration; their P members are gathered into registers (padded
+// rows are masked out), and every matrix entry read from the staged pool
+// (the same address for all threads: a broadcast) serves both classes --
+// for complex64 two adjacent entries come in one 16-byte load.  All inputs
+// are in registers before the first store.
 template <typename R, int PP>
 __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGate& G,
                                            const typename Cplx<R>::T2* pool) {
@@ -292,39 +293,77 @@ __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGa
 #pragma unroll
     for (int r = 0; r < PP; ++r) off[r] = G.off[r];
     const T2* M = pool + G.u_off;
-    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
-        const uint32_t b = G.map.map(c);
-        T2 x[PP];
+    // complex128 has no register room for two classes of a 16-wide block
+    constexpr uint32_t kPer = sizeof(R) == 4 ? 2u : 1u;
+    for (uint32_t c = kPer * threadIdx.x; c < nc; c += kPer * blockDim.x) {
+        const bool two = kPer == 2 && c + 1 < nc;
+        const uint32_t b0 = G.map.map(c);
+        const uint32_t b1 = two ? G.map.map(c + 1) : b0;
+        T2 x0[PP], x1[kPer == 2 ? PP : 1];
 #pragma unroll
         for (int k = 0; k < PP; ++k) {
-            x[k].x = 0;
-            x[k].y = 0;
-            if (lmask >> k & 1u) x[k] = tile[b + off[k]];
+            x0[k].x = 0;
+            x0[k].y = 0;
+            if (lmask >> k & 1u) x0[k] = tile[b0 + off[k]];
+            if constexpr (kPer == 2) x1[k] = (lmask >> k & 1u) ? tile[b1 + off[k]] : x0[k];
         }
         if (kind == kDense) {
 #pragma unroll
             for (int r = 0; r < PP; ++r) {
                 if (!(smask >> r & 1u)) continue;
                 const T2* Mr = M + r * PP;
-                T2 acc = fcmul(Mr[0], x[0]);
+                T2 a0, a1;
+                a0.x = a0.y = a1.x = a1.y = 0;
+                if constexpr (sizeof(R) == 4 && PP % 2 == 0) {
 #pragma unroll
-                for (int k = 1; k < PP; ++k) fcmac(acc, Mr[k], x[k]);
-                tile[b + off[r]] = acc;
+                    for (int k = 0; k < PP; k += 2) {
+                        const float4 m2 = *reinterpret_cast<const float4*>(Mr + k);
+                        const float2 mA = make_float2(m2.x, m2.y), mB = make_float2(m2.z, m2.w);
+                        fcmac(a0, mA, x0[k]);
+                        fcmac(a1, mA, x1[k]);
+                        fcmac(a0, mB, x0[k + 1]);
+                        fcmac(a1, mB, x1[k + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < PP; ++k) {
+                        const T2 m = Mr[k];
+                        fcmac(a0, m, x0[k]);
+                        if constexpr (kPer == 2) fcmac(a1, m, x1[k]);
+                    }
+                }
+                tile[b0 + off[r]] = a0;
+                if (two) tile[b1 + off[r]] = a1;
             }
         } else if (kind == kDiag) {
 #pragma unroll
             for (int r = 0; r < PP; ++r)
-                if (smask >> r & 1u) tile[b + off[r]] = fcmul(M[r * PP + r], x[r]);
+                if (smask >> r & 1u) {
+                    const T2 m = M[r * PP + r];
+                    tile[b0 + off[r]] = fcmul(m, x0[r]);
+                    if constexpr (kPer == 2)
+                        if (two) tile[b1 + off[r]] = fcmul(m, x1[r]);
+                }
         } else {
 #pragma unroll
             for (int r = 0; r < PP; ++r) {
                 if (!(smask >> r & 1u)) continue;
                 const int src = G.perm[r];
-                T2 v = x[0];
+                T2 v0 = x0[0], v1 = x1[0];
 #pragma unroll
                 for (int k = 1; k < PP; ++k)
-                    if (src == k) v = x[k];
-                tile[b + off[r]] = pure ? v : fcmul(M[r * PP + src], v);
+                    if (src == k) {
+                        v0 = x0[k];
+                        if constexpr (kPer == 2) v1 = x1[k];
+                    }
+                if (!pure) {
+                    const T2 m = M[r * PP + src];
+                    v0 = fcmul(m, v0);
+                    v1 = fcmul(m, v1);
+                }
+                tile[b0 + off[r]] = v0;
+                if constexpr (kPer == 2)
+                    if (two) tile[b1 + off[r]] = v1;
             }
         }
     }
@@ -977,6 +1016,7 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
         f.kind = kDense;
         f.lmask = f.smask = (uint16_t)((1u << P) - 1u);
     }
+    if (pool.size() % 2) pool.push_back(typename Cplx<R>::T2{});  // 16-byte aligned rows for paired loads
     f.u_off = (uint32_t)pool.size();
     for (int r = 0; r < PP; ++r)
         for (int c = 0; c < PP; ++c) {
@@ -1033,7 +1073,7 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
             const size_t need = bp.single ? (size_t)G[bp.gates[0]].plan.d * G[bp.gates[0]].plan.d
                                           : (size_t)padded_dim((int)local_prod(geo, bp.lw)) *
                                                 padded_dim((int)local_prod(geo, bp.lw));
-            if (pool.size() + need > (size_t)kPoolEntries && !fg.empty()) break;
+            if (pool.size() + need + 1 > (size_t)kPoolEntries && !fg.empty()) break;
             FGate f;
             if (bp.single) {
                 fill_single<R>(geo, G[bp.gates[0]], f, pool);
