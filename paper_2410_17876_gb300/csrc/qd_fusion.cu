@@ -276,12 +276,11 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
     }
 }
 
-// Apply one composed block (P <= PP) to the tile.  Each thread takes two
-// classes per iteration; their P members are gathered into registers (padded
-// rows are masked out), and every matrix entry read from the staged pool
-// (the same address for all threads: a broadcast) serves both classes --
-// for complex64 two adjacent entries come in one 16-byte load.  All inputs
-// are in registers before the first store.
+// Apply one composed block (P <= PP) to the tile.  A class's P members are
+// gathered into registers (padded rows are masked out); each output row is
+// accumulated from the matrix row in the staged pool, read by all threads at
+// the same address (a broadcast) -- for complex64 two adjacent entries per
+// 16-byte load.  All inputs are in registers before the first store.
 template <typename R, int PP>
 __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGate& G,
                                            const typename Cplx<R>::T2* pool) {
@@ -293,8 +292,9 @@ __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGa
 #pragma unroll
     for (int r = 0; r < PP; ++r) off[r] = G.off[r];
     const T2* M = pool + G.u_off;
-    // complex128 has no register room for two classes of a 16-wide block
-    constexpr uint32_t kPer = sizeof(R) == 4 ? 2u : 1u;
+    // one class per iteration: a second class's registers cost more than the
+    // matrix loads they would share (measured)
+    constexpr uint32_t kPer = 1u;
     for (uint32_t c = kPer * threadIdx.x; c < nc; c += kPer * blockDim.x) {
         const bool two = kPer == 2 && c + 1 < nc;
         const uint32_t b0 = G.map.map(c);
