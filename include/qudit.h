@@ -176,8 +176,13 @@ typedef struct qd_gate_desc {
     int64_t matrix_offset;
 } qd_gate_desc;
 
-#define QD_FUSE_OFF 0  /* one kernel pass per gate */
-#define QD_FUSE_TILE 1 /* shared-memory tile passes over cached wire sets */
+#define QD_FUSE_OFF 0   /* one kernel pass per gate */
+#define QD_FUSE_TILE 1  /* shared-memory tile passes over cached wire sets */
+#define QD_FUSE_BLOCK 2 /* the circuit is grouped into blocks of at most block_dim (default 64 for
+                           complex64, 8 for complex128) dimensions, each composed in binary64 and
+                           applied in one pass over the state; complex64 blocks of 17 or more
+                           dimensions run on the tensor cores (TF32 with split operands, FP32
+                           accumulation) */
 
 typedef struct qd_fusion_opts {
     int32_t mode;          /* QD_FUSE_OFF or QD_FUSE_TILE */

@@ -39,7 +39,7 @@ class qd_plan_info(ctypes.Structure):
 
 
 QD_MAX_GATE_WIRES = 6
-QD_FUSE_OFF, QD_FUSE_TILE = 0, 1
+QD_FUSE_OFF, QD_FUSE_TILE, QD_FUSE_BLOCK = 0, 1, 2
 
 
 class qd_gate_desc(ctypes.Structure):
@@ -562,9 +562,14 @@ class State:
         else:
             qd_apply_multi(self.handle, gate.wires, gate.U, gate.controls, gate.values)
 
-    def run(self, circuit, fuse: bool = False, **opts) -> None:
-        """Apply the circuit's gates through one qd_apply_circuit call (tile fusion if ``fuse``)."""
-        qd_apply_circuit(self.handle, circuit, QD_FUSE_TILE if fuse else QD_FUSE_OFF, **opts)
+    def run(self, circuit, fuse=False, **opts) -> None:
+        """Apply the circuit's gates through one qd_apply_circuit call.  ``fuse``:
+        False / "off" (one pass per gate), True / "tile" (shared-memory tile
+        passes) or "block" (composed blocks over the whole state, tensor cores
+        for large complex64 blocks)."""
+        mode = {False: QD_FUSE_OFF, "off": QD_FUSE_OFF, True: QD_FUSE_TILE, "tile": QD_FUSE_TILE,
+                "block": QD_FUSE_BLOCK}[fuse]
+        qd_apply_circuit(self.handle, circuit, mode, **opts)
 
     def run_gate_by_gate(self, circuit) -> None:
         for g in circuit.gates:

@@ -346,16 +346,37 @@ qd_status qd::apply_any(qd_state* st, const int32_t* wires, int32_t k, const dou
         if (e != cudaSuccess) return cuda_fail(e, "gate kernel");
         return QD_OK;
     }
+    if (st->prec == QD_C64 && p.P >= kTcMinP) {
+        // tensor-core block: through the circuit entry point (descriptor upload + launch)
+        qd_gate_desc g{};
+        g.n_wires = k;
+        g.n_ctrl = nc;
+        for (int i = 0; i < k; ++i) g.wires[i] = wires[i];
+        for (int i = 0; i < nc; ++i) {
+            g.ctrl_wires[i] = cw[i];
+            g.ctrl_vals[i] = cv[i];
+        }
+        g.matrix_offset = 0;
+        return qd_apply_circuit(st, &g, 1, U, nullptr);
+    }
     return st->prec == QD_C64 ? run_tile<float>(st, p, U) : run_tile<double>(st, p, U);
 }
 
 // ---------------------------------------------------------------------------
 // Readout helpers
 // ---------------------------------------------------------------------------
+static qd_status check_device_status(qd_state* st) {
+    const int32_t e = tc_status_take(st->stream);
+    if (e != 0) return fail(QD_ERR_TIMEOUT, "a tensor-core kernel gave up waiting for its MMAs (status %d)", e);
+    return QD_OK;
+}
+
 qd_status qd::read_out(qd_state* st, int count, double* host) {
     QD_CUDA(cudaMemcpyAsync(st->host_out, st->dev_out, sizeof(double) * count, cudaMemcpyDeviceToHost, st->stream),
             "readout copy");
     QD_CUDA(cudaStreamSynchronize(st->stream), "readout sync");
+    qd_status rc = check_device_status(st);
+    if (rc != QD_OK) return rc;
     std::memcpy(host, st->host_out, sizeof(double) * count);
     return QD_OK;
 }
@@ -599,7 +620,7 @@ qd_status qd_synchronize(qd_state* st) {
     QD_GUARD_BEGIN
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
     QD_CUDA(cudaStreamSynchronize(st->stream), "synchronize");
-    return QD_OK;
+    return check_device_status(st);
     QD_GUARD_END
 }
 

@@ -579,6 +579,7 @@ cudaError_t launch_batch_small(const SmallTask* tasks, int ntasks, int dmax, uin
 // ---------------------------------------------------------------------------
 struct PassPlan {
     bool tile;
+    bool block = false;  // QD_FUSE_BLOCK: gates composed into one block over the whole state
     std::vector<int> gates;
     uint64_t smask;   // cached wires
     int64_t T;
@@ -593,8 +594,13 @@ FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     c.Tmax = (o && o->max_tile_amps > 0) ? o->max_tile_amps : (prec == QD_C64 ? 8192 : 4096);
     c.min_gates = (o && o->min_gates > 0) ? o->min_gates : 2;
     c.min_row = (o && o->min_row > 0) ? o->min_row : (prec == QD_C64 ? 16 : 8);
-    c.block_dim = (o && o->block_dim > 0) ? o->block_dim : kMaxBlock;
-    if (c.block_dim > kMaxBlock) c.block_dim = kMaxBlock;
+    if (c.mode == QD_FUSE_BLOCK) {
+        c.block_dim = (o && o->block_dim > 0) ? o->block_dim : (prec == QD_C64 ? 64 : 8);
+        if (c.block_dim > 64) c.block_dim = 64;
+    } else {
+        c.block_dim = (o && o->block_dim > 0) ? o->block_dim : kMaxBlock;
+        if (c.block_dim > kMaxBlock) c.block_dim = kMaxBlock;
+    }
     // rows per tile are bounded by the row table
     const int64_t need = (c.Tmax + kMaxRows - 1) / kMaxRows;
     if (c.min_row < need) c.min_row = need;
@@ -642,9 +648,16 @@ qd_status load_gates(const Layout& L, int32_t prec, const qd_gate_desc* gates, i
 // wires fit the tile; otherwise it is deferred and blocks the wires it
 // writes (targets of non-diagonal gates) and reads (controls, diagonal
 // targets) for later gates.
+static void plan_blocks(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg,
+                        std::vector<PassPlan>& passes);
+
 static void plan_passes(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg,
                         std::vector<PassPlan>& passes) {
     passes.clear();
+    if (cfg.mode == QD_FUSE_BLOCK) {
+        plan_blocks(L, G, cfg, passes);
+        return;
+    }
     const int n = (int)G.size();
     std::vector<int> rem(n);
     for (int i = 0; i < n; ++i) rem[i] = i;
@@ -722,7 +735,7 @@ struct TileGeom {
     uint64_t free_b[kMaxWires];
 };
 
-static void tile_geometry(const Layout& L, uint64_t S, int64_t min_row, TileGeom& g) {
+static void tile_geometry(const Layout& L, uint64_t S, int64_t min_row, TileGeom& g, bool with_rows = true) {
     g.ns = 0;
     g.nfree = 0;
     for (int w = 0; w < L.n; ++w) g.loc[w] = -1;
@@ -746,6 +759,10 @@ static void tile_geometry(const Layout& L, uint64_t S, int64_t min_row, TileGeom
     g.L0 = L0;
     g.bL = (uint32_t)L.b[L0];
     g.R = (uint32_t)(g.local.D / (int64_t)g.bL);
+    if (!with_rows) {
+        g.R = 0;
+        return;
+    }
     g.rowoff.assign(g.R, 0);
     // row r enumerates the digits of the high cached wires (local wires L0..ns-1)
     for (uint32_t r = 0; r < g.R; ++r) {
@@ -795,7 +812,7 @@ static int64_t local_prod(const TileGeom& geo, uint64_t lw) {
 static double sweep_cost(int kind, int64_t P) { return 4.0 + (kind == kDense ? (double)P : 1.0); }
 
 static void form_blocks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<int>& pg, int Pmax,
-                        std::vector<BlockPlan>& out) {
+                        std::vector<BlockPlan>& out, bool one_pass_each = false) {
     out.clear();
     std::vector<int> rem = pg;
     auto outside = [&](const HGate& h) {
@@ -834,7 +851,8 @@ static void form_blocks(const TileGeom& geo, const std::vector<HGate>& G, const 
             bool all_diag = true;
             for (int idx : sel) all_diag = all_diag && G[idx].diag;
             const double cost_block = sweep_cost(all_diag ? kDiag : kDense, local_prod(geo, W));
-            if (sel.size() > 1 && cost_block <= cost_single) {
+            // one_pass_each: every block or gate costs one pass over the state
+            if (sel.size() > 1 && (one_pass_each || cost_block <= cost_single)) {
                 bp.single = false;
                 bp.gates = sel;
                 bp.lw = W;
@@ -1100,6 +1118,48 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
     return prog.put(buf.data(), buf.size());
 }
 
+// QD_FUSE_BLOCK: blocks over the whole state, one pass each.
+static void plan_blocks(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg,
+                        std::vector<PassPlan>& passes) {
+    TileGeom geo;
+    tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo, false);
+    std::vector<int> all(G.size());
+    for (size_t i = 0; i < G.size(); ++i) all[i] = (int)i;
+    std::vector<BlockPlan> blocks;
+    form_blocks(geo, G, all, cfg.block_dim, blocks, true);
+    for (const BlockPlan& bp : blocks) {
+        PassPlan p;
+        p.tile = false;
+        p.block = !bp.single;
+        p.gates = bp.gates;
+        p.smask = bp.lw;  // local wires == global wires here
+        p.T = 0;
+        passes.push_back(p);
+    }
+}
+
+// The single gate equivalent to a QD_FUSE_BLOCK pass: its wires (ascending)
+// and its composed matrix.
+static qd_status block_gate_of(const Layout& L, int32_t prec, const std::vector<HGate>& G, const PassPlan& p,
+                               std::vector<int>& wl, std::vector<double>& M, Plan& q) {
+    TileGeom geo;
+    tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo, false);
+    BlockPlan bp;
+    bp.gates = p.gates;
+    bp.lw = p.smask;
+    bp.single = false;
+    int P = 0;
+    compose_block(geo, G, bp, M, P, wl);
+    std::vector<int32_t> w32(wl.begin(), wl.end());
+    return make_plan(L, prec, w32.data(), (int32_t)w32.size(), M.data(), nullptr, nullptr, 0, q);
+}
+
+// ---------------------------------------------------------------------------
+// Programs: the launches of a circuit with their descriptors.  Building a
+// program makes no CUDA call; running it uploads the descriptors once and
+// issues the launches, so many programs can share one upload and be issued
+// on several streams or inside a CUDA graph capture.
+// ---------------------------------------------------------------------------
 qd_status Arena::upload(const void* bytes, size_t n, cudaStream_t s) {
     if (n == 0) return QD_OK;
     if (n > cap) {
@@ -1179,6 +1239,19 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog) {
         }
     }
     const int P = p.P;
+    if (sizeof(R) == 4 && P >= kTcMinP) {
+        // complex64 block of 17..64 dimensions: tensor cores
+        std::vector<float> A(block_tc_operand_bytes() / sizeof(float));
+        block_tc_pack(U, P, A.data());
+        const size_t aoff = prog.put(A.data(), block_tc_operand_bytes());
+        const uint64_t classes = p.classes;
+        const IndexMap map = p.map;
+        std::vector<uint64_t> off(p.off, p.off + P);
+        float2* dpsi = reinterpret_cast<float2*>(psi);
+        return [dpsi, aoff, classes, map, P, off](cudaStream_t s, const char* base) {
+            return launch_block_tc(dpsi, reinterpret_cast<const float*>(base + aoff), classes, map, P, off.data(), s);
+        };
+    }
     std::vector<T2> m((size_t)P * P);
     for (int i = 0; i < P * P; ++i) {
         m[i].x = (R)U[2 * i];
@@ -1214,6 +1287,15 @@ void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, cons
     std::vector<PassPlan> passes;
     plan_passes(L, G, cfg, passes);
     for (const PassPlan& p : passes) {
+        if (p.block) {
+            std::vector<int> wl;
+            std::vector<double> M;
+            Plan q;
+            if (block_gate_of(L, sizeof(R) == 4 ? QD_C64 : QD_C128, G, p, wl, M, q) != QD_OK) continue;
+            if (q.family == 0 && q.smask == 0) continue;  // identity
+            prog.ops.push_back(gate_op<R>(psi, q, M.data(), prog));
+            continue;
+        }
         if (!p.tile) {
             const HGate& h = G[p.gates[0]];
             if (h.plan.family == 0 && h.plan.smask == 0) continue;  // identity
@@ -1263,7 +1345,8 @@ qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
 }
 
 qd_status check_cfg(const FuseCfg& cfg, int32_t prec) {
-    if (cfg.mode != QD_FUSE_OFF && cfg.mode != QD_FUSE_TILE) return fail(QD_ERR_ARG, "unknown fusion mode");
+    if (cfg.mode != QD_FUSE_OFF && cfg.mode != QD_FUSE_TILE && cfg.mode != QD_FUSE_BLOCK)
+        return fail(QD_ERR_ARG, "unknown fusion mode");
     if (cfg.mode == QD_FUSE_TILE && cfg.Tmax > tile_limit(prec))
         return fail(QD_ERR_UNSUPPORTED, "tile of %lld amplitudes exceeds shared memory (limit %lld)",
                     (long long)cfg.Tmax, (long long)tile_limit(prec));
@@ -1285,7 +1368,7 @@ template <typename R>
 size_t put_small_chunks(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg, Program& prog,
                         uint32_t* nchunks) {
     TileGeom geo;
-    tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo);
+    tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo, false);
     std::vector<int> all(G.size());
     for (size_t i = 0; i < G.size(); ++i) all[i] = (int)i;
     std::vector<BlockPlan> blocks;
@@ -1309,6 +1392,14 @@ static double unit_flops(int kind, bool pure, int P, int changed_rows, double cl
 
 static double pass_arith(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg, const PassPlan& p) {
     auto popc = [](uint32_t m) { int c = 0; while (m) { c += m & 1u; m >>= 1; } return c; };
+    if (p.block) {
+        std::vector<int> wl;
+        std::vector<double> M;
+        Plan q;
+        if (block_gate_of(L, QD_C128, G, p, wl, M, q) != QD_OK) return 0.0;
+        if (q.family == 1) return 8.0 * q.P * q.P * (double)q.classes;
+        return unit_flops(q.kind, q.pure, q.d, popc(q.smask), (double)q.classes);
+    }
     if (!p.tile) {
         const Plan& q = G[p.gates[0]].plan;
         if (q.family == 1) return 8.0 * q.P * q.P * (double)q.classes;

@@ -158,6 +158,14 @@ cudaError_t launch_widen(const void* psi, int64_t D, double* out, cudaStream_t s
 template <typename R>
 cudaError_t launch_narrow(const double* in, int64_t D, void* psi, cudaStream_t s);
 
+// Tensor-core path for composed blocks (qd_tc.cu, complex64 only).
+size_t block_tc_operand_bytes();
+void block_tc_pack(const double* U, int P, float* out);
+cudaError_t launch_block_tc(float2* psi, const float* a_hilo, uint64_t n_classes, const IndexMap& map, int P,
+                            const uint64_t* off, cudaStream_t s);
+int32_t tc_status_take(cudaStream_t s);
+constexpr int kTcMinP = 17;  // complex64 blocks of at least this dimension go to the tensor cores
+
 int reduce_blocks(int64_t D);
 
 void count_launch(int n = 1);
