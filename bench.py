@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,6 +42,17 @@ L2_BYTES = 129e6
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 FP64_TFLOPS = 1.25
 ALU_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s (FP64: 1.25 TFLOP/s nominal)"
+
+
+def tf32_peak() -> float:
+    """Dense TF32 tensor peak in TFLOP/s: the measured bf16 burst figure times the
+    nominal TF32/BF16 ratio (1.1 / 2.25)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    bf16 = 1900.0
+    if os.path.exists(p):
+        with open(p) as f:
+            bf16 = float(json.load(f).get("bf16_tflops", bf16))
+    return bf16 * 1.1 / 2.25
 
 
 # ----------------------------------------------------------------------------------------------
@@ -141,8 +153,10 @@ def measured_peaks():
 KERNEL_SOURCES = {
     "gate": ("qd_kernels.cu", "qd_internal.cuh"),
     "fused": ("qd_fusion.cu", "qd_internal.cuh", "qd_program.h"),
+    "tc": ("qd_tc.cu", "qd_internal.cuh"),
 }
-TRAFFIC_FILES = {"gate": "gate_kernel_traffic.json", "fused": "fused_kernel_traffic.json"}
+TRAFFIC_FILES = {"gate": "gate_kernel_traffic.json", "fused": "fused_kernel_traffic.json",
+                 "tc": "tc_kernel_traffic.json"}
 
 
 def kernel_source_hash(kind: str = "gate") -> str:
@@ -271,7 +285,7 @@ def measure_large(qb, gen, torch, stream, amp_bytes_c64=8):
     out = {"workload": "18 qubits + 8 qutrits (1,719,926,784 amplitudes), 200 gates, complex64",
            "updates_per_circuit": upd}
     peak, _ = measured_peaks()
-    for name, fuse in (("per_gate", False), ("fused", True)):
+    for name, fuse in (("per_gate", False), ("tile_fused", "tile"), ("block_fused", "block")):
         st.reset()
         st.run(circ, fuse=fuse)
         torch.cuda.synchronize()
@@ -422,11 +436,11 @@ def run_gpu(args):
         from paper_2410_17876_gb300 import autotune
 
         tuned = autotune.tune_circuit(st, circ)
-        fuse = bool(tuned["fuse"])
+        fuse = tuned["mode"] if tuned["mode"] != "off" else False
         fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"]} if fuse else {}
     else:
-        fuse = args.fuse == "tile"
-        fopts = {"max_tile_amps": args.tile} if fuse and args.tile else {}
+        fuse = args.fuse if args.fuse != "off" else False
+        fopts = {"max_tile_amps": args.tile} if fuse == "tile" and args.tile else {}
 
     def step():
         st.reset()
@@ -463,7 +477,9 @@ def run_gpu(args):
              for g in circ.gates]
     if fuse:
         # one qd_apply_circuit call per planned pass, CUDA events around each
-        order, pass_of, tiles, pflops = qb.qd_plan_circuit(circ.dims, prec, circ, with_flops=True, **fopts)
+        mode = {"tile": qb.QD_FUSE_TILE, "block": qb.QD_FUSE_BLOCK}[fuse]
+        order, pass_of, tiles, pflops = qb.qd_plan_circuit(circ.dims, prec, circ, mode=mode, with_flops=True,
+                                                           **fopts)
         groups = [[] for _ in range(len(tiles))]
         for g_idx, p_idx in zip(order, pass_of):
             groups[p_idx].append(circ.gates[g_idx])
@@ -473,17 +489,38 @@ def run_gpu(args):
         torch.cuda.synchronize()
         evs[0].record(stream)
         for i, sc in enumerate(subs):
-            st.run(sc, fuse=True, **fopts)
+            st.run(sc, fuse=fuse, **fopts)
             evs[i + 1].record(stream)
         torch.cuda.synchronize()
-        k_time, k_flops, k_bytes, k_n = 0.0, 0.0, 0, 0
-        for i, t in enumerate(tiles):
-            if t > 0:
-                k_time += evs[i].elapsed_time(evs[i + 1]) / 1e3
-                k_flops += float(pflops[i])
-                k_bytes += 2 * amp_bytes * circ.D
-                k_n += 1
-        kname = "k_fused_tile (shared-memory tile pass, all tile passes of the circuit)"
+        fam = {}
+        for i, gl in enumerate(groups):
+            t = evs[i].elapsed_time(evs[i + 1]) / 1e3
+            wires = set()
+            for g in gl:
+                wires |= set(g.wires) | set(g.controls)
+            P = int(np.prod([circ.dims[w] for w in wires]))
+            if tiles[i] > 0:
+                k, nbytes = "tile", 2 * amp_bytes * circ.D
+            elif len(gl) > 1 and prec == qb.QD_C64 and P >= 17:
+                k, nbytes = "tc", 2 * amp_bytes * circ.D
+            else:
+                k, nbytes = "gate", algorithmic_bytes(
+                    qb.qd_plan_gate(circ.dims, prec, gl[0].wires, gl[0].U, gl[0].controls or None,
+                                    gl[0].values or None), amp_bytes) if len(gl) == 1 else 2 * amp_bytes * circ.D
+            f = fam.setdefault(k, {"time": 0.0, "bytes": 0, "flops": 0.0, "n": 0, "mma_flops": 0.0})
+            f["time"] += t
+            f["bytes"] += nbytes
+            f["flops"] += float(pflops[i])
+            f["n"] += 1
+            if k == "tc":  # 3 products x 16 k-steps of M=128, N=64, K=8 per 64 classes
+                f["mma_flops"] += math.ceil(circ.D / P / 64) * 48 * 2 * 128 * 64 * 8
+        dom = max(fam, key=lambda k: fam[k]["time"])
+        f = fam[dom]
+        kname = {"tile": "k_fused_tile (shared-memory tile pass)",
+                 "tc": "k_block_tc (tcgen05 tensor-core block pass)",
+                 "gate": "k_gate1 / k_gate_tile (per-gate passes)"}[dom]
+        k_time, k_flops, k_bytes, k_n = f["time"], f["flops"], f["bytes"], f["n"]
+        fam_summary = {k: {"seconds": v["time"], "passes": v["n"]} for k, v in fam.items()}
     else:
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(circ.gates) + 1)]
         st.reset()
@@ -500,9 +537,10 @@ def run_gpu(args):
                 k_bytes += algorithmic_bytes(p, amp_bytes)
                 k_n += 1
         kname = "k_gate1 (per-class register kernel, all gates of the circuit)"
+        dom, fam_summary = "gate", None
     peak, peak_kind = measured_peaks()
-    if fuse:
-        # a fused pass is bound by its on-chip arithmetic (composed blocks), not by HBM:
+    if fuse and dom == "tile":
+        # a tile pass is bound by its on-chip arithmetic (composed blocks), not by HBM:
         # FP32 (complex64) or FP64 (complex128) pipe peak from unit counts and clocks
         alu_peak = FP32_TFLOPS if prec == qb.QD_C64 else FP64_TFLOPS
         roof = {"kernel": kname, "bound": "alu", "achieved": k_flops / k_time / 1e12 if k_time > 0 else 0.0,
@@ -513,8 +551,15 @@ def run_gpu(args):
     else:
         achieved = k_bytes / k_time / 1e9 if k_time > 0 else 0.0
         roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind, "traffic": ncu_traffic(args.prec),
-                "launches_measured": k_n}
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": ncu_traffic(args.prec, "tc" if dom == "tc" else "gate"), "launches_measured": k_n}
+        if fuse and dom == "tc":
+            tf32 = tf32_peak()
+            roof["tensor_view"] = {"achieved_tflops": f["mma_flops"] / k_time / 1e12, "peak_tflops": tf32,
+                                   "frac": f["mma_flops"] / k_time / 1e12 / tf32,
+                                   "peak_source": "measured bf16 burst x 0.489 (nominal TF32/BF16 dense ratio)"}
+    if fam_summary:
+        roof["passes_by_kernel"] = fam_summary
 
     # ---- end to end through the public API with host buffers ----
     pinned = torch.empty(circ.D, dtype=torch.complex64 if prec == qb.QD_C64 else torch.complex128,
@@ -566,7 +611,7 @@ def run_gpu(args):
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == qb.QD_C64 else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prec": args.prec, "fusion": "tile" if fuse else "off",
+            "config": {"workload": WORKLOAD, "prec": args.prec, "fusion": fuse or "off",
                        "fusion_opts": fopts, "autotuned": tuned is not None,
                        "amplitudes": circ.D, "gates": len(circ.gates),
                        "state_bytes": circ.D * amp_bytes,
@@ -622,7 +667,8 @@ def run_ncu_fused_case(args):
     prec = qb.QD_C64 if args.prec == "c64" else qb.QD_C128
     circ = gen.config1_circuit()
     st = qb.State(circ.dims, prec=prec)
-    st.run(circ, fuse=True, **({"max_tile_amps": args.tile} if args.tile else {}))
+    fuse = "tile" if args.fuse in ("auto", "tile") else args.fuse
+    st.run(circ, fuse=fuse, **({"max_tile_amps": args.tile} if args.tile and fuse == "tile" else {}))
     st.synchronize()
     st.close()
     torch.cuda.synchronize()
@@ -635,7 +681,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
-    ap.add_argument("--fuse", choices=["auto", "tile", "off"], default="auto",
+    ap.add_argument("--fuse", choices=["auto", "tile", "block", "off"], default="auto",
                     help="tile: consecutive gates share one shared-memory pass over the state; off: one pass per "
                          "gate; auto: the autotuner's choice of the two (and of tile size and block width)")
     ap.add_argument("--tile", type=int, default=0, help="amplitudes per fused tile (0 = library default)")
@@ -647,8 +693,8 @@ def main(argv=None):
                     help="run only six dense single-wire gates (wires 0, 5, 10, 15, 19, 3) on the workload's "
                          "state, for a profiler capture of launches 4-6; prints nothing")
     ap.add_argument("--ncu-fused-case", action="store_true",
-                    help="run only the workload circuit once with tile fusion (reset + passes), for a profiler "
-                         "capture of one k_fused_tile launch; prints nothing")
+                    help="run only the workload circuit once, fused (--fuse tile or block; auto means tile), "
+                         "for a profiler capture of one fused launch; prints nothing")
     args = ap.parse_args(argv)
     if args.ncu_case:
         return run_ncu_case(args)

@@ -19,11 +19,15 @@ from typing import Callable, Dict, Iterable, Optional, Sequence, Tuple
 
 import numpy as np
 
-# (max_tile_amps, block_dim); (0, 0) = one kernel pass per gate
+# (mode, max_tile_amps, block_dim): mode 0 = one kernel pass per gate,
+# 1 = shared-memory tile passes, 2 = whole-state composed blocks
 FUSION_CANDIDATES = {
-    0: [(0, 0)] + [(t, b) for t in (2048, 4096, 8192, 16384) for b in (1, 4, 8, 16)],
-    1: [(0, 0)] + [(t, b) for t in (1024, 2048, 4096, 8192) for b in (1, 4, 8, 16)],
+    0: [(0, 0, 0)] + [(1, t, b) for t in (2048, 4096, 8192, 16384) for b in (1, 4, 8, 16)]
+       + [(2, 0, b) for b in (32, 64)],
+    1: [(0, 0, 0)] + [(1, t, b) for t in (1024, 2048, 4096, 8192) for b in (1, 4, 8, 16)]
+       + [(2, 0, b) for b in (4, 8)],
 }
+MODE_NAMES = {0: "off", 1: "tile", 2: "block"}
 
 
 def cache_path() -> str:
@@ -91,8 +95,9 @@ def time_candidates(run: Callable[[Tuple[int, int]], None], candidates: Iterable
 
 def tune_circuit(state, circuit, retune: bool = False, reps: int = 3, budget_s: float = 30.0) -> dict:
     """Best fusion settings for ``circuit`` on ``state`` (a ``binding.State`` of
-    the circuit's dims).  Returns {"max_tile_amps", "block_dim", "fuse",
-    "seconds", "table"}; the state is left in an unspecified state."""
+    the circuit's dims).  Returns {"mode" ("off" / "tile" / "block"),
+    "max_tile_amps", "block_dim", "seconds", "table"}; the state is left in
+    an unspecified state."""
     key = shape_key("circuit", state.prec, circuit.dims, len(circuit.gates))
     cache = _load()
     if not retune and key in cache:
@@ -100,15 +105,15 @@ def tune_circuit(state, circuit, retune: bool = False, reps: int = 3, budget_s: 
 
     def run(c):
         state.reset()
-        if c == (0, 0):
+        if c[0] == 0:
             state.run(circuit, fuse=False)
         else:
-            state.run(circuit, fuse=True, max_tile_amps=c[0], block_dim=c[1])
+            state.run(circuit, fuse=MODE_NAMES[c[0]], max_tile_amps=c[1], block_dim=c[2])
 
     table = time_candidates(run, FUSION_CANDIDATES[state.prec], state.stream, reps=reps, budget_s=budget_s)
     best = min(table, key=table.get)
-    entry = {"max_tile_amps": best[0], "block_dim": best[1], "fuse": best != (0, 0), "seconds": table[best],
-             "table": {f"{t}/{b}": v for (t, b), v in table.items()}}
+    entry = {"mode": MODE_NAMES[best[0]], "max_tile_amps": best[1], "block_dim": best[2], "seconds": table[best],
+             "table": {f"{MODE_NAMES[m]}/{t}/{b}": v for (m, t, b), v in table.items()}}
     cache[key] = entry
     _save(cache)
     return entry
