@@ -52,8 +52,9 @@ def test_tc_single_block_small(qb, gen):
     assert_close(got, ref, qb.QD_C64, "tc P=64")
 
 
-@pytest.mark.parametrize("wires,extra", [((3, 0, 5), ()), ((1, 4), ((2,), (1,))), ((0, 2, 6), ()),
-                                         ((5, 6, 7), ((0,), (2,))), ((2, 3, 4, 7), ())])
+@pytest.mark.parametrize("wires,extra", [((3, 0, 5), ()), ((1, 3, 4), ((2,), (1,))), ((0, 2, 6), ()),
+                                         ((5, 6, 7), ((0,), (2,))), ((2, 3, 4, 7), ()), ((3, 6, 2, 4), ()),
+                                         ((0, 1, 2), ((9,), (1,)))])
 def test_tc_block_sizes_and_controls(qb, gen, wires, extra):
     rng = np.random.Generator(np.random.PCG64(sum(wires)))
     dims = (3, 3, 2, 4, 2, 3, 4, 2, 2, 3)
