@@ -155,28 +155,42 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
     const uint64_t n_chunks = (a.n_classes + kTcN - 1) / kTcN;
     float* Y = reinterpret_cast<float*>(sB);  // staged accumulator, [128][kYStride]
 
-    for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
-        // 1. gather: thread -> class n = tid % 64, member quads q = tid / 64 + 4 j
-        const int n = tid & (kTcN - 1);
+    // thread -> class n = tid % 64 of each chunk, member quads q = tid / 64 + 4 j (j < 4)
+    const int n = tid & (kTcN - 1);
+    const int q0 = tid >> 6;
+    float2 pre[16];  // the next chunk's members, prefetched while the current chunk computes
+    uint64_t pre_base = 0;
+    bool pre_valid = false;
+    auto prefetch = [&](uint64_t chunk) {
         const uint64_t g = chunk * kTcN + (uint64_t)n;
-        const bool valid = g < a.n_classes;
-        const uint64_t base = valid ? a.map.map(g) : 0;
-#pragma unroll 1
-        for (int q = tid >> 6; q < 16; q += 4) {
-            float re[4], im[4];
+        pre_valid = chunk < n_chunks && g < a.n_classes;
+        pre_base = pre_valid ? a.map.map(g) : 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int r = 4 * q + j;
-                float2 v = make_float2(0.f, 0.f);
-                if (valid && r < a.P) v = a.psi[base + a.off[r]];
-                re[j] = v.x;
-                im[j] = v.y;
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int r = 4 * (q0 + 4 * j) + i;
+                pre[4 * j + i] = (pre_valid && r < a.P) ? a.psi[pre_base + a.off[r]] : make_float2(0.f, 0.f);
             }
+    };
+    prefetch(blockIdx.x);
+
+    for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
+        // 1. split the prefetched members into the B operands
+        const bool valid = pre_valid;
+        const uint64_t base = pre_base;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int q = q0 + 4 * j;
             float4 rh, rl, ih, il;
-            rh.x = tf32_hi(re[0]); rh.y = tf32_hi(re[1]); rh.z = tf32_hi(re[2]); rh.w = tf32_hi(re[3]);
-            ih.x = tf32_hi(im[0]); ih.y = tf32_hi(im[1]); ih.z = tf32_hi(im[2]); ih.w = tf32_hi(im[3]);
-            rl.x = re[0] - rh.x; rl.y = re[1] - rh.y; rl.z = re[2] - rh.z; rl.w = re[3] - rh.w;
-            il.x = im[0] - ih.x; il.y = im[1] - ih.y; il.z = im[2] - ih.z; il.w = im[3] - ih.w;
+            rh.x = tf32_hi(pre[4 * j].x); rh.y = tf32_hi(pre[4 * j + 1].x);
+            rh.z = tf32_hi(pre[4 * j + 2].x); rh.w = tf32_hi(pre[4 * j + 3].x);
+            ih.x = tf32_hi(pre[4 * j].y); ih.y = tf32_hi(pre[4 * j + 1].y);
+            ih.z = tf32_hi(pre[4 * j + 2].y); ih.w = tf32_hi(pre[4 * j + 3].y);
+            rl.x = pre[4 * j].x - rh.x; rl.y = pre[4 * j + 1].x - rh.y;
+            rl.z = pre[4 * j + 2].x - rh.z; rl.w = pre[4 * j + 3].x - rh.w;
+            il.x = pre[4 * j].y - ih.x; il.y = pre[4 * j + 1].y - ih.y;
+            il.z = pre[4 * j + 2].y - ih.z; il.w = pre[4 * j + 3].y - ih.w;
             // K index: real parts at 4q..4q+3, imaginary parts at 64 + 4q..
             *reinterpret_cast<float4*>(sB + kmajor_off(n, 4 * q, kTcN)) = rh;
             *reinterpret_cast<float4*>(sB + kmajor_off(n, 64 + 4 * q, kTcN)) = ih;
@@ -207,6 +221,9 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
                              smem_u32(&mbar))
                          : "memory");
         }
+        // the next chunk's loads are in flight while the tensor cores work
+        // (classes of different chunks share no amplitude)
+        prefetch(chunk + gridDim.x);
         // 3. wait for the accumulator (bounded); on timeout wait once more for
         //    the MMAs in flight before the tensor memory is released
         if (!mbar_wait(smem_u32(&mbar), phase)) {
@@ -230,14 +247,13 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        // 4. outputs: y_r = (Y[r][n], Y[64 + r][n]) for the chunk's classes, lanes along n
-        // (thread -> class n = tid % 64 as in the gather, rows r = tid / 64 + 4 j)
+        // 4. outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
         if (valid) {
 #pragma unroll 4
-            for (int r = tid >> 6; r < a.P; r += 4)
+            for (int r = q0; r < a.P; r += 4)
                 a.psi[base + a.off[r]] = make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]);
         }
-        __syncthreads();  // Y (the B region) is rewritten by the next gather
+        __syncthreads();  // Y (the B region) is rewritten by the next chunk
     }
     if (abort_flag && tid == 0) atomicExch(a.status, QD_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
