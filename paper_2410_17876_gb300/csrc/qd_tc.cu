@@ -13,15 +13,16 @@
 // A_lo X_lo term is below 2^-21 relative).
 //
 // One persistent CTA per SM keeps A_hi and A_lo (the real-embedded block in
-// the UMMA K-major canonical layout, 64 KB each) in shared memory and loops
-// over chunks of 64 classes:
-//   1. all 256 threads gather the chunk's members, split them and store the
-//      B operands (K-major, no swizzle) with 16-byte stores;
-//   2. one thread issues 3 x 16 MMAs (M = 128, N = 64, K = 8) and commits them
-//      to an mbarrier;
-//   3. the CTA waits on the mbarrier (bounded), reads the accumulator with
-//      tcgen05.ld, stages it in shared memory and writes the outputs with
-//      warps running along the classes (coalesced).
+// the UMMA K-major canonical layout, 64 KB each) in shared memory and runs a
+// two-stage pipeline over chunks of 32 classes:
+//   - the 256 threads split the next chunk's members (prefetched into
+//     registers) into that stage's B operands (K-major, no swizzle, 16-byte
+//     stores), and one thread issues its 3 x 16 MMAs (M = 128, N = 32, K = 8)
+//     into that stage's tensor-memory accumulator, committed to an mbarrier;
+//   - meanwhile the chunk after it is loaded into registers, and the current
+//     chunk's accumulator is waited for (bounded), read with tcgen05.ld,
+//     staged in shared memory and written out with warps running along the
+//     classes (coalesced).
 // Every wait is bounded: on timeout the kernel records the error in a status
 // word, stops issuing work, releases its tensor memory and returns.
 #include <cstdint>
@@ -33,12 +34,13 @@ namespace qd {
 
 namespace {
 
-constexpr int kTcN = 64;              // classes per chunk (MMA N)
+constexpr int kTcN = 32;              // classes per chunk (MMA N)
 constexpr int kTcK = 128;             // real K (64 members x re/im)
 constexpr int kTcM = 128;             // real M (64 outputs x re/im)
 constexpr uint32_t kABytes = kTcM * kTcK * 4;   // one of A_hi / A_lo
 constexpr uint32_t kBBytes = kTcN * kTcK * 4;   // one of B_hi / B_lo
-constexpr int kYStride = 68;          // floats per staged accumulator row (bank-conflict-free float4 stores)
+constexpr uint32_t kStageBytes = 2 * kBBytes;   // B_hi | B_lo of one pipeline stage
+constexpr int kYStride = kTcN + 4;    // floats per staged accumulator row (bank-conflict-free float4 stores)
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -121,9 +123,10 @@ struct TcArgs {
 
 __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                   // A_hi | A_lo
-    unsigned char* sB = smem + 2 * kABytes;     // B_hi | B_lo; reused to stage the accumulator
-    __shared__ __align__(8) uint64_t mbar;
+    unsigned char* sA = smem;                          // A_hi | A_lo
+    unsigned char* sB = smem + 2 * kABytes;            // two stages of B_hi | B_lo
+    float* Y = reinterpret_cast<float*>(sB + 2 * kStageBytes);  // staged accumulator, [128][kYStride]
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -136,29 +139,29 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
     }
     if (tid == 0) {
         abort_flag = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {
+    if (warp == 0) {  // two accumulators of kTcN columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"((uint32_t)kTcN));
+                     "r"((uint32_t)(2 * kTcN)));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem_d = tmem_base;
+    const uint32_t tmem0 = tmem_base;
     const uint32_t idesc = tc_idesc();
     const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
-    uint32_t phase = 0;
+    uint32_t phase[2] = {0u, 0u};
     const uint64_t n_chunks = (a.n_classes + kTcN - 1) / kTcN;
-    float* Y = reinterpret_cast<float*>(sB);  // staged accumulator, [128][kYStride]
 
-    // thread -> class n = tid % 64 of each chunk, member quads q = tid / 64 + 4 j (j < 4)
+    // thread -> class n = tid % 32 of each chunk, member quads q = tid / 32 + 8 j (j < 2)
     const int n = tid & (kTcN - 1);
-    const int q0 = tid >> 6;
-    float2 pre[16];  // the next chunk's members, prefetched while the current chunk computes
+    const int q0 = tid >> 5;
+    float2 pre[8];  // members of the next chunk to stage, prefetched while the tensor cores work
     uint64_t pre_base = 0;
     bool pre_valid = false;
     auto prefetch = [&](uint64_t chunk) {
@@ -166,22 +169,19 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         pre_valid = chunk < n_chunks && g < a.n_classes;
         pre_base = pre_valid ? a.map.map(g) : 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < 2; ++j)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int r = 4 * (q0 + 4 * j) + i;
+                const int r = 4 * (q0 + 8 * j) + i;
                 pre[4 * j + i] = (pre_valid && r < a.P) ? a.psi[pre_base + a.off[r]] : make_float2(0.f, 0.f);
             }
     };
-    prefetch(blockIdx.x);
-
-    for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gridDim.x) {
-        // 1. split the prefetched members into the B operands
-        const bool valid = pre_valid;
-        const uint64_t base = pre_base;
+    // split the prefetched members into stage s's B operands
+    auto stage_b = [&](int st) {
+        unsigned char* b = sB + st * kStageBytes;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int q = q0 + 4 * j;
+        for (int j = 0; j < 2; ++j) {
+            const int q = q0 + 8 * j;
             float4 rh, rl, ih, il;
             rh.x = tf32_hi(pre[4 * j].x); rh.y = tf32_hi(pre[4 * j + 1].x);
             rh.z = tf32_hi(pre[4 * j + 2].x); rh.w = tf32_hi(pre[4 * j + 3].x);
@@ -192,74 +192,102 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
             il.x = pre[4 * j].y - ih.x; il.y = pre[4 * j + 1].y - ih.y;
             il.z = pre[4 * j + 2].y - ih.z; il.w = pre[4 * j + 3].y - ih.w;
             // K index: real parts at 4q..4q+3, imaginary parts at 64 + 4q..
-            *reinterpret_cast<float4*>(sB + kmajor_off(n, 4 * q, kTcN)) = rh;
-            *reinterpret_cast<float4*>(sB + kmajor_off(n, 64 + 4 * q, kTcN)) = ih;
-            *reinterpret_cast<float4*>(sB + kBBytes + kmajor_off(n, 4 * q, kTcN)) = rl;
-            *reinterpret_cast<float4*>(sB + kBBytes + kmajor_off(n, 64 + 4 * q, kTcN)) = il;
+            *reinterpret_cast<float4*>(b + kmajor_off(n, 4 * q, kTcN)) = rh;
+            *reinterpret_cast<float4*>(b + kmajor_off(n, 64 + 4 * q, kTcN)) = ih;
+            *reinterpret_cast<float4*>(b + kBBytes + kmajor_off(n, 4 * q, kTcN)) = rl;
+            *reinterpret_cast<float4*>(b + kBBytes + kmajor_off(n, 64 + 4 * q, kTcN)) = il;
         }
+    };
+    // one thread: the 3 x 16 MMAs of stage st into accumulator st, committed to mbar[st]
+    auto issue_mma = [&](int st) {
+        const uint32_t lboA = (kTcM / 8) * 128, lboB = (kTcN / 8) * 128;
+        const uint32_t bbase = sB_u + (uint32_t)st * kStageBytes;
+        const uint32_t d = tmem0 + (uint32_t)st * kTcN;
+        uint32_t acc = 0;
+#pragma unroll 1
+        for (int term = 0; term < 3; ++term) {
+            const uint32_t aoff = term == 2 ? kABytes : 0;   // A_lo for the third product
+            const uint32_t boff = term == 1 ? kBBytes : 0;   // B_lo for the second
+#pragma unroll 1
+            for (int ks = 0; ks < kTcK / 8; ++ks) {
+                const uint64_t ad = smem_desc(sA_u + aoff + (uint32_t)ks * 2 * lboA, lboA, 128);
+                const uint64_t bd = smem_desc(bbase + boff + (uint32_t)ks * 2 * lboB, lboB, 128);
+                mma_tf32(d, ad, bd, idesc, acc);
+                acc = 1;
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&mbar[st]))
+                     : "memory");
+    };
+    auto publish_b = [&]() {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // 2. one thread issues the 3 x 16 MMAs and commits them to the mbarrier
-        if (tid == 0) {
-            const uint32_t lboA = (kTcM / 8) * 128, lboB = (kTcN / 8) * 128;
-            uint32_t acc = 0;
-#pragma unroll 1
-            for (int term = 0; term < 3; ++term) {
-                const uint32_t aoff = term == 2 ? kABytes : 0;   // A_lo for the third product
-                const uint32_t boff = term == 1 ? kBBytes : 0;   // B_lo for the second
-#pragma unroll 1
-                for (int ks = 0; ks < kTcK / 8; ++ks) {
-                    const uint64_t ad = smem_desc(sA_u + aoff + (uint32_t)ks * 2 * lboA, lboA, 128);
-                    const uint64_t bd = smem_desc(sB_u + boff + (uint32_t)ks * 2 * lboB, lboB, 128);
-                    mma_tf32(tmem_d, ad, bd, idesc, acc);
-                    acc = 1;
-                }
-            }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_u32(&mbar))
-                         : "memory");
+    };
+
+    // prologue: stage the first chunk and start its MMAs
+    uint64_t chunk = blockIdx.x;
+    prefetch(chunk);
+    bool cur_valid = pre_valid;
+    uint64_t cur_base = pre_base;
+    int st = 0;
+    stage_b(st);
+    publish_b();
+    if (chunk < n_chunks && tid == 0) issue_mma(st);
+    prefetch(chunk + gridDim.x);
+
+    for (; chunk < n_chunks; chunk += gridDim.x) {
+        const uint64_t next = chunk + gridDim.x;
+        const bool nxt_valid = pre_valid;
+        const uint64_t nxt_base = pre_base;
+        // stage the next chunk and start its MMAs while this chunk's finish
+        if (next < n_chunks) {
+            stage_b(st ^ 1);
+            publish_b();
+            if (tid == 0) issue_mma(st ^ 1);
+            prefetch(next + gridDim.x);
         }
-        // the next chunk's loads are in flight while the tensor cores work
-        // (classes of different chunks share no amplitude)
-        prefetch(chunk + gridDim.x);
-        // 3. wait for the accumulator (bounded); on timeout wait once more for
-        //    the MMAs in flight before the tensor memory is released
-        if (!mbar_wait(smem_u32(&mbar), phase)) {
+        // wait for this chunk's accumulator (bounded); on timeout wait once
+        // more for the MMAs in flight before the tensor memory is released
+        if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) {
             if (lane == 0) atomicExch(&abort_flag, 1);
-            mbar_wait(smem_u32(&mbar), phase);
+            mbar_wait(smem_u32(&mbar[st]), phase[st]);
+            if (next < n_chunks) mbar_wait(smem_u32(&mbar[st ^ 1]), phase[st ^ 1]);
         }
-        phase ^= 1u;
+        phase[st] ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         __syncthreads();
         if (abort_flag) break;
-        // TMEM -> registers -> shared: warp w reads lanes 32 (w % 4) .. +31,
-        // warps 0-3 columns 0..31, warps 4-7 columns 32..63
-        {
-            const uint32_t row = 32u * (uint32_t)(warp & 3) + (uint32_t)lane;
-            const uint32_t col = (uint32_t)(warp >> 2) * 32u;
+        // TMEM -> registers -> shared: warps 0-3 read lanes 32 w .. 32 w + 31
+        if (warp < 4) {
+            const uint32_t row = 32u * (uint32_t)warp + (uint32_t)lane;
             float v[32];
-            tmem_ld32(tmem_d + ((32u * (uint32_t)(warp & 3)) << 16) + col, v);
+            tmem_ld32(tmem0 + ((32u * (uint32_t)warp) << 16) + (uint32_t)st * kTcN, v);
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
-                *reinterpret_cast<float4*>(Y + row * kYStride + col + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                *reinterpret_cast<float4*>(Y + row * kYStride + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        // 4. outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
-        if (valid) {
+        // outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
+        if (cur_valid) {
 #pragma unroll 4
-            for (int r = q0; r < a.P; r += 4)
-                a.psi[base + a.off[r]] = make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]);
+            for (int r = q0; r < a.P; r += 8)
+                a.psi[cur_base + a.off[r]] = make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]);
         }
-        __syncthreads();  // Y (the B region) is rewritten by the next chunk
+        cur_valid = nxt_valid;
+        cur_base = nxt_base;
+        st ^= 1;
+        // Y is rewritten by the next epilogue only after the next stage_b / publish_b barrier
     }
+    __syncthreads();
     if (abort_flag && tid == 0) atomicExch(a.status, QD_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_d), "r"((uint32_t)kTcN));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem0), "r"((uint32_t)(2 * kTcN)));
 }
 
 // Status word of the tensor-core kernels: 0, or an error code set by a
@@ -338,7 +366,7 @@ cudaError_t launch_block_tc(float2* psi, const float* a_hilo, uint64_t n_classes
     static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
-    const size_t smem = 2 * (size_t)kABytes + 2 * (size_t)kBBytes;
+    const size_t smem = 2 * (size_t)kABytes + 2 * (size_t)kStageBytes + sizeof(float) * kTcM * kYStride;
     if (attr_dev != dev) {
         cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
