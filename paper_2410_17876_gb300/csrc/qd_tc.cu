@@ -12,13 +12,14 @@
 // products are accumulated: A_hi X_hi + A_hi X_lo + A_lo X_hi (the dropped
 // A_lo X_lo term is below 2^-21 relative).
 //
-// One persistent CTA per SM keeps A_hi and A_lo (the real-embedded block in
-// the UMMA K-major canonical layout, 64 KB each) in shared memory and runs a
-// two-stage pipeline over chunks of 32 classes:
+// One persistent CTA per SM keeps A_hi and A_lo in tensor memory (loaded
+// once with tcgen05.st: lane = output row, column = K) next to two FP32
+// accumulators, and runs a two-stage pipeline over chunks of 64 classes:
 //   - the 256 threads split the next chunk's members (prefetched into
-//     registers) into that stage's B operands (K-major, no swizzle, 16-byte
-//     stores), and one thread issues its 3 x 16 MMAs (M = 128, N = 32, K = 8)
-//     into that stage's tensor-memory accumulator, committed to an mbarrier;
+//     registers) into that stage's B operand in shared memory (K-major, no
+//     swizzle, 16-byte stores); one thread issues its 3 x 16 MMAs (M = 128,
+//     N = 64, K = 8, A from tensor memory) into that stage's accumulator and
+//     commits them to the stage's mbarrier;
 //   - meanwhile the chunk after it is loaded into registers, and the current
 //     chunk's accumulator is waited for (bounded), read with tcgen05.ld,
 //     staged in shared memory and written out with warps running along the
@@ -34,13 +35,14 @@ namespace qd {
 
 namespace {
 
-constexpr int kTcN = 32;              // classes per chunk (MMA N)
+constexpr int kTcN = 64;              // classes per chunk (MMA N)
 constexpr int kTcK = 128;             // real K (64 members x re/im)
 constexpr int kTcM = 128;             // real M (64 outputs x re/im)
 constexpr uint32_t kABytes = kTcM * kTcK * 4;   // one of A_hi / A_lo
 constexpr uint32_t kBBytes = kTcN * kTcK * 4;   // one of B_hi / B_lo
 constexpr uint32_t kStageBytes = 2 * kBBytes;   // B_hi | B_lo of one pipeline stage
-constexpr int kYStride = kTcN + 4;    // floats per staged accumulator row (bank-conflict-free float4 stores)
+constexpr uint32_t kTmemCols = 512;             // A_hi [0,128) A_lo [128,256) D0 [256,320) D1 [320,384)
+constexpr int kYStride = 68;          // floats per staged accumulator row (bank-conflict-free float4 stores)
 constexpr uint32_t kSpinLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -81,6 +83,35 @@ __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64
         : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+__device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+        :
+        : "r"(tmem_d), "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+        :
+        : "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+          "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+          "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+          "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+          "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])),
+          "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])),
+          "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])),
+          "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+          "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])),
+          "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])));
+}
+
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     for (uint32_t it = 0; it < kSpinLimit; ++it) {
         uint32_t done;
@@ -113,7 +144,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 struct TcArgs {
     float2* psi;
-    const float* a_hilo;  // A_hi then A_lo, each kABytes in the K-major layout
+    const float* a_hilo;  // A_hi then A_lo, each 128 x 128 row-major (row = output, column = K)
     uint64_t n_classes;
     IndexMap map;
     int32_t P;
@@ -123,45 +154,63 @@ struct TcArgs {
 
 __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;                          // A_hi | A_lo
-    unsigned char* sB = smem + 2 * kABytes;            // two stages of B_hi | B_lo
-    float* Y = reinterpret_cast<float*>(sB + 2 * kStageBytes);  // staged accumulator, [128][kYStride]
+    unsigned char* sB = smem;                                   // two stages of B_hi | B_lo
+    float* Y = reinterpret_cast<float*>(smem + 2 * kStageBytes);  // staged accumulator, [128][kYStride]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // A operands: host-prepared in the canonical layout, copied once per CTA
-    {
-        const uint4* src = reinterpret_cast<const uint4*>(a.a_hilo);
-        uint4* dst = reinterpret_cast<uint4*>(sA);
-        for (uint32_t i = tid; i < 2 * kABytes / 16; i += blockDim.x) dst[i] = src[i];
-    }
     if (tid == 0) {
         abort_flag = 0;
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    if (warp == 0) {  // two accumulators of kTcN columns
+    if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"((uint32_t)(2 * kTcN)));
+                     "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem0 = tmem_base;
+    const uint32_t tm = tmem_base;
+    // A_hi, A_lo -> tensor memory: warp w (< 4) writes lanes 32 w .. 32 w + 31
+    if (warp < 4) {
+        const uint32_t row = 32u * (uint32_t)warp + (uint32_t)lane;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h)
+#pragma unroll 1
+            for (int c = 0; c < 4; ++c) {
+                float v[32];
+                const float4* src = reinterpret_cast<const float4*>(a.a_hilo + (size_t)h * kTcM * kTcK +
+                                                                    (size_t)row * kTcK + 32 * c);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float4 t = src[i];
+                    v[4 * i] = t.x;
+                    v[4 * i + 1] = t.y;
+                    v[4 * i + 2] = t.z;
+                    v[4 * i + 3] = t.w;
+                }
+                tmem_st32(tm + ((32u * (uint32_t)warp) << 16) + (uint32_t)(h * 128 + 32 * c), v);
+            }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
     const uint32_t idesc = tc_idesc();
-    const uint32_t sA_u = smem_u32(sA), sB_u = smem_u32(sB);
-    uint32_t phase[2] = {0u, 0u};
+    const uint32_t sB_u = smem_u32(sB);
+    uint32_t phase0 = 0u, phase1 = 0u;
     const uint64_t n_chunks = (a.n_classes + kTcN - 1) / kTcN;
 
-    // thread -> class n = tid % 32 of each chunk, member quads q = tid / 32 + 8 j (j < 2)
+    // thread -> class n = tid % 64 of each chunk, member quads q = tid / 64 + 4 j (j < 4)
     const int n = tid & (kTcN - 1);
-    const int q0 = tid >> 5;
-    float2 pre[8];  // members of the next chunk to stage, prefetched while the tensor cores work
+    const int q0 = tid >> 6;
+    float2 pre[16];  // the members of the next chunk to stage
     uint64_t pre_base = 0;
     bool pre_valid = false;
     auto prefetch = [&](uint64_t chunk) {
@@ -169,19 +218,18 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         pre_valid = chunk < n_chunks && g < a.n_classes;
         pre_base = pre_valid ? a.map.map(g) : 0;
 #pragma unroll
-        for (int j = 0; j < 2; ++j)
+        for (int j = 0; j < 4; ++j)
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
-                const int r = 4 * (q0 + 8 * j) + i;
+                const int r = 4 * (q0 + 4 * j) + i;
                 pre[4 * j + i] = (pre_valid && r < a.P) ? a.psi[pre_base + a.off[r]] : make_float2(0.f, 0.f);
             }
     };
-    // split the prefetched members into stage s's B operands
     auto stage_b = [&](int st) {
         unsigned char* b = sB + st * kStageBytes;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            const int q = q0 + 8 * j;
+        for (int j = 0; j < 4; ++j) {
+            const int q = q0 + 4 * j;
             float4 rh, rl, ih, il;
             rh.x = tf32_hi(pre[4 * j].x); rh.y = tf32_hi(pre[4 * j + 1].x);
             rh.z = tf32_hi(pre[4 * j + 2].x); rh.w = tf32_hi(pre[4 * j + 3].x);
@@ -198,23 +246,19 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
             *reinterpret_cast<float4*>(b + kBBytes + kmajor_off(n, 64 + 4 * q, kTcN)) = il;
         }
     };
-    // one thread: the 3 x 16 MMAs of stage st into accumulator st, committed to mbar[st]
+    // one thread: 3 products x 16 k-steps into accumulator st, committed to mbar[st]
     auto issue_mma = [&](int st) {
-        const uint32_t lboA = (kTcM / 8) * 128, lboB = (kTcN / 8) * 128;
-        const uint32_t bbase = sB_u + (uint32_t)st * kStageBytes;
-        const uint32_t d = tmem0 + (uint32_t)st * kTcN;
-        uint32_t acc = 0;
-#pragma unroll 1
+        const uint32_t lboB = (kTcN / 8) * 128;
+        const uint64_t bd0 = smem_desc(sB_u + (uint32_t)st * kStageBytes, lboB, 128);
+        constexpr uint64_t kStepB = 2 * (kTcN / 8) * 128 / 16;  // descriptor address field: 16-byte units
+        const uint32_t d = tm + 256u + (uint32_t)st * kTcN;
+#pragma unroll
         for (int term = 0; term < 3; ++term) {
-            const uint32_t aoff = term == 2 ? kABytes : 0;   // A_lo for the third product
-            const uint32_t boff = term == 1 ? kBBytes : 0;   // B_lo for the second
-#pragma unroll 1
-            for (int ks = 0; ks < kTcK / 8; ++ks) {
-                const uint64_t ad = smem_desc(sA_u + aoff + (uint32_t)ks * 2 * lboA, lboA, 128);
-                const uint64_t bd = smem_desc(bbase + boff + (uint32_t)ks * 2 * lboB, lboB, 128);
-                mma_tf32(d, ad, bd, idesc, acc);
-                acc = 1;
-            }
+            const uint32_t a0 = tm + (term == 2 ? 128u : 0u);                       // A_lo for the third product
+            const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytes >> 4) : 0);  // B_lo for the second
+#pragma unroll
+            for (int ks = 0; ks < kTcK / 8; ++ks)
+                mma_tf32_ta(d, a0 + 8u * (uint32_t)ks, b0 + (uint64_t)ks * kStepB, idesc, (term | ks) != 0 ? 1u : 0u);
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mbar[st]))
@@ -227,67 +271,68 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     };
 
-    // prologue: stage the first chunk and start its MMAs
     uint64_t chunk = blockIdx.x;
     prefetch(chunk);
     bool cur_valid = pre_valid;
     uint64_t cur_base = pre_base;
     int st = 0;
-    stage_b(st);
+    stage_b(0);
     publish_b();
-    if (chunk < n_chunks && tid == 0) issue_mma(st);
+    if (chunk < n_chunks && tid == 0) issue_mma(0);
     prefetch(chunk + gridDim.x);
 
     for (; chunk < n_chunks; chunk += gridDim.x) {
         const uint64_t next = chunk + gridDim.x;
         const bool nxt_valid = pre_valid;
         const uint64_t nxt_base = pre_base;
-        // stage the next chunk and start its MMAs while this chunk's finish
+        // stage the next chunk and start its MMAs; they run during this chunk's epilogue
         if (next < n_chunks) {
             stage_b(st ^ 1);
             publish_b();
             if (tid == 0) issue_mma(st ^ 1);
             prefetch(next + gridDim.x);
         }
-        // wait for this chunk's accumulator (bounded); on timeout wait once
-        // more for the MMAs in flight before the tensor memory is released
-        if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) {
+        // wait for this chunk's accumulator (bounded); on timeout also wait
+        // (bounded) for the other stage before the tensor memory is released
+        uint32_t& ph = st ? phase1 : phase0;
+        if (!mbar_wait(smem_u32(&mbar[st]), ph)) {
             if (lane == 0) atomicExch(&abort_flag, 1);
-            mbar_wait(smem_u32(&mbar[st]), phase[st]);
-            if (next < n_chunks) mbar_wait(smem_u32(&mbar[st ^ 1]), phase[st ^ 1]);
+            mbar_wait(smem_u32(&mbar[st]), ph);
+            if (next < n_chunks) mbar_wait(smem_u32(&mbar[st ^ 1]), st ? phase0 : phase1);
         }
-        phase[st] ^= 1u;
+        ph ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         __syncthreads();
         if (abort_flag) break;
-        // TMEM -> registers -> shared: warps 0-3 read lanes 32 w .. 32 w + 31
-        if (warp < 4) {
-            const uint32_t row = 32u * (uint32_t)warp + (uint32_t)lane;
+        // TMEM -> registers -> shared: warp w reads lanes 32 (w % 4) .. +31,
+        // warps 0-3 columns 0..31 of the accumulator, warps 4-7 columns 32..63
+        {
+            const uint32_t row = 32u * (uint32_t)(warp & 3) + (uint32_t)lane;
+            const uint32_t col = (uint32_t)(warp >> 2) * 32u;
             float v[32];
-            tmem_ld32(tmem0 + ((32u * (uint32_t)warp) << 16) + (uint32_t)st * kTcN, v);
+            tmem_ld32(tm + ((32u * (uint32_t)(warp & 3)) << 16) + 256u + (uint32_t)st * kTcN + col, v);
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
-                *reinterpret_cast<float4*>(Y + row * kYStride + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+                *reinterpret_cast<float4*>(Y + row * kYStride + col + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         // outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
         if (cur_valid) {
 #pragma unroll 4
-            for (int r = q0; r < a.P; r += 8)
+            for (int r = q0; r < a.P; r += 4)
                 a.psi[cur_base + a.off[r]] = make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]);
         }
         cur_valid = nxt_valid;
         cur_base = nxt_base;
         st ^= 1;
-        // Y is rewritten by the next epilogue only after the next stage_b / publish_b barrier
+        // Y is rewritten only after the next iteration's publish_b barrier
     }
     __syncthreads();
     if (abort_flag && tid == 0) atomicExch(a.status, QD_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem0), "r"((uint32_t)(2 * kTcN)));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols));
 }
 
 // Status word of the tensor-core kernels: 0, or an error code set by a
@@ -324,12 +369,12 @@ int32_t tc_status_take(cudaStream_t s) {
     return h;
 }
 
-// A_hi | A_lo in the canonical layout from a P x P complex binary64 matrix
-// (row-major interleaved), padded with zeros to 64.
+// A_hi | A_lo (each 128 x 128 row-major, row = output, column = K) from a
+// P x P complex binary64 matrix (row-major interleaved), padded with zeros.
 void block_tc_pack(const double* U, int P, float* out) {
     for (int i = 0; i < 2 * kTcM * kTcK; ++i) out[i] = 0.f;
-    unsigned char* hi = reinterpret_cast<unsigned char*>(out);
-    unsigned char* lo = hi + kABytes;
+    float* hi = out;
+    float* lo = out + kTcM * kTcK;
     auto put = [&](int m, int k, double v) {
         const float f = (float)v;
         uint32_t bits;
@@ -337,9 +382,8 @@ void block_tc_pack(const double* U, int P, float* out) {
         bits &= 0xFFFFE000u;
         float h;
         __builtin_memcpy(&h, &bits, 4);
-        const float l = (float)(v - (double)h);
-        *reinterpret_cast<float*>(hi + kmajor_off((uint32_t)m, (uint32_t)k, kTcM)) = h;
-        *reinterpret_cast<float*>(lo + kmajor_off((uint32_t)m, (uint32_t)k, kTcM)) = l;
+        hi[m * kTcK + k] = h;
+        lo[m * kTcK + k] = (float)(v - (double)h);
     };
     for (int r = 0; r < P; ++r)
         for (int c = 0; c < P; ++c) {
@@ -366,7 +410,7 @@ cudaError_t launch_block_tc(float2* psi, const float* a_hilo, uint64_t n_classes
     static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
-    const size_t smem = 2 * (size_t)kABytes + 2 * (size_t)kStageBytes + sizeof(float) * kTcM * kYStride;
+    const size_t smem = 2 * (size_t)kStageBytes + sizeof(float) * kTcM * kYStride;
     if (attr_dev != dev) {
         cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
