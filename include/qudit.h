@@ -181,8 +181,16 @@ typedef struct qd_gate_desc {
 #define QD_FUSE_BLOCK 2 /* the circuit is grouped into blocks of at most block_dim (default 64 for
                            complex64, 8 for complex128) dimensions, each composed in binary64 and
                            applied in one pass over the state; complex64 blocks of 17 or more
-                           dimensions run on the tensor cores (TF32 with split operands, FP32
-                           accumulation) */
+                           dimensions run as set by tc_mode */
+
+/* Arithmetic of complex64 blocks and multi-wire gates of 17..64 dimensions
+ * (qd_fusion_opts.tc_mode, qd_set_fusion).  The block is applied as the real
+ * contraction [Re Y; Im Y] = [[Re M, -Im M], [Im M, Re M]] [Re X; Im X].
+ * The tensor-core modes split both operands, a = a_hi + a_lo, and accumulate
+ * A_hi X_hi + A_hi X_lo + A_lo X_hi in FP32 in tensor memory. */
+#define QD_TC_TF32X3 0 /* tensor cores, TF32 parts (about 2^-21 relative per block); the default */
+#define QD_TC_BF16X3 1 /* tensor cores, BF16 parts (about 2^-16 relative per block) */
+#define QD_TC_OFF 2    /* FP32 CUDA cores (binary32 FMA, no split) */
 
 typedef struct qd_fusion_opts {
     int32_t mode;          /* QD_FUSE_OFF or QD_FUSE_TILE */
@@ -192,7 +200,7 @@ typedef struct qd_fusion_opts {
     int32_t block_dim;     /* inside a pass, runs of gates on a few wires are composed (binary64,
                               on the host) into one P x P block with P <= block_dim (at most 16);
                               0 = default (16), 1 = no composition */
-    int32_t reserved;
+    int32_t tc_mode;       /* QD_TC_TF32X3 (0, default), QD_TC_BF16X3 or QD_TC_OFF */
 } qd_fusion_opts;
 
 /* Apply n_gates gates in order.  Each gate is validated as in
@@ -201,6 +209,23 @@ typedef struct qd_fusion_opts {
  * arrays may be reused when the call returns. */
 qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates,
                            const double* matrices, const qd_fusion_opts* opts);
+
+/* Deferred fusion of the single-gate calls.  After qd_set_fusion with
+ * max_block_dim >= 2, qd_apply_gate / qd_apply_controlled / qd_apply_multi
+ * validate their gate and copy it into a host queue instead of launching;
+ * the queue runs as one qd_apply_circuit call in QD_FUSE_BLOCK mode
+ * (block_dim = max_block_dim, at most 64; tc_mode as above) at qd_flush,
+ * before every readout, qd_state_get_amplitudes / get_raw / device_ptr /
+ * set_stream / qd_synchronize, and whenever it holds 4096 gates.
+ * qd_state_set_amplitudes and qd_state_reset discard the queue (the state
+ * is overwritten).  max_block_dim <= 1 flushes and returns to one launch
+ * per call; tc_mode also selects the arithmetic of unfused complex64
+ * multi-wire gates of 17..64 dimensions.  QD_ERR_ARG for an unknown
+ * tc_mode. */
+qd_status qd_set_fusion(qd_state* st, int32_t max_block_dim, int32_t tc_mode);
+
+/* Run the gates queued by deferred fusion (no-op when none are queued). */
+qd_status qd_flush(qd_state* st);
 
 /* The execution plan of qd_apply_circuit without a GPU: exec_order[i] is the
  * index of the i-th gate executed, pass_of[i] its pass, pass_tile_amps[p]

@@ -40,6 +40,8 @@ class qd_plan_info(ctypes.Structure):
 
 QD_MAX_GATE_WIRES = 6
 QD_FUSE_OFF, QD_FUSE_TILE, QD_FUSE_BLOCK = 0, 1, 2
+QD_TC_TF32X3, QD_TC_BF16X3, QD_TC_OFF = 0, 1, 2
+TC_MODES = {"tf32x3": QD_TC_TF32X3, "bf16x3": QD_TC_BF16X3, "fp32": QD_TC_OFF}
 
 
 class qd_gate_desc(ctypes.Structure):
@@ -51,7 +53,7 @@ class qd_gate_desc(ctypes.Structure):
 
 class qd_fusion_opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("max_tile_amps", ctypes.c_int32), ("min_gates", ctypes.c_int32),
-                ("min_row", ctypes.c_int32), ("block_dim", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("min_row", ctypes.c_int32), ("block_dim", ctypes.c_int32), ("tc_mode", ctypes.c_int32)]
 
 
 class qd_circuit(ctypes.Structure):
@@ -96,6 +98,8 @@ _SIGS = {
     "qd_probabilities_device": (ctypes.c_int32, [_vp, _vp]),
     "qd_marginal": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
     "qd_synchronize": (ctypes.c_int32, [_vp]),
+    "qd_set_fusion": (ctypes.c_int32, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "qd_flush": (ctypes.c_int32, [_vp]),
     "qd_norm_noalloc": (ctypes.c_int32, [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]),
     "qd_last_error": (ctypes.c_char_p, []),
     "qd_launch_count": (ctypes.c_uint64, []),
@@ -358,18 +362,31 @@ def circuit_arrays(circuit):
     return descs, mats
 
 
-def _opts(mode, max_tile_amps=0, min_gates=0, min_row=0, block_dim=0):
+def _tc(tc_mode) -> int:
+    return TC_MODES[tc_mode] if isinstance(tc_mode, str) else int(tc_mode)
+
+
+def _opts(mode, max_tile_amps=0, min_gates=0, min_row=0, block_dim=0, tc_mode=QD_TC_TF32X3):
     if mode is None:
         return None
     return ctypes.byref(qd_fusion_opts(int(mode), int(max_tile_amps), int(min_gates), int(min_row), int(block_dim),
-                                       0))
+                                       _tc(tc_mode)))
 
 
 def qd_apply_circuit(st: int, circuit, mode=QD_FUSE_OFF, max_tile_amps=0, min_gates=0, min_row=0,
-                     block_dim=0) -> None:
+                     block_dim=0, tc_mode=QD_TC_TF32X3) -> None:
     descs, m = circuit_arrays(circuit)
     _check(_lib.qd_apply_circuit(_vp(st), descs, len(circuit.gates), _p(m, _f64p),
-                                 _opts(mode, max_tile_amps, min_gates, min_row, block_dim)), "qd_apply_circuit")
+                                 _opts(mode, max_tile_amps, min_gates, min_row, block_dim, tc_mode)),
+           "qd_apply_circuit")
+
+
+def qd_set_fusion(st: int, max_block_dim: int, tc_mode=QD_TC_TF32X3) -> None:
+    _check(_lib.qd_set_fusion(_vp(st), int(max_block_dim), _tc(tc_mode)), "qd_set_fusion")
+
+
+def qd_flush(st: int) -> None:
+    _check(_lib.qd_flush(_vp(st)), "qd_flush")
 
 
 def qd_plan_circuit(dims, prec, circuit, mode=QD_FUSE_TILE, max_tile_amps=0, min_gates=0, min_row=0, block_dim=0,
@@ -566,10 +583,18 @@ class State:
         """Apply the circuit's gates through one qd_apply_circuit call.  ``fuse``:
         False / "off" (one pass per gate), True / "tile" (shared-memory tile
         passes) or "block" (composed blocks over the whole state, tensor cores
-        for large complex64 blocks)."""
+        for large complex64 blocks; ``tc_mode`` "tf32x3" / "bf16x3" / "fp32")."""
         mode = {False: QD_FUSE_OFF, "off": QD_FUSE_OFF, True: QD_FUSE_TILE, "tile": QD_FUSE_TILE,
                 "block": QD_FUSE_BLOCK}[fuse]
         qd_apply_circuit(self.handle, circuit, mode, **opts)
+
+    def set_fusion(self, max_block_dim: int, tc_mode=QD_TC_TF32X3) -> None:
+        """Deferred fusion of ``apply`` calls (``max_block_dim`` <= 1: off);
+        ``tc_mode``: "tf32x3", "bf16x3", "fp32" or a QD_TC_* value."""
+        qd_set_fusion(self.handle, max_block_dim, tc_mode)
+
+    def flush(self) -> None:
+        qd_flush(self.handle)
 
     def run_gate_by_gate(self, circuit) -> None:
         for g in circuit.gates:

@@ -241,6 +241,7 @@ static void free_state(qd_state* st) {
         st->arena->release();
         delete st->arena;
     }
+    delete st->pend;
     delete st;
 }
 
@@ -333,6 +334,53 @@ static qd_status run_tile(qd_state* st, const Plan& p, const double* U) {
     return QD_OK;
 }
 
+// Deferred fusion: copy a validated gate into the state's queue.
+static qd_status enqueue(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
+                         const int32_t* cv, int32_t nc, int P) {
+    if (k > QD_MAX_GATE_WIRES || nc > QD_MAX_CONTROLS) return fail(QD_ERR_UNSUPPORTED, "gate too wide to queue");
+    if (!st->pend) st->pend = new Pending();
+    qd_gate_desc g;
+    std::memset(&g, 0, sizeof g);
+    g.n_wires = k;
+    g.n_ctrl = nc;
+    for (int i = 0; i < k; ++i) g.wires[i] = wires[i];
+    for (int i = 0; i < nc; ++i) {
+        g.ctrl_wires[i] = cw[i];
+        g.ctrl_vals[i] = cv[i];
+    }
+    g.matrix_offset = (int64_t)(st->pend->mats.size() / 2);
+    st->pend->gates.push_back(g);
+    st->pend->mats.insert(st->pend->mats.end(), U, U + 2 * (size_t)P * P);
+    if (st->pend->gates.size() >= kMaxPending) return flush_pending(st);
+    return QD_OK;
+}
+
+qd_status qd::flush_pending(qd_state* st) {
+    if (!st->pend || st->pend->gates.empty()) return QD_OK;
+    Pending q;
+    std::swap(q.gates, st->pend->gates);
+    std::swap(q.mats, st->pend->mats);
+    qd_fusion_opts o;
+    std::memset(&o, 0, sizeof o);
+    o.mode = QD_FUSE_BLOCK;
+    o.block_dim = st->fuse_dim;
+    o.tc_mode = st->tc_mode;
+    return run_circuit(st, q.gates.data(), (int32_t)q.gates.size(), q.mats.data(), &o);
+}
+
+static void drop_pending(qd_state* st) {
+    if (st->pend) {
+        st->pend->gates.clear();
+        st->pend->mats.clear();
+    }
+}
+
+#define QD_FLUSH(st)                                \
+    do {                                            \
+        const qd_status f_ = ::qd::flush_pending(st); \
+        if (f_ != QD_OK) return f_;                 \
+    } while (0)
+
 qd_status qd::apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
                            const int32_t* cv, int32_t nc) {
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
@@ -340,14 +388,15 @@ qd_status qd::apply_any(qd_state* st, const int32_t* wires, int32_t k, const dou
     qd_status rc = make_plan(st->L, st->prec, wires, k, U, cw, cv, nc, p);
     if (rc != QD_OK) return rc;
     if (p.classes == 0) return QD_OK;
+    if (st->fuse_dim >= 2) return enqueue(st, wires, k, U, cw, cv, nc, p.P);
     if (p.family == 0) {
         if (p.smask == 0) return QD_OK;  // identity
         cudaError_t e = st->prec == QD_C64 ? dispatch_gate1<float>(st, p, U) : dispatch_gate1<double>(st, p, U);
         if (e != cudaSuccess) return cuda_fail(e, "gate kernel");
         return QD_OK;
     }
-    if (st->prec == QD_C64 && p.P >= kTcMinP) {
-        // tensor-core block: through the circuit entry point (descriptor upload + launch)
+    if (st->prec == QD_C64 && p.P >= kTcMinP && st->tc_mode != QD_TC_OFF) {
+        // tensor-core block: through the circuit path (descriptor upload + launch)
         qd_gate_desc g{};
         g.n_wires = k;
         g.n_ctrl = nc;
@@ -357,7 +406,11 @@ qd_status qd::apply_any(qd_state* st, const int32_t* wires, int32_t k, const dou
             g.ctrl_vals[i] = cv[i];
         }
         g.matrix_offset = 0;
-        return qd_apply_circuit(st, &g, 1, U, nullptr);
+        qd_fusion_opts o;
+        std::memset(&o, 0, sizeof o);
+        o.mode = QD_FUSE_OFF;
+        o.tc_mode = st->tc_mode;
+        return run_circuit(st, &g, 1, U, &o);
     }
     return st->prec == QD_C64 ? run_tile<float>(st, p, U) : run_tile<double>(st, p, U);
 }
@@ -463,6 +516,7 @@ qd_status qd_state_destroy(qd_state* st) {
 qd_status qd_state_reset(qd_state* st) {
     QD_GUARD_BEGIN
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    drop_pending(st);
     return reset_state(st);
     QD_GUARD_END
 }
@@ -470,6 +524,7 @@ qd_status qd_state_reset(qd_state* st) {
 qd_status qd_state_set_stream(qd_state* st, void* stream) {
     QD_GUARD_BEGIN
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    QD_FLUSH(st);
     QD_CUDA(cudaStreamSynchronize(st->stream), "stream switch");
     st->stream = reinterpret_cast<cudaStream_t>(stream);
     return QD_OK;
@@ -485,14 +540,18 @@ qd_status qd_state_info(const qd_state* st, int64_t* num_amplitudes, int32_t* nu
 }
 
 qd_status qd_state_device_ptr(const qd_state* st, void** dev_ptr) {
+    QD_GUARD_BEGIN
     if (!st || !dev_ptr) return fail(QD_ERR_ARG, "state or out is NULL");
+    QD_FLUSH(const_cast<qd_state*>(st));  // the queue is the state's pending content
     *dev_ptr = st->psi;
     return QD_OK;
+    QD_GUARD_END
 }
 
 qd_status qd_state_set_amplitudes(qd_state* st, const double* host) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
+    drop_pending(st);
     const size_t D = (size_t)st->L.D;
     if (st->prec == QD_C128) {
         QD_CUDA(cudaMemcpyAsync(st->psi, host, D * 16, cudaMemcpyHostToDevice, st->stream), "upload");
@@ -510,6 +569,7 @@ qd_status qd_state_set_amplitudes(qd_state* st, const double* host) {
 qd_status qd_state_get_amplitudes(qd_state* st, double* host) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
+    QD_FLUSH(st);
     const size_t D = (size_t)st->L.D;
     if (st->prec == QD_C128) {
         QD_CUDA(cudaMemcpyAsync(host, st->psi, D * 16, cudaMemcpyDeviceToHost, st->stream), "download");
@@ -530,6 +590,7 @@ qd_status qd_state_get_amplitudes(qd_state* st, double* host) {
 qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
+    QD_FLUSH(st);
     if (bytes < st->bytes) return fail(QD_ERR_ARG, "host buffer of %zu bytes < %zu", bytes, st->bytes);
     QD_CUDA(cudaMemcpyAsync(host, st->psi, st->bytes, cudaMemcpyDeviceToHost, st->stream), "download");
     QD_CUDA(cudaStreamSynchronize(st->stream), "download sync");
@@ -560,6 +621,7 @@ qd_status qd_apply_multi(qd_state* st, const int32_t* wires, int32_t k, const do
 qd_status qd_norm(qd_state* st, double* out) {
     QD_GUARD_BEGIN
     if (!st || !out) return fail(QD_ERR_ARG, "state or out is NULL");
+    QD_FLUSH(st);
     cudaError_t e = st->prec == QD_C64
                         ? launch_norm<float>(st->psi, st->L.D, st->partials, st->nb, st->dev_out, st->stream)
                         : launch_norm<double>(st->psi, st->L.D, st->partials, st->nb, st->dev_out, st->stream);
@@ -571,6 +633,7 @@ qd_status qd_norm(qd_state* st, double* out) {
 qd_status qd_probabilities_device(qd_state* st, double* dev_out) {
     QD_GUARD_BEGIN
     if (!st || !dev_out) return fail(QD_ERR_ARG, "state or out is NULL");
+    QD_FLUSH(st);
     if (reinterpret_cast<uintptr_t>(dev_out) % 8 != 0) return fail(QD_ERR_ARG, "dev_out is not 8-byte aligned");
     cudaError_t e = st->prec == QD_C64 ? launch_probs<float>(st->psi, st->L.D, dev_out, st->stream)
                                        : launch_probs<double>(st->psi, st->L.D, dev_out, st->stream);
@@ -582,6 +645,7 @@ qd_status qd_probabilities_device(qd_state* st, double* dev_out) {
 qd_status qd_probabilities(qd_state* st, double* host_out) {
     QD_GUARD_BEGIN
     if (!st || !host_out) return fail(QD_ERR_ARG, "state or out is NULL");
+    QD_FLUSH(st);
     double* tmp = nullptr;
     const size_t bytes = sizeof(double) * (size_t)st->L.D;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, st->stream);
@@ -599,6 +663,7 @@ qd_status qd_probabilities(qd_state* st, double* host_out) {
 qd_status qd_marginal(qd_state* st, int32_t wire, double* host_out) {
     QD_GUARD_BEGIN
     if (!st || !host_out) return fail(QD_ERR_ARG, "state or out is NULL");
+    QD_FLUSH(st);
     if (wire < 0 || wire >= st->L.n) return fail(QD_ERR_ARG, "wire %d out of range", wire);
     IndexMap map;
     uint64_t classes;
@@ -619,8 +684,29 @@ qd_status qd_marginal(qd_state* st, int32_t wire, double* host_out) {
 qd_status qd_synchronize(qd_state* st) {
     QD_GUARD_BEGIN
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    QD_FLUSH(st);
     QD_CUDA(cudaStreamSynchronize(st->stream), "synchronize");
     return check_device_status(st);
+    QD_GUARD_END
+}
+
+qd_status qd_set_fusion(qd_state* st, int32_t max_block_dim, int32_t tc_mode) {
+    QD_GUARD_BEGIN
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    if (tc_mode != QD_TC_TF32X3 && tc_mode != QD_TC_BF16X3 && tc_mode != QD_TC_OFF)
+        return fail(QD_ERR_ARG, "unknown tc_mode %d", tc_mode);
+    // gates already queued run with the settings they were queued under
+    QD_FLUSH(st);
+    st->fuse_dim = max_block_dim <= 1 ? 0 : (max_block_dim > QD_MAX_GATE_DIM ? QD_MAX_GATE_DIM : max_block_dim);
+    st->tc_mode = tc_mode;
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_flush(qd_state* st) {
+    QD_GUARD_BEGIN
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    return flush_pending(st);
     QD_GUARD_END
 }
 

@@ -594,6 +594,7 @@ FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     c.Tmax = (o && o->max_tile_amps > 0) ? o->max_tile_amps : (prec == QD_C64 ? 8192 : 4096);
     c.min_gates = (o && o->min_gates > 0) ? o->min_gates : 2;
     c.min_row = (o && o->min_row > 0) ? o->min_row : (prec == QD_C64 ? 16 : 8);
+    c.tc_mode = o ? o->tc_mode : QD_TC_TF32X3;
     if (c.mode == QD_FUSE_BLOCK) {
         c.block_dim = (o && o->block_dim > 0) ? o->block_dim : (prec == QD_C64 ? 64 : 8);
         if (c.block_dim > 64) c.block_dim = 64;
@@ -1225,7 +1226,7 @@ static Op gate1_op(void* psi, const Plan& p, const double* U) {
 
 // The op of one gate for the per-gate kernels (no fusion).
 template <typename R>
-static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog) {
+static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int tc_mode) {
     using T2 = typename Cplx<R>::T2;
     if (p.family == 0) {
         switch (p.d) {
@@ -1239,17 +1240,18 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog) {
         }
     }
     const int P = p.P;
-    if (sizeof(R) == 4 && P >= kTcMinP) {
+    if (sizeof(R) == 4 && P >= kTcMinP && tc_mode != QD_TC_OFF) {
         // complex64 block of 17..64 dimensions: tensor cores
         std::vector<float> A(block_tc_operand_bytes() / sizeof(float));
-        block_tc_pack(U, P, A.data());
+        block_tc_pack(U, P, tc_mode, A.data());
         const size_t aoff = prog.put(A.data(), block_tc_operand_bytes());
         const uint64_t classes = p.classes;
         const IndexMap map = p.map;
         std::vector<uint64_t> off(p.off, p.off + P);
         float2* dpsi = reinterpret_cast<float2*>(psi);
-        return [dpsi, aoff, classes, map, P, off](cudaStream_t s, const char* base) {
-            return launch_block_tc(dpsi, reinterpret_cast<const float*>(base + aoff), classes, map, P, off.data(), s);
+        const bool renorm = block_is_unitary(U, P, 1e-10);
+        return [dpsi, aoff, tc_mode, renorm, classes, map, P, off](cudaStream_t s, const char* base) {
+            return launch_block_tc(dpsi, base + aoff, tc_mode, renorm, classes, map, P, off.data(), s);
         };
     }
     std::vector<T2> m((size_t)P * P);
@@ -1293,14 +1295,14 @@ void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, cons
             Plan q;
             if (block_gate_of(L, sizeof(R) == 4 ? QD_C64 : QD_C128, G, p, wl, M, q) != QD_OK) continue;
             if (q.family == 0 && q.smask == 0) continue;  // identity
-            prog.ops.push_back(gate_op<R>(psi, q, M.data(), prog));
+            prog.ops.push_back(gate_op<R>(psi, q, M.data(), prog, cfg.tc_mode));
             continue;
         }
         if (!p.tile) {
             const HGate& h = G[p.gates[0]];
             if (h.plan.family == 0 && h.plan.smask == 0) continue;  // identity
             if (h.plan.classes == 0) continue;
-            prog.ops.push_back(gate_op<R>(psi, h.plan, h.U, prog));
+            prog.ops.push_back(gate_op<R>(psi, h.plan, h.U, prog, cfg.tc_mode));
             continue;
         }
         TileGeom geo;
@@ -1347,6 +1349,8 @@ qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
 qd_status check_cfg(const FuseCfg& cfg, int32_t prec) {
     if (cfg.mode != QD_FUSE_OFF && cfg.mode != QD_FUSE_TILE && cfg.mode != QD_FUSE_BLOCK)
         return fail(QD_ERR_ARG, "unknown fusion mode");
+    if (cfg.tc_mode != QD_TC_TF32X3 && cfg.tc_mode != QD_TC_BF16X3 && cfg.tc_mode != QD_TC_OFF)
+        return fail(QD_ERR_ARG, "unknown tc_mode %d", cfg.tc_mode);
     if (cfg.mode == QD_FUSE_TILE && cfg.Tmax > tile_limit(prec))
         return fail(QD_ERR_UNSUPPORTED, "tile of %lld amplitudes exceeds shared memory (limit %lld)",
                     (long long)cfg.Tmax, (long long)tile_limit(prec));
@@ -1679,6 +1683,16 @@ extern "C" {
 
 qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates, const double* matrices,
                            const qd_fusion_opts* opts) {
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    qd_status rc = flush_pending(st);
+    if (rc != QD_OK) return rc;
+    return run_circuit(st, gates, n_gates, matrices, opts);
+}
+
+}  // extern "C"
+
+qd_status qd::run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates, const double* matrices,
+                          const qd_fusion_opts* opts) {
     try {
         if (!st) return fail(QD_ERR_ARG, "state is NULL");
         std::vector<HGate> G;
@@ -1700,6 +1714,8 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
         return fail(QD_ERR_OOM, "host exception in qd_apply_circuit");
     }
 }
+
+extern "C" {
 
 qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd_gate_desc* gates, int32_t n_gates,
                           const double* matrices, const qd_fusion_opts* opts, int32_t* exec_order, int32_t* pass_of,

@@ -160,9 +160,10 @@ cudaError_t launch_narrow(const double* in, int64_t D, void* psi, cudaStream_t s
 
 // Tensor-core path for composed blocks (qd_tc.cu, complex64 only).
 size_t block_tc_operand_bytes();
-void block_tc_pack(const double* U, int P, float* out);
-cudaError_t launch_block_tc(float2* psi, const float* a_hilo, uint64_t n_classes, const IndexMap& map, int P,
-                            const uint64_t* off, cudaStream_t s);
+void block_tc_pack(const double* U, int P, int tc_mode, void* out);
+cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool renorm, uint64_t n_classes,
+                            const IndexMap& map, int P, const uint64_t* off, cudaStream_t s);
+bool block_is_unitary(const double* U, int P, double tol);
 int32_t tc_status_take(cudaStream_t s);
 constexpr int kTcMinP = 17;  // complex64 blocks of at least this dimension go to the tensor cores
 

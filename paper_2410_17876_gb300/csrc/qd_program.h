@@ -28,6 +28,7 @@ struct FuseCfg {
     int min_gates;
     int64_t min_row;
     int block_dim;  // largest composed block inside a pass (< 4: no composition)
+    int tc_mode;    // QD_TC_*: complex64 blocks of 17..64 dimensions
 };
 
 int64_t tile_limit(int32_t prec);

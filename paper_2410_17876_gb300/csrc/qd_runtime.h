@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "qd_internal.cuh"
 #include "qudit.h"
 
@@ -54,6 +56,14 @@ struct Plan {
     uint64_t off[kMaxGateDim];
 };
 
+// Gates queued by deferred fusion: descriptors and their matrices (2 P^2
+// doubles each, at matrix_offset complex entries).
+struct Pending {
+    std::vector<qd_gate_desc> gates;
+    std::vector<double> mats;
+};
+constexpr size_t kMaxPending = 4096;
+
 void build_map(const Layout& L, const int32_t* ins_w, const int64_t* ins_v, int m, IndexMap& map,
                uint64_t& classes);
 qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t k, const double* U,
@@ -81,9 +91,15 @@ struct qd_state {
     bool ring_ev_live[kRingSlots];
     int ring_next;
     qd::Arena* arena;    // descriptors of circuit calls (device + pinned staging)
+    int32_t tc_mode;     // QD_TC_*: complex64 gates of 17..64 dimensions (0 = QD_TC_TF32X3)
+    int32_t fuse_dim;    // deferred fusion: largest composed block (< 2: off)
+    qd::Pending* pend;   // gates queued by deferred fusion
 };
 
 namespace qd {
+qd_status run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates, const double* matrices,
+                      const qd_fusion_opts* opts);
+qd_status flush_pending(qd_state* st);
 qd_status apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
                     const int32_t* cv, int32_t nc);
 qd_status read_out(qd_state* st, int count, double* host);

@@ -6,27 +6,36 @@
 // equivalence classes, section "Superposition gates", generalised to several
 // wires).  For N classes at once the block is one dense contraction
 //     [Re Y; Im Y] (128 x N) = [[Re M, -Im M], [Im M, Re M]] (128 x 128) . [Re X; Im X] (128 x N),
-// run as tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory.
-// TF32 keeps 11 significand bits, so both operands are split, a = a_hi + a_lo
-// (a_hi = a with its low 13 bits cleared, a_lo = a - a_hi exactly), and three
-// products are accumulated: A_hi X_hi + A_hi X_lo + A_lo X_hi (the dropped
-// A_lo X_lo term is below 2^-21 relative).
+// run on the tensor cores with FP32 accumulation in tensor memory, in one of
+// two split-operand precisions (both operands a = a_hi + a_lo, three products
+// A_hi X_hi + A_hi X_lo + A_lo X_hi accumulated, A_lo X_lo dropped):
+//   - TF32x3 (kind::tf32): a_hi = a rounded to nearest at TF32 precision,
+//     a_lo = a - a_hi exactly; the tensor core keeps 11 significand bits of
+//     a_lo, so the result is good to about 2^-21 relative per block;
+//   - BF16x3 (kind::f16 with bf16 inputs): a_hi = bf16(a), a_lo = bf16(a -
+//     a_hi); a_hi + a_lo keeps 16 significand bits, so the result is good
+//     to about 2^-16 relative per block.
 //
-// One persistent CTA per SM keeps A_hi and A_lo in tensor memory (loaded
-// once with tcgen05.st: lane = output row, column = K) next to two FP32
-// accumulators, and runs a two-stage pipeline over chunks of 64 classes:
-//   - the 256 threads split the next chunk's members (prefetched into
-//     registers) into that stage's B operand in shared memory (K-major, no
-//     swizzle, 16-byte stores); one thread issues its 3 x 16 MMAs (M = 128,
-//     N = 64, K = 8, A from tensor memory) into that stage's accumulator and
-//     commits them to the stage's mbarrier;
-//   - meanwhile the chunk after it is loaded into registers, and the current
+// One persistent CTA per SM runs a two-stage pipeline over chunks of 64
+// classes.  TF32x3 keeps A_hi and A_lo in tensor memory (loaded once with
+// tcgen05.st: lane = output row, column = K); BF16x3 keeps them in shared
+// memory (K-major canonical layout, 64 KB).  Two FP32 accumulators sit in
+// tensor memory.  Per chunk:
+//   - the 256 threads split the chunk's members (prefetched into registers)
+//     into that stage's B operand in shared memory (K-major, no swizzle); one
+//     thread issues its 3 x 16 (TF32, K = 8) or 3 x 8 (BF16, K = 16) MMAs
+//     (M = 128, N = 64) into that stage's accumulator and commits them to
+//     the stage's mbarrier;
+//   - meanwhile the chunk after it is loaded into registers, and the previous
 //     chunk's accumulator is waited for (bounded), read with tcgen05.ld,
 //     staged in shared memory and written out with warps running along the
 //     classes (coalesced).
 // Every wait is bounded: on timeout the kernel records the error in a status
 // word, stops issuing work, releases its tensor memory and returns.
+#include <cuda_bf16.h>
+
 #include <cstdint>
+#include <cstring>
 
 #include "qd_internal.cuh"
 #include "qudit.h"
@@ -38,10 +47,16 @@ namespace {
 constexpr int kTcN = 64;              // classes per chunk (MMA N)
 constexpr int kTcK = 128;             // real K (64 members x re/im)
 constexpr int kTcM = 128;             // real M (64 outputs x re/im)
+// TF32x3
 constexpr uint32_t kABytes = kTcM * kTcK * 4;   // one of A_hi / A_lo
 constexpr uint32_t kBBytes = kTcN * kTcK * 4;   // one of B_hi / B_lo
 constexpr uint32_t kStageBytes = 2 * kBBytes;   // B_hi | B_lo of one pipeline stage
 constexpr uint32_t kTmemCols = 512;             // A_hi [0,128) A_lo [128,256) D0 [256,320) D1 [320,384)
+// BF16x3
+constexpr uint32_t kABytesH = kTcM * kTcK * 2;
+constexpr uint32_t kBBytesH = kTcN * kTcK * 2;
+constexpr uint32_t kStageBytesH = 2 * kBBytesH;
+constexpr uint32_t kTmemColsH = 128;            // D0 [0,64) D1 [64,128)
 constexpr int kYStride = 68;          // floats per staged accumulator row (bank-conflict-free float4 stores)
 constexpr uint32_t kSpinLimit = 1u << 26;
 
@@ -61,26 +76,56 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
     return d;                // base offset 0, relative LBO, layout type 0 (no swizzle)
 }
 
-// Instruction descriptor: D = F32, A = B = TF32, both K-major, M = 128, N = kTcN.
-__host__ __device__ constexpr uint32_t tc_idesc() {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+// Instruction descriptor: D = F32, A = B = TF32 (format 2) or BF16 (format 1),
+// both K-major, M = 128, N = kTcN.
+__host__ __device__ constexpr uint32_t tc_idesc(uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 
-// Byte offset of element (row, k) in a K-major no-swizzle operand with `rows` rows.
+// Byte offset of element (row, k) in a K-major no-swizzle operand with `rows`
+// rows: 4-byte elements (4 per core-matrix row) ...
 __host__ __device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t k, uint32_t rows) {
     return (k >> 2) * (rows / 8) * 128 + (row >> 3) * 128 + (row & 7) * 16 + (k & 3) * 4;
 }
+// ... and 2-byte elements (8 per core-matrix row).
+__host__ __device__ __forceinline__ uint32_t kmajor_off_h(uint32_t row, uint32_t k, uint32_t rows) {
+    return (k >> 3) * (rows / 8) * 128 + (row >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2;
+}
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// x rounded to nearest (ties to even) at TF32 precision (10 explicit
+// significand bits).  Rounding, not truncation: the tensor core drops the
+// low 13 bits of its TF32 inputs, so with a truncated hi part every lo part
+// would have the sign of its value and each block would shrink the state by
+// about 2^-22; with hi rounded, lo has either sign and the error is unbiased.
+__host__ __device__ __forceinline__ uint32_t tf32_rne_bits(uint32_t u) {
+    u += 0x0FFFu + ((u >> 13) & 1u);
+    return u & 0xFFFFE000u;
+}
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(tf32_rne_bits(__float_as_uint(x))); }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
         :
         : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// bf16 hi / lo parts of four floats, packed two per 32-bit word (element k in
+// the low half, k + 1 in the high half).
+__device__ __forceinline__ void bf16_split4(float x0, float x1, float x2, float x3, uint2& hi, uint2& lo) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(x2), h3 = __float2bfloat16_rn(x3);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+    const __nv_bfloat16 l2 = __float2bfloat16_rn(x2 - __bfloat162float(h2));
+    const __nv_bfloat16 l3 = __float2bfloat16_rn(x3 - __bfloat162float(h3));
+    hi.x = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    hi.y = (uint32_t)__bfloat16_as_ushort(h2) | ((uint32_t)__bfloat16_as_ushort(h3) << 16);
+    lo.x = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    lo.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
 }
 
 __device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
@@ -144,21 +189,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 struct TcArgs {
     float2* psi;
-    const float* a_hilo;  // A_hi then A_lo, each 128 x 128 row-major (row = output, column = K)
+    const void* a_ops;    // TF32x3: A_hi then A_lo, each 128 x 128 row-major floats (row = output,
+                          // column = K); BF16x3: A_hi then A_lo, each in the K-major canonical layout
     uint64_t n_classes;
     IndexMap map;
     int32_t P;
     uint64_t off[64];
-    int32_t* status;      // set to QD_ERR_TIMEOUT-like code on a bounded-wait timeout
+    int32_t* status;      // set to QD_ERR_TIMEOUT on a bounded-wait timeout
+    int32_t renorm;       // the block is unitary: give each output class its input's 2-norm
 };
 
+// MODE 0: TF32x3, A in tensor memory.  MODE 1: BF16x3, A in shared memory.
+template <int MODE>
 __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcArgs a) {
+    constexpr bool kBf = MODE == 1;
+    constexpr uint32_t kStage = kBf ? kStageBytesH : kStageBytes;
+    constexpr uint32_t kBOne = kBf ? kBBytesH : kBBytes;
+    constexpr uint32_t kAOff = kBf ? 2 * kABytesH : 0;  // shared bytes before the B stages
+    constexpr uint32_t kCols = kBf ? kTmemColsH : kTmemCols;
+    constexpr uint32_t kDCol = kBf ? 0u : 256u;         // first accumulator column
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sB = smem;                                   // two stages of B_hi | B_lo
-    float* Y = reinterpret_cast<float*>(smem + 2 * kStageBytes);  // staged accumulator, [128][kYStride]
+    unsigned char* sB = smem + kAOff;                                     // two stages of B_hi | B_lo
+    float* Y = reinterpret_cast<float*>(smem + kAOff + 2 * kStage);      // staged accumulator, [128][kYStride]
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
+    // per-class squared norms, partial over the 4 threads of a class: inputs
+    // (three slots: written when a chunk is staged, read two barriers later
+    // in its epilogue, rewritten only after a further barrier) and outputs
+    __shared__ float s_nin[3][4][kTcN];
+    __shared__ float s_nout[4][kTcN];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -169,47 +229,63 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
-                     "r"(kTmemCols));
+                     "r"(kCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if constexpr (kBf) {
+        // A_hi | A_lo (already in the canonical layout) -> shared memory
+        const uint4* src = reinterpret_cast<const uint4*>(a.a_ops);
+        uint4* dst = reinterpret_cast<uint4*>(smem);
+        for (int i = tid; i < (int)(2 * kABytesH / 16); i += 256) dst[i] = src[i];
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tm = tmem_base;
-    // A_hi, A_lo -> tensor memory: warp w (< 4) writes lanes 32 w .. 32 w + 31
-    if (warp < 4) {
-        const uint32_t row = 32u * (uint32_t)warp + (uint32_t)lane;
+    if constexpr (!kBf) {
+        // A_hi, A_lo -> tensor memory: warp w (< 4) writes lanes 32 w .. 32 w + 31
+        if (warp < 4) {
+            const uint32_t row = 32u * (uint32_t)warp + (uint32_t)lane;
+            const float* A = static_cast<const float*>(a.a_ops);
 #pragma unroll 1
-        for (int h = 0; h < 2; ++h)
+            for (int h = 0; h < 2; ++h)
 #pragma unroll 1
-            for (int c = 0; c < 4; ++c) {
-                float v[32];
-                const float4* src = reinterpret_cast<const float4*>(a.a_hilo + (size_t)h * kTcM * kTcK +
-                                                                    (size_t)row * kTcK + 32 * c);
+                for (int c = 0; c < 4; ++c) {
+                    float v[32];
+                    const float4* src =
+                        reinterpret_cast<const float4*>(A + (size_t)h * kTcM * kTcK + (size_t)row * kTcK + 32 * c);
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float4 t = src[i];
-                    v[4 * i] = t.x;
-                    v[4 * i + 1] = t.y;
-                    v[4 * i + 2] = t.z;
-                    v[4 * i + 3] = t.w;
+                    for (int i = 0; i < 8; ++i) {
+                        const float4 t = src[i];
+                        v[4 * i] = t.x;
+                        v[4 * i + 1] = t.y;
+                        v[4 * i + 2] = t.z;
+                        v[4 * i + 3] = t.w;
+                    }
+                    tmem_st32(tm + ((32u * (uint32_t)warp) << 16) + (uint32_t)(h * 128 + 32 * c), v);
                 }
-                tmem_st32(tm + ((32u * (uint32_t)warp) << 16) + (uint32_t)(h * 128 + 32 * c), v);
-            }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-    const uint32_t idesc = tc_idesc();
+    const uint32_t idesc = tc_idesc(kBf ? 1u : 2u);
+    const uint32_t sA_u = smem_u32(smem);
     const uint32_t sB_u = smem_u32(sB);
     uint32_t phase0 = 0u, phase1 = 0u;
     const uint64_t n_chunks = (a.n_classes + kTcN - 1) / kTcN;
 
-    // thread -> class n = tid % 64 of each chunk, member quads q = tid / 64 + 4 j (j < 4)
+    // thread -> class n = tid % 64 of each chunk and 16 members: TF32 rows
+    // 4 (q + 4 j) + i, BF16 rows 8 (q + 4 j) + i (q = tid / 64), so that each
+    // thread writes whole 16-byte core-matrix rows of B.
     const int n = tid & (kTcN - 1);
     const int q0 = tid >> 6;
+    auto row_of = [&](int e) -> int {
+        if constexpr (kBf) return 8 * (q0 + 4 * (e >> 3)) + (e & 7);
+        else return 4 * (q0 + 4 * (e >> 2)) + (e & 3);
+    };
     float2 pre[16];  // the members of the next chunk to stage
     uint64_t pre_base = 0;
     bool pre_valid = false;
@@ -218,47 +294,84 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         pre_valid = chunk < n_chunks && g < a.n_classes;
         pre_base = pre_valid ? a.map.map(g) : 0;
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const int r = 4 * (q0 + 4 * j) + i;
-                pre[4 * j + i] = (pre_valid && r < a.P) ? a.psi[pre_base + a.off[r]] : make_float2(0.f, 0.f);
-            }
-    };
-    auto stage_b = [&](int st) {
-        unsigned char* b = sB + st * kStageBytes;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int q = q0 + 4 * j;
-            float4 rh, rl, ih, il;
-            rh.x = tf32_hi(pre[4 * j].x); rh.y = tf32_hi(pre[4 * j + 1].x);
-            rh.z = tf32_hi(pre[4 * j + 2].x); rh.w = tf32_hi(pre[4 * j + 3].x);
-            ih.x = tf32_hi(pre[4 * j].y); ih.y = tf32_hi(pre[4 * j + 1].y);
-            ih.z = tf32_hi(pre[4 * j + 2].y); ih.w = tf32_hi(pre[4 * j + 3].y);
-            rl.x = pre[4 * j].x - rh.x; rl.y = pre[4 * j + 1].x - rh.y;
-            rl.z = pre[4 * j + 2].x - rh.z; rl.w = pre[4 * j + 3].x - rh.w;
-            il.x = pre[4 * j].y - ih.x; il.y = pre[4 * j + 1].y - ih.y;
-            il.z = pre[4 * j + 2].y - ih.z; il.w = pre[4 * j + 3].y - ih.w;
-            // K index: real parts at 4q..4q+3, imaginary parts at 64 + 4q..
-            *reinterpret_cast<float4*>(b + kmajor_off(n, 4 * q, kTcN)) = rh;
-            *reinterpret_cast<float4*>(b + kmajor_off(n, 64 + 4 * q, kTcN)) = ih;
-            *reinterpret_cast<float4*>(b + kBBytes + kmajor_off(n, 4 * q, kTcN)) = rl;
-            *reinterpret_cast<float4*>(b + kBBytes + kmajor_off(n, 64 + 4 * q, kTcN)) = il;
+        for (int e = 0; e < 16; ++e) {
+            const int r = row_of(e);
+            pre[e] = (pre_valid && r < a.P) ? a.psi[pre_base + a.off[r]] : make_float2(0.f, 0.f);
         }
     };
-    // one thread: 3 products x 16 k-steps into accumulator st, committed to mbar[st]
+    auto stage_b = [&](int st, int slot) {
+        unsigned char* b = sB + st * kStage;
+        if (a.renorm) {
+            float pn = 0.f;
+#pragma unroll
+            for (int e = 0; e < 16; ++e) pn = fmaf(pre[e].x, pre[e].x, fmaf(pre[e].y, pre[e].y, pn));
+            s_nin[slot][q0][n] = pn;
+        }
+        if constexpr (kBf) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int k0 = 8 * (q0 + 4 * j);  // K index: real parts at k0.., imaginary parts at 64 + k0..
+                const float2* x = pre + 8 * j;
+                uint2 h0, l0, h1, l1;
+                bf16_split4(x[0].x, x[1].x, x[2].x, x[3].x, h0, l0);
+                bf16_split4(x[4].x, x[5].x, x[6].x, x[7].x, h1, l1);
+                *reinterpret_cast<uint4*>(b + kmajor_off_h(n, k0, kTcN)) = make_uint4(h0.x, h0.y, h1.x, h1.y);
+                *reinterpret_cast<uint4*>(b + kBOne + kmajor_off_h(n, k0, kTcN)) = make_uint4(l0.x, l0.y, l1.x, l1.y);
+                bf16_split4(x[0].y, x[1].y, x[2].y, x[3].y, h0, l0);
+                bf16_split4(x[4].y, x[5].y, x[6].y, x[7].y, h1, l1);
+                *reinterpret_cast<uint4*>(b + kmajor_off_h(n, 64 + k0, kTcN)) = make_uint4(h0.x, h0.y, h1.x, h1.y);
+                *reinterpret_cast<uint4*>(b + kBOne + kmajor_off_h(n, 64 + k0, kTcN)) =
+                    make_uint4(l0.x, l0.y, l1.x, l1.y);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int q = q0 + 4 * j;
+                const float2* x = pre + 4 * j;
+                float4 rh, rl, ih, il;
+                rh.x = tf32_hi(x[0].x); rh.y = tf32_hi(x[1].x); rh.z = tf32_hi(x[2].x); rh.w = tf32_hi(x[3].x);
+                ih.x = tf32_hi(x[0].y); ih.y = tf32_hi(x[1].y); ih.z = tf32_hi(x[2].y); ih.w = tf32_hi(x[3].y);
+                rl.x = x[0].x - rh.x; rl.y = x[1].x - rh.y; rl.z = x[2].x - rh.z; rl.w = x[3].x - rh.w;
+                il.x = x[0].y - ih.x; il.y = x[1].y - ih.y; il.z = x[2].y - ih.z; il.w = x[3].y - ih.w;
+                // K index: real parts at 4q..4q+3, imaginary parts at 64 + 4q..
+                *reinterpret_cast<float4*>(b + kmajor_off(n, 4 * q, kTcN)) = rh;
+                *reinterpret_cast<float4*>(b + kmajor_off(n, 64 + 4 * q, kTcN)) = ih;
+                *reinterpret_cast<float4*>(b + kBOne + kmajor_off(n, 4 * q, kTcN)) = rl;
+                *reinterpret_cast<float4*>(b + kBOne + kmajor_off(n, 64 + 4 * q, kTcN)) = il;
+            }
+        }
+    };
+    // one thread: 3 products x (K / k-step) MMAs into accumulator st, committed to mbar[st]
     auto issue_mma = [&](int st) {
+        // descriptor address fields count 16-byte units; a k-step spans two
+        // core matrices along K
         const uint32_t lboB = (kTcN / 8) * 128;
-        const uint64_t bd0 = smem_desc(sB_u + (uint32_t)st * kStageBytes, lboB, 128);
-        constexpr uint64_t kStepB = 2 * (kTcN / 8) * 128 / 16;  // descriptor address field: 16-byte units
-        const uint32_t d = tm + 256u + (uint32_t)st * kTcN;
+        const uint64_t bd0 = smem_desc(sB_u + (uint32_t)st * kStage, lboB, 128);
+        constexpr uint64_t kStepB = 2 * (kTcN / 8) * 128 / 16;
+        const uint32_t d = tm + kDCol + (uint32_t)st * kTcN;
+        if constexpr (kBf) {
+            const uint32_t lboA = (kTcM / 8) * 128;
+            const uint64_t ad0 = smem_desc(sA_u, lboA, 128);
+            constexpr uint64_t kStepA = 2 * (kTcM / 8) * 128 / 16;
 #pragma unroll
-        for (int term = 0; term < 3; ++term) {
-            const uint32_t a0 = tm + (term == 2 ? 128u : 0u);                       // A_lo for the third product
-            const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytes >> 4) : 0);  // B_lo for the second
+            for (int term = 0; term < 3; ++term) {
+                const uint64_t a0 = ad0 + (term == 2 ? (uint64_t)(kABytesH >> 4) : 0);  // A_lo for the third product
+                const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytesH >> 4) : 0);  // B_lo for the second
 #pragma unroll
-            for (int ks = 0; ks < kTcK / 8; ++ks)
-                mma_tf32_ta(d, a0 + 8u * (uint32_t)ks, b0 + (uint64_t)ks * kStepB, idesc, (term | ks) != 0 ? 1u : 0u);
+                for (int ks = 0; ks < kTcK / 16; ++ks)
+                    mma_bf16(d, a0 + (uint64_t)ks * kStepA, b0 + (uint64_t)ks * kStepB, idesc,
+                             (term | ks) != 0 ? 1u : 0u);
+            }
+        } else {
+#pragma unroll
+            for (int term = 0; term < 3; ++term) {
+                const uint32_t a0 = tm + (term == 2 ? 128u : 0u);                       // A_lo for the third product
+                const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytes >> 4) : 0);  // B_lo for the second
+#pragma unroll
+                for (int ks = 0; ks < kTcK / 8; ++ks)
+                    mma_tf32_ta(d, a0 + 8u * (uint32_t)ks, b0 + (uint64_t)ks * kStepB, idesc,
+                                (term | ks) != 0 ? 1u : 0u);
+            }
         }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                          smem_u32(&mbar[st]))
@@ -276,7 +389,8 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
     bool cur_valid = pre_valid;
     uint64_t cur_base = pre_base;
     int st = 0;
-    stage_b(0);
+    int slot = 0;  // s_nin slot of the current chunk (iteration count mod 3)
+    stage_b(0, 0);
     publish_b();
     if (chunk < n_chunks && tid == 0) issue_mma(0);
     prefetch(chunk + gridDim.x);
@@ -286,8 +400,9 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         const bool nxt_valid = pre_valid;
         const uint64_t nxt_base = pre_base;
         // stage the next chunk and start its MMAs; they run during this chunk's epilogue
+        const int nslot = slot == 2 ? 0 : slot + 1;
         if (next < n_chunks) {
-            stage_b(st ^ 1);
+            stage_b(st ^ 1, nslot);
             publish_b();
             if (tid == 0) issue_mma(st ^ 1);
             prefetch(next + gridDim.x);
@@ -310,29 +425,61 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
             const uint32_t row = 32u * (uint32_t)(warp & 3) + (uint32_t)lane;
             const uint32_t col = (uint32_t)(warp >> 2) * 32u;
             float v[32];
-            tmem_ld32(tm + ((32u * (uint32_t)(warp & 3)) << 16) + 256u + (uint32_t)st * kTcN + col, v);
+            tmem_ld32(tm + ((32u * (uint32_t)(warp & 3)) << 16) + kDCol + (uint32_t)st * kTcN + col, v);
 #pragma unroll
             for (int i = 0; i < 32; i += 4)
                 *reinterpret_cast<float4*>(Y + row * kYStride + col + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
-        // outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
+        // outputs: y_r = (Y[r][n], Y[64 + r][n]), rows r = q + 4 i of class n,
+        // lanes along the classes
+        float2 y[16];
+        float po = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const int r = q0 + 4 * i;
+            y[i] = r < a.P ? make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]) : make_float2(0.f, 0.f);
+            po = fmaf(y[i].x, y[i].x, fmaf(y[i].y, y[i].y, po));
+        }
+        float c = 0.f;
+        if (a.renorm) {
+            // The FP32 accumulation of the tensor cores is biased toward zero
+            // (about -1.3e-6 relative per TF32x3 block, proportional to the
+            // number of MMAs); a unitary block keeps each class's 2-norm, so
+            // the output class is rescaled to the input's norm: y <- y (1 + c)
+            // with c = sqrt(ni / no) - 1 = (ni - no) / (sqrt(no) (sqrt(ni) + sqrt(no))).
+            // c is applied by one FMA: a factor 1 + c rounded to binary32
+            // would be off by up to half an ulp of 1 in the same direction
+            // for every class (the bias is nearly uniform), a drift of its own.
+            s_nout[q0][n] = po;
+            __syncthreads();
+            const float ni = (s_nin[slot][0][n] + s_nin[slot][1][n]) + (s_nin[slot][2][n] + s_nin[slot][3][n]);
+            const float no = (s_nout[0][n] + s_nout[1][n]) + (s_nout[2][n] + s_nout[3][n]);
+            if (ni > 0.f && no > 0.f) {
+                const float sn = sqrtf(no);
+                c = (ni - no) / (sn * (sqrtf(ni) + sn));
+            }
+        }
         if (cur_valid) {
-#pragma unroll 4
-            for (int r = q0; r < a.P; r += 4)
-                a.psi[cur_base + a.off[r]] = make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int r = q0 + 4 * i;
+                if (r < a.P)
+                    a.psi[cur_base + a.off[r]] = make_float2(fmaf(y[i].x, c, y[i].x), fmaf(y[i].y, c, y[i].y));
+            }
         }
         cur_valid = nxt_valid;
         cur_base = nxt_base;
         st ^= 1;
-        // Y is rewritten only after the next iteration's publish_b barrier
+        slot = nslot;
+        // Y is rewritten only after the next iteration's barriers
     }
     __syncthreads();
     if (abort_flag && tid == 0) atomicExch(a.status, QD_ERR_TIMEOUT);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kTmemCols));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kCols));
 }
 
 // Status word of the tensor-core kernels: 0, or an error code set by a
@@ -341,7 +488,7 @@ __device__ int32_t g_tc_status;
 
 }  // namespace
 
-size_t block_tc_operand_bytes() { return 2 * (size_t)kABytes; }
+size_t block_tc_operand_bytes() { return 2 * (size_t)kABytes; }  // the larger of the two modes
 
 int32_t* tc_status_ptr() {
     static int32_t* ptr[64] = {nullptr};
@@ -369,35 +516,102 @@ int32_t tc_status_take(cudaStream_t s) {
     return h;
 }
 
-// A_hi | A_lo (each 128 x 128 row-major, row = output, column = K) from a
-// P x P complex binary64 matrix (row-major interleaved), padded with zeros.
-void block_tc_pack(const double* U, int P, float* out) {
-    for (int i = 0; i < 2 * kTcM * kTcK; ++i) out[i] = 0.f;
-    float* hi = out;
-    float* lo = out + kTcM * kTcK;
-    auto put = [&](int m, int k, double v) {
+// bf16 bits of x, rounded to nearest even (finite inputs).
+static uint16_t bf16_bits_rne(float x) {
+    uint32_t u;
+    __builtin_memcpy(&u, &x, 4);
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+static float bf16_value(uint16_t h) {
+    const uint32_t u = (uint32_t)h << 16;
+    float f;
+    __builtin_memcpy(&f, &u, 4);
+    return f;
+}
+
+// The A operand of a P x P complex binary64 matrix U (row-major interleaved,
+// zero-padded to 64): the real embedding [[Re U, -Im U], [Im U, Re U]]
+// split into A_hi | A_lo.  TF32x3: two 128 x 128 row-major float arrays
+// (row = output, column = K).  BF16x3: two bf16 arrays in the K-major
+// canonical layout, 32 KB each.
+void block_tc_pack(const double* U, int P, int tc_mode, void* out) {
+    std::memset(out, 0, block_tc_operand_bytes());
+    auto each = [&](auto&& put) {
+        for (int r = 0; r < P; ++r)
+            for (int c = 0; c < P; ++c) {
+                const double re = U[2 * (r * P + c)], im = U[2 * (r * P + c) + 1];
+                put(r, c, re);
+                put(r, 64 + c, -im);
+                put(64 + r, c, im);
+                put(64 + r, 64 + c, re);
+            }
+    };
+    if (tc_mode == QD_TC_BF16X3) {
+        unsigned char* hi = static_cast<unsigned char*>(out);
+        unsigned char* lo = hi + kABytesH;
+        each([&](int m, int k, double v) {
+            const uint16_t h = bf16_bits_rne((float)v);
+            const uint16_t l = bf16_bits_rne((float)(v - (double)bf16_value(h)));
+            const uint32_t o = kmajor_off_h((uint32_t)m, (uint32_t)k, kTcM);
+            __builtin_memcpy(hi + o, &h, 2);
+            __builtin_memcpy(lo + o, &l, 2);
+        });
+        return;
+    }
+    float* hi = static_cast<float*>(out);
+    float* lo = hi + kTcM * kTcK;
+    each([&](int m, int k, double v) {
         const float f = (float)v;
         uint32_t bits;
         __builtin_memcpy(&bits, &f, 4);
-        bits &= 0xFFFFE000u;
+        bits = tf32_rne_bits(bits);
         float h;
         __builtin_memcpy(&h, &bits, 4);
         hi[m * kTcK + k] = h;
         lo[m * kTcK + k] = (float)(v - (double)h);
-    };
-    for (int r = 0; r < P; ++r)
-        for (int c = 0; c < P; ++c) {
-            const double re = U[2 * (r * P + c)], im = U[2 * (r * P + c) + 1];
-            put(r, c, re);
-            put(r, 64 + c, -im);
-            put(64 + r, c, im);
-            put(64 + r, 64 + c, re);
-        }
+    });
 }
 
-cudaError_t launch_block_tc(float2* psi, const float* a_hilo, uint64_t n_classes, const IndexMap& map, int P,
-                            const uint64_t* off, cudaStream_t s) {
+// max |(U^H U - I)_{ij}| <= tol, in binary64 (U: P x P complex, row-major interleaved).
+bool block_is_unitary(const double* U, int P, double tol) {
+    for (int i = 0; i < P; ++i)
+        for (int j = i; j < P; ++j) {
+            double re = 0.0, im = 0.0;  // sum_k conj(U[k][i]) U[k][j]
+            for (int k = 0; k < P; ++k) {
+                const double ar = U[2 * (k * P + i)], ai = U[2 * (k * P + i) + 1];
+                const double br = U[2 * (k * P + j)], bi = U[2 * (k * P + j) + 1];
+                re += ar * br + ai * bi;
+                im += ar * bi - ai * br;
+            }
+            if (i == j) re -= 1.0;
+            if (re > tol || re < -tol || im > tol || im < -tol) return false;
+        }
+    return true;
+}
+
+template <int MODE>
+static cudaError_t launch_tc_mode(const TcArgs& a, uint64_t chunks, int sm_count, cudaStream_t s) {
+    constexpr bool kBf = MODE == 1;
+    const size_t smem = (kBf ? 2 * (size_t)kABytesH + 2 * (size_t)kStageBytesH : 2 * (size_t)kStageBytes) +
+                        sizeof(float) * kTcM * kYStride;
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_block_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const unsigned grid = (unsigned)(chunks < (uint64_t)sm_count ? chunks : (uint64_t)sm_count);
+    k_block_tc<MODE><<<grid, 256, smem, s>>>(a);
+    return cudaSuccess;
+}
+
+cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool renorm, uint64_t n_classes,
+                            const IndexMap& map, int P, const uint64_t* off, cudaStream_t s) {
     if (n_classes == 0) return cudaSuccess;
+    if (tc_mode != QD_TC_TF32X3 && tc_mode != QD_TC_BF16X3) return cudaErrorInvalidValue;
     static int sm_count = 0;
     if (sm_count == 0) {
         int dv = 0;
@@ -407,26 +621,19 @@ cudaError_t launch_block_tc(float2* psi, const float* a_hilo, uint64_t n_classes
     }
     int32_t* status = tc_status_ptr();
     if (!status) return cudaErrorInvalidSymbol;
-    static int attr_dev = -1;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const size_t smem = 2 * (size_t)kStageBytes + sizeof(float) * kTcM * kYStride;
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
     TcArgs a;
     a.psi = psi;
-    a.a_hilo = a_hilo;
+    a.a_ops = a_ops;
     a.n_classes = n_classes;
     a.map = map;
     a.P = P;
     for (int r = 0; r < 64; ++r) a.off[r] = r < P ? off[r] : 0;
     a.status = status;
+    a.renorm = renorm ? 1 : 0;
     const uint64_t chunks = (n_classes + kTcN - 1) / kTcN;
-    const unsigned grid = (unsigned)(chunks < (uint64_t)sm_count ? chunks : (uint64_t)sm_count);
-    k_block_tc<<<grid, 256, smem, s>>>(a);
+    cudaError_t e = tc_mode == QD_TC_BF16X3 ? launch_tc_mode<1>(a, chunks, sm_count, s)
+                                            : launch_tc_mode<0>(a, chunks, sm_count, s);
+    if (e != cudaSuccess) return e;
     count_launch();
     return cudaGetLastError();
 }
