@@ -276,27 +276,40 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------------------
+LARGE_PATHS = (("per_gate", False, None), ("tile_fused", "tile", None), ("block_fused_tf32x3", "block", "tf32x3"),
+               ("block_fused_bf16x3", "block", "bf16x3"), ("block_fused_fp32", "block", "fp32"))
+
+
 def measure_large(qb, gen, torch, stream, amp_bytes_c64=8):
     """18 qubits + 8 qutrits (1,719,926,784 amplitudes, 13.76 GB complex64), 200 gates:
-    one timed run per path; the per-gate kernel's HBM fraction on its dense gates."""
+    one timed run per path -- per-gate kernels, shared-memory tile passes, and
+    composed blocks of up to 64 dimensions on TF32x3 / BF16x3 tensor cores or
+    FP32 CUDA cores; the per-gate kernel's HBM fraction on its dense gates.
+    Each path also runs the circuit's 20-wire prefix; those outputs are kept
+    (``_prefix``) for the comparison with the FP64 oracle in the CPU leg."""
     circ = gen.config2_circuit()
     upd = circuit_updates(circ)
     st = qb.State(circ.dims, prec=qb.QD_C64, stream=stream)
     out = {"workload": "18 qubits + 8 qutrits (1,719,926,784 amplitudes), 200 gates, complex64",
            "updates_per_circuit": upd}
     peak, _ = measured_peaks()
-    for name, fuse in (("per_gate", False), ("tile_fused", "tile"), ("block_fused", "block")):
+    for name, fuse, tc in LARGE_PATHS:
+        kw = {"tc_mode": tc} if tc else {}
         st.reset()
-        st.run(circ, fuse=fuse)
+        st.run(circ, fuse=fuse, **kw)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         st.reset()
         e0.record(stream)
-        st.run(circ, fuse=fuse)
+        st.run(circ, fuse=fuse, **kw)
         e1.record(stream)
         torch.cuda.synchronize()
         t = e0.elapsed_time(e1) / 1e3
         out[name] = {"seconds": t, "value": upd / t, "unit": UNIT}
+        if fuse == "block":
+            mode = qb.QD_FUSE_BLOCK
+            _, _, tiles, _ = qb.qd_plan_circuit(circ.dims, qb.QD_C64, circ, mode=mode, with_flops=True)
+            out[name]["passes"] = len(tiles)
     # per-launch roofline of the dense single-wire gates (uncontrolled Haar)
     dense = [g for g in circ.gates if not g.controls][:12]
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(dense) + 1)]
@@ -309,6 +322,17 @@ def measure_large(qb, gen, torch, stream, amp_bytes_c64=8):
     gbs = len(dense) * 2 * amp_bytes_c64 * circ.D / tt / 1e9
     out["dense_gate_kernel"] = {"achieved_gbs": gbs, "frac_of_measured_hbm": gbs / peak, "launches": len(dense)}
     st.close()
+    torch.cuda.empty_cache()
+    # the 20-wire prefix through every path (outputs for the oracle comparison)
+    pre = gen.prefix_circuit(circ, 20)
+    sp = qb.State(pre.dims, prec=qb.QD_C64, stream=stream)
+    outs = {}
+    for name, fuse, tc in LARGE_PATHS:
+        sp.reset()
+        sp.run(pre, fuse=fuse, **({"tc_mode": tc} if tc else {}))
+        outs[name] = sp.raw().astype(np.complex64)
+    sp.close()
+    out["_prefix"] = (pre, outs)
     return out
 
 
@@ -339,16 +363,15 @@ def measure_batched(qb, gen, torch, stream):
             "first_run_wall_s": t_first, "generate_s": t_gen, "max_norm_error": float(np.max(np.abs(norms - 1.0)))}
 
 
-def measure_serving(qb, gen, torch, duration=3.0, plain_budget_s=6.0, oracle_budget_s=20.0):
+def measure_serving(qb, gen, torch, duration=3.0, plain_budget_s=6.0):
     """Open-loop serving: Poisson arrivals (mean 2000/s) for ``duration`` seconds of circuits
     with widths 4-16, dims {2,3,4}, 16 <= D <= 1.6e7, depths 50-500, complex64 states with
     FP64 norms.  All requests are submitted ahead with their arrival times on the server
-    clock.  p50/p99 latency = done - arrival.  1% of the requests (those with D <= 2^20)
-    are kept and compared with the FP64 oracle.  The plain path -- one circuit at a time,
+    clock.  p50/p99 latency = done - arrival.  1% of the requests (drawn among those with
+    D <= 2^20) are kept (``_sample``) for the comparison with the FP64 oracle in the CPU
+    leg.  The plain path -- one circuit at a time,
     complex128, one kernel per gate, state created and destroyed per request -- is timed
     on the same circuits in arrival order for about ``plain_budget_s`` seconds."""
-    import oracle
-
     trace = gen.config4_trace(duration=duration)
     circs = [c for _, c in trace]
     arr = np.array([t for t, _ in trace])
@@ -373,16 +396,8 @@ def measure_serving(qb, gen, torch, duration=3.0, plain_budget_s=6.0, oracle_bud
     done = np.array([res[i]["t_done"] for i in ids])
     ok = all(res[i]["status"] == 0 for i in ids)
     span = float(done.max() - (base + arr.min()))
-    errs, infs = [], []
-    t0 = time.perf_counter()
-    for i in sample:
-        if time.perf_counter() - t0 > oracle_budget_s:
-            break
-        got = qb.qd_server_get_amplitudes(srv, ids[i], circs[i].D)
-        ref = oracle.run_circuit(circs[i], nthreads=oracle.max_threads())
-        errs.append(float(np.max(np.abs(got - ref))))
-        ov = np.vdot(ref, got)
-        infs.append(float(1 - abs(ov) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real)))
+    # the sampled requests' results, compared with the FP64 oracle in the CPU leg
+    kept = [(circs[i], qb.qd_server_get_amplitudes(srv, ids[i], circs[i].D).astype(np.complex64)) for i in sample]
     qb.qd_server_destroy(srv)
     # plain path: complex128, one circuit at a time, one kernel per gate
     n_plain, t_plain = 0, 0.0
@@ -403,12 +418,48 @@ def measure_serving(qb, gen, torch, duration=3.0, plain_budget_s=6.0, oracle_bud
             "circuits_per_s": served_cps, "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "offered_updates_per_s": float(upd.sum() / duration),
             "served_updates_per_s": float(upd.sum() / span), "all_ok": ok, "submission_late": bool(late),
-            "oracle_sample": {"requests": len(errs), "max_abs_err": max(errs) if errs else None,
-                              "max_infidelity": max(infs) if infs else None,
-                              "rule": "1% of requests drawn among those with D <= 2^20"},
+            "_sample": kept,
             "plain_c128_one_at_a_time": {"circuits_per_s": plain_cps, "requests_timed": n_plain,
                                          "seconds": t_plain},
             "served_over_plain": served_cps / plain_cps}
+
+
+def oracle_checks(extra, nthreads: int, budget_s: float = 60.0) -> dict:
+    """CPU leg: the FP64 oracle on what the GPU measurements kept -- the large
+    workload's 20-wire prefix (every path's error) and the 1% serving sample
+    (until ``budget_s`` is spent).  Fills the reports in ``extra`` in place."""
+    import oracle
+
+    def errs(ref, got):
+        got = np.asarray(got, dtype=np.complex128)
+        ov = np.vdot(ref, got)
+        inf = float(1 - abs(ov) ** 2 / (np.vdot(ref, ref).real * np.vdot(got, got).real))
+        return float(np.max(np.abs(got - ref))), inf
+
+    t0 = time.perf_counter()
+    if "large_state" in extra:
+        pre, outs = extra["large_state"].pop("_prefix")
+        ref = oracle.run_circuit(pre, nthreads=nthreads)
+        rep = {"prefix": f"lowest 20 wires ({pre.D} amplitudes), {len(pre.gates)} gates"}
+        for name, got in outs.items():
+            e, inf = errs(ref, got)
+            g64 = np.asarray(got, dtype=np.complex128)
+            rep[name] = {"max_abs_err": e, "infidelity": inf, "norm_minus_1": float(np.vdot(g64, g64).real - 1.0)}
+        extra["large_state"]["error_vs_fp64_oracle"] = rep
+    if "serving" in extra:
+        kept = extra["serving"].pop("_sample")
+        es, infs = [], []
+        for c, got in kept:
+            if time.perf_counter() - t0 > budget_s:
+                break
+            e, inf = errs(oracle.run_circuit(c, nthreads=nthreads), got)
+            es.append(e)
+            infs.append(inf)
+        extra["serving"]["oracle_sample"] = {"requests": len(es), "of_sampled": len(kept),
+                                             "max_abs_err": max(es) if es else None,
+                                             "max_infidelity": max(infs) if infs else None,
+                                             "rule": "1% of requests drawn among those with D <= 2^20"}
+    return {"seconds": time.perf_counter() - t0}
 
 
 def run_gpu(args):
@@ -603,6 +654,11 @@ def run_gpu(args):
         cpu = {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
                "sample": f"first {n} of the 500 gates on the full 26,873,856-amplitude state, FP64, "
                          f"{dt:.1f} s"}
+        if extra:
+            cpu["checks"] = oracle_checks(extra, nthreads)
+    for rep in extra.values():  # outputs kept for checks that did not run
+        for k in [k for k in rep if k.startswith("_")]:
+            rep.pop(k)
     st.close()
 
     if rank == 0:

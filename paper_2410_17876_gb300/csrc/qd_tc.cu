@@ -199,32 +199,97 @@ struct TcArgs {
     int32_t renorm;       // the block is unitary: give each output class its input's 2-norm
 };
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Barrier among the consumer warps only (named barrier 1, NC threads).
+template <int NC>
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(NC) : "memory");
+}
+
+// Barrier among the consumer warps (named barrier 2) that also ORs a flag
+// over them: every consumer gets the same answer, so all of them leave the
+// loop together (none is left waiting at a later barrier).
+template <int NC>
+__device__ __forceinline__ bool consumer_sync_or(bool flag) {
+    uint32_t any;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 2, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(any)
+        : "r"((uint32_t)flag), "n"(NC)
+        : "memory");
+    return any != 0;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
 // MODE 0: TF32x3, A in tensor memory.  MODE 1: BF16x3, A in shared memory.
+// Warp-specialised, three roles that meet only at mbarriers (every wait
+// bounded):
+//   producers (warps 0..7): load a chunk's members into registers (two
+//     chunks in flight: the next chunk's loads are issued before the current
+//     one is staged), split them and write the B operand of stage s;
+//   MMA warp (warp 12, one thread): issues the chunk's 3 x 16 (TF32, K = 8)
+//     or 3 x 8 (BF16, K = 16) MMAs (M = 128, N = 64) into accumulator s;
+//   consumers (warps 8..11): read accumulator s (tcgen05.ld), stage it in
+//     shared memory and write the outputs with lanes along the classes.
+// Barriers: full[s] producers -> MMA (stage s staged); mma[s] commit ->
+// consumers (accumulator s ready) and producers (stage s free again);
+// dfree[s] consumers -> MMA (accumulator s read out).
+constexpr int kProd = 256;  // producer threads: 4 per class, 16 members each
+constexpr int kCons = 128;  // consumer threads: 2 per class, 32 outputs each
+constexpr int kTcThreads = kProd + kCons + 32;
+constexpr int kNinSlots = 8;  // producers run at most 4 chunks ahead of the consumers' norm reads
+
 template <int MODE>
-__global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constant__ TcArgs a) {
     constexpr bool kBf = MODE == 1;
+    constexpr int GP = kProd / 64, MPT = 64 / GP;  // producer threads per class, members per thread
+    constexpr int GC = kCons / 64, OPT = 64 / GC;  // consumer threads per class, outputs per thread
+    constexpr int PW = kProd / 32, CWn = kCons / 32;
+    constexpr int MMA_WARP = PW + CWn;
     constexpr uint32_t kStage = kBf ? kStageBytesH : kStageBytes;
     constexpr uint32_t kBOne = kBf ? kBBytesH : kBBytes;
     constexpr uint32_t kAOff = kBf ? 2 * kABytesH : 0;  // shared bytes before the B stages
     constexpr uint32_t kCols = kBf ? kTmemColsH : kTmemCols;
     constexpr uint32_t kDCol = kBf ? 0u : 256u;         // first accumulator column
+    static_assert(CWn == 4, "one consumer warp per TMEM lane quarter");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sB = smem + kAOff;                                     // two stages of B_hi | B_lo
     float* Y = reinterpret_cast<float*>(smem + kAOff + 2 * kStage);      // staged accumulator, [128][kYStride]
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t mbar_mma[2], mbar_full[2], mbar_dfree[2];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
-    // per-class squared norms, partial over the 4 threads of a class: inputs
-    // (three slots: written when a chunk is staged, read two barriers later
-    // in its epilogue, rewritten only after a further barrier) and outputs
-    __shared__ float s_nin[3][4][kTcN];
-    __shared__ float s_nout[4][kTcN];
+    // per-class squared norms: inputs (partial over the GP producers of a
+    // class, slot = chunk iteration mod kNinSlots) and outputs (over the GC
+    // consumers)
+    __shared__ float s_nin[kNinSlots][GP][kTcN];
+    __shared__ float s_nout[GC][kTcN];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
         abort_flag = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[1])), "r"(1));
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_mma[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_full[i])), "r"(PW));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar_dfree[i])), "r"(CWn));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -236,7 +301,7 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         // A_hi | A_lo (already in the canonical layout) -> shared memory
         const uint4* src = reinterpret_cast<const uint4*>(a.a_ops);
         uint4* dst = reinterpret_cast<uint4*>(smem);
-        for (int i = tid; i < (int)(2 * kABytesH / 16); i += 256) dst[i] = src[i];
+        for (int i = tid; i < (int)(2 * kABytesH / 16); i += kTcThreads) dst[i] = src[i];
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -271,209 +336,248 @@ __global__ void __launch_bounds__(256, 1) k_block_tc(const __grid_constant__ TcA
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
 
-    const uint32_t idesc = tc_idesc(kBf ? 1u : 2u);
-    const uint32_t sA_u = smem_u32(smem);
-    const uint32_t sB_u = smem_u32(sB);
-    uint32_t phase0 = 0u, phase1 = 0u;
     const uint64_t n_chunks = (a.n_classes + kTcN - 1) / kTcN;
+    const uint64_t gs = gridDim.x;
 
-    // thread -> class n = tid % 64 of each chunk and 16 members: TF32 rows
-    // 4 (q + 4 j) + i, BF16 rows 8 (q + 4 j) + i (q = tid / 64), so that each
-    // thread writes whole 16-byte core-matrix rows of B.
-    const int n = tid & (kTcN - 1);
-    const int q0 = tid >> 6;
-    auto row_of = [&](int e) -> int {
-        if constexpr (kBf) return 8 * (q0 + 4 * (e >> 3)) + (e & 7);
-        else return 4 * (q0 + 4 * (e >> 2)) + (e & 3);
-    };
-    float2 pre[16];  // the members of the next chunk to stage
-    uint64_t pre_base = 0;
-    bool pre_valid = false;
-    auto prefetch = [&](uint64_t chunk) {
-        const uint64_t g = chunk * kTcN + (uint64_t)n;
-        pre_valid = chunk < n_chunks && g < a.n_classes;
-        pre_base = pre_valid ? a.map.map(g) : 0;
+    if (warp == MMA_WARP) {
+        // ---------------- MMA warp ----------------
+        if (lane == 0) {
+            const uint32_t idesc = tc_idesc(kBf ? 1u : 2u);
+            const uint32_t sA_u = smem_u32(smem);
+            const uint32_t sB_u = smem_u32(sB);
+            uint32_t ph_full[2] = {0u, 0u}, ph_df[2] = {0u, 0u};
+            int issued[2] = {0, 0};
+            int i = 0;
+            for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gs, ++i) {
+                const int st = i & 1;
+                if (i >= 2) {
+                    if (!mbar_wait(smem_u32(&mbar_dfree[st]), ph_df[st])) {
+                        atomicExch(&abort_flag, 1);
+                        break;
+                    }
+                    ph_df[st] ^= 1u;
+                }
+                if (!mbar_wait(smem_u32(&mbar_full[st]), ph_full[st])) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                ph_full[st] ^= 1u;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // descriptor address fields count 16-byte units; a k-step spans
+                // two core matrices along K
+                const uint32_t lboB = (kTcN / 8) * 128;
+                const uint64_t bd0 = smem_desc(sB_u + (uint32_t)st * kStage, lboB, 128);
+                constexpr uint64_t kStepB = 2 * (kTcN / 8) * 128 / 16;
+                const uint32_t d = tm + kDCol + (uint32_t)st * kTcN;
+                if constexpr (kBf) {
+                    const uint32_t lboA = (kTcM / 8) * 128;
+                    const uint64_t ad0 = smem_desc(sA_u, lboA, 128);
+                    constexpr uint64_t kStepA = 2 * (kTcM / 8) * 128 / 16;
 #pragma unroll
-        for (int e = 0; e < 16; ++e) {
-            const int r = row_of(e);
-            pre[e] = (pre_valid && r < a.P) ? a.psi[pre_base + a.off[r]] : make_float2(0.f, 0.f);
-        }
-    };
-    auto stage_b = [&](int st, int slot) {
-        unsigned char* b = sB + st * kStage;
-        if (a.renorm) {
-            float pn = 0.f;
+                    for (int term = 0; term < 3; ++term) {
+                        const uint64_t a0 = ad0 + (term == 2 ? (uint64_t)(kABytesH >> 4) : 0);  // A_lo, third product
+                        const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytesH >> 4) : 0);  // B_lo, second
 #pragma unroll
-            for (int e = 0; e < 16; ++e) pn = fmaf(pre[e].x, pre[e].x, fmaf(pre[e].y, pre[e].y, pn));
-            s_nin[slot][q0][n] = pn;
-        }
-        if constexpr (kBf) {
+                        for (int ks = 0; ks < kTcK / 16; ++ks)
+                            mma_bf16(d, a0 + (uint64_t)ks * kStepA, b0 + (uint64_t)ks * kStepB, idesc,
+                                     (term | ks) != 0 ? 1u : 0u);
+                    }
+                } else {
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                const int k0 = 8 * (q0 + 4 * j);  // K index: real parts at k0.., imaginary parts at 64 + k0..
-                const float2* x = pre + 8 * j;
-                uint2 h0, l0, h1, l1;
-                bf16_split4(x[0].x, x[1].x, x[2].x, x[3].x, h0, l0);
-                bf16_split4(x[4].x, x[5].x, x[6].x, x[7].x, h1, l1);
-                *reinterpret_cast<uint4*>(b + kmajor_off_h(n, k0, kTcN)) = make_uint4(h0.x, h0.y, h1.x, h1.y);
-                *reinterpret_cast<uint4*>(b + kBOne + kmajor_off_h(n, k0, kTcN)) = make_uint4(l0.x, l0.y, l1.x, l1.y);
-                bf16_split4(x[0].y, x[1].y, x[2].y, x[3].y, h0, l0);
-                bf16_split4(x[4].y, x[5].y, x[6].y, x[7].y, h1, l1);
-                *reinterpret_cast<uint4*>(b + kmajor_off_h(n, 64 + k0, kTcN)) = make_uint4(h0.x, h0.y, h1.x, h1.y);
-                *reinterpret_cast<uint4*>(b + kBOne + kmajor_off_h(n, 64 + k0, kTcN)) =
-                    make_uint4(l0.x, l0.y, l1.x, l1.y);
+                    for (int term = 0; term < 3; ++term) {
+                        const uint32_t a0 = tm + (term == 2 ? 128u : 0u);                       // A_lo, third product
+                        const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytes >> 4) : 0);  // B_lo, second
+#pragma unroll
+                        for (int ks = 0; ks < kTcK / 8; ++ks)
+                            mma_tf32_ta(d, a0 + 8u * (uint32_t)ks, b0 + (uint64_t)ks * kStepB, idesc,
+                                        (term | ks) != 0 ? 1u : 0u);
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&mbar_mma[st]))
+                             : "memory");
+                ++issued[st];
             }
-        } else {
+            // before the tensor memory is released: every committed group has
+            // completed (already true on the normal path; bounded on abort)
+            for (int t = 0; t < 2; ++t)
+                if (issued[t] > 0) mbar_wait(smem_u32(&mbar_mma[t]), (uint32_t)((issued[t] - 1) & 1));
+        }
+        __syncwarp();
+    } else if (warp < PW) {
+        // ---------------- producers ----------------
+        // thread -> class n = tid % 64 of each chunk and MPT members: TF32
+        // rows 4 (q + GP j) + i, BF16 rows 8 (q + GP j) + i (q = tid / 64),
+        // so that each thread writes whole 16-byte core-matrix rows of B.
+        const int n = tid & (kTcN - 1);
+        const int q0 = tid >> 6;
+        auto row_of = [&](int e) -> int {
+            if constexpr (kBf) return 8 * (q0 + GP * (e >> 3)) + (e & 7);
+            else return 4 * (q0 + GP * (e >> 2)) + (e & 3);
+        };
+        auto load = [&](float2 (&x)[MPT], uint64_t chunk) {
+            const uint64_t g = chunk * kTcN + (uint64_t)n;
+            const bool ok = chunk < n_chunks && g < a.n_classes;
+            const uint64_t base = ok ? a.map.map(g) : 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int q = q0 + 4 * j;
-                const float2* x = pre + 4 * j;
-                float4 rh, rl, ih, il;
-                rh.x = tf32_hi(x[0].x); rh.y = tf32_hi(x[1].x); rh.z = tf32_hi(x[2].x); rh.w = tf32_hi(x[3].x);
-                ih.x = tf32_hi(x[0].y); ih.y = tf32_hi(x[1].y); ih.z = tf32_hi(x[2].y); ih.w = tf32_hi(x[3].y);
-                rl.x = x[0].x - rh.x; rl.y = x[1].x - rh.y; rl.z = x[2].x - rh.z; rl.w = x[3].x - rh.w;
-                il.x = x[0].y - ih.x; il.y = x[1].y - ih.y; il.z = x[2].y - ih.z; il.w = x[3].y - ih.w;
-                // K index: real parts at 4q..4q+3, imaginary parts at 64 + 4q..
-                *reinterpret_cast<float4*>(b + kmajor_off(n, 4 * q, kTcN)) = rh;
-                *reinterpret_cast<float4*>(b + kmajor_off(n, 64 + 4 * q, kTcN)) = ih;
-                *reinterpret_cast<float4*>(b + kBOne + kmajor_off(n, 4 * q, kTcN)) = rl;
-                *reinterpret_cast<float4*>(b + kBOne + kmajor_off(n, 64 + 4 * q, kTcN)) = il;
+            for (int e = 0; e < MPT; ++e) {
+                const int r = row_of(e);
+                x[e] = (ok && r < a.P) ? a.psi[base + a.off[r]] : make_float2(0.f, 0.f);
+            }
+        };
+        uint32_t ph_mma[2] = {0u, 0u};
+        // one chunk: issue the next chunk's loads, wait (bounded) until stage
+        // st is free, split `cur` into it, signal the MMA warp
+        auto step = [&](float2 (&cur)[MPT], float2 (&nxt)[MPT], int i, uint64_t chunk) -> bool {
+            const int st = i & 1;
+            if (chunk + gs < n_chunks) load(nxt, chunk + gs);
+            if (i >= 2) {
+                bool bad = !mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
+                ph_mma[st] ^= 1u;
+                if (__any_sync(0xffffffffu, bad)) return false;  // the whole warp leaves together
+            }
+            unsigned char* b = sB + st * kStage;
+            if (a.renorm) {
+                float pn = 0.f;
+#pragma unroll
+                for (int e = 0; e < MPT; ++e) pn = fmaf(cur[e].x, cur[e].x, fmaf(cur[e].y, cur[e].y, pn));
+                s_nin[i % kNinSlots][q0][n] = pn;
+            }
+            if constexpr (kBf) {
+#pragma unroll
+                for (int j = 0; j < MPT / 8; ++j) {
+                    const int k0 = 8 * (q0 + GP * j);  // K: real parts at k0.., imaginary parts at 64 + k0..
+                    const float2* xj = cur + 8 * j;
+                    uint2 h0, l0, h1, l1;
+                    bf16_split4(xj[0].x, xj[1].x, xj[2].x, xj[3].x, h0, l0);
+                    bf16_split4(xj[4].x, xj[5].x, xj[6].x, xj[7].x, h1, l1);
+                    *reinterpret_cast<uint4*>(b + kmajor_off_h(n, k0, kTcN)) = make_uint4(h0.x, h0.y, h1.x, h1.y);
+                    *reinterpret_cast<uint4*>(b + kBOne + kmajor_off_h(n, k0, kTcN)) =
+                        make_uint4(l0.x, l0.y, l1.x, l1.y);
+                    bf16_split4(xj[0].y, xj[1].y, xj[2].y, xj[3].y, h0, l0);
+                    bf16_split4(xj[4].y, xj[5].y, xj[6].y, xj[7].y, h1, l1);
+                    *reinterpret_cast<uint4*>(b + kmajor_off_h(n, 64 + k0, kTcN)) =
+                        make_uint4(h0.x, h0.y, h1.x, h1.y);
+                    *reinterpret_cast<uint4*>(b + kBOne + kmajor_off_h(n, 64 + k0, kTcN)) =
+                        make_uint4(l0.x, l0.y, l1.x, l1.y);
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < MPT / 4; ++j) {
+                    const int q = q0 + GP * j;
+                    const float2* xj = cur + 4 * j;
+                    float4 rh, rl, ih, il;
+                    rh.x = tf32_hi(xj[0].x); rh.y = tf32_hi(xj[1].x); rh.z = tf32_hi(xj[2].x); rh.w = tf32_hi(xj[3].x);
+                    ih.x = tf32_hi(xj[0].y); ih.y = tf32_hi(xj[1].y); ih.z = tf32_hi(xj[2].y); ih.w = tf32_hi(xj[3].y);
+                    rl.x = xj[0].x - rh.x; rl.y = xj[1].x - rh.y; rl.z = xj[2].x - rh.z; rl.w = xj[3].x - rh.w;
+                    il.x = xj[0].y - ih.x; il.y = xj[1].y - ih.y; il.z = xj[2].y - ih.z; il.w = xj[3].y - ih.w;
+                    // K index: real parts at 4q..4q+3, imaginary parts at 64 + 4q..
+                    *reinterpret_cast<float4*>(b + kmajor_off(n, 4 * q, kTcN)) = rh;
+                    *reinterpret_cast<float4*>(b + kmajor_off(n, 64 + 4 * q, kTcN)) = ih;
+                    *reinterpret_cast<float4*>(b + kBOne + kmajor_off(n, 4 * q, kTcN)) = rl;
+                    *reinterpret_cast<float4*>(b + kBOne + kmajor_off(n, 64 + 4 * q, kTcN)) = il;
+                }
+            }
+            // generic-proxy writes -> async proxy, then one arrival per warp
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&mbar_full[st]));
+            return true;
+        };
+        float2 xa[MPT], xb[MPT];
+        uint64_t chunk = blockIdx.x;
+        load(xa, chunk);
+        for (int i = 0; chunk < n_chunks;) {
+            if (!step(xa, xb, i, chunk)) break;
+            chunk += gs;
+            ++i;
+            if (chunk >= n_chunks) break;
+            if (!step(xb, xa, i, chunk)) break;
+            chunk += gs;
+            ++i;
+        }
+    } else {
+        // ---------------- consumers ----------------
+        // thread -> class n of the chunk and OPT outputs, rows r = h + GC i
+        // (h = consumer index / 64); consumer warp c reads TMEM lanes 32 c ..
+        const int c = tid - kProd;
+        const int cw = warp - PW;
+        const int n = c & (kTcN - 1);
+        const int h = c >> 6;
+        uint32_t ph_mma[2] = {0u, 0u};
+        int i = 0;
+        for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gs, ++i) {
+            const int st = i & 1;
+            // wait (bounded) for this chunk's accumulator; the barrier also
+            // means every consumer is done reading Y of the previous chunk
+            const bool timed_out = !mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
+            ph_mma[st] ^= 1u;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (consumer_sync_or<kCons>(timed_out)) {
+                if (c == 0) atomicExch(&abort_flag, 1);
+                break;
+            }
+            // TMEM -> registers -> shared (all 64 accumulator columns of lanes 32 cw ..)
+            {
+                const uint32_t row = 32u * (uint32_t)cw + (uint32_t)lane;
+                const uint32_t ta = tm + ((32u * (uint32_t)cw) << 16) + kDCol + (uint32_t)st * kTcN;
+                float v[32], w[32];
+                tmem_ld32(ta, v);
+                tmem_ld32(ta + 32u, w);
+                // accumulator st may be overwritten from here on
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&mbar_dfree[st]));
+#pragma unroll
+                for (int k = 0; k < 32; k += 4) {
+                    *reinterpret_cast<float4*>(Y + row * kYStride + k) = make_float4(v[k], v[k + 1], v[k + 2], v[k + 3]);
+                    *reinterpret_cast<float4*>(Y + row * kYStride + 32 + k) =
+                        make_float4(w[k], w[k + 1], w[k + 2], w[k + 3]);
+                }
+            }
+            consumer_sync<kCons>();
+            // outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
+            float2 y[OPT];
+            float po = 0.f;
+#pragma unroll
+            for (int k = 0; k < OPT; ++k) {
+                const int r = h + GC * k;
+                y[k] = r < a.P ? make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]) : make_float2(0.f, 0.f);
+                po = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, po));
+            }
+            float cc = 0.f;
+            if (a.renorm) {
+                // The FP32 accumulation of the tensor cores is biased toward
+                // zero (about -1.3e-6 relative per TF32x3 block, proportional
+                // to the number of MMAs); a unitary block keeps each class's
+                // 2-norm, so the output class is rescaled to the input's norm:
+                // y <- y (1 + c), c = sqrt(ni / no) - 1 = (ni - no) / (sqrt(no) (sqrt(ni) + sqrt(no))).
+                // c is applied by one FMA: a factor 1 + c rounded to binary32
+                // would be off by up to half an ulp of 1 in the same direction
+                // for every class (the bias is nearly uniform), a drift of its own.
+                s_nout[h][n] = po;
+                consumer_sync<kCons>();
+                float ni = 0.f, no = 0.f;
+#pragma unroll
+                for (int g = 0; g < GP; ++g) ni += s_nin[i % kNinSlots][g][n];
+#pragma unroll
+                for (int g = 0; g < GC; ++g) no += s_nout[g][n];
+                if (ni > 0.f && no > 0.f) {
+                    const float sn = sqrtf(no);
+                    cc = (ni - no) / (sn * (sqrtf(ni) + sn));
+                }
+            }
+            const uint64_t g = chunk * kTcN + (uint64_t)n;
+            if (g < a.n_classes) {
+                const uint64_t base = a.map.map(g);
+#pragma unroll
+                for (int k = 0; k < OPT; ++k) {
+                    const int r = h + GC * k;
+                    if (r < a.P)
+                        a.psi[base + a.off[r]] = make_float2(fmaf(y[k].x, cc, y[k].x), fmaf(y[k].y, cc, y[k].y));
+                }
             }
         }
-    };
-    // one thread: 3 products x (K / k-step) MMAs into accumulator st, committed to mbar[st]
-    auto issue_mma = [&](int st) {
-        // descriptor address fields count 16-byte units; a k-step spans two
-        // core matrices along K
-        const uint32_t lboB = (kTcN / 8) * 128;
-        const uint64_t bd0 = smem_desc(sB_u + (uint32_t)st * kStage, lboB, 128);
-        constexpr uint64_t kStepB = 2 * (kTcN / 8) * 128 / 16;
-        const uint32_t d = tm + kDCol + (uint32_t)st * kTcN;
-        if constexpr (kBf) {
-            const uint32_t lboA = (kTcM / 8) * 128;
-            const uint64_t ad0 = smem_desc(sA_u, lboA, 128);
-            constexpr uint64_t kStepA = 2 * (kTcM / 8) * 128 / 16;
-#pragma unroll
-            for (int term = 0; term < 3; ++term) {
-                const uint64_t a0 = ad0 + (term == 2 ? (uint64_t)(kABytesH >> 4) : 0);  // A_lo for the third product
-                const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytesH >> 4) : 0);  // B_lo for the second
-#pragma unroll
-                for (int ks = 0; ks < kTcK / 16; ++ks)
-                    mma_bf16(d, a0 + (uint64_t)ks * kStepA, b0 + (uint64_t)ks * kStepB, idesc,
-                             (term | ks) != 0 ? 1u : 0u);
-            }
-        } else {
-#pragma unroll
-            for (int term = 0; term < 3; ++term) {
-                const uint32_t a0 = tm + (term == 2 ? 128u : 0u);                       // A_lo for the third product
-                const uint64_t b0 = bd0 + (term == 1 ? (uint64_t)(kBBytes >> 4) : 0);  // B_lo for the second
-#pragma unroll
-                for (int ks = 0; ks < kTcK / 8; ++ks)
-                    mma_tf32_ta(d, a0 + 8u * (uint32_t)ks, b0 + (uint64_t)ks * kStepB, idesc,
-                                (term | ks) != 0 ? 1u : 0u);
-            }
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&mbar[st]))
-                     : "memory");
-    };
-    auto publish_b = [&]() {
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    };
-
-    uint64_t chunk = blockIdx.x;
-    prefetch(chunk);
-    bool cur_valid = pre_valid;
-    uint64_t cur_base = pre_base;
-    int st = 0;
-    int slot = 0;  // s_nin slot of the current chunk (iteration count mod 3)
-    stage_b(0, 0);
-    publish_b();
-    if (chunk < n_chunks && tid == 0) issue_mma(0);
-    prefetch(chunk + gridDim.x);
-
-    for (; chunk < n_chunks; chunk += gridDim.x) {
-        const uint64_t next = chunk + gridDim.x;
-        const bool nxt_valid = pre_valid;
-        const uint64_t nxt_base = pre_base;
-        // stage the next chunk and start its MMAs; they run during this chunk's epilogue
-        const int nslot = slot == 2 ? 0 : slot + 1;
-        if (next < n_chunks) {
-            stage_b(st ^ 1, nslot);
-            publish_b();
-            if (tid == 0) issue_mma(st ^ 1);
-            prefetch(next + gridDim.x);
-        }
-        // wait for this chunk's accumulator (bounded); on timeout also wait
-        // (bounded) for the other stage before the tensor memory is released
-        uint32_t& ph = st ? phase1 : phase0;
-        if (!mbar_wait(smem_u32(&mbar[st]), ph)) {
-            if (lane == 0) atomicExch(&abort_flag, 1);
-            mbar_wait(smem_u32(&mbar[st]), ph);
-            if (next < n_chunks) mbar_wait(smem_u32(&mbar[st ^ 1]), st ? phase0 : phase1);
-        }
-        ph ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        __syncthreads();
-        if (abort_flag) break;
-        // TMEM -> registers -> shared: warp w reads lanes 32 (w % 4) .. +31,
-        // warps 0-3 columns 0..31 of the accumulator, warps 4-7 columns 32..63
-        {
-            const uint32_t row = 32u * (uint32_t)(warp & 3) + (uint32_t)lane;
-            const uint32_t col = (uint32_t)(warp >> 2) * 32u;
-            float v[32];
-            tmem_ld32(tm + ((32u * (uint32_t)(warp & 3)) << 16) + kDCol + (uint32_t)st * kTcN + col, v);
-#pragma unroll
-            for (int i = 0; i < 32; i += 4)
-                *reinterpret_cast<float4*>(Y + row * kYStride + col + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        // outputs: y_r = (Y[r][n], Y[64 + r][n]), rows r = q + 4 i of class n,
-        // lanes along the classes
-        float2 y[16];
-        float po = 0.f;
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const int r = q0 + 4 * i;
-            y[i] = r < a.P ? make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]) : make_float2(0.f, 0.f);
-            po = fmaf(y[i].x, y[i].x, fmaf(y[i].y, y[i].y, po));
-        }
-        float c = 0.f;
-        if (a.renorm) {
-            // The FP32 accumulation of the tensor cores is biased toward zero
-            // (about -1.3e-6 relative per TF32x3 block, proportional to the
-            // number of MMAs); a unitary block keeps each class's 2-norm, so
-            // the output class is rescaled to the input's norm: y <- y (1 + c)
-            // with c = sqrt(ni / no) - 1 = (ni - no) / (sqrt(no) (sqrt(ni) + sqrt(no))).
-            // c is applied by one FMA: a factor 1 + c rounded to binary32
-            // would be off by up to half an ulp of 1 in the same direction
-            // for every class (the bias is nearly uniform), a drift of its own.
-            s_nout[q0][n] = po;
-            __syncthreads();
-            const float ni = (s_nin[slot][0][n] + s_nin[slot][1][n]) + (s_nin[slot][2][n] + s_nin[slot][3][n]);
-            const float no = (s_nout[0][n] + s_nout[1][n]) + (s_nout[2][n] + s_nout[3][n]);
-            if (ni > 0.f && no > 0.f) {
-                const float sn = sqrtf(no);
-                c = (ni - no) / (sn * (sqrtf(ni) + sn));
-            }
-        }
-        if (cur_valid) {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int r = q0 + 4 * i;
-                if (r < a.P)
-                    a.psi[cur_base + a.off[r]] = make_float2(fmaf(y[i].x, c, y[i].x), fmaf(y[i].y, c, y[i].y));
-            }
-        }
-        cur_valid = nxt_valid;
-        cur_base = nxt_base;
-        st ^= 1;
-        slot = nslot;
-        // Y is rewritten only after the next iteration's barriers
     }
     __syncthreads();
     if (abort_flag && tid == 0) atomicExch(a.status, QD_ERR_TIMEOUT);
@@ -604,7 +708,7 @@ static cudaError_t launch_tc_mode(const TcArgs& a, uint64_t chunks, int sm_count
         attr_dev = dev;
     }
     const unsigned grid = (unsigned)(chunks < (uint64_t)sm_count ? chunks : (uint64_t)sm_count);
-    k_block_tc<MODE><<<grid, 256, smem, s>>>(a);
+    k_block_tc<MODE><<<grid, kTcThreads, smem, s>>>(a);
     return cudaSuccess;
 }
 
