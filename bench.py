@@ -336,6 +336,90 @@ def measure_large(qb, gen, torch, stream, amp_bytes_c64=8):
     return out
 
 
+def measure_stride_sweep(qb, gen, torch, stream, reps=20, amp_bytes=8):
+    """Per-gate kernel over every wire position of the 12-qubit + 8-qutrit layout
+    (complex64): a Haar dense gate, a diagonal phase gate (no unit entry) and a
+    dense gate controlled by the next wire (value d_c - 1), each timed over ``reps``
+    launches with CUDA events; achieved GB/s from the algorithmic bytes."""
+    circ = gen.config1_circuit()
+    dims = circ.dims
+    rng = np.random.Generator(np.random.PCG64(20))
+    st = qb.State(dims, prec=qb.QD_C64, stream=stream)
+    peak, _ = measured_peaks()
+    rows = []
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    for w, d in enumerate(dims):
+        H = gen.haar(d, rng)
+        Z = np.diag(np.exp(2j * np.pi * (np.arange(d) + 0.5) / d))
+        c = (w + 1) % len(dims)
+        row = {"wire": w, "d": d, "stride": int(np.prod(dims[:w], dtype=np.int64))}
+        for kind, fn, touched in (
+                ("dense", lambda: qb.qd_apply_gate(st.handle, w, H), circ.D),
+                ("diagonal", lambda: qb.qd_apply_gate(st.handle, w, Z), circ.D),
+                ("controlled", lambda: qb.qd_apply_controlled(st.handle, w, H, [c], [dims[c] - 1]),
+                 circ.D // dims[c])):
+            t = timed(fn)
+            gbs = 2 * amp_bytes * touched / t / 1e9
+            row[kind] = {"us": 1e6 * t, "gbs": gbs, "frac_of_measured_hbm": gbs / peak}
+        rows.append(row)
+    st.close()
+    return {"workload": "12 qubits + 8 qutrits (26,873,856 amplitudes), complex64, every wire",
+            "repeats": reps, "rows": rows,
+            "dense_frac_min": min(r["dense"]["frac_of_measured_hbm"] for r in rows),
+            "dense_frac_median": float(np.median([r["dense"]["frac_of_measured_hbm"] for r in rows]))}
+
+
+def measure_many_controls(qb, gen, torch, stream, reps=10):
+    """Controlled X_{+1} with M = 1..16 controls on the 12-qubit + 8-qutrit layout
+    (26,873,856 complex64 amplitudes): the digit-insertion enumeration
+    (qd_apply_controlled, only matching classes visited) against the paper's
+    scanning formulation (qd_apply_controlled_scan, every target class visited and
+    its M control digits tested).  Controls: the highest wires other than the
+    target, values drawn from a fixed seed."""
+    circ = gen.config1_circuit()
+    dims = circ.dims
+    rng = np.random.Generator(np.random.PCG64(16))
+    target = [w for w, d in enumerate(dims) if d == 2][0]
+    others = sorted((w for w in range(len(dims)) if w != target), reverse=True)
+    st = qb.State(dims, prec=qb.QD_C64, stream=stream)
+    X = gen.x_plus(2, 1)
+    out = {"workload": "12 qubits + 8 qutrits (26,873,856 amplitudes), complex64, controlled X_{+1} on wire "
+                       f"{target}", "rows": []}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    for m in (1, 2, 4, 8, 12, 16):
+        cw = others[:m]
+        cv = [int(rng.integers(0, dims[w])) for w in cw]
+        t_enum = timed(lambda: qb.qd_apply_controlled(st.handle, target, X, cw, cv))
+        t_scan = timed(lambda: qb.qd_apply_controlled_scan(st.handle, target, X, cw, cv))
+        matched = circ.D // 2 // int(np.prod([dims[w] for w in cw]))
+        out["rows"].append({"controls": m, "matching_classes": matched, "enumeration_us": 1e6 * t_enum,
+                            "scan_us": 1e6 * t_scan, "scan_over_enumeration": t_scan / t_enum})
+    st.close()
+    return out
+
+
 def measure_batched(qb, gen, torch, stream):
     """8192 independent circuits (widths 4-12, dims {2,3,4,5}, depths 20-300), complex64,
     captured in a CUDA graph: build+first run wall time, then relaunches timed with events."""
@@ -636,6 +720,10 @@ def run_gpu(args):
         st.close()
         torch.cuda.empty_cache()
         extra["large_state"] = measure_large(qb, gen, torch, stream, amp_bytes_c64=8)
+        torch.cuda.empty_cache()
+        extra["stride_sweep"] = measure_stride_sweep(qb, gen, torch, stream)
+        torch.cuda.empty_cache()
+        extra["many_controls"] = measure_many_controls(qb, gen, torch, stream)
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(qb, gen, torch, stream)
         torch.cuda.empty_cache()

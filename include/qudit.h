@@ -137,6 +137,18 @@ qd_status qd_apply_controlled(qd_state* st, int32_t target, const double* U,
                               const int32_t* ctrl_wires, const int32_t* ctrl_vals,
                               int32_t n_ctrl);
 
+/* The same controlled gate in the paper's formulation, for comparison with
+ * qd_apply_controlled (section "Controlled and Multi-Controlled Gates": the
+ * control condition floor(i / b_k) mod d_k = v_k is checked index by index,
+ * O(D M) tests for M controls): every one of the D / d_target classes of the
+ * target wire is visited and its M control digits are tested; matching
+ * classes get the update qd_apply_controlled gives them, bit for bit.
+ * Arguments and validation as qd_apply_controlled; single wires of
+ * dimension <= 8 only (QD_ERR_UNSUPPORTED otherwise).  Asynchronous. */
+qd_status qd_apply_controlled_scan(qd_state* st, int32_t target, const double* U,
+                                   const int32_t* ctrl_wires, const int32_t* ctrl_vals,
+                                   int32_t n_ctrl);
+
 /* Multi-wire gate: a P x P matrix on k distinct wires wires[0..k-1]
  * (P = prod dims[wires[m]] <= QD_MAX_GATE_DIM; local index with wires[0]
  * least significant), optionally controlled as in qd_apply_controlled

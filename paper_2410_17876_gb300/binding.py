@@ -99,6 +99,7 @@ _SIGS = {
     "qd_marginal": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
     "qd_synchronize": (ctypes.c_int32, [_vp]),
     "qd_set_fusion": (ctypes.c_int32, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "qd_apply_controlled_scan": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p, _i32p, _i32p, ctypes.c_int32]),
     "qd_flush": (ctypes.c_int32, [_vp]),
     "qd_norm_noalloc": (ctypes.c_int32, [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]),
     "qd_last_error": (ctypes.c_char_p, []),
@@ -246,6 +247,16 @@ def qd_apply_controlled(st: int, target: int, U, ctrl_wires, ctrl_vals) -> None:
     cv, cva = _opt_i32(ctrl_vals)
     n = 0 if ctrl_wires is None else len(ctrl_wires)
     _check(_lib.qd_apply_controlled(_vp(st), int(target), _p(_mat(U), _f64p), cw, cv, n), "qd_apply_controlled")
+
+
+def qd_apply_controlled_scan(st: int, target: int, U, ctrl_wires, ctrl_vals) -> None:
+    """The paper's scanning formulation of a controlled gate (every target class visited,
+    its control digits tested), for comparison with ``qd_apply_controlled``."""
+    cw, cwa = _opt_i32(ctrl_wires)
+    cv, cva = _opt_i32(ctrl_vals)
+    n = 0 if ctrl_wires is None else len(ctrl_wires)
+    _check(_lib.qd_apply_controlled_scan(_vp(st), int(target), _p(_mat(U), _f64p), cw, cv, n),
+           "qd_apply_controlled_scan")
 
 
 def qd_apply_multi(st: int, wires, U, ctrl_wires=None, ctrl_vals=None) -> None:

@@ -238,8 +238,9 @@ static void free_state(qd_state* st) {
     for (int i = 0; i < kRingSlots; ++i)
         if (st->ring_ev_live[i]) cudaEventDestroy(st->ring_ev[i]);
     if (st->arena) {
-        st->arena->release();
-        delete st->arena;
+        st->arena[0].release();
+        st->arena[1].release();
+        delete[] st->arena;
     }
     delete st->pend;
     delete st;
@@ -288,6 +289,41 @@ static cudaError_t run_gate1(qd_state* st, const Plan& p, const double* U) {
         if constexpr (sizeof(R) == 4) return launch_gate1<R, DT, 2>(a, st->stream);
     }
     return launch_gate1<R, DT, 1>(a, st->stream);
+}
+
+template <typename R, int DT>
+static cudaError_t run_gate1_scan(qd_state* st, const Plan& p, const double* U, const ScanControls& c) {
+    using T2 = typename Cplx<R>::T2;
+    Gate1Args<R, DT> a;
+    std::memset(static_cast<void*>(&a), 0, sizeof a);
+    a.psi = reinterpret_cast<T2*>(st->psi);
+    a.n_elems = p.classes;  // one class per thread
+    a.bt = (uint64_t)p.bt;
+    a.map = p.map;
+    a.kind = p.kind;
+    a.lmask = p.lmask;
+    a.smask = p.smask;
+    a.pure_perm = p.pure ? 1u : 0u;
+    for (int r = 0; r < DT; ++r) a.perm[r] = p.perm[r];
+    for (int i = 0; i < DT * DT; ++i) {
+        a.U[i].x = (R)U[2 * i];
+        a.U[i].y = (R)U[2 * i + 1];
+    }
+    return launch_gate1_scan<R, DT>(a, c, st->stream);
+}
+
+template <typename R>
+static cudaError_t dispatch_gate1_scan(qd_state* st, const Plan& p, const double* U, const ScanControls& c) {
+    switch (p.d) {
+        case 2: return run_gate1_scan<R, 2>(st, p, U, c);
+        case 3: return run_gate1_scan<R, 3>(st, p, U, c);
+        case 4: return run_gate1_scan<R, 4>(st, p, U, c);
+        case 5: return run_gate1_scan<R, 5>(st, p, U, c);
+        case 6: return run_gate1_scan<R, 6>(st, p, U, c);
+        case 7: return run_gate1_scan<R, 7>(st, p, U, c);
+        case 8: return run_gate1_scan<R, 8>(st, p, U, c);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <typename R>
@@ -687,6 +723,33 @@ qd_status qd_synchronize(qd_state* st) {
     QD_FLUSH(st);
     QD_CUDA(cudaStreamSynchronize(st->stream), "synchronize");
     return check_device_status(st);
+    QD_GUARD_END
+}
+
+qd_status qd_apply_controlled_scan(qd_state* st, int32_t target, const double* U, const int32_t* cw,
+                                   const int32_t* cv, int32_t nc) {
+    QD_GUARD_BEGIN
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    QD_FLUSH(st);  // gates queued by deferred fusion come first
+    Plan full;  // validates the gate and its controls exactly as qd_apply_controlled does
+    qd_status rc = make_plan(st->L, st->prec, &target, 1, U, cw, cv, nc, full);
+    if (rc != QD_OK) return rc;
+    if (full.family != 0) return fail(QD_ERR_UNSUPPORTED, "scan formulation: single wires of dimension <= 8");
+    if (full.classes == 0 || full.smask == 0) return QD_OK;
+    Plan p;  // every class of the target wire
+    rc = make_plan(st->L, st->prec, &target, 1, U, nullptr, nullptr, 0, p);
+    if (rc != QD_OK) return rc;
+    ScanControls c;
+    std::memset(static_cast<void*>(&c), 0, sizeof c);
+    c.m = nc;
+    for (int m = 0; m < nc; ++m) {
+        c.stride[m].init((uint64_t)st->L.b[cw[m]]);
+        c.dim[m].init((uint64_t)st->L.dims[cw[m]]);
+        c.val[m] = (uint64_t)cv[m];
+    }
+    cudaError_t e = st->prec == QD_C64 ? dispatch_gate1_scan<float>(st, p, U, c) : dispatch_gate1_scan<double>(st, p, U, c);
+    if (e != cudaSuccess) return cuda_fail(e, "scan gate kernel");
+    return QD_OK;
     QD_GUARD_END
 }
 

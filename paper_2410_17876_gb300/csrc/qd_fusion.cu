@@ -48,6 +48,7 @@ constexpr int kMaxTileCtrl = 7;    // controls of a fused gate (inside or outsid
 constexpr int kMaxLocalIns = 1 + kMaxTileCtrl;
 constexpr int kMaxPassGates = 64;  // gates per fused pass (their descriptors live in shared memory)
 constexpr int kMaxRows = 2048;
+constexpr double kPipeMaxFlops = 150.0;  // tile passes below this many flop per amplitude use the persistent kernel
 
 // Class enumeration inside a tile (local index space of S), 32-bit.
 struct __align__(16) LocalMap {
@@ -120,8 +121,10 @@ struct FusedArgs {
     int32_t nfree;   // wires outside S, ascending
     int32_t free_w[kMaxWires];
     uint32_t free_d[kMaxWires];
+    FastDiv32 free_div[kMaxWires];  // division by free_d (tile indices are below 2^32)
     uint64_t free_b[kMaxWires];
     const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
+    int32_t* status;         // persistent kernel: set to QD_ERR_TIMEOUT if a bounded wait gave up
 };
 
 
@@ -427,10 +430,11 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
     __shared__ uint64_t sbase;
     for (uint32_t r = threadIdx.x; r < a.rows; r += blockDim.x) srow[r] = a.rowoff[r];
     if (threadIdx.x == 0) {
-        uint64_t rem = blockIdx.x, base = 0;
+        uint32_t rem = blockIdx.x;
+        uint64_t base = 0;
         for (int i = 0; i < a.nfree; ++i) {
-            const uint64_t q = rem / a.free_d[i];
-            const uint32_t dig = (uint32_t)(rem - q * a.free_d[i]);
+            const uint32_t q = a.free_div[i].div(rem);
+            const uint32_t dig = rem - q * a.free_d[i];
             odig[a.free_w[i]] = (int32_t)dig;
             base += (uint64_t)dig * a.free_b[i];
             rem = q;
@@ -467,6 +471,142 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
     }
 }
 
+// ---------------------------------------------------------------------------
+// Persistent tile passes: one CTA of 512 threads per SM walks tiles t =
+// blockIdx.x, + gridDim.x, ... with two tile buffers.  While the gates of
+// tile t are applied in one buffer, tile t + gridDim.x arrives in the other:
+// warp 0 issues one cp.async.bulk per contiguous row (bL amplitudes), all
+// completing on that buffer's mbarrier; after the gates, warp 0 writes the
+// tile back with bulk stores and waits for their shared-memory reads only
+// before the buffer is refilled.  Rows are 16-byte multiples (complex64 with
+// even bL, every complex128 layout), so every bulk copy is aligned.  Waits
+// are bounded; on a timeout the CTA records QD_ERR_TIMEOUT, waits (bounded)
+// for its copies in flight and stops.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ bool mbar_try_wait_bounded(uint32_t mbar, uint32_t phase) {
+    for (uint32_t it = 0; it < (1u << 26); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, P;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase));
+        if (done) return true;
+    }
+    return false;
+}
+
+template <typename R, int DMAX>
+__global__ void __launch_bounds__(512, 1) k_fused_pipe(const __grid_constant__ FusedArgs<R> a) {
+    using T2 = typename Cplx<R>::T2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* stage = smem_raw;
+    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + chunk_smem_max<R>());
+    T2* buf[2];
+    buf[0] = reinterpret_cast<T2*>(smem_raw + chunk_smem_max<R>() + fused_rows_bytes(a.rows));
+    buf[1] = buf[0] + a.T;
+    __shared__ int32_t odig[kMaxWires];
+    __shared__ __align__(8) uint64_t mbar[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t row_bytes = a.bL * (uint32_t)sizeof(T2);
+    for (uint32_t r = tid; r < a.rows; r += blockDim.x) srow[r] = a.rowoff[r];
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // base offset (and, optionally, the digits of the wires outside the tile) of tile t
+    auto tile_base = [&](uint64_t t, int32_t* dig) -> uint64_t {
+        uint32_t rem = (uint32_t)t;
+        uint64_t base = 0;
+        for (int i = 0; i < a.nfree; ++i) {
+            const uint32_t q = a.free_div[i].div(rem);
+            const uint32_t dg = rem - q * a.free_d[i];
+            if (dig) dig[a.free_w[i]] = (int32_t)dg;
+            base += (uint64_t)dg * a.free_b[i];
+            rem = q;
+        }
+        return base;
+    };
+    // warp 0: tile t -> buf[b] (one bulk copy per row, completing on mbar[b])
+    auto issue_load = [&](uint64_t t, int b) {
+        uint64_t base = 0;
+        if (lane == 0) {
+            base = tile_base(t, nullptr);
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&mbar[b])),
+                         "r"(a.T * (uint32_t)sizeof(T2))
+                         : "memory");
+        }
+        base = __shfl_sync(0xffffffffu, base, 0);
+        const T2* g = a.psi + base;
+        const uint32_t dst0 = smem_addr(buf[b]);
+        for (uint32_t r = lane; r < a.rows; r += 32)
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                    dst0 + r * row_bytes),
+                "l"(g + srow[r]), "r"(row_bytes), "r"(smem_addr(&mbar[b]))
+                : "memory");
+    };
+    uint32_t ph[2] = {0u, 0u};
+    bool pending[2] = {false, false};  // a load into the buffer has been issued and not yet waited for
+    bool aborted = false;
+    uint64_t t = blockIdx.x;
+    if (t < a.ntiles) {
+        if (warp == 0) issue_load(t, 0);
+        pending[0] = true;
+    }
+    for (int k = 0; t < a.ntiles; t += gridDim.x, ++k) {
+        const int b = k & 1;
+        const uint64_t tn = t + gridDim.x;
+        if (tn < a.ntiles) {
+            if (warp == 0) {
+                // buf[b ^ 1] was last written back by this warp's bulk stores
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                __syncwarp();
+                issue_load(tn, b ^ 1);
+            }
+            pending[b ^ 1] = true;
+        }
+        const bool bad = !mbar_try_wait_bounded(smem_addr(&mbar[b]), ph[b]);
+        if (__syncthreads_or(bad)) {
+            aborted = true;
+            break;
+        }
+        ph[b] ^= 1u;
+        pending[b] = false;
+        if (tid == 0) (void)tile_base(t, odig);
+        __syncthreads();
+        apply_chunks<R, DMAX>(buf[b], a.chunks, a.nchunks, stage, odig);
+        // generic-proxy writes of the tile -> async proxy, then write it back
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (warp == 0) {
+            uint64_t base = lane == 0 ? tile_base(t, nullptr) : 0;
+            base = __shfl_sync(0xffffffffu, base, 0);
+            T2* g = a.psi + base;
+            const uint32_t src0 = smem_addr(buf[b]);
+            for (uint32_t r = lane; r < a.rows; r += 32)
+                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g + srow[r]),
+                             "r"(src0 + r * row_bytes), "r"(row_bytes)
+                             : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+    }
+    if (aborted && tid == 0) {
+        // loads still in flight land in this CTA's shared memory: wait (bounded) before leaving
+        for (int i = 0; i < 2; ++i)
+            if (pending[i]) (void)mbar_try_wait_bounded(smem_addr(&mbar[i]), ph[i]);
+        atomicExch(a.status, QD_ERR_TIMEOUT);
+    }
+    if (warp == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    __syncthreads();
+}
+
 template <typename R>
 size_t fused_smem(const FusedArgs<R>& a) {
     return chunk_smem_max<R>() + fused_rows_bytes(a.rows) + sizeof(typename Cplx<R>::T2) * (size_t)a.T;
@@ -491,6 +631,43 @@ cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
         k_fused_tile<R, 3><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
     else
         k_fused_tile<R, 5><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// Shared memory of the persistent kernel (two tile buffers), and whether a
+// pass can use it: rows of whole 16-byte units and the buffers within the
+// 227 KB a CTA may use.
+template <typename R>
+size_t fused_pipe_smem(uint32_t T, uint32_t rows) {
+    return chunk_smem_max<R>() + fused_rows_bytes(rows) + 2 * sizeof(typename Cplx<R>::T2) * (size_t)T;
+}
+template <typename R>
+bool fused_pipe_ok(uint32_t T, uint32_t bL, uint32_t rows) {
+    return (bL * sizeof(typename Cplx<R>::T2)) % 16 == 0 && fused_pipe_smem<R>(T, rows) <= 220 * 1024;
+}
+
+template <typename R>
+cudaError_t launch_fused_pipe(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
+    static int attr_dev = -1, sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused_pipe<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_pipe<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const uint64_t grid = a.ntiles < (uint64_t)sms ? a.ntiles : (uint64_t)sms;
+    if (grid == 0) return cudaSuccess;
+    const size_t smem = fused_pipe_smem<R>(a.T, a.rows);
+    if (dmax <= 3)
+        k_fused_pipe<R, 3><<<(unsigned)grid, 512, smem, s>>>(a);
+    else
+        k_fused_pipe<R, 5><<<(unsigned)grid, 512, smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -595,6 +772,7 @@ FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     c.min_gates = (o && o->min_gates > 0) ? o->min_gates : 2;
     c.min_row = (o && o->min_row > 0) ? o->min_row : (prec == QD_C64 ? 16 : 8);
     c.tc_mode = o ? o->tc_mode : QD_TC_TF32X3;
+    c.persistent = true;
     if (c.mode == QD_FUSE_BLOCK) {
         c.block_dim = (o && o->block_dim > 0) ? o->block_dim : (prec == QD_C64 ? 64 : 8);
         if (c.block_dim > 64) c.block_dim = 64;
@@ -635,6 +813,7 @@ qd_status load_gates(const Layout& L, int32_t prec, const qd_gate_desc* gates, i
         }
         h.P = h.plan.P;
         h.diag = h.plan.family == 0 && h.plan.kind == kDiag;
+        h.unitary = block_is_unitary(h.U, h.P, 1e-10);
         h.fusable = h.plan.family == 0 && h.plan.d <= kMaxFusedD && h.nc <= kMaxTileCtrl;
         h.tmask = 0;
         h.cmask = 0;
@@ -665,7 +844,8 @@ static void plan_passes(const Layout& L, const std::vector<HGate>& G, const Fuse
     int L0 = 0;
     while (L0 < L.n && L.b[L0] < cfg.min_row) ++L0;
     const int64_t T0 = L.b[L0];
-    const bool can_tile = cfg.mode == QD_FUSE_TILE && T0 <= cfg.Tmax;
+    // tile indices are 32-bit (grid size, digit arithmetic)
+    const bool can_tile = cfg.mode == QD_FUSE_TILE && T0 <= cfg.Tmax && L.D / T0 < ((int64_t)1 << 31);
     uint64_t low = 0;
     for (int w = 0; w < L0; ++w) low |= 1ull << w;
     std::vector<char> taken(n, 0);
@@ -696,6 +876,14 @@ static void plan_passes(const Layout& L, const std::vector<HGate>& G, const Fuse
                 BR |= Rd;
             }
             if ((int)sched.size() >= cfg.min_gates) {
+                // fill the tile with the lowest remaining wires while it fits:
+                // longer contiguous rows and fewer, fuller tiles
+                for (int w = 0; w < L.n; ++w) {
+                    if (S >> w & 1) continue;
+                    if (T * L.dims[w] > cfg.Tmax) break;
+                    S |= 1ull << w;
+                    T *= L.dims[w];
+                }
                 PassPlan p;
                 p.tile = true;
                 p.gates = sched;
@@ -755,8 +943,10 @@ static void tile_geometry(const Layout& L, uint64_t S, int64_t min_row, TileGeom
         }
     }
     make_layout(ldims, g.ns, g.local);
+    // rows: the run of the lowest wires (at least min_row amplitudes, all in S)
     int L0 = 0;
     while (L0 < L.n && L.b[L0] < min_row) ++L0;
+    while (L0 < L.n && (S >> L0 & 1)) ++L0;
     g.L0 = L0;
     g.bL = (uint32_t)L.b[L0];
     g.R = (uint32_t)(g.local.D / (int64_t)g.bL);
@@ -815,33 +1005,55 @@ static double sweep_cost(int kind, int64_t P) { return 4.0 + (kind == kDense ? (
 static void form_blocks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<int>& pg, int Pmax,
                         std::vector<BlockPlan>& out, bool one_pass_each = false) {
     out.clear();
-    std::vector<int> rem = pg;
-    auto outside = [&](const HGate& h) {
-        for (int c = 0; c < h.nc; ++c)
-            if (geo.loc[h.cw[c]] < 0) return true;
-        return h.k != 1;
+    // per gate (index into pg): local wire mask, and whether it can join a block
+    const size_t n = pg.size();
+    std::vector<uint64_t> lwm(n);
+    std::vector<char> inside(n);
+    for (size_t i = 0; i < n; ++i) {
+        const HGate& h = G[pg[i]];
+        lwm[i] = local_mask(geo, h.tmask | h.cmask);
+        bool in = h.k == 1;
+        for (int c = 0; c < h.nc && in; ++c) in = geo.loc[h.cw[c]] >= 0;
+        inside[i] = in;
+    }
+    // product of the local dimensions of the wires in `add`, times p
+    auto grow = [&](int64_t p, uint64_t add) {
+        while (add) {
+            const int w = __builtin_ctzll(add);
+            add &= add - 1;
+            p *= geo.local.dims[w];
+        }
+        return p;
     };
+    std::vector<size_t> rem(n);
+    for (size_t i = 0; i < n; ++i) rem[i] = i;
+    std::vector<char> taken(n, 0);
     while (!rem.empty()) {
-        const HGate& g0 = G[rem[0]];
+        const size_t i0 = rem[0];
+        const HGate& g0 = G[pg[i0]];
         BlockPlan bp;
         bp.single = true;
-        bp.gates = {rem[0]};
-        bp.lw = local_mask(geo, g0.tmask | g0.cmask);
-        if (Pmax >= 4 && !outside(g0) && local_prod(geo, bp.lw) <= Pmax) {
+        bp.gates = {pg[i0]};
+        bp.lw = lwm[i0];
+        std::vector<size_t> sel = {i0};
+        const int64_t P0 = grow(1, bp.lw);
+        if (Pmax >= 4 && inside[i0] && P0 <= Pmax) {
             uint64_t W = bp.lw, BW = 0, BR = 0;
-            std::vector<int> sel = {rem[0]};
+            int64_t PW = P0;
             double cost_single = sweep_cost(g0.plan.kind, g0.plan.d);
             for (size_t j = 1; j < rem.size(); ++j) {
-                const HGate& g = G[rem[j]];
+                const size_t ij = rem[j];
+                const HGate& g = G[pg[ij]];
                 const uint64_t Wg = g.diag ? 0 : g.tmask;
                 const uint64_t Rg = g.cmask | (g.diag ? g.tmask : 0);
                 const bool blocked = (Wg & (BW | BR)) || (Rg & BW);
-                bool ok = !blocked && !outside(g);
-                if (ok) {
-                    const uint64_t W2 = W | local_mask(geo, g.tmask | g.cmask);
-                    if (local_prod(geo, W2) <= Pmax) {
-                        W = W2;
-                        sel.push_back(rem[j]);
+                if (!blocked && inside[ij]) {
+                    const uint64_t add = lwm[ij] & ~W;
+                    const int64_t P2 = add ? grow(PW, add) : PW;
+                    if (P2 <= Pmax) {
+                        W |= add;
+                        PW = P2;
+                        sel.push_back(ij);
                         cost_single += sweep_cost(g.plan.kind, g.plan.d);
                         continue;
                     }
@@ -850,19 +1062,24 @@ static void form_blocks(const TileGeom& geo, const std::vector<HGate>& G, const 
                 BR |= Rg;
             }
             bool all_diag = true;
-            for (int idx : sel) all_diag = all_diag && G[idx].diag;
-            const double cost_block = sweep_cost(all_diag ? kDiag : kDense, local_prod(geo, W));
+            for (size_t ij : sel) all_diag = all_diag && G[pg[ij]].diag;
+            const double cost_block = sweep_cost(all_diag ? kDiag : kDense, PW);
             // one_pass_each: every block or gate costs one pass over the state
             if (sel.size() > 1 && (one_pass_each || cost_block <= cost_single)) {
                 bp.single = false;
-                bp.gates = sel;
+                bp.gates.clear();
+                for (size_t ij : sel) bp.gates.push_back(pg[ij]);
                 bp.lw = W;
+            } else {
+                sel.resize(1);
             }
         }
         out.push_back(bp);
-        std::vector<int> rest;
-        for (int idx : rem)
-            if (std::find(bp.gates.begin(), bp.gates.end(), idx) == bp.gates.end()) rest.push_back(idx);
+        for (size_t ij : sel) taken[ij] = 1;
+        std::vector<size_t> rest;
+        rest.reserve(rem.size());
+        for (size_t ij : rem)
+            if (!taken[ij]) rest.push_back(ij);
         rem.swap(rest);
     }
 }
@@ -890,7 +1107,7 @@ static void compose_block(const TileGeom& geo, const std::vector<HGate>& G, cons
     };
     M.assign((size_t)2 * P * P, 0.0);
     for (int i = 0; i < P; ++i) M[2 * ((size_t)i * P + i)] = 1.0;
-    std::vector<double> col(2 * (size_t)P), nxt(2 * (size_t)P);
+    std::vector<double> col(2 * (size_t)P * P);  // the d rows of one class (d <= P)
     for (int idx : bp.gates) {
         const HGate& h = G[idx];
         const int pt = pos(geo.loc[h.wires[0]]);
@@ -900,33 +1117,44 @@ static void compose_block(const TileGeom& geo, const std::vector<HGate>& G, cons
             cp.push_back(pos(geo.loc[h.cw[c]]));
             cv.push_back(h.cv[c]);
         }
-        for (int j = 0; j < P; ++j) {  // column j of M
-            for (int r = 0; r < P; ++r) {
-                col[2 * r] = M[2 * ((size_t)r * P + j)];
-                col[2 * r + 1] = M[2 * ((size_t)r * P + j) + 1];
+        // M <- U_g M: the gate acts on M's rows.  For each class (target
+        // digit 0, controls met) its d rows are transformed together across
+        // all P columns (contiguous inner loop).
+        const bool diagonal = h.diag;
+        for (int base = 0; base < P; ++base) {
+            if ((base / st) % d != 0) continue;  // class representatives: target digit 0
+            bool ok = true;
+            for (size_t c = 0; c < cp.size(); ++c)
+                if ((base / ws[cp[c]]) % wd[cp[c]] != cv[c]) ok = false;
+            if (!ok) continue;
+            if (diagonal) {
+                for (int k = 0; k < d; ++k) {
+                    const double ur = h.U[2 * (k * d + k)], ui = h.U[2 * (k * d + k) + 1];
+                    if (ur == 1.0 && ui == 0.0) continue;
+                    double* row = &M[2 * (size_t)(base + k * st) * P];
+                    for (int j = 0; j < P; ++j) {
+                        const double xr = row[2 * j], xi = row[2 * j + 1];
+                        row[2 * j] = ur * xr - ui * xi;
+                        row[2 * j + 1] = ur * xi + ui * xr;
+                    }
+                }
+                continue;
             }
-            nxt = col;
-            for (int base = 0; base < P; ++base) {
-                if ((base / st) % d != 0) continue;  // class representatives: target digit 0
-                bool ok = true;
-                for (size_t c = 0; c < cp.size(); ++c)
-                    if ((base / ws[cp[c]]) % wd[cp[c]] != cv[c]) ok = false;
-                if (!ok) continue;
-                for (int r = 0; r < d; ++r) {
+            for (int k = 0; k < d; ++k)
+                std::memcpy(&col[2 * (size_t)k * P], &M[2 * (size_t)(base + k * st) * P], sizeof(double) * 2 * P);
+            for (int r = 0; r < d; ++r) {
+                double* out = &M[2 * (size_t)(base + r * st) * P];
+                for (int j = 0; j < P; ++j) {
                     double re = 0.0, im = 0.0;
                     for (int k = 0; k < d; ++k) {
                         const double ur = h.U[2 * (r * d + k)], ui = h.U[2 * (r * d + k) + 1];
-                        const double xr = col[2 * (base + k * st)], xi = col[2 * (base + k * st) + 1];
+                        const double xr = col[2 * ((size_t)k * P + j)], xi = col[2 * ((size_t)k * P + j) + 1];
                         re += ur * xr - ui * xi;
                         im += ur * xi + ui * xr;
                     }
-                    nxt[2 * (base + r * st)] = re;
-                    nxt[2 * (base + r * st) + 1] = im;
+                    out[2 * j] = re;
+                    out[2 * j + 1] = im;
                 }
-            }
-            for (int r = 0; r < P; ++r) {
-                M[2 * ((size_t)r * P + j)] = nxt[2 * r];
-                M[2 * ((size_t)r * P + j) + 1] = nxt[2 * r + 1];
             }
         }
     }
@@ -1226,7 +1454,7 @@ static Op gate1_op(void* psi, const Plan& p, const double* U) {
 
 // The op of one gate for the per-gate kernels (no fusion).
 template <typename R>
-static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int tc_mode) {
+static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int tc_mode, bool unitary) {
     using T2 = typename Cplx<R>::T2;
     if (p.family == 0) {
         switch (p.d) {
@@ -1249,7 +1477,7 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int 
         const IndexMap map = p.map;
         std::vector<uint64_t> off(p.off, p.off + P);
         float2* dpsi = reinterpret_cast<float2*>(psi);
-        const bool renorm = block_is_unitary(U, P, 1e-10);
+        const bool renorm = unitary;
         return [dpsi, aoff, tc_mode, renorm, classes, map, P, off](cudaStream_t s, const char* base) {
             return launch_block_tc(dpsi, base + aoff, tc_mode, renorm, classes, map, P, off.data(), s);
         };
@@ -1276,33 +1504,33 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int 
     };
 }
 
+static double pass_arith(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg, const PassPlan& p);
+
 // Ops of a whole circuit on the state at psi (layout L): optional reset to
 // |0...0>, then the planned passes in order.
+// Ops of passes[begin, end) (composition, chunk records, launch closures).
 template <typename R>
-void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
-                          bool reset_first, Program& prog) {
+static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
+                         const std::vector<PassPlan>& passes, size_t begin, size_t end, Program& prog) {
     using T2 = typename Cplx<R>::T2;
-    if (reset_first) {
-        const int64_t D = L.D;
-        prog.ops.push_back([psi, D](cudaStream_t s, const char*) { return launch_set_basis<R>(psi, D, 0, s); });
-    }
-    std::vector<PassPlan> passes;
-    plan_passes(L, G, cfg, passes);
-    for (const PassPlan& p : passes) {
+    for (size_t pi = begin; pi < end; ++pi) {
+        const PassPlan& p = passes[pi];
         if (p.block) {
             std::vector<int> wl;
             std::vector<double> M;
             Plan q;
             if (block_gate_of(L, sizeof(R) == 4 ? QD_C64 : QD_C128, G, p, wl, M, q) != QD_OK) continue;
             if (q.family == 0 && q.smask == 0) continue;  // identity
-            prog.ops.push_back(gate_op<R>(psi, q, M.data(), prog, cfg.tc_mode));
+            bool unitary = true;
+            for (int idx : p.gates) unitary = unitary && G[idx].unitary;
+            prog.ops.push_back(gate_op<R>(psi, q, M.data(), prog, cfg.tc_mode, unitary));
             continue;
         }
         if (!p.tile) {
             const HGate& h = G[p.gates[0]];
             if (h.plan.family == 0 && h.plan.smask == 0) continue;  // identity
             if (h.plan.classes == 0) continue;
-            prog.ops.push_back(gate_op<R>(psi, h.plan, h.U, prog, cfg.tc_mode));
+            prog.ops.push_back(gate_op<R>(psi, h.plan, h.U, prog, cfg.tc_mode, h.unitary));
             continue;
         }
         TileGeom geo;
@@ -1327,15 +1555,42 @@ void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, cons
         for (int i = 0; i < geo.nfree; ++i) {
             a.free_w[i] = geo.free_w[i];
             a.free_d[i] = geo.free_d[i];
+            a.free_div[i].init(geo.free_d[i]);
             a.free_b[i] = geo.free_b[i];
         }
-        prog.ops.push_back([a, offC, offR, dmax](cudaStream_t s, const char* base) {
+        a.status = tc_status_ptr();
+        // The persistent kernel (one CTA of 512 threads per SM, bulk copies
+        // overlapping the next tile's load with this tile's gates) wins on
+        // passes that are light on arithmetic (measured on the 26.9M-amplitude
+        // layout: 157 vs 214 us for two diagonal gates, 215 vs 244 us for one
+        // 16-dimensional block); on heavy passes (214 flop per amplitude and
+        // more) two independent 256-thread CTAs per SM, which overlap each
+        // other's per-gate barriers, win.  Bulk copies also need 16-byte
+        // aligned rows: the state itself 16-byte aligned too.  The server
+        // turns it off: a kernel holding every SM would serialise requests
+        // that otherwise overlap on their streams.
+        const double flops_per_amp = pass_arith(L, G, cfg, p) / (double)L.D;
+        const bool pipe = cfg.persistent && a.status != nullptr && flops_per_amp < kPipeMaxFlops &&
+                          reinterpret_cast<uintptr_t>(psi) % 16 == 0 && fused_pipe_ok<R>(a.T, a.bL, a.rows);
+        prog.ops.push_back([a, offC, offR, dmax, pipe](cudaStream_t s, const char* base) {
             FusedArgs<R> b = a;
             b.chunks = base + offC;
             b.rowoff = reinterpret_cast<const uint64_t*>(base + offR);
-            return launch_fused<R>(b, dmax, s);
+            return pipe ? launch_fused_pipe<R>(b, dmax, s) : launch_fused<R>(b, dmax, s);
         });
     }
+}
+
+template <typename R>
+void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
+                          bool reset_first, Program& prog) {
+    if (reset_first) {
+        const int64_t D = L.D;
+        prog.ops.push_back([psi, D](cudaStream_t s, const char*) { return launch_set_basis<R>(psi, D, 0, s); });
+    }
+    std::vector<PassPlan> passes;
+    plan_passes(L, G, cfg, passes);
+    build_passes<R>(L, psi, G, cfg, passes, 0, passes.size(), prog);
 }
 
 qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
@@ -1701,15 +1956,30 @@ qd_status qd::run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gat
         const FuseCfg cfg = fuse_cfg(opts, st->prec);
         rc = check_cfg(cfg, st->prec);
         if (rc != QD_OK) return rc;
-        Program prog;
-        if (st->prec == QD_C64)
-            build_program<float>(st->L, st->psi, G, cfg, false, prog);
-        else
-            build_program<double>(st->L, st->psi, G, cfg, false, prog);
-        if (!st->arena) st->arena = new Arena();
-        rc = st->arena->upload(prog.desc.data(), prog.desc.size(), st->stream);
-        if (rc != QD_OK) return rc;
-        return issue(prog, static_cast<const char*>(st->arena->dev), st->stream);
+        // Build, upload and launch the passes in segments of 1, 2, 4, ...
+        // passes: the host composes the next segment while the GPU runs the
+        // previous one.  Two descriptor arenas alternate, so an upload only
+        // waits for the copy two segments back.
+        std::vector<PassPlan> passes;
+        plan_passes(st->L, G, cfg, passes);
+        if (!st->arena) st->arena = new Arena[2];
+        size_t i = 0;
+        for (int seg = 0; i < passes.size(); ++seg) {
+            const size_t n = std::min(passes.size() - i, (size_t)1 << (seg < 16 ? seg : 16));
+            Program prog;
+            if (st->prec == QD_C64)
+                build_passes<float>(st->L, st->psi, G, cfg, passes, i, i + n, prog);
+            else
+                build_passes<double>(st->L, st->psi, G, cfg, passes, i, i + n, prog);
+            i += n;
+            if (prog.ops.empty()) continue;
+            Arena& ar = st->arena[seg & 1];
+            rc = ar.upload(prog.desc.data(), prog.desc.size(), st->stream);
+            if (rc != QD_OK) return rc;
+            rc = issue(prog, static_cast<const char*>(ar.dev), st->stream);
+            if (rc != QD_OK) return rc;
+        }
+        return QD_OK;
     } catch (...) {
         return fail(QD_ERR_OOM, "host exception in qd_apply_circuit");
     }

@@ -121,6 +121,15 @@ struct Gate1Args {
     T2 U[DT * DT];
 };
 
+// Control tests of the scanning formulation: digit m of index j is
+// (j / stride[m]) mod dim[m].d, compared with val[m].
+struct ScanControls {
+    int32_t m;
+    FastDiv stride[kMaxInserted];
+    FastDiv dim[kMaxInserted];
+    uint64_t val[kMaxInserted];
+};
+
 // Arguments of the shared-memory tile kernel (any gate with P <= 64).
 template <typename R>
 struct GateTileArgs {
@@ -137,6 +146,8 @@ struct GateTileArgs {
 // Launchers (qd_kernels.cu).  All return a cudaError_t of the launch.
 template <typename R, int DT, int VEC>
 cudaError_t launch_gate1(const Gate1Args<R, DT>& a, cudaStream_t s);
+template <typename R, int DT>
+cudaError_t launch_gate1_scan(const Gate1Args<R, DT>& a, const ScanControls& c, cudaStream_t s);
 template <typename R>
 cudaError_t launch_gate_tile(const GateTileArgs<R>& a, cudaStream_t s, int smem_bytes);
 template <typename R>
@@ -165,6 +176,7 @@ cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool re
                             const IndexMap& map, int P, const uint64_t* off, cudaStream_t s);
 bool block_is_unitary(const double* U, int P, double tol);
 int32_t tc_status_take(cudaStream_t s);
+int32_t* tc_status_ptr();  // device status word shared by the kernels with bounded waits
 constexpr int kTcMinP = 17;  // complex64 blocks of at least this dimension go to the tensor cores
 
 int reduce_blocks(int64_t D);

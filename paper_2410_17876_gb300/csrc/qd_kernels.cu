@@ -45,16 +45,10 @@ template <> struct Ld<2> {  // complex64 only: one 16-byte access
     }
 };
 
-// One thread = VEC consecutive classes of a single-wire gate of dimension DT.
-// Members of a class sit bt apart; consecutive threads own consecutive
-// classes, so each row access of a warp is one contiguous run whenever the
-// enumeration's run (the smallest inserted stride) is at least 32*VEC.
+// The update of VEC consecutive classes whose first member is psi[j].
 template <typename R, int DT, int VEC>
-__global__ void __launch_bounds__(256) k_gate1(const __grid_constant__ Gate1Args<R, DT> a) {
+__device__ __forceinline__ void gate1_class(const Gate1Args<R, DT>& a, uint64_t j) {
     using T2 = typename Cplx<R>::T2;
-    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= a.n_elems) return;
-    const uint64_t j = a.map.map(e * VEC);
     T2* base = a.psi + j;
     T2 x[DT][VEC];
 #pragma unroll
@@ -93,6 +87,37 @@ __global__ void __launch_bounds__(256) k_gate1(const __grid_constant__ Gate1Args
 #pragma unroll
     for (int r = 0; r < DT; ++r)
         if (a.smask >> r & 1u) Ld<VEC>::store(base + (uint64_t)r * a.bt, y[r]);
+}
+
+// One thread = VEC consecutive classes of a single-wire gate of dimension DT.
+// Members of a class sit bt apart; consecutive threads own consecutive
+// classes, so each row access of a warp is one contiguous run whenever the
+// enumeration's run (the smallest inserted stride) is at least 32*VEC.
+// Control digits are inserted into the enumeration: only matching classes
+// are visited.
+template <typename R, int DT, int VEC>
+__global__ void __launch_bounds__(256) k_gate1(const __grid_constant__ Gate1Args<R, DT> a) {
+    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.n_elems) return;
+    gate1_class<R, DT, VEC>(a, a.map.map(e * VEC));
+}
+
+// The paper's formulation of a controlled gate, kept for comparison: every
+// class of the target wire is visited and its control digits
+// floor(j / b_c) mod d_c are tested against the control values one by one
+// (section "Controlled and Multi-Controlled Gates": a check per index and
+// control, O(D M)); matching classes get the same update as in k_gate1.
+template <typename R, int DT>
+__global__ void __launch_bounds__(256) k_gate1_scan(const __grid_constant__ Gate1Args<R, DT> a,
+                                                    const __grid_constant__ ScanControls c) {
+    const uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= a.n_elems) return;
+    const uint64_t j = a.map.map(e);
+    for (int m = 0; m < c.m; ++m) {
+        const uint64_t q = c.stride[m].div(j);
+        if (q - c.dim[m].div(q) * c.dim[m].d != c.val[m]) return;
+    }
+    gate1_class<R, DT, 1>(a, j);
 }
 
 // Shared-memory tile kernel for any gate with P <= 64 (multi-wire gates and
@@ -226,6 +251,58 @@ __global__ void __launch_bounds__(256) k_norm_partial(const typename Cplx<R>::T2
     }
 }
 
+// Complex64 norm with little binary64 work (binary64 is slow on this part):
+// |a|^2 = x^2 + y^2 is exactly p1 + e1 + p2 + e2 with p = x*x and e =
+// fma(x, x, -p) (TwoProduct); runs of 16 amplitudes are summed in binary32
+// with Neumaier compensation, the exact product errors going into the
+// compensation, and each run's (s, c) is added to the binary64 compensated
+// sum.  The binary32 run sum errs by at most about 16 u^2 sum|x| (u = 2^-24),
+// below 1e-14 relative.  Two amplitudes per 16-byte load; psi 16-byte aligned.
+__device__ __forceinline__ void fsum_add(float& s, float& c, float x) {
+    const float t = s + x;
+    if (fabsf(s) >= fabsf(x))
+        c += (s - t) + x;
+    else
+        c += (x - t) + s;
+    s = t;
+}
+__device__ __forceinline__ void fsum_prob(float& s, float& c, float x, float y) {
+    const float p1 = x * x, p2 = y * y;
+    c += fmaf(x, x, -p1) + fmaf(y, y, -p2);
+    fsum_add(s, c, p1);
+    fsum_add(s, c, p2);
+}
+
+__global__ void __launch_bounds__(256) k_norm_partial_c64(const float4* psi2, int64_t D, double* partials) {
+    CSum acc{0.0, 0.0};
+    const int64_t pairs = D >> 1;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    while (i < pairs) {
+        float s = 0.f, c = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 8 && i < pairs; ++k, i += stride) {
+            const float4 v = psi2[i];
+            fsum_prob(s, c, v.x, v.y);
+            fsum_prob(s, c, v.z, v.w);
+        }
+        csum_add(acc, (double)s);
+        acc.c += (double)c;
+    }
+    if ((D & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const float2 v = reinterpret_cast<const float2*>(psi2)[D - 1];
+        float s = 0.f, c = 0.f;
+        fsum_prob(s, c, v.x, v.y);
+        csum_add(acc, (double)s);
+        acc.c += (double)c;
+    }
+    acc = block_reduce(acc);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = acc.s;
+        partials[2 * blockIdx.x + 1] = acc.c;
+    }
+}
+
 // Reduce rows of partials: out[row] = sum over nb (s, c) pairs of row `blockIdx.x`.
 __global__ void __launch_bounds__(256) k_reduce_final(const double* partials, int nb, double* out) {
     const double* p = partials + (size_t)blockIdx.x * 2 * nb;
@@ -324,6 +401,15 @@ cudaError_t launch_gate_tile(const GateTileArgs<R>& a, cudaStream_t s, int smem_
     return cudaGetLastError();
 }
 
+template <typename R, int DT>
+cudaError_t launch_gate1_scan(const Gate1Args<R, DT>& a, const ScanControls& c, cudaStream_t s) {
+    if (a.n_elems == 0) return cudaSuccess;
+    const uint64_t blocks = (a.n_elems + 255) / 256;
+    k_gate1_scan<R, DT><<<(unsigned)blocks, 256, 0, s>>>(a, c);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_set_basis(void* psi, int64_t D, int64_t index, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(psi, 0, (size_t)D * sizeof(typename Cplx<R>::T2), s);
@@ -336,8 +422,11 @@ cudaError_t launch_set_basis(void* psi, int64_t D, int64_t index, cudaStream_t s
 template <typename R>
 cudaError_t launch_norm(const void* psi, int64_t D, double* partials, int nblocks, double* dev_out,
                         cudaStream_t s) {
-    k_norm_partial<R><<<nblocks, 256, 0, s>>>(reinterpret_cast<const typename Cplx<R>::T2*>(psi), D,
-                                              partials);
+    if (sizeof(R) == 4 && reinterpret_cast<uintptr_t>(psi) % 16 == 0)
+        k_norm_partial_c64<<<nblocks, 256, 0, s>>>(reinterpret_cast<const float4*>(psi), D, partials);
+    else
+        k_norm_partial<R><<<nblocks, 256, 0, s>>>(reinterpret_cast<const typename Cplx<R>::T2*>(psi), D,
+                                                  partials);
     k_reduce_final<<<1, 256, 0, s>>>(partials, nblocks, dev_out);
     count_launch(2);
     return cudaGetLastError();
@@ -378,10 +467,14 @@ cudaError_t launch_narrow(const double* in, int64_t D, void* psi, cudaStream_t s
 // Explicit instantiations.
 #define QD_INST_GATE1(R, DT, VEC) \
     template cudaError_t launch_gate1<R, DT, VEC>(const Gate1Args<R, DT>&, cudaStream_t);
+#define QD_INST_SCAN(R, DT) \
+    template cudaError_t launch_gate1_scan<R, DT>(const Gate1Args<R, DT>&, const ScanControls&, cudaStream_t);
 #define QD_INST_GATE1_ALL(DT)       \
     QD_INST_GATE1(float, DT, 1)     \
     QD_INST_GATE1(float, DT, 2)     \
-    QD_INST_GATE1(double, DT, 1)
+    QD_INST_GATE1(double, DT, 1)    \
+    QD_INST_SCAN(float, DT)         \
+    QD_INST_SCAN(double, DT)
 QD_INST_GATE1_ALL(2)
 QD_INST_GATE1_ALL(3)
 QD_INST_GATE1_ALL(4)

@@ -19,6 +19,7 @@ struct HGate {
     const double* U;
     Plan plan;
     bool diag, fusable;
+    bool unitary;  // U^H U = I to 1e-10 (binary64); blocks of unitary gates are unitary
     uint64_t tmask, cmask;
 };
 
@@ -29,6 +30,7 @@ struct FuseCfg {
     int64_t min_row;
     int block_dim;  // largest composed block inside a pass (< 4: no composition)
     int tc_mode;    // QD_TC_*: complex64 blocks of 17..64 dimensions
+    bool persistent;  // light tile passes may use the persistent kernel (one CTA per SM, whole GPU)
 };
 
 int64_t tile_limit(int32_t prec);

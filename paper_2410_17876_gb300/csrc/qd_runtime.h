@@ -90,7 +90,7 @@ struct qd_state {
     cudaEvent_t ring_ev[kRingSlots];
     bool ring_ev_live[kRingSlots];
     int ring_next;
-    qd::Arena* arena;    // descriptors of circuit calls (device + pinned staging)
+    qd::Arena* arena;    // two descriptor arenas of circuit calls (device + pinned staging), alternating
     int32_t tc_mode;     // QD_TC_*: complex64 gates of 17..64 dimensions (0 = QD_TC_TF32X3)
     int32_t fuse_dim;    // deferred fusion: largest composed block (< 2: off)
     qd::Pending* pend;   // gates queued by deferred fusion

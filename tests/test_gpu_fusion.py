@@ -105,3 +105,38 @@ def test_tile_too_large_is_rejected(qb, gen):
         st.run(circ, fuse=True, max_tile_amps=1 << 20)
     assert ei.value.status == qb.QD_ERR_UNSUPPORTED
     st.close()
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_light_passes_persistent_kernel(qb, gen, prec):
+    """Passes light on arithmetic (phase and permutation gates, a few
+    controlled) run on the persistent double-buffered tile kernel: 2.98M
+    amplitudes in tiles of at most 4096, so every CTA walks several tiles
+    through both buffers, with controls outside the tile evaluated per tile."""
+    p = qb.QD_C64 if prec == "c64" else qb.QD_C128
+    rng = np.random.Generator(np.random.PCG64(77))
+    dims = (2,) * 12 + (3,) * 6
+    gates = []
+    for i in range(60):
+        w = int(rng.integers(0, len(dims)))
+        d = dims[w]
+        k = i % 3
+        if k == 0:
+            U = np.diag(np.exp(2j * np.pi * rng.random(d)))
+        elif k == 1:
+            U = gen.x_plus(d, 1)
+        else:
+            U = np.diag(np.exp(2j * np.pi * np.arange(d) / d))
+        if i % 7 == 3:
+            c = int(rng.integers(0, len(dims)))
+            if c != w:
+                gates.append(gen.Gate((w,), U, (c,), (int(rng.integers(0, dims[c])),)))
+                continue
+        gates.append(gen.Gate((w,), U))
+    circ = gen.Circuit(dims, gates)
+    psi0 = gen.random_state(circ.D, rng)
+    plan = qb.qd_plan_circuit(dims, p, circ, mode=qb.QD_FUSE_TILE, max_tile_amps=4096, with_flops=True)
+    assert any(t > 0 for t in plan[2]) and max(plan[3]) / circ.D < 150  # tile passes, all light
+    got = _run(qb, circ, p, psi0, max_tile_amps=4096)
+    assert_close(got, oracle.run_circuit(circ, psi0, nthreads=max(1, oracle.max_threads())), p,
+                 f"light passes {prec}")
