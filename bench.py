@@ -380,6 +380,39 @@ def measure_stride_sweep(qb, gen, torch, stream, reps=20, amp_bytes=8):
             "dense_frac_median": float(np.median([r["dense"]["frac_of_measured_hbm"] for r in rows]))}
 
 
+def measure_sparse_ghz(qb, gen, reps=20):
+    """GHZ preparation on sparse states (qd_sparse_run: one launch per circuit, the
+    non-zero amplitudes in one CTA's shared memory), at the sizes of the paper's
+    sparse runs (62 qubits, 39 qutrits, 31 ququads, 27 ququints: 0.15 / 0.188 / 0.2 /
+    0.21 ms on its CPU) and beyond 64-bit indices.  Wall time of the synchronous call
+    (gate upload, kernel, status read-back), median of ``reps``; the result is checked
+    against the closed form sum_k |k...k> / sqrt(d)."""
+    paper_ms = {(2, 62): 0.15, (3, 39): 0.188, (4, 31): 0.2, (5, 27): 0.21}
+    rows = []
+    for d, n in ((2, 62), (3, 39), (4, 31), (5, 27), (2, 127), (3, 64), (5, 42)):
+        dims = (d,) * n
+        circ = gen.ghz_circuit(dims)
+        qb.circuit_arrays(circ)
+        ts = []
+        ok = True
+        for _ in range(reps + 2):
+            s = qb.qd_sparse_create(dims)
+            t0 = time.perf_counter()
+            qb.qd_sparse_run(s, circ)
+            ts.append(time.perf_counter() - t0)
+            got = qb.qd_sparse_get(s)
+            qb.qd_sparse_destroy(s)
+            stride_sum = sum(d ** w for w in range(n))
+            ok = ok and len(got) == d and all(abs(got.get(k * stride_sum, 0) - d ** -0.5) < 1e-15 for k in range(d))
+        t = float(np.median(ts[2:]))
+        row = {"d": d, "wires": n, "gates": len(circ.gates), "ms": 1e3 * t, "closed_form_ok": ok}
+        if (d, n) in paper_ms:
+            row["paper_ms_cpu"] = paper_ms[(d, n)]
+        rows.append(row)
+    return {"workload": "GHZ circuits on sparse states (F_d on wire 0, then controlled X_{+v} on every other "
+                        "wire), complex128", "rows": rows}
+
+
 def measure_many_controls(qb, gen, torch, stream, reps=10):
     """Controlled X_{+1} with M = 1..16 controls on the 12-qubit + 8-qutrit layout
     (26,873,856 complex64 amplitudes): the digit-insertion enumeration
@@ -724,6 +757,7 @@ def run_gpu(args):
         extra["stride_sweep"] = measure_stride_sweep(qb, gen, torch, stream)
         torch.cuda.empty_cache()
         extra["many_controls"] = measure_many_controls(qb, gen, torch, stream)
+        extra["sparse_ghz"] = measure_sparse_ghz(qb, gen)
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(qb, gen, torch, stream)
         torch.cuda.empty_cache()

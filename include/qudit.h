@@ -253,6 +253,45 @@ qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd
                           double* pass_flops, int32_t* n_passes);
 
 /* ------------------------------------------------------------------------
+ * Sparse states (the paper's sparse variant: only the non-zero amplitudes
+ * are stored, and a unitary is applied by inspecting their indices; end of
+ * section "Example Circuit", GHZ runs of section "Experimental Analysis").
+ * complex128 amplitudes; single-wire gates on wires of dimension 2..8,
+ * optionally controlled.  Basis states are 128-bit keys, so the basis
+ * may be far larger than 2^64 (the paper's keys are 64-bit): the wires'
+ * bit widths ceil(log2 d) must sum to at most 128 and D must stay below
+ * 2^128.  A whole circuit runs in one launch on one CTA with the
+ * amplitudes in shared memory: at most QD_SPARSE_MAX_NNZ non-zero
+ * amplitudes after every gate.
+ * --------------------------------------------------------------------- */
+#define QD_SPARSE_MAX_NNZ 512
+#define QD_SPARSE_MAX_WIRES 128
+
+typedef struct qd_sparse qd_sparse;
+
+/* A sparse state in |0...0> on n wires (dims[w] in 2..8).  stream: the
+ * cudaStream_t its work runs on (NULL = legacy default stream).
+ * QD_ERR_ARG for a dimension out of range or a basis beyond 128 bits. */
+qd_status qd_sparse_create(const int32_t* dims, int32_t n, void* stream, qd_sparse** out);
+qd_status qd_sparse_destroy(qd_sparse* s);
+
+/* Apply n_gates single-wire gates (qd_gate_desc with n_wires = 1, controls
+ * allowed; matrices as in qd_apply_circuit) in order.  Synchronous.  Exact
+ * zeros are dropped.  QD_ERR_UNSUPPORTED (state left as before the call)
+ * if a gate has more than one wire or the support exceeds QD_SPARSE_MAX_NNZ. */
+qd_status qd_sparse_run(qd_sparse* s, const qd_gate_desc* gates, int32_t n_gates, const double* matrices);
+
+/* Number of stored (non-zero) amplitudes. */
+qd_status qd_sparse_nnz(const qd_sparse* s, int64_t* nnz);
+
+/* The stored amplitudes in ascending basis-index order: index i =
+ * index_lo[i] + 2^64 index_hi[i] (mixed-radix, q_0 least significant),
+ * amplitude (amps[2i], amps[2i+1]).  max = room in each array
+ * (QD_ERR_ARG if it is below the count); *n_out = count. */
+qd_status qd_sparse_get(qd_sparse* s, uint64_t* index_lo, uint64_t* index_hi, double* amps_interleaved,
+                        int64_t max, int64_t* n_out);
+
+/* ------------------------------------------------------------------------
  * Batches of independent circuits.  Each circuit starts from its own
  * |0...0> state; the states of one run live side by side in one device
  * buffer owned by the batch.  The paper simulates one circuit at a time;

@@ -99,6 +99,12 @@ _SIGS = {
     "qd_marginal": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
     "qd_synchronize": (ctypes.c_int32, [_vp]),
     "qd_set_fusion": (ctypes.c_int32, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "qd_sparse_create": (ctypes.c_int32, [_i32p, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
+    "qd_sparse_destroy": (ctypes.c_int32, [_vp]),
+    "qd_sparse_run": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_gate_desc), ctypes.c_int32, _f64p]),
+    "qd_sparse_nnz": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "qd_sparse_get": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _f64p,
+                                       ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "qd_apply_controlled_scan": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p, _i32p, _i32p, ctypes.c_int32]),
     "qd_flush": (ctypes.c_int32, [_vp]),
     "qd_norm_noalloc": (ctypes.c_int32, [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]),
@@ -390,6 +396,44 @@ def qd_apply_circuit(st: int, circuit, mode=QD_FUSE_OFF, max_tile_amps=0, min_ga
     _check(_lib.qd_apply_circuit(_vp(st), descs, len(circuit.gates), _p(m, _f64p),
                                  _opts(mode, max_tile_amps, min_gates, min_row, block_dim, tc_mode)),
            "qd_apply_circuit")
+
+
+QD_SPARSE_MAX_NNZ = 512
+
+
+def qd_sparse_create(dims, stream=None) -> int:
+    d = _i32(dims)
+    out = _vp()
+    _check(_lib.qd_sparse_create(_p(d, _i32p), len(d), _vp(stream), ctypes.byref(out)), "qd_sparse_create")
+    return out.value
+
+
+def qd_sparse_destroy(s: int) -> None:
+    _check(_lib.qd_sparse_destroy(_vp(s)), "qd_sparse_destroy")
+
+
+def qd_sparse_run(s: int, circuit) -> None:
+    descs, m = circuit_arrays(circuit)
+    _check(_lib.qd_sparse_run(_vp(s), descs, len(circuit.gates), _p(m, _f64p)), "qd_sparse_run")
+
+
+def qd_sparse_nnz(s: int) -> int:
+    n = ctypes.c_int64()
+    _check(_lib.qd_sparse_nnz(_vp(s), ctypes.byref(n)), "qd_sparse_nnz")
+    return n.value
+
+
+def qd_sparse_get(s: int) -> dict:
+    """{basis index (Python int): complex amplitude}, ascending indices."""
+    n = qd_sparse_nnz(s)
+    lo = np.zeros(max(n, 1), dtype=np.uint64)
+    hi = np.zeros(max(n, 1), dtype=np.uint64)
+    amps = np.zeros(2 * max(n, 1), dtype=np.float64)
+    got = ctypes.c_int64()
+    _check(_lib.qd_sparse_get(_vp(s), lo.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                              hi.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), _p(amps, _f64p), max(n, 1),
+                              ctypes.byref(got)), "qd_sparse_get")
+    return {int(lo[i]) + (int(hi[i]) << 64): complex(amps[2 * i], amps[2 * i + 1]) for i in range(got.value)}
 
 
 def qd_set_fusion(st: int, max_block_dim: int, tc_mode=QD_TC_TF32X3) -> None:
