@@ -23,6 +23,7 @@ import numpy as np
 # 1 = shared-memory tile passes, 2 = whole-state composed blocks
 FUSION_CANDIDATES = {
     0: [(0, 0, 0)] + [(1, t, b) for t in (2048, 4096, 8192, 16384) for b in (1, 4, 8, 16)]
+       + [(1, t, b) for t in (4096, 8192) for b in (24, 32)]  # blocks of 17..32 dims on tensor cores in tiles
        + [(2, 0, b) for b in (32, 64)],
     1: [(0, 0, 0)] + [(1, t, b) for t in (1024, 2048, 4096, 8192) for b in (1, 4, 8, 16)]
        + [(2, 0, b) for b in (4, 8)],

@@ -20,6 +20,7 @@
 
 #include "qd_internal.cuh"
 #include "qd_program.h"
+#include "qd_tc_common.cuh"
 #include "qd_runtime.h"
 
 namespace qd {
@@ -68,7 +69,9 @@ struct __align__(16) LocalMap {
     }
 };
 
-constexpr int kMaxBlock = 16;       // largest composed block (product of its wires' dimensions)
+constexpr int kMaxBlock = 16;       // largest composed block on CUDA cores (product of its wires' dimensions)
+constexpr int kMaxTcBlock = 32;     // complex64: blocks of 17..32 dimensions run on the tensor cores inside tiles
+constexpr uint8_t kTcBlock = 3;     // FGate kind of such a block
 constexpr int kMaxChunkGates = 64;  // gate records per chunk
 constexpr int kPoolEntries = 2048;  // matrix entries per chunk (complex, in the state's precision)
 
@@ -84,12 +87,12 @@ struct __align__(16) FGate {
     uint32_t lst, step;
     uint32_t u_off;  // matrix: entries [u_off, u_off + PP * PP) of the chunk pool, row-major, PP columns
     uint8_t P, PP, kind, single;
-    uint8_t n_out, pure, pad0[2];
+    uint8_t n_out, pure, unitary, pad0;
     uint16_t lmask, smask;
-    uint8_t pad1[4];
+    uint32_t op_off;  // kTcBlock: byte offset of the B operand (hi | lo, 32 KB) from the descriptor base
     uint8_t perm[kMaxBlock];
     uint8_t out_w[8], out_v[8];  // controls outside the tile: global wire, value
-    uint16_t off[kMaxBlock];
+    uint16_t off[kMaxTcBlock];
 };
 
 // Chunk header; the chunk is [header][ngates FGate][npool matrix entries], 16-byte aligned.
@@ -124,7 +127,8 @@ struct FusedArgs {
     FastDiv32 free_div[kMaxWires];  // division by free_d (tile indices are below 2^32)
     uint64_t free_b[kMaxWires];
     const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
-    int32_t* status;         // persistent kernel: set to QD_ERR_TIMEOUT if a bounded wait gave up
+    int32_t* status;         // persistent and tensor-core kernels: QD_ERR_TIMEOUT if a bounded wait gave up
+    const char* desc_base;   // the program's descriptors (tensor-core operands)
 };
 
 
@@ -372,11 +376,140 @@ __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGa
     }
 }
 
+// Tensor-core blocks inside a tile (complex64, blocks of 17..32 dimensions).
+// For 128 classes at a time the block is the contraction
+//     Y (128 x 64) = X (128 x 64) . B^T,  B = [[Re U, -Im U], [Im U, Re U]]
+// with the members' real parts at K = 0..31 and imaginary parts at 32..63
+// (zero-padded beyond P), outputs likewise along N.  X is staged from the
+// tile into tensor memory (tcgen05.st, lane = class) as TF32 hi / lo parts;
+// B (hi | lo, 32 KB, K-major) comes from the program's descriptors into
+// shared memory; one thread issues 3 x 8 MMAs (M = 128, N = 64, K = 8,
+// A_hi B_hi + A_hi B_lo + A_lo B_hi) into the accumulator, commits to an
+// mbarrier, and every thread waits (bounded).  The epilogue reads its
+// outputs back (tcgen05.ld), restores each class's 2-norm when the block is
+// unitary (the tensor cores' FP32 accumulation is biased toward zero) and
+// writes them into the tile.  Tensor memory: A_hi [0, 64), A_lo [64, 128),
+// D [128, 192).  256 threads: thread t handles class t % 128 of the group,
+// members / outputs 16 (t / 128) .. + 15.
+struct TcTileCtx {
+    uint32_t tm;      // tensor memory base
+    uint32_t mbar;    // shared address of the MMA mbarrier
+    uint32_t phase;   // its next phase parity
+    float* sB;        // shared: B_hi | B_lo (2 x 64 x 64 floats)
+    const char* desc; // the program's descriptors (global)
+    float* s_nin;     // shared [2][128]: input norms, two halves per class
+    float* s_nout;    // shared [2][128]
+};
+constexpr uint32_t kTileTcOpBytes = 2u * 64u * 64u * 4u;
+
+__device__ bool tile_tc_block(float2* tile, const FGate& G, TcTileCtx& c) {
+    const int tid = threadIdx.x, warp = tid >> 5;
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(c.desc + G.op_off);
+        uint4* dst = reinterpret_cast<uint4*>(c.sB);
+        for (int i = tid; i < (int)(kTileTcOpBytes / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    const int row = tid & 127, half = tid >> 7;
+    const uint32_t lanes = (uint32_t)(32 * (warp & 3)) << 16;
+    const int P = G.P;
+    const uint32_t nc = G.nclasses;
+    const uint32_t idesc = tc_idesc(2u);  // TF32, M = 128, N = 64
+    for (uint32_t g0 = 0; g0 < nc; g0 += 128) {
+        const uint32_t cls = g0 + (uint32_t)row;
+        const bool valid = cls < nc;
+        const uint32_t base = valid ? G.map.map(cls) : 0u;
+        float pn = 0.f;
+        {
+            float xr[16], xi[16], h[16], l[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int r = 16 * half + i;
+                const float2 v = (valid && r < P) ? tile[base + G.off[r]] : make_float2(0.f, 0.f);
+                xr[i] = v.x;
+                xi[i] = v.y;
+                pn = fmaf(v.x, v.x, fmaf(v.y, v.y, pn));
+            }
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                h[i] = tf32_hi(xr[i]);
+                l[i] = xr[i] - h[i];
+            }
+            tmem_st16(c.tm + lanes + 16u * half, h);
+            tmem_st16(c.tm + lanes + 64u + 16u * half, l);
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                h[i] = tf32_hi(xi[i]);
+                l[i] = xi[i] - h[i];
+            }
+            tmem_st16(c.tm + lanes + 32u + 16u * half, h);
+            tmem_st16(c.tm + lanes + 96u + 16u * half, l);
+        }
+        c.s_nin[half * 128 + row] = pn;
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // every member gathered before any output is written back
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            const uint32_t lbo = (64 / 8) * 128;  // bytes between core matrices along K (64 rows)
+            const uint64_t bd0 = smem_desc(smem_u32(c.sB), lbo, 128);
+            constexpr uint64_t kStep = 2 * (64 / 8) * 128 / 16;  // one k-step: two core matrices, 16-byte units
+            constexpr uint64_t kLo = (64u * 64u * 4u) >> 4;        // B_lo
+#pragma unroll
+            for (int term = 0; term < 3; ++term) {
+                const uint32_t a0 = c.tm + (term == 2 ? 64u : 0u);         // A_lo for the third product
+                const uint64_t b0 = bd0 + (term == 1 ? kLo : 0);            // B_lo for the second
+#pragma unroll
+                for (int ks = 0; ks < 8; ++ks)
+                    mma_tf32_ta(c.tm + 128u, a0 + 8u * (uint32_t)ks, b0 + (uint64_t)ks * kStep, idesc,
+                                (term | ks) != 0 ? 1u : 0u);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(c.mbar)
+                         : "memory");
+        }
+        const bool ok = mbar_wait(c.mbar, c.phase);
+        c.phase ^= 1u;
+        if (__syncthreads_or(!ok)) return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float yr[16], yi[16];
+        tmem_ld16(c.tm + lanes + 128u + 16u * half, yr);
+        tmem_ld16(c.tm + lanes + 160u + 16u * half, yi);
+        float po = 0.f;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) po = fmaf(yr[i], yr[i], fmaf(yi[i], yi[i], po));
+        c.s_nout[half * 128 + row] = po;
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        float cc = 0.f;
+        if (G.unitary) {
+            // as in the whole-state kernel: y <- y (1 + c), c = sqrt(ni / no) - 1
+            const float ni = c.s_nin[row] + c.s_nin[128 + row], no = c.s_nout[row] + c.s_nout[128 + row];
+            if (ni > 0.f && no > 0.f) {
+                const float sn = sqrtf(no);
+                cc = (ni - no) / (sn * (sqrtf(ni) + sn));
+            }
+        }
+        if (valid) {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int r = 16 * half + i;
+                if (r < P) tile[base + G.off[r]] = make_float2(fmaf(yr[i], cc, yr[i]), fmaf(yi[i], cc, yi[i]));
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();  // the next group reuses tensor memory and the norm arrays
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    }
+    return true;
+}
+
 // Apply a list of chunks to a tile in shared memory.  stage: shared memory
-// for one chunk; odig: digits of the wires outside the tile (fused passes).
-template <typename R, int DMAX>
-__device__ __forceinline__ void apply_chunks(typename Cplx<R>::T2* tile, const char* chunk, int nchunks,
-                                             unsigned char* stage, const int32_t* odig) {
+// for one chunk; odig: digits of the wires outside the tile (fused passes);
+// tc: tensor-core context (TC = true: complex64 tiles with kTcBlock gates).
+// Returns false (the same on every thread) if a tensor-core wait gave up.
+template <typename R, int DMAX, bool TC = false>
+__device__ __forceinline__ bool apply_chunks(typename Cplx<R>::T2* tile, const char* chunk, int nchunks,
+                                             unsigned char* stage, const int32_t* odig, TcTileCtx* tc = nullptr) {
     using T2 = typename Cplx<R>::T2;
     for (int ci = 0; ci < nchunks; ++ci) {
         const ChunkHdr h = *reinterpret_cast<const ChunkHdr*>(chunk);
@@ -395,6 +528,12 @@ __device__ __forceinline__ void apply_chunks(typename Cplx<R>::T2* tile, const c
                 bool ok = true;
                 for (int c = 0; c < G.n_out; ++c) ok = ok && (odig[G.out_w[c]] == (int32_t)G.out_v[c]);
                 if (!ok) continue;  // uniform across the CTA
+            }
+            if constexpr (TC && sizeof(R) == 4) {
+                if (G.kind == kTcBlock) {
+                    if (!tile_tc_block(reinterpret_cast<float2*>(tile), G, *tc)) return false;
+                    continue;  // tile_tc_block ends with a barrier
+                }
             }
             if (G.single) {
                 if (G.P == 2) tile_gate<R, 2>(tile, G, pool);
@@ -415,6 +554,7 @@ __device__ __forceinline__ void apply_chunks(typename Cplx<R>::T2* tile, const c
         }
         chunk += h.bytes;
     }
+    return true;
 }
 
 __host__ __device__ inline size_t fused_rows_bytes(uint32_t rows) { return ((size_t)rows * 8 + 15) & ~(size_t)15; }
@@ -607,6 +747,114 @@ __global__ void __launch_bounds__(512, 1) k_fused_pipe(const __grid_constant__ F
     __syncthreads();
 }
 
+// Tile pass whose chunks hold tensor-core blocks (complex64): k_fused_tile
+// plus tensor memory (256 columns), an MMA mbarrier and the 32 KB operand
+// buffer.  At most two CTAs per SM (shared memory is padded to keep it so),
+// which is what the 512 tensor-memory columns of an SM hold.  A timed-out
+// MMA wait stops the tile (status QD_ERR_TIMEOUT, tile not written back).
+constexpr size_t kTcTileMinSmem = 80 * 1024;  // > 228 KB / 3: at most two CTAs per SM
+
+template <int DMAX>
+__global__ void __launch_bounds__(256, 2) k_fused_tile_tc(const __grid_constant__ FusedArgs<float> a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* stage = smem_raw;
+    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + chunk_smem_max<float>());
+    float2* tile = reinterpret_cast<float2*>(smem_raw + chunk_smem_max<float>() + fused_rows_bytes(a.rows));
+    float* sB = reinterpret_cast<float*>(
+        smem_raw + ((chunk_smem_max<float>() + fused_rows_bytes(a.rows) + 8 * (size_t)a.T + 127) & ~(size_t)127));
+    __shared__ int32_t odig[kMaxWires];
+    __shared__ uint64_t sbase;
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    __shared__ float s_nin[256], s_nout[256];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((tid >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (uint32_t r = tid; r < a.rows; r += blockDim.x) srow[r] = a.rowoff[r];
+    if (tid == 0) {
+        uint32_t rem = blockIdx.x;
+        uint64_t base = 0;
+        for (int i = 0; i < a.nfree; ++i) {
+            const uint32_t q = a.free_div[i].div(rem);
+            const uint32_t dig = rem - q * a.free_d[i];
+            odig[a.free_w[i]] = (int32_t)dig;
+            base += (uint64_t)dig * a.free_b[i];
+            rem = q;
+        }
+        sbase = base;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float2* g = a.psi + sbase;
+    if (a.vec2) {
+        for (uint32_t e = 2 * tid; e < a.T; e += 2 * blockDim.x) {
+            const uint32_t r = a.bLdiv.div(e);
+            reinterpret_cast<float4*>(tile)[e >> 1] = *reinterpret_cast<const float4*>(g + srow[r] + (e - r * a.bL));
+        }
+    } else {
+        for (uint32_t e = tid; e < a.T; e += blockDim.x) {
+            const uint32_t r = a.bLdiv.div(e);
+            tile[e] = g[srow[r] + (e - r * a.bL)];
+        }
+    }
+    TcTileCtx ctx{tmem_base, smem_u32(&mbar), 0u, sB, a.desc_base, s_nin, s_nout};
+    const bool ok = apply_chunks<float, DMAX, true>(tile, a.chunks, a.nchunks, stage, odig, &ctx);
+    __syncthreads();
+    if (ok) {
+        if (a.vec2) {
+            for (uint32_t e = 2 * tid; e < a.T; e += 2 * blockDim.x) {
+                const uint32_t r = a.bLdiv.div(e);
+                *reinterpret_cast<float4*>(g + srow[r] + (e - r * a.bL)) = reinterpret_cast<const float4*>(tile)[e >> 1];
+            }
+        } else {
+            for (uint32_t e = tid; e < a.T; e += blockDim.x) {
+                const uint32_t r = a.bLdiv.div(e);
+                g[srow[r] + (e - r * a.bL)] = tile[e];
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(a.status, QD_ERR_TIMEOUT);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if ((tid >> 5) == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(256));
+}
+
+size_t fused_tc_smem(uint32_t T, uint32_t rows) {
+    const size_t s = ((chunk_smem_max<float>() + fused_rows_bytes(rows) + 8 * (size_t)T + 127) & ~(size_t)127) +
+                     kTileTcOpBytes;
+    return s < kTcTileMinSmem ? kTcTileMinSmem : s;
+}
+
+cudaError_t launch_fused_tc(const FusedArgs<float>& a, int dmax, cudaStream_t s) {
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused_tile_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_tile_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const size_t smem = fused_tc_smem(a.T, a.rows);
+    if (smem > 220 * 1024) return cudaErrorInvalidValue;
+    if (dmax <= 3)
+        k_fused_tile_tc<3><<<(unsigned)a.ntiles, 256, smem, s>>>(a);
+    else
+        k_fused_tile_tc<5><<<(unsigned)a.ntiles, 256, smem, s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
 template <typename R>
 size_t fused_smem(const FusedArgs<R>& a) {
     return chunk_smem_max<R>() + fused_rows_bytes(a.rows) + sizeof(typename Cplx<R>::T2) * (size_t)a.T;
@@ -768,17 +1016,19 @@ int64_t tile_limit(int32_t prec) { return prec == QD_C64 ? 16384 : 8192; }
 FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     FuseCfg c;
     c.mode = o ? o->mode : QD_FUSE_OFF;
+    c.tc_mode = o ? o->tc_mode : QD_TC_TF32X3;
     c.Tmax = (o && o->max_tile_amps > 0) ? o->max_tile_amps : (prec == QD_C64 ? 8192 : 4096);
     c.min_gates = (o && o->min_gates > 0) ? o->min_gates : 2;
     c.min_row = (o && o->min_row > 0) ? o->min_row : (prec == QD_C64 ? 16 : 8);
-    c.tc_mode = o ? o->tc_mode : QD_TC_TF32X3;
     c.persistent = true;
     if (c.mode == QD_FUSE_BLOCK) {
         c.block_dim = (o && o->block_dim > 0) ? o->block_dim : (prec == QD_C64 ? 64 : 8);
         if (c.block_dim > 64) c.block_dim = 64;
     } else {
+        // blocks of 17..32 dimensions run on the tensor cores (complex64 tiles only)
+        const int cap = (prec == QD_C64 && c.tc_mode != QD_TC_OFF) ? kMaxTcBlock : kMaxBlock;
         c.block_dim = (o && o->block_dim > 0) ? o->block_dim : kMaxBlock;
-        if (c.block_dim > kMaxBlock) c.block_dim = kMaxBlock;
+        if (c.block_dim > cap) c.block_dim = cap;
     }
     // rows per tile are bounded by the row table
     const int64_t need = (c.Tmax + kMaxRows - 1) / kMaxRows;
@@ -981,7 +1231,7 @@ static int padded_dim(int P) {
     static const int sizes[] = {4, 6, 8, 9, 12, 16};
     for (int q : sizes)
         if (P <= q) return q;
-    return 16;
+    return P <= kMaxBlock ? kMaxBlock : kMaxTcBlock;
 }
 
 static uint64_t local_mask(const TileGeom& geo, uint64_t global) {
@@ -1211,23 +1461,69 @@ static void fill_single(const TileGeom& geo, const HGate& h, FGate& f, std::vect
     f.nclasses = (uint32_t)classes;
 }
 
+// B operand of a tensor-core tile block: the real embedding of the P x P
+// complex matrix M (binary64, row-major interleaved; P <= 32, zero-padded)
+// as 64 rows (outputs: real parts 0..31, imaginary parts 32..63) by 64
+// columns (inputs, same order), split into TF32 hi (rounded to nearest) and
+// lo = value - hi, each 64 x 64 floats in the K-major no-swizzle layout.
+static void tile_tc_pack(const std::vector<double>& M, int P, float* out) {
+    std::memset(out, 0, kTileTcOpBytes);
+    unsigned char* hi = reinterpret_cast<unsigned char*>(out);
+    unsigned char* lo = hi + kTileTcOpBytes / 2;
+    auto put = [&](int n, int k, double v) {
+        const float f = (float)v;
+        uint32_t bits;
+        std::memcpy(&bits, &f, 4);
+        bits = tf32_rne_bits(bits);
+        float h;
+        std::memcpy(&h, &bits, 4);
+        const float l = (float)(v - (double)h);
+        const uint32_t o = kmajor_off((uint32_t)n, (uint32_t)k, 64);
+        std::memcpy(hi + o, &h, 4);
+        std::memcpy(lo + o, &l, 4);
+    };
+    for (int r = 0; r < P; ++r)
+        for (int c = 0; c < P; ++c) {
+            const double re = M[2 * ((size_t)r * P + c)], im = M[2 * ((size_t)r * P + c) + 1];
+            put(r, c, re);
+            put(r, 32 + c, -im);
+            put(32 + r, c, im);
+            put(32 + r, 32 + c, re);
+        }
+}
+
 template <typename R>
 static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const BlockPlan& bp, FGate& f,
-                       std::vector<typename Cplx<R>::T2>& pool) {
+                       std::vector<typename Cplx<R>::T2>& pool, Program* prog = nullptr) {
     std::memset(static_cast<void*>(&f), 0, sizeof f);
     std::vector<double> M;
     std::vector<int> wl;
     int P = 0;
     compose_block(geo, G, bp, M, P, wl);
     const int PP = padded_dim(P);
+    const bool tc = P > kMaxBlock;  // 17..32 dimensions: a tensor-core block (complex64 tiles)
+    if (tc) {
+        f.single = 0;
+        f.P = (uint8_t)P;
+        f.PP = (uint8_t)PP;
+        f.kind = kTcBlock;
+        bool unitary = true;
+        for (int idx : bp.gates) unitary = unitary && G[idx].unitary;
+        f.unitary = unitary ? 1 : 0;
+        if (prog) {
+            std::vector<float> B(kTileTcOpBytes / sizeof(float));
+            tile_tc_pack(M, P, B.data());
+            f.op_off = (uint32_t)prog->put(B.data(), kTileTcOpBytes);
+        }
+    }
     auto re = [&](int r, int c) { return M[2 * ((size_t)r * P + c)]; };
     auto im = [&](int r, int c) { return M[2 * ((size_t)r * P + c) + 1]; };
     auto nz = [&](int r, int c) { return re(r, c) != 0.0 || im(r, c) != 0.0; };
     auto one = [&](int r, int c) { return re(r, c) == 1.0 && im(r, c) == 0.0; };
-    bool diag = true, mono = true;
+    bool diag = !tc, mono = !tc;
     int src[kMaxBlock];
     bool used[kMaxBlock] = {false};
-    for (int r = 0; r < P; ++r) {
+    for (int r = 0; r < P && !tc; ++r) {
         int cnt = 0;
         for (int c = 0; c < P; ++c)
             if (nz(r, c)) {
@@ -1238,6 +1534,7 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
         if (cnt != 1 || used[src[r]]) mono = false;
         else used[src[r]] = true;
     }
+    if (!tc) {
     f.single = 0;
     f.P = (uint8_t)P;
     f.PP = (uint8_t)PP;
@@ -1272,6 +1569,7 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
             v.y = (r < P && c < P) ? (R)im(r, c) : (R)0;
             pool.push_back(v);
         }
+    }  // !tc
     for (int r = 0; r < P; ++r) {
         uint32_t o = 0;
         int rem = r;
@@ -1306,7 +1604,7 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
 // largest single-wire dimension (kernel instance).
 template <typename R>
 static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<BlockPlan>& blocks,
-                          Program& prog, uint32_t* nchunks, int* dmax) {
+                          Program& prog, uint32_t* nchunks, int* dmax, bool* has_tc = nullptr) {
     using T2 = typename Cplx<R>::T2;
     std::vector<char> buf;
     uint32_t n = 0;
@@ -1317,16 +1615,17 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
         std::vector<T2> pool;
         while (i < blocks.size() && fg.size() < (size_t)kMaxChunkGates) {
             const BlockPlan& bp = blocks[i];
+            const int64_t Pb = bp.single ? 0 : local_prod(geo, bp.lw);
             const size_t need = bp.single ? (size_t)G[bp.gates[0]].plan.d * G[bp.gates[0]].plan.d
-                                          : (size_t)padded_dim((int)local_prod(geo, bp.lw)) *
-                                                padded_dim((int)local_prod(geo, bp.lw));
+                                          : (Pb > kMaxBlock ? 0 : (size_t)padded_dim((int)Pb) * padded_dim((int)Pb));
             if (pool.size() + need + 1 > (size_t)kPoolEntries && !fg.empty()) break;
             FGate f;
             if (bp.single) {
                 fill_single<R>(geo, G[bp.gates[0]], f, pool);
                 dm = G[bp.gates[0]].plan.d > dm ? G[bp.gates[0]].plan.d : dm;
             } else {
-                fill_block<R>(geo, G, bp, f, pool);
+                fill_block<R>(geo, G, bp, f, pool, &prog);
+                if (f.kind == kTcBlock && has_tc) *has_tc = true;
             }
             fg.push_back(f);
             ++i;
@@ -1539,7 +1838,8 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
         form_blocks(geo, G, p.gates, cfg.block_dim, blocks);
         uint32_t nchunks = 0;
         int dmax = 2;
-        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax);
+        bool has_tc = false;
+        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax, &has_tc);
         const size_t offR = prog.put(geo.rowoff.data(), sizeof(uint64_t) * geo.R);
         FusedArgs<R> a;
         std::memset(static_cast<void*>(&a), 0, sizeof a);
@@ -1570,12 +1870,19 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
         // turns it off: a kernel holding every SM would serialise requests
         // that otherwise overlap on their streams.
         const double flops_per_amp = pass_arith(L, G, cfg, p) / (double)L.D;
-        const bool pipe = cfg.persistent && a.status != nullptr && flops_per_amp < kPipeMaxFlops &&
+        const bool pipe = !has_tc && cfg.persistent && a.status != nullptr && flops_per_amp < kPipeMaxFlops &&
                           reinterpret_cast<uintptr_t>(psi) % 16 == 0 && fused_pipe_ok<R>(a.T, a.bL, a.rows);
-        prog.ops.push_back([a, offC, offR, dmax, pipe](cudaStream_t s, const char* base) {
+        prog.ops.push_back([a, offC, offR, dmax, pipe, has_tc](cudaStream_t s, const char* base) {
             FusedArgs<R> b = a;
             b.chunks = base + offC;
             b.rowoff = reinterpret_cast<const uint64_t*>(base + offR);
+            b.desc_base = base;
+            if constexpr (sizeof(R) == 4) {
+                if (has_tc) {
+                    if (!b.status) return cudaErrorInvalidSymbol;
+                    return launch_fused_tc(b, dmax, s);
+                }
+            }
             return pipe ? launch_fused_pipe<R>(b, dmax, s) : launch_fused<R>(b, dmax, s);
         });
     }
@@ -1631,7 +1938,8 @@ size_t put_small_chunks(const Layout& L, const std::vector<HGate>& G, const Fuse
     std::vector<int> all(G.size());
     for (size_t i = 0; i < G.size(); ++i) all[i] = (int)i;
     std::vector<BlockPlan> blocks;
-    form_blocks(geo, G, all, cfg.block_dim, blocks);
+    // one-CTA circuits apply chunks without tensor cores: blocks of at most 16 dimensions
+    form_blocks(geo, G, all, cfg.block_dim < kMaxBlock ? cfg.block_dim : kMaxBlock, blocks);
     return emit_chunks<R>(geo, G, blocks, prog, nchunks, nullptr);
 }
 
@@ -1675,7 +1983,8 @@ static double pass_arith(const Layout& L, const std::vector<HGate>& G, const Fus
         FGate fg;
         if (bp.single) fill_single<double>(geo, G[bp.gates[0]], fg, pool);
         else fill_block<double>(geo, G, bp, fg, pool);
-        f += tiles * unit_flops(fg.kind, fg.pure != 0, fg.P, popc(fg.smask), (double)fg.nclasses);
+        if (fg.kind == kTcBlock) f += tiles * 8.0 * fg.P * fg.P * (double)fg.nclasses;  // dense block
+        else f += tiles * unit_flops(fg.kind, fg.pure != 0, fg.P, popc(fg.smask), (double)fg.nclasses);
     }
     return f;
 }

@@ -140,3 +140,31 @@ def test_light_passes_persistent_kernel(qb, gen, prec):
     got = _run(qb, circ, p, psi0, max_tile_amps=4096)
     assert_close(got, oracle.run_circuit(circ, psi0, nthreads=max(1, oracle.max_threads())), p,
                  f"light passes {prec}")
+
+
+@pytest.mark.parametrize("max_tile,block_dim", [(4096, 32), (8192, 24), (2048, 32)])
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_tensor_core_blocks_in_tiles(qb, gen, max_tile, block_dim, seed):
+    """complex64 tile passes whose composed blocks of 17..32 dimensions run on
+    the tensor cores (TF32x3, TMEM-staged classes, per-class norm restoration)."""
+    rng = np.random.Generator(np.random.PCG64(600 + seed))
+    dims = tuple(int(x) for x in rng.choice([2, 3], size=int(rng.integers(12, 16))))
+    circ = gen.random_mixed_circuit(dims, 200, rng)
+    psi0 = gen.random_state(circ.D, rng)
+    got = _run(qb, circ, qb.QD_C64, psi0, max_tile_amps=max_tile, block_dim=block_dim)
+    ref = oracle.run_circuit(circ, psi0, nthreads=max(1, oracle.max_threads()))
+    assert_close(got, ref, qb.QD_C64, f"tc tiles {max_tile}/{block_dim} dims={dims}")
+
+
+def test_tensor_core_tiles_on_benchmark_circuit(qb, gen):
+    """The 500-gate 12-qubit + 8-qutrit circuit in tile mode with blocks up to 32
+    dimensions, against the oracle; the norm stays 1 (no accumulation drift)."""
+    circ = gen.config1_circuit()
+    st = qb.State(circ.dims, prec=qb.QD_C64)
+    st.run(circ, fuse="tile", max_tile_amps=8192, block_dim=32)
+    nrm = st.norm()
+    got = st.amplitudes()
+    st.close()
+    ref = oracle.run_circuit(circ, nthreads=max(1, oracle.max_threads()))
+    assert_close(got, ref, qb.QD_C64, "benchmark circuit, tensor-core tiles")
+    assert abs(nrm - 1.0) < 1e-5
