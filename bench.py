@@ -413,6 +413,35 @@ def measure_sparse_ghz(qb, gen, reps=20):
                         "wire), complex128", "rows": rows}
 
 
+def measure_lazy(qb, gen, torch, stream):
+    """The benchmark circuit applied gate by gate through the C ABI (qd_apply_gate /
+    qd_apply_controlled), complex64, without and with the lazy frame (qd_set_lazy:
+    single-wire phase and permutation gates folded into a per-wire relabeling and
+    phase vector, no launch).  CUDA events around the 500 calls plus, with the frame,
+    the final materialisation (qd_set_lazy(st, 0))."""
+    circ = gen.config1_circuit()
+    st = qb.State(circ.dims, prec=qb.QD_C64, stream=stream)
+    out = {"workload": "12 qubits + 8 qutrits (26,873,856 amplitudes), 500 gates, complex64, one call per gate"}
+    for name, lazy in (("eager", False), ("lazy", True)):
+        for rep in range(2):  # the first run warms up
+            st.reset()
+            torch.cuda.synchronize()
+            n0 = qb.qd_launch_count()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if lazy:
+                st.set_lazy(True)
+            st.run_gate_by_gate(circ)
+            if lazy:
+                st.set_lazy(False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        out[name] = {"ms": e0.elapsed_time(e1), "launches": qb.qd_launch_count() - n0,
+                     "updates_per_s": circuit_updates(circ) / (e0.elapsed_time(e1) / 1e3)}
+    st.close()
+    return out
+
+
 def measure_many_controls(qb, gen, torch, stream, reps=10):
     """Controlled X_{+1} with M = 1..16 controls on the 12-qubit + 8-qutrit layout
     (26,873,856 complex64 amplitudes): the digit-insertion enumeration
@@ -758,6 +787,8 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         extra["many_controls"] = measure_many_controls(qb, gen, torch, stream)
         extra["sparse_ghz"] = measure_sparse_ghz(qb, gen)
+        torch.cuda.empty_cache()
+        extra["lazy_frame"] = measure_lazy(qb, gen, torch, stream)
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(qb, gen, torch, stream)
         torch.cuda.empty_cache()

@@ -236,6 +236,22 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
  * tc_mode. */
 qd_status qd_set_fusion(qd_state* st, int32_t max_block_dim, int32_t tc_mode);
 
+/* Lazy permutations and phases for the single-gate calls (off by default).
+ * With enable = 1 an uncontrolled single-wire gate whose matrix has exactly
+ * one entry of modulus 1 per row and column (X_{+a}, Z_d, S, T and their
+ * products) launches nothing: it is folded into a per-wire digit relabeling
+ * and phase vector kept on the host.  Every other gate runs with its
+ * control values and matrix rewritten for that frame (the wire's pending
+ * phases folded into the matrix; a controlled gate applies its target
+ * wires' pending phases first, as one diagonal launch per wire, since its
+ * unmatched classes keep them).  qd_norm and qd_marginal need no extra
+ * work; amplitude readouts, probabilities, qd_state_device_ptr,
+ * qd_apply_circuit, qd_set_fusion and qd_set_lazy(st, 0) first apply the
+ * frame (one pass per touched wire); set_amplitudes and reset clear it.
+ * Deferred fusion (qd_set_fusion >= 2) takes precedence: its queued gates
+ * are not folded. */
+qd_status qd_set_lazy(qd_state* st, int32_t enable);
+
 /* Run the gates queued by deferred fusion (no-op when none are queued). */
 qd_status qd_flush(qd_state* st);
 

@@ -99,6 +99,7 @@ _SIGS = {
     "qd_marginal": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
     "qd_synchronize": (ctypes.c_int32, [_vp]),
     "qd_set_fusion": (ctypes.c_int32, [_vp, ctypes.c_int32, ctypes.c_int32]),
+    "qd_set_lazy": (ctypes.c_int32, [_vp, ctypes.c_int32]),
     "qd_sparse_create": (ctypes.c_int32, [_i32p, ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
     "qd_sparse_destroy": (ctypes.c_int32, [_vp]),
     "qd_sparse_run": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_gate_desc), ctypes.c_int32, _f64p]),
@@ -440,6 +441,10 @@ def qd_set_fusion(st: int, max_block_dim: int, tc_mode=QD_TC_TF32X3) -> None:
     _check(_lib.qd_set_fusion(_vp(st), int(max_block_dim), _tc(tc_mode)), "qd_set_fusion")
 
 
+def qd_set_lazy(st: int, enable: bool) -> None:
+    _check(_lib.qd_set_lazy(_vp(st), 1 if enable else 0), "qd_set_lazy")
+
+
 def qd_flush(st: int) -> None:
     _check(_lib.qd_flush(_vp(st)), "qd_flush")
 
@@ -650,6 +655,10 @@ class State:
 
     def flush(self) -> None:
         qd_flush(self.handle)
+
+    def set_lazy(self, enable: bool = True) -> None:
+        """Fold single-wire phase / permutation gates into a per-wire frame (no launch)."""
+        qd_set_lazy(self.handle, enable)
 
     def run_gate_by_gate(self, circuit) -> None:
         for g in circuit.gates:

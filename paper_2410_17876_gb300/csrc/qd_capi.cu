@@ -2,6 +2,7 @@
 // gate classification, planning of the class enumeration and kernel
 // dispatch.  Host code only; the kernels live in qd_kernels.cu.
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -243,6 +244,7 @@ static void free_state(qd_state* st) {
         delete[] st->arena;
     }
     delete st->pend;
+    delete st->lazy;
     delete st;
 }
 
@@ -417,7 +419,193 @@ static void drop_pending(qd_state* st) {
         if (f_ != QD_OK) return f_;                 \
     } while (0)
 
+// queued gates, then the lazy frame: the device buffer holds the logical state
+#define QD_MATERIALIZE(st)                            \
+    do {                                              \
+        QD_FLUSH(st);                                 \
+        const qd_status m_ = ::qd::materialize(st);   \
+        if (m_ != QD_OK) return m_;                   \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Lazy permutations and phases (qd_set_lazy).  The frame (sigma, phi) of
+// each wire makes psi_L[x] = prod_w phi_w[x_w] psi_P[sigma(x)]:
+//   - an uncontrolled single-wire gate with one unit-modulus entry per row
+//     and column (X_{+a}, Z_d, S, T, their products: U[y, pi(y)]) only
+//     updates the frame: sigma_w <- sigma_w o pi, phi_w[y] <- U[y, pi(y)]
+//     phi_w[pi(y)]; no launch, no traffic;
+//   - any other gate on wires W runs in the physical frame: control values
+//     v -> sigma_c(v); U_phys[sigma_W(r), sigma_W(c)] = U[r, c] phi_W(c), and
+//     phi_w = 1 for w in W afterwards (a controlled gate first applies the
+//     phases of W as a diagonal gate: its unmatched classes keep them);
+//   - materialize() applies psi[x] <- phi_w[x_w] psi[x with x_w -> sigma_w(x_w)]
+//     on every touched wire (one monomial pass each) and resets the frame.
+// ---------------------------------------------------------------------------
+static bool unit_monomial(const double* U, int d, int* pi) {
+    for (int r = 0; r < d; ++r) {
+        int cnt = 0;
+        for (int c = 0; c < d; ++c) {
+            const double re = U[2 * (r * d + c)], im = U[2 * (r * d + c) + 1];
+            if (re != 0.0 || im != 0.0) {
+                ++cnt;
+                pi[r] = c;
+                if (std::fabs(std::sqrt(re * re + im * im) - 1.0) > 1e-12) return false;
+            }
+        }
+        if (cnt != 1) return false;
+    }
+    bool seen[QD_MAX_DIM] = {false};
+    for (int r = 0; r < d; ++r) {
+        if (seen[pi[r]]) return false;
+        seen[pi[r]] = true;
+    }
+    return true;
+}
+
+static void lazy_reset(LazyFrame& f, const Layout& L) {
+    f.sigma.assign(L.n, {});
+    f.phi.assign(L.n, {});
+    f.touched.assign(L.n, 0);
+    for (int w = 0; w < L.n; ++w) {
+        f.sigma[w].resize(L.dims[w]);
+        f.phi[w].assign(2 * (size_t)L.dims[w], 0.0);
+        for (int y = 0; y < L.dims[w]; ++y) {
+            f.sigma[w][y] = y;
+            f.phi[w][2 * y] = 1.0;
+        }
+    }
+}
+
+static qd_status apply_now(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
+                           const int32_t* cv, int32_t nc);
+
+qd_status qd::materialize(qd_state* st) {
+    if (!st->lazy) return QD_OK;
+    LazyFrame& f = *st->lazy;
+    for (int w = 0; w < st->L.n; ++w) {
+        if (!f.touched[w]) continue;
+        const int d = st->L.dims[w];
+        std::vector<double> M(2 * (size_t)d * d, 0.0);
+        for (int r = 0; r < d; ++r) {
+            M[2 * (r * d + f.sigma[w][r])] = f.phi[w][2 * r];
+            M[2 * (r * d + f.sigma[w][r]) + 1] = f.phi[w][2 * r + 1];
+        }
+        const int32_t ww = w;
+        const qd_status rc = apply_now(st, &ww, 1, M.data(), nullptr, nullptr, 0);
+        if (rc != QD_OK) return rc;
+        for (int y = 0; y < d; ++y) {
+            f.sigma[w][y] = y;
+            f.phi[w][2 * y] = 1.0;
+            f.phi[w][2 * y + 1] = 0.0;
+        }
+        f.touched[w] = 0;
+    }
+    return QD_OK;
+}
+
 qd_status qd::apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
+                        const int32_t* cv, int32_t nc) {
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    if (!st->lazy || st->fuse_dim >= 2) return apply_now(st, wires, k, U, cw, cv, nc);
+    Plan p;  // validation of the gate as given
+    qd_status rc = make_plan(st->L, st->prec, wires, k, U, cw, cv, nc, p);
+    if (rc != QD_OK) return rc;
+    LazyFrame& f = *st->lazy;
+    if (k == 1 && nc == 0) {
+        const int w = wires[0], d = st->L.dims[w];
+        int pi[QD_MAX_DIM];
+        if (unit_monomial(U, d, pi)) {
+            std::vector<int32_t> s2(d);
+            std::vector<double> p2(2 * (size_t)d);
+            for (int y = 0; y < d; ++y) {
+                s2[y] = f.sigma[w][pi[y]];
+                const double ur = U[2 * (y * d + pi[y])], ui = U[2 * (y * d + pi[y]) + 1];
+                const double fr = f.phi[w][2 * pi[y]], fi = f.phi[w][2 * pi[y] + 1];
+                p2[2 * y] = ur * fr - ui * fi;
+                p2[2 * y + 1] = ur * fi + ui * fr;
+            }
+            f.sigma[w] = s2;
+            f.phi[w] = p2;
+            f.touched[w] = 1;
+            return QD_OK;
+        }
+    }
+    // run in the physical frame.  A controlled gate leaves the classes whose
+    // controls are not met untouched, so the phases of its target wires
+    // cannot be absorbed into its matrix: they are applied first, as a
+    // diagonal gate in the physical frame.
+    if (nc > 0) {
+        for (int j = 0; j < k; ++j) {
+            const int w = wires[j], d = st->L.dims[w];
+            bool unit = true;
+            for (int y = 0; y < d; ++y) unit = unit && f.phi[w][2 * y] == 1.0 && f.phi[w][2 * y + 1] == 0.0;
+            if (unit) continue;
+            std::vector<double> Dg(2 * (size_t)d * d, 0.0);
+            for (int y = 0; y < d; ++y) {
+                const int py = f.sigma[w][y];
+                Dg[2 * ((size_t)py * d + py)] = f.phi[w][2 * y];
+                Dg[2 * ((size_t)py * d + py) + 1] = f.phi[w][2 * y + 1];
+            }
+            const int32_t ww = w;
+            rc = apply_now(st, &ww, 1, Dg.data(), nullptr, nullptr, 0);
+            if (rc != QD_OK) return rc;
+            for (int y = 0; y < d; ++y) {
+                f.phi[w][2 * y] = 1.0;
+                f.phi[w][2 * y + 1] = 0.0;
+            }
+        }
+    }
+    int P = 1;
+    int dw[QD_MAX_GATE_WIRES];
+    for (int j = 0; j < k; ++j) {
+        dw[j] = st->L.dims[wires[j]];
+        P *= dw[j];
+    }
+    std::vector<int> phys(P);
+    std::vector<double> ph(2 * (size_t)P);
+    for (int i = 0; i < P; ++i) {  // local index -> physical local index, phase of its digits
+        int rem = i, o = 0, s = 1;
+        double pr = 1.0, pim = 0.0;
+        for (int j = 0; j < k; ++j) {
+            const int x = rem % dw[j];
+            rem /= dw[j];
+            o += f.sigma[wires[j]][x] * s;
+            s *= dw[j];
+            const double fr = f.phi[wires[j]][2 * x], fi = f.phi[wires[j]][2 * x + 1];
+            const double t = pr * fr - pim * fi;
+            pim = pr * fi + pim * fr;
+            pr = t;
+        }
+        phys[i] = o;
+        ph[2 * i] = pr;
+        ph[2 * i + 1] = pim;
+    }
+    std::vector<double> U2(2 * (size_t)P * P);
+    for (int r = 0; r < P; ++r)
+        for (int c = 0; c < P; ++c) {
+            const double ur = U[2 * (r * P + c)], ui = U[2 * (r * P + c) + 1];
+            const size_t o = 2 * ((size_t)phys[r] * P + phys[c]);
+            U2[o] = ur * ph[2 * c] - ui * ph[2 * c + 1];
+            U2[o + 1] = ur * ph[2 * c + 1] + ui * ph[2 * c];
+        }
+    std::vector<int32_t> cv2(nc > 0 ? nc : 1);
+    for (int m = 0; m < nc; ++m) cv2[m] = f.sigma[cw[m]][cv[m]];
+    rc = apply_now(st, wires, k, U2.data(), cw, nc > 0 ? cv2.data() : cv, nc);
+    if (rc != QD_OK) return rc;
+    for (int j = 0; j < k; ++j) {  // the wires' phases now live in the state
+        const int w = wires[j];
+        for (int y = 0; y < dw[j]; ++y) {
+            f.phi[w][2 * y] = 1.0;
+            f.phi[w][2 * y + 1] = 0.0;
+        }
+        bool id = true;
+        for (int y = 0; y < dw[j]; ++y) id = id && f.sigma[w][y] == y;
+        f.touched[w] = id ? 0 : 1;
+    }
+    return QD_OK;
+}
+
+static qd_status apply_now(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
                            const int32_t* cv, int32_t nc) {
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
     Plan p;
@@ -553,6 +741,7 @@ qd_status qd_state_reset(qd_state* st) {
     QD_GUARD_BEGIN
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
     drop_pending(st);
+    if (st->lazy) lazy_reset(*st->lazy, st->L);
     return reset_state(st);
     QD_GUARD_END
 }
@@ -560,7 +749,7 @@ qd_status qd_state_reset(qd_state* st) {
 qd_status qd_state_set_stream(qd_state* st, void* stream) {
     QD_GUARD_BEGIN
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
-    QD_FLUSH(st);
+    QD_MATERIALIZE(st);
     QD_CUDA(cudaStreamSynchronize(st->stream), "stream switch");
     st->stream = reinterpret_cast<cudaStream_t>(stream);
     return QD_OK;
@@ -578,7 +767,7 @@ qd_status qd_state_info(const qd_state* st, int64_t* num_amplitudes, int32_t* nu
 qd_status qd_state_device_ptr(const qd_state* st, void** dev_ptr) {
     QD_GUARD_BEGIN
     if (!st || !dev_ptr) return fail(QD_ERR_ARG, "state or out is NULL");
-    QD_FLUSH(const_cast<qd_state*>(st));  // the queue is the state's pending content
+    QD_MATERIALIZE(const_cast<qd_state*>(st));  // queued gates and the lazy frame are the state's pending content
     *dev_ptr = st->psi;
     return QD_OK;
     QD_GUARD_END
@@ -588,6 +777,7 @@ qd_status qd_state_set_amplitudes(qd_state* st, const double* host) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
     drop_pending(st);
+    if (st->lazy) lazy_reset(*st->lazy, st->L);
     const size_t D = (size_t)st->L.D;
     if (st->prec == QD_C128) {
         QD_CUDA(cudaMemcpyAsync(st->psi, host, D * 16, cudaMemcpyHostToDevice, st->stream), "upload");
@@ -605,7 +795,7 @@ qd_status qd_state_set_amplitudes(qd_state* st, const double* host) {
 qd_status qd_state_get_amplitudes(qd_state* st, double* host) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
-    QD_FLUSH(st);
+    QD_MATERIALIZE(st);
     const size_t D = (size_t)st->L.D;
     if (st->prec == QD_C128) {
         QD_CUDA(cudaMemcpyAsync(host, st->psi, D * 16, cudaMemcpyDeviceToHost, st->stream), "download");
@@ -626,7 +816,7 @@ qd_status qd_state_get_amplitudes(qd_state* st, double* host) {
 qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
-    QD_FLUSH(st);
+    QD_MATERIALIZE(st);
     if (bytes < st->bytes) return fail(QD_ERR_ARG, "host buffer of %zu bytes < %zu", bytes, st->bytes);
     QD_CUDA(cudaMemcpyAsync(host, st->psi, st->bytes, cudaMemcpyDeviceToHost, st->stream), "download");
     QD_CUDA(cudaStreamSynchronize(st->stream), "download sync");
@@ -669,7 +859,7 @@ qd_status qd_norm(qd_state* st, double* out) {
 qd_status qd_probabilities_device(qd_state* st, double* dev_out) {
     QD_GUARD_BEGIN
     if (!st || !dev_out) return fail(QD_ERR_ARG, "state or out is NULL");
-    QD_FLUSH(st);
+    QD_MATERIALIZE(st);
     if (reinterpret_cast<uintptr_t>(dev_out) % 8 != 0) return fail(QD_ERR_ARG, "dev_out is not 8-byte aligned");
     cudaError_t e = st->prec == QD_C64 ? launch_probs<float>(st->psi, st->L.D, dev_out, st->stream)
                                        : launch_probs<double>(st->psi, st->L.D, dev_out, st->stream);
@@ -681,7 +871,7 @@ qd_status qd_probabilities_device(qd_state* st, double* dev_out) {
 qd_status qd_probabilities(qd_state* st, double* host_out) {
     QD_GUARD_BEGIN
     if (!st || !host_out) return fail(QD_ERR_ARG, "state or out is NULL");
-    QD_FLUSH(st);
+    QD_MATERIALIZE(st);
     double* tmp = nullptr;
     const size_t bytes = sizeof(double) * (size_t)st->L.D;
     cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tmp), bytes, st->stream);
@@ -713,7 +903,12 @@ qd_status qd_marginal(qd_state* st, int32_t wire, double* host_out) {
                         : launch_marginal<double>(st->psi, map, classes, (uint64_t)st->L.b[wire], d, st->partials,
                                                   st->nb, st->dev_out, st->stream);
     if (e != cudaSuccess) return cuda_fail(e, "marginal kernel");
-    return read_out(st, d, host_out);
+    const qd_status rc = read_out(st, d, host_out);
+    if (rc != QD_OK || !st->lazy || !st->lazy->touched[wire]) return rc;
+    // logical digit k sits at physical digit sigma(k); phases do not change probabilities
+    std::vector<double> phys(host_out, host_out + d);
+    for (int k2 = 0; k2 < d; ++k2) host_out[k2] = phys[st->lazy->sigma[wire][k2]];
+    return QD_OK;
     QD_GUARD_END
 }
 
@@ -730,7 +925,7 @@ qd_status qd_apply_controlled_scan(qd_state* st, int32_t target, const double* U
                                    const int32_t* cv, int32_t nc) {
     QD_GUARD_BEGIN
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
-    QD_FLUSH(st);  // gates queued by deferred fusion come first
+    QD_MATERIALIZE(st);  // queued gates and the lazy frame come first
     Plan full;  // validates the gate and its controls exactly as qd_apply_controlled does
     qd_status rc = make_plan(st->L, st->prec, &target, 1, U, cw, cv, nc, full);
     if (rc != QD_OK) return rc;
@@ -759,9 +954,27 @@ qd_status qd_set_fusion(qd_state* st, int32_t max_block_dim, int32_t tc_mode) {
     if (tc_mode != QD_TC_TF32X3 && tc_mode != QD_TC_BF16X3 && tc_mode != QD_TC_OFF)
         return fail(QD_ERR_ARG, "unknown tc_mode %d", tc_mode);
     // gates already queued run with the settings they were queued under
-    QD_FLUSH(st);
+    QD_MATERIALIZE(st);
     st->fuse_dim = max_block_dim <= 1 ? 0 : (max_block_dim > QD_MAX_GATE_DIM ? QD_MAX_GATE_DIM : max_block_dim);
     st->tc_mode = tc_mode;
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_set_lazy(qd_state* st, int32_t enable) {
+    QD_GUARD_BEGIN
+    if (!st) return fail(QD_ERR_ARG, "state is NULL");
+    if (enable) {
+        if (!st->lazy) {
+            QD_FLUSH(st);
+            st->lazy = new LazyFrame();
+            lazy_reset(*st->lazy, st->L);
+        }
+        return QD_OK;
+    }
+    QD_MATERIALIZE(st);
+    delete st->lazy;
+    st->lazy = nullptr;
     return QD_OK;
     QD_GUARD_END
 }

@@ -283,11 +283,73 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
     }
 }
 
-// Apply one composed block (P <= PP) to the tile.  A class's P members are
-// gathered into registers (padded rows are masked out); each output row is
-// accumulated from the matrix row in the staged pool, read by all threads at
-// the same address (a broadcast) -- for complex64 two adjacent entries per
-// 16-byte load.  All inputs are in registers before the first store.
+// Dense composed block (P <= PP): a thread owns CT classes and accumulates
+// all PP output rows of each as outer products over the inputs k, so every
+// accumulator has CT * PP - 1 independent FMAs between its updates (the
+// row-by-row inner product is one dependent chain per row).  Per step of k
+// (two columns for complex64), each row's matrix entries are one 16-byte
+// broadcast load shared by the CT classes; a class's inputs are read once.
+// Its outputs are written after all its inputs were read, and no other
+// thread touches its members, so the update is in place.
+template <typename R, int PP, int CT>
+__device__ __forceinline__ void dense_block(typename Cplx<R>::T2* tile, const FGate& G,
+                                            const typename Cplx<R>::T2* M, const uint32_t (&off)[PP]) {
+    using T2 = typename Cplx<R>::T2;
+    const uint32_t nc = G.nclasses, lmask = G.lmask, smask = G.smask;
+    constexpr int KS = (sizeof(R) == 4 && PP % 2 == 0) ? 2 : 1;  // columns per matrix load
+    for (uint32_t c = CT * threadIdx.x; c < nc; c += CT * blockDim.x) {
+        uint32_t b[CT];
+        bool live[CT];
+#pragma unroll
+        for (int j = 0; j < CT; ++j) {
+            live[j] = c + j < nc;
+            b[j] = G.map.map(live[j] ? c + j : c);
+        }
+        T2 acc[CT][PP];
+#pragma unroll
+        for (int j = 0; j < CT; ++j)
+#pragma unroll
+            for (int r = 0; r < PP; ++r) acc[j][r].x = acc[j][r].y = 0;
+#pragma unroll
+        for (int k = 0; k < PP; k += KS) {
+            T2 x[CT][KS];
+#pragma unroll
+            for (int j = 0; j < CT; ++j)
+#pragma unroll
+                for (int q = 0; q < KS; ++q) {
+                    x[j][q].x = x[j][q].y = 0;
+                    if (lmask >> (k + q) & 1u) x[j][q] = tile[b[j] + off[k + q]];
+                }
+#pragma unroll
+            for (int r = 0; r < PP; ++r) {
+                if (!(smask >> r & 1u)) continue;
+                if constexpr (KS == 2) {
+                    const float4 m2 = *reinterpret_cast<const float4*>(M + r * PP + k);
+                    const float2 mA = make_float2(m2.x, m2.y), mB = make_float2(m2.z, m2.w);
+#pragma unroll
+                    for (int j = 0; j < CT; ++j) {
+                        fcmac(acc[j][r], mA, x[j][0]);
+                        fcmac(acc[j][r], mB, x[j][1]);
+                    }
+                } else {
+                    const T2 m = M[r * PP + k];
+#pragma unroll
+                    for (int j = 0; j < CT; ++j) fcmac(acc[j][r], m, x[j][0]);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < CT; ++j)
+            if (live[j])
+#pragma unroll
+                for (int r = 0; r < PP; ++r)
+                    if (smask >> r & 1u) tile[b[j] + off[r]] = acc[j][r];
+    }
+}
+
+// Apply one composed block (P <= PP) to the tile.  Dense complex64 blocks:
+// above.  Otherwise one class per thread, its P members gathered into
+// registers (padded rows masked out) before the first store.
 template <typename R, int PP>
 __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGate& G,
                                            const typename Cplx<R>::T2* pool) {
@@ -299,78 +361,56 @@ __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGa
 #pragma unroll
     for (int r = 0; r < PP; ++r) off[r] = G.off[r];
     const T2* M = pool + G.u_off;
-    // one class per iteration: a second class's registers cost more than the
-    // matrix loads they would share (measured)
-    constexpr uint32_t kPer = 1u;
-    for (uint32_t c = kPer * threadIdx.x; c < nc; c += kPer * blockDim.x) {
-        const bool two = kPer == 2 && c + 1 < nc;
+    if (kind == kDense) {
+        // complex64: two classes per thread unless that leaves too many
+        // threads idle (a pair costs about 1.6 single-class steps);
+        // complex128: one (a second class's accumulators do not fit)
+        if constexpr (sizeof(R) == 4) {
+            const uint32_t n1 = (nc + blockDim.x - 1) / blockDim.x, n2 = (nc + 2 * blockDim.x - 1) / (2 * blockDim.x);
+            if (16u * n2 <= 10u * n1 + 4u) {
+                dense_block<R, PP, 2>(tile, G, M, off);
+                return;
+            }
+        }
+        if constexpr (sizeof(R) == 4) {
+            dense_block<R, PP, 1>(tile, G, M, off);
+            return;
+        }
+    }
+    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
         const uint32_t b0 = G.map.map(c);
-        const uint32_t b1 = two ? G.map.map(c + 1) : b0;
-        T2 x0[PP], x1[kPer == 2 ? PP : 1];
+        T2 x0[PP];
 #pragma unroll
         for (int k = 0; k < PP; ++k) {
             x0[k].x = 0;
             x0[k].y = 0;
             if (lmask >> k & 1u) x0[k] = tile[b0 + off[k]];
-            if constexpr (kPer == 2) x1[k] = (lmask >> k & 1u) ? tile[b1 + off[k]] : x0[k];
         }
-        if (kind == kDense) {
+        if (kind == kDense) {  // complex128: FP64-bound, inputs in registers, one row at a time
 #pragma unroll
             for (int r = 0; r < PP; ++r) {
                 if (!(smask >> r & 1u)) continue;
-                const T2* Mr = M + r * PP;
-                T2 a0, a1;
-                a0.x = a0.y = a1.x = a1.y = 0;
-                if constexpr (sizeof(R) == 4 && PP % 2 == 0) {
+                T2 a0;
+                a0.x = a0.y = 0;
 #pragma unroll
-                    for (int k = 0; k < PP; k += 2) {
-                        const float4 m2 = *reinterpret_cast<const float4*>(Mr + k);
-                        const float2 mA = make_float2(m2.x, m2.y), mB = make_float2(m2.z, m2.w);
-                        fcmac(a0, mA, x0[k]);
-                        fcmac(a1, mA, x1[k]);
-                        fcmac(a0, mB, x0[k + 1]);
-                        fcmac(a1, mB, x1[k + 1]);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < PP; ++k) {
-                        const T2 m = Mr[k];
-                        fcmac(a0, m, x0[k]);
-                        if constexpr (kPer == 2) fcmac(a1, m, x1[k]);
-                    }
-                }
+                for (int k = 0; k < PP; ++k) fcmac(a0, M[r * PP + k], x0[k]);
                 tile[b0 + off[r]] = a0;
-                if (two) tile[b1 + off[r]] = a1;
             }
         } else if (kind == kDiag) {
 #pragma unroll
             for (int r = 0; r < PP; ++r)
-                if (smask >> r & 1u) {
-                    const T2 m = M[r * PP + r];
-                    tile[b0 + off[r]] = fcmul(m, x0[r]);
-                    if constexpr (kPer == 2)
-                        if (two) tile[b1 + off[r]] = fcmul(m, x1[r]);
-                }
+                if (smask >> r & 1u) tile[b0 + off[r]] = fcmul(M[r * PP + r], x0[r]);
         } else {
 #pragma unroll
             for (int r = 0; r < PP; ++r) {
                 if (!(smask >> r & 1u)) continue;
                 const int src = G.perm[r];
-                T2 v0 = x0[0], v1 = x1[0];
+                T2 v0 = x0[0];
 #pragma unroll
                 for (int k = 1; k < PP; ++k)
-                    if (src == k) {
-                        v0 = x0[k];
-                        if constexpr (kPer == 2) v1 = x1[k];
-                    }
-                if (!pure) {
-                    const T2 m = M[r * PP + src];
-                    v0 = fcmul(m, v0);
-                    v1 = fcmul(m, v1);
-                }
+                    if (src == k) v0 = x0[k];
+                if (!pure) v0 = fcmul(M[r * PP + src], v0);
                 tile[b0 + off[r]] = v0;
-                if constexpr (kPer == 2)
-                    if (two) tile[b1 + off[r]] = v1;
             }
         }
     }
@@ -515,9 +555,11 @@ __device__ __forceinline__ bool apply_chunks(typename Cplx<R>::T2* tile, const c
         const ChunkHdr h = *reinterpret_cast<const ChunkHdr*>(chunk);
         __syncthreads();  // the previous chunk is done with the stage
         {
-            const uint4* src = reinterpret_cast<const uint4*>(chunk);
-            uint4* dst = reinterpret_cast<uint4*>(stage);
-            for (uint32_t i = threadIdx.x; i < h.bytes / 16; i += blockDim.x) dst[i] = src[i];
+            // every 16-byte piece in flight at once (cp.async), then wait
+            const uint32_t d0 = static_cast<uint32_t>(__cvta_generic_to_shared(stage));
+            for (uint32_t i = threadIdx.x; i < h.bytes / 16; i += blockDim.x)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16u * i), "l"(chunk + 16u * i));
+            asm volatile("cp.async.wait_all;" ::: "memory");
         }
         __syncthreads();
         const FGate* gates = reinterpret_cast<const FGate*>(stage + sizeof(ChunkHdr));
@@ -557,6 +599,35 @@ __device__ __forceinline__ bool apply_chunks(typename Cplx<R>::T2* tile, const c
     return true;
 }
 
+// Load tile at g (rows of bL amplitudes at the offsets srow) into shared
+// memory with cp.async: every 16-byte piece (8-byte for complex64 with odd
+// rows) of a thread is in flight at once.  Staged through registers, each
+// load would wait for the previous shared-memory store, which the compiler
+// cannot move past the next row-offset read (both are shared memory): one
+// load in flight per thread, the fixed cost of a pass.  The caller's next
+// barrier publishes the other threads' pieces.
+template <typename R>
+__device__ __forceinline__ void tile_load_async(typename Cplx<R>::T2* tile, const typename Cplx<R>::T2* g,
+                                                const uint64_t* srow, const FusedArgs<R>& a) {
+    constexpr uint32_t kEl = sizeof(typename Cplx<R>::T2);
+    const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(tile));
+    if (kEl == 16 || a.vec2) {
+        constexpr uint32_t per = 16 / kEl;
+        for (uint32_t e = per * threadIdx.x; e < a.T; e += per * blockDim.x) {
+            const uint32_t r = a.bLdiv.div(e);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + e * kEl),
+                         "l"(g + srow[r] + (e - r * a.bL)));
+        }
+    } else {
+        for (uint32_t e = threadIdx.x; e < a.T; e += blockDim.x) {
+            const uint32_t r = a.bLdiv.div(e);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s0 + e * kEl),
+                         "l"(g + srow[r] + (e - r * a.bL)));
+        }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __host__ __device__ inline size_t fused_rows_bytes(uint32_t rows) { return ((size_t)rows * 8 + 15) & ~(size_t)15; }
 
 template <typename R, int DMAX>
@@ -568,7 +639,12 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
     T2* tile = reinterpret_cast<T2*>(smem_raw + chunk_smem_max<R>() + fused_rows_bytes(a.rows));
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
-    for (uint32_t r = threadIdx.x; r < a.rows; r += blockDim.x) srow[r] = a.rowoff[r];
+    {
+        const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(srow));
+        for (uint32_t r = threadIdx.x; r < a.rows; r += blockDim.x)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s0 + 8u * r), "l"(a.rowoff + r));
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
     if (threadIdx.x == 0) {
         uint32_t rem = blockIdx.x;
         uint64_t base = 0;
@@ -583,18 +659,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
     }
     __syncthreads();
     T2* g = a.psi + sbase;
-    if (a.vec2) {
-        for (uint32_t e = 2 * threadIdx.x; e < a.T; e += 2 * blockDim.x) {
-            const uint32_t r = a.bLdiv.div(e);
-            reinterpret_cast<float4*>(tile)[e >> 1] =
-                *reinterpret_cast<const float4*>(reinterpret_cast<const float2*>(g) + srow[r] + (e - r * a.bL));
-        }
-    } else {
-        for (uint32_t e = threadIdx.x; e < a.T; e += blockDim.x) {
-            const uint32_t r = a.bLdiv.div(e);
-            tile[e] = g[srow[r] + (e - r * a.bL)];
-        }
-    }
+    tile_load_async<R>(tile, g, srow, a);  // published by apply_chunks' first barrier
     apply_chunks<R, DMAX>(tile, a.chunks, a.nchunks, stage, odig);
     __syncthreads();
     if (a.vec2) {
@@ -794,17 +859,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile_tc(const __grid_constant_
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     float2* g = a.psi + sbase;
-    if (a.vec2) {
-        for (uint32_t e = 2 * tid; e < a.T; e += 2 * blockDim.x) {
-            const uint32_t r = a.bLdiv.div(e);
-            reinterpret_cast<float4*>(tile)[e >> 1] = *reinterpret_cast<const float4*>(g + srow[r] + (e - r * a.bL));
-        }
-    } else {
-        for (uint32_t e = tid; e < a.T; e += blockDim.x) {
-            const uint32_t r = a.bLdiv.div(e);
-            tile[e] = g[srow[r] + (e - r * a.bL)];
-        }
-    }
+    tile_load_async<float>(tile, g, srow, a);  // published by apply_chunks' first barrier
     TcTileCtx ctx{tmem_base, smem_u32(&mbar), 0u, sB, a.desc_base, s_nin, s_nout};
     const bool ok = apply_chunks<float, DMAX, true>(tile, a.chunks, a.nchunks, stage, odig, &ctx);
     __syncthreads();
@@ -2249,6 +2304,7 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
                            const qd_fusion_opts* opts) {
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
     qd_status rc = flush_pending(st);
+    if (rc == QD_OK) rc = materialize(st);
     if (rc != QD_OK) return rc;
     return run_circuit(st, gates, n_gates, matrices, opts);
 }

@@ -64,6 +64,15 @@ struct Pending {
 };
 constexpr size_t kMaxPending = 4096;
 
+// Lazy permutations and phases of the per-gate path: the logical state is
+// psi_L[x] = prod_w phi_w[x_w] * psi_P[sigma(x)], sigma acting digit by digit
+// (sigma_w a permutation of wire w's digits, phi_w unit-modulus phases).
+struct LazyFrame {
+    std::vector<std::vector<int32_t>> sigma;  // per wire, indexed by logical digit
+    std::vector<std::vector<double>> phi;     // per wire, interleaved (re, im) per logical digit
+    std::vector<char> touched;                // wire's sigma / phi differ from the identity
+};
+
 void build_map(const Layout& L, const int32_t* ins_w, const int64_t* ins_v, int m, IndexMap& map,
                uint64_t& classes);
 qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t k, const double* U,
@@ -94,12 +103,14 @@ struct qd_state {
     int32_t tc_mode;     // QD_TC_*: complex64 gates of 17..64 dimensions (0 = QD_TC_TF32X3)
     int32_t fuse_dim;    // deferred fusion: largest composed block (< 2: off)
     qd::Pending* pend;   // gates queued by deferred fusion
+    qd::LazyFrame* lazy; // lazy permutations and phases (NULL: off)
 };
 
 namespace qd {
 qd_status run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates, const double* matrices,
                       const qd_fusion_opts* opts);
 qd_status flush_pending(qd_state* st);
+qd_status materialize(qd_state* st);  // apply the lazy frame to the device state (no-op when off or identity)
 qd_status apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
                     const int32_t* cv, int32_t nc);
 qd_status read_out(qd_state* st, int count, double* host);
