@@ -413,6 +413,59 @@ def measure_sparse_ghz(qb, gen, reps=20):
                         "wire), complex128", "rows": rows}
 
 
+def measure_tile_costs(qb, gen, torch, stream, reps=5):
+    """Marginal cost of one gate or composed block inside a shared-memory tile pass
+    on the 12-qubit + 8-qutrit layout (complex64): the pass with N + 6 copies minus
+    the pass with N, over 6 (N = 2), timed with CUDA events through
+    qd_apply_circuit.  Single gates use block_dim 1 (no composition); blocks are
+    runs of gates on 2-4 wires composed in binary64, consecutive blocks sharing a
+    wire so that they neither commute nor merge.  The pass floor is the cost of a
+    pass holding two phase gates."""
+    circ = gen.config1_circuit()
+    dims = circ.dims
+    rng = np.random.Generator(np.random.PCG64(21))
+    qub = [i for i, d in enumerate(dims) if d == 2]
+    qut = [i for i, d in enumerate(dims) if d == 3]
+    st = qb.State(dims, prec=qb.QD_C64, stream=stream)
+
+    def timed(gates, bd):
+        c = gen.Circuit(dims, gates)
+        st.run(c, fuse="tile", block_dim=bd)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            st.run(c, fuse="tile", block_dim=bd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    def block(ws):
+        g = [gen.Gate((w,), gen.haar(dims[w], rng)) for w in ws]
+        return g + [gen.Gate((ws[i + 1],), gen.haar(dims[ws[i + 1]], rng), (ws[i],), (1,)) for i in range(len(ws) - 1)]
+
+    kinds = {
+        "qubit_gate": (lambda i: [gen.Gate((qub[2 + i % 2],), gen.haar(2, rng))], 1, 16),
+        "qutrit_gate": (lambda i: [gen.Gate((qut[2 + i % 2],), gen.haar(3, rng))], 1, 24),
+        "qubit_phase_gate": (lambda i: [gen.Gate((qub[2 + i % 2],), np.diag(np.exp(1j * rng.random(2))))], 1, 6),
+        "qutrit_shift_gate": (lambda i: [gen.Gate((qut[2 + i % 2],), gen.x_plus(3, 1))], 1, 24),
+        "block_9_two_qutrits": (lambda i: block(qut[0:2] if i % 2 == 0 else qut[1:3]), 9, 72),
+        "block_16_four_qubits": (lambda i: block(qub[0:4] if i % 2 == 0 else qub[3:7]), 16, 128),
+    }
+    out = {"workload": "12 qubits + 8 qutrits (26,873,856 amplitudes), complex64, one tile pass",
+           "alu_peak_tflops": FP32_TFLOPS, "rows": {}}
+    Z = np.diag([1, -1]).astype(complex)
+    out["pass_floor_us"] = 1e6 * timed([gen.Gate((qub[-1],), Z), gen.Gate((qub[-2],), Z)], 1)
+    for name, (mk, bd, flop_per_amp) in kinds.items():
+        base = sum((mk(i) for i in range(2)), [])
+        more = sum((mk(i) for i in range(8)), [])
+        t = (timed(more, bd) - timed(base, bd)) / 6
+        out["rows"][name] = {"us": 1e6 * t, "flop_per_amp": flop_per_amp,
+                             "tflops": flop_per_amp * circ.D / t / 1e12 if t > 0 else None}
+    st.close()
+    return out
+
+
 def measure_lazy(qb, gen, torch, stream):
     """The benchmark circuit applied gate by gate through the C ABI (qd_apply_gate /
     qd_apply_controlled), complex64, without and with the lazy frame (qd_set_lazy:
@@ -789,6 +842,7 @@ def run_gpu(args):
         extra["sparse_ghz"] = measure_sparse_ghz(qb, gen)
         torch.cuda.empty_cache()
         extra["lazy_frame"] = measure_lazy(qb, gen, torch, stream)
+        extra["tile_costs"] = measure_tile_costs(qb, gen, torch, stream)
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(qb, gen, torch, stream)
         torch.cuda.empty_cache()

@@ -49,7 +49,6 @@ constexpr int kMaxTileCtrl = 7;    // controls of a fused gate (inside or outsid
 constexpr int kMaxLocalIns = 1 + kMaxTileCtrl;
 constexpr int kMaxPassGates = 64;  // gates per fused pass (their descriptors live in shared memory)
 constexpr int kMaxRows = 2048;
-constexpr double kPipeMaxFlops = 150.0;  // tile passes below this many flop per amplitude use the persistent kernel
 
 // Class enumeration inside a tile (local index space of S), 32-bit.
 struct __align__(16) LocalMap {
@@ -127,7 +126,8 @@ struct FusedArgs {
     FastDiv32 free_div[kMaxWires];  // division by free_d (tile indices are below 2^32)
     uint64_t free_b[kMaxWires];
     const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
-    int32_t* status;         // persistent and tensor-core kernels: QD_ERR_TIMEOUT if a bounded wait gave up
+    int32_t* status;         // tensor-core kernel: QD_ERR_TIMEOUT if a bounded wait gave up
+    uint32_t stage;          // bytes of the pass's largest chunk: k_fused_tile's shared-memory stage
     const char* desc_base;   // the program's descriptors (tensor-core operands)
 };
 
@@ -147,18 +147,24 @@ template <typename T2> __device__ __forceinline__ void fcmac(T2& acc, const T2& 
     acc.y = fma(u.y, x.x, acc.y);
 }
 
-// Small fixed-size arrays passed by value, so that they stay in registers.
+// Small fixed-size arrays, indexed only by unrolled loop counters so that
+// they stay in registers.
 template <typename T, int N>
 struct Arr {
     T v[N];
 };
 
-// y = G x for one class held in registers (dense, diagonal or permutation).
+// y = G x for one class held in registers.  Monomial (permutation) gates run
+// as dense ones: their zero entries contribute exact zeros, and a pure
+// permutation's unit entries move values exactly.  Selecting x_{pi(r)} by a
+// data-dependent index instead is compiled into a local-memory copy of the
+// class -- for the whole kernel, whichever gate kind runs -- which made every
+// qutrit gate of a tile pass five times slower than a qubit gate (measured:
+// 99 vs 17 us per gate on 26.9M amplitudes).
 template <typename T2, int DT>
-__device__ __forceinline__ Arr<T2, DT> class_math(const Arr<T2, DT> x, int kind, bool pure, const Arr<int, DT> perm,
-                                                  const Arr<T2, DT * DT> u) {
+__device__ __forceinline__ Arr<T2, DT> class_math(const Arr<T2, DT> x, int kind, const Arr<T2, DT * DT> u) {
     Arr<T2, DT> y;
-    if (kind == kDense) {
+    if (kind != kDiag) {
 #pragma unroll
         for (int r = 0; r < DT; ++r) {
             T2 acc = fcmul(u.v[r * DT], x.v[0]);
@@ -166,28 +172,16 @@ __device__ __forceinline__ Arr<T2, DT> class_math(const Arr<T2, DT> x, int kind,
             for (int k = 1; k < DT; ++k) fcmac(acc, u.v[r * DT + k], x.v[k]);
             y.v[r] = acc;
         }
-    } else if (kind == kDiag) {
-#pragma unroll
-        for (int r = 0; r < DT; ++r) y.v[r] = fcmul(u.v[r * DT + r], x.v[r]);
     } else {
 #pragma unroll
-        for (int r = 0; r < DT; ++r) {
-            T2 v = x.v[0], w = u.v[r * DT];
-#pragma unroll
-            for (int k = 1; k < DT; ++k)
-                if (perm.v[r] == k) {
-                    v = x.v[k];
-                    w = u.v[r * DT + k];
-                }
-            y.v[r] = pure ? v : fcmul(w, v);
-        }
+        for (int r = 0; r < DT; ++r) y.v[r] = fcmul(u.v[r * DT + r], x.v[r]);
     }
     return y;
 }
 
 // Apply one single-wire gate of dimension DT to the tile in shared memory.
-// Matrix, permutation and masks are loop invariants read once per gate from
-// the staged chunk.  With no control inside the tile (m == 1) a class index
+// Matrix and masks are loop invariants read once per gate from the staged
+// chunk.  With no control inside the tile (m == 1) a class index
 // c = hi * lst + lo has base hi * lst * d + lo (one division); complex64 with
 // an even local stride processes two adjacent classes with 16-byte accesses.
 template <typename R, int DT>
@@ -196,10 +190,6 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
     using T2 = typename Cplx<R>::T2;
     const int kind = G.kind;
     const uint32_t lmask = G.lmask, smask = G.smask, lst = G.lst, nc = G.nclasses;
-    const bool pure = G.pure != 0;
-    Arr<int, DT> perm;
-#pragma unroll
-    for (int r = 0; r < DT; ++r) perm.v[r] = G.perm[r];
     Arr<T2, DT * DT> u;
     const T2* gu = pool + G.u_off;
 #pragma unroll
@@ -222,8 +212,8 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
                         x0.v[k] = make_float2(v.x, v.y);
                         x1.v[k] = make_float2(v.z, v.w);
                     }
-                    const Arr<T2, DT> y0 = class_math<T2, DT>(x0, kind, pure, perm, u);
-                    const Arr<T2, DT> y1 = class_math<T2, DT>(x1, kind, pure, perm, u);
+                    const Arr<T2, DT> y0 = class_math<T2, DT>(x0, kind, u);
+                    const Arr<T2, DT> y1 = class_math<T2, DT>(x1, kind, u);
 #pragma unroll
                     for (int r = 0; r < DT; ++r)
                         if (smask >> r & 1u)
@@ -238,7 +228,7 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
                     Arr<T2, DT> x;
                     x.v[0] = make_float2(v.x, v.y);
                     x.v[DT - 1] = make_float2(v.z, v.w);
-                    const Arr<T2, DT> y = class_math<T2, DT>(x, kind, pure, perm, u);
+                    const Arr<T2, DT> y = class_math<T2, DT>(x, kind, u);
                     if (smask == 3u)
                         *reinterpret_cast<float4*>(tile + 2 * c) = make_float4(y.v[0].x, y.v[0].y, y.v[DT - 1].x,
                                                                                y.v[DT - 1].y);
@@ -260,7 +250,7 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
                 x.v[k].y = 0;
                 if (lmask >> k & 1u) x.v[k] = tile[b + k * lst];
             }
-            const Arr<T2, DT> y = class_math<T2, DT>(x, kind, pure, perm, u);
+            const Arr<T2, DT> y = class_math<T2, DT>(x, kind, u);
 #pragma unroll
             for (int r = 0; r < DT; ++r)
                 if (smask >> r & 1u) tile[b + r * lst] = y.v[r];
@@ -275,7 +265,7 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
                 x.v[k].y = 0;
                 if (lmask >> k & 1u) x.v[k] = tile[b + k * lst];
             }
-            const Arr<T2, DT> y = class_math<T2, DT>(x, kind, pure, perm, u);
+            const Arr<T2, DT> y = class_math<T2, DT>(x, kind, u);
 #pragma unroll
             for (int r = 0; r < DT; ++r)
                 if (smask >> r & 1u) tile[b + r * lst] = y.v[r];
@@ -283,100 +273,27 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
     }
 }
 
-// Dense composed block (P <= PP): a thread owns CT classes and accumulates
-// all PP output rows of each as outer products over the inputs k, so every
-// accumulator has CT * PP - 1 independent FMAs between its updates (the
-// row-by-row inner product is one dependent chain per row).  Per step of k
-// (two columns for complex64), each row's matrix entries are one 16-byte
-// broadcast load shared by the CT classes; a class's inputs are read once.
-// Its outputs are written after all its inputs were read, and no other
-// thread touches its members, so the update is in place.
-template <typename R, int PP, int CT>
-__device__ __forceinline__ void dense_block(typename Cplx<R>::T2* tile, const FGate& G,
-                                            const typename Cplx<R>::T2* M, const uint32_t (&off)[PP]) {
-    using T2 = typename Cplx<R>::T2;
-    const uint32_t nc = G.nclasses, lmask = G.lmask, smask = G.smask;
-    constexpr int KS = (sizeof(R) == 4 && PP % 2 == 0) ? 2 : 1;  // columns per matrix load
-    for (uint32_t c = CT * threadIdx.x; c < nc; c += CT * blockDim.x) {
-        uint32_t b[CT];
-        bool live[CT];
-#pragma unroll
-        for (int j = 0; j < CT; ++j) {
-            live[j] = c + j < nc;
-            b[j] = G.map.map(live[j] ? c + j : c);
-        }
-        T2 acc[CT][PP];
-#pragma unroll
-        for (int j = 0; j < CT; ++j)
-#pragma unroll
-            for (int r = 0; r < PP; ++r) acc[j][r].x = acc[j][r].y = 0;
-#pragma unroll
-        for (int k = 0; k < PP; k += KS) {
-            T2 x[CT][KS];
-#pragma unroll
-            for (int j = 0; j < CT; ++j)
-#pragma unroll
-                for (int q = 0; q < KS; ++q) {
-                    x[j][q].x = x[j][q].y = 0;
-                    if (lmask >> (k + q) & 1u) x[j][q] = tile[b[j] + off[k + q]];
-                }
-#pragma unroll
-            for (int r = 0; r < PP; ++r) {
-                if (!(smask >> r & 1u)) continue;
-                if constexpr (KS == 2) {
-                    const float4 m2 = *reinterpret_cast<const float4*>(M + r * PP + k);
-                    const float2 mA = make_float2(m2.x, m2.y), mB = make_float2(m2.z, m2.w);
-#pragma unroll
-                    for (int j = 0; j < CT; ++j) {
-                        fcmac(acc[j][r], mA, x[j][0]);
-                        fcmac(acc[j][r], mB, x[j][1]);
-                    }
-                } else {
-                    const T2 m = M[r * PP + k];
-#pragma unroll
-                    for (int j = 0; j < CT; ++j) fcmac(acc[j][r], m, x[j][0]);
-                }
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < CT; ++j)
-            if (live[j])
-#pragma unroll
-                for (int r = 0; r < PP; ++r)
-                    if (smask >> r & 1u) tile[b[j] + off[r]] = acc[j][r];
-    }
-}
-
-// Apply one composed block (P <= PP) to the tile.  Dense complex64 blocks:
-// above.  Otherwise one class per thread, its P members gathered into
-// registers (padded rows masked out) before the first store.
+// Apply one composed block (P <= PP) to the tile, one class per thread.  A
+// class's P members are gathered into registers (padded rows are masked
+// out); each output row is accumulated from the matrix row in the staged
+// pool, read by all threads at the same address (a broadcast) -- for
+// complex64 two adjacent entries per 16-byte load.  All inputs are in
+// registers before the first store.  Monomial blocks run as dense ones (see
+// class_math).  Measured alternatives that were slower on the benchmark
+// circuit's passes: a second class per thread (its registers cost more than
+// the matrix loads it shares); all rows of one or two classes accumulated as
+// outer products over the inputs (20-28% slower); monomial blocks gathered
+// from the tile by source address (register pressure of the whole kernel).
 template <typename R, int PP>
 __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGate& G,
                                            const typename Cplx<R>::T2* pool) {
     using T2 = typename Cplx<R>::T2;
     const uint32_t nc = G.nclasses, lmask = G.lmask, smask = G.smask;
     const int kind = G.kind;
-    const bool pure = G.pure != 0;
     uint32_t off[PP];
 #pragma unroll
     for (int r = 0; r < PP; ++r) off[r] = G.off[r];
     const T2* M = pool + G.u_off;
-    if (kind == kDense) {
-        // complex64: two classes per thread unless that leaves too many
-        // threads idle (a pair costs about 1.6 single-class steps);
-        // complex128: one (a second class's accumulators do not fit)
-        if constexpr (sizeof(R) == 4) {
-            const uint32_t n1 = (nc + blockDim.x - 1) / blockDim.x, n2 = (nc + 2 * blockDim.x - 1) / (2 * blockDim.x);
-            if (16u * n2 <= 10u * n1 + 4u) {
-                dense_block<R, PP, 2>(tile, G, M, off);
-                return;
-            }
-        }
-        if constexpr (sizeof(R) == 4) {
-            dense_block<R, PP, 1>(tile, G, M, off);
-            return;
-        }
-    }
     for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
         const uint32_t b0 = G.map.map(c);
         T2 x0[PP];
@@ -386,32 +303,30 @@ __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGa
             x0[k].y = 0;
             if (lmask >> k & 1u) x0[k] = tile[b0 + off[k]];
         }
-        if (kind == kDense) {  // complex128: FP64-bound, inputs in registers, one row at a time
+        if (kind != kDiag) {  // dense, or monomial through the dense path
 #pragma unroll
             for (int r = 0; r < PP; ++r) {
                 if (!(smask >> r & 1u)) continue;
+                const T2* Mr = M + r * PP;
                 T2 a0;
                 a0.x = a0.y = 0;
+                if constexpr (sizeof(R) == 4 && PP % 2 == 0) {
 #pragma unroll
-                for (int k = 0; k < PP; ++k) fcmac(a0, M[r * PP + k], x0[k]);
+                    for (int k = 0; k < PP; k += 2) {
+                        const float4 m2 = *reinterpret_cast<const float4*>(Mr + k);
+                        fcmac(a0, make_float2(m2.x, m2.y), x0[k]);
+                        fcmac(a0, make_float2(m2.z, m2.w), x0[k + 1]);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < PP; ++k) fcmac(a0, Mr[k], x0[k]);
+                }
                 tile[b0 + off[r]] = a0;
             }
-        } else if (kind == kDiag) {
+        } else {
 #pragma unroll
             for (int r = 0; r < PP; ++r)
                 if (smask >> r & 1u) tile[b0 + off[r]] = fcmul(M[r * PP + r], x0[r]);
-        } else {
-#pragma unroll
-            for (int r = 0; r < PP; ++r) {
-                if (!(smask >> r & 1u)) continue;
-                const int src = G.perm[r];
-                T2 v0 = x0[0];
-#pragma unroll
-                for (int k = 1; k < PP; ++k)
-                    if (src == k) v0 = x0[k];
-                if (!pure) v0 = fcmul(M[r * PP + src], v0);
-                tile[b0 + off[r]] = v0;
-            }
         }
     }
 }
@@ -631,12 +546,12 @@ __device__ __forceinline__ void tile_load_async(typename Cplx<R>::T2* tile, cons
 __host__ __device__ inline size_t fused_rows_bytes(uint32_t rows) { return ((size_t)rows * 8 + 15) & ~(size_t)15; }
 
 template <typename R, int DMAX>
-__global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ FusedArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ FusedArgs<R> a) {
     using T2 = typename Cplx<R>::T2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* stage = smem_raw;
-    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + chunk_smem_max<R>());
-    T2* tile = reinterpret_cast<T2*>(smem_raw + chunk_smem_max<R>() + fused_rows_bytes(a.rows));
+    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + a.stage);
+    T2* tile = reinterpret_cast<T2*>(smem_raw + a.stage + fused_rows_bytes(a.rows));
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
     {
@@ -674,142 +589,6 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile(const __grid_constant__ F
             g[srow[r] + (e - r * a.bL)] = tile[e];
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// Persistent tile passes: one CTA of 512 threads per SM walks tiles t =
-// blockIdx.x, + gridDim.x, ... with two tile buffers.  While the gates of
-// tile t are applied in one buffer, tile t + gridDim.x arrives in the other:
-// warp 0 issues one cp.async.bulk per contiguous row (bL amplitudes), all
-// completing on that buffer's mbarrier; after the gates, warp 0 writes the
-// tile back with bulk stores and waits for their shared-memory reads only
-// before the buffer is refilled.  Rows are 16-byte multiples (complex64 with
-// even bL, every complex128 layout), so every bulk copy is aligned.  Waits
-// are bounded; on a timeout the CTA records QD_ERR_TIMEOUT, waits (bounded)
-// for its copies in flight and stops.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ bool mbar_try_wait_bounded(uint32_t mbar, uint32_t phase) {
-    for (uint32_t it = 0; it < (1u << 26); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred P;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
-            "selp.b32 %0, 1, 0, P;\n\t}"
-            : "=r"(done)
-            : "r"(mbar), "r"(phase));
-        if (done) return true;
-    }
-    return false;
-}
-
-template <typename R, int DMAX>
-__global__ void __launch_bounds__(512, 1) k_fused_pipe(const __grid_constant__ FusedArgs<R> a) {
-    using T2 = typename Cplx<R>::T2;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned char* stage = smem_raw;
-    uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + chunk_smem_max<R>());
-    T2* buf[2];
-    buf[0] = reinterpret_cast<T2*>(smem_raw + chunk_smem_max<R>() + fused_rows_bytes(a.rows));
-    buf[1] = buf[0] + a.T;
-    __shared__ int32_t odig[kMaxWires];
-    __shared__ __align__(8) uint64_t mbar[2];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const uint32_t row_bytes = a.bL * (uint32_t)sizeof(T2);
-    for (uint32_t r = tid; r < a.rows; r += blockDim.x) srow[r] = a.rowoff[r];
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // base offset (and, optionally, the digits of the wires outside the tile) of tile t
-    auto tile_base = [&](uint64_t t, int32_t* dig) -> uint64_t {
-        uint32_t rem = (uint32_t)t;
-        uint64_t base = 0;
-        for (int i = 0; i < a.nfree; ++i) {
-            const uint32_t q = a.free_div[i].div(rem);
-            const uint32_t dg = rem - q * a.free_d[i];
-            if (dig) dig[a.free_w[i]] = (int32_t)dg;
-            base += (uint64_t)dg * a.free_b[i];
-            rem = q;
-        }
-        return base;
-    };
-    // warp 0: tile t -> buf[b] (one bulk copy per row, completing on mbar[b])
-    auto issue_load = [&](uint64_t t, int b) {
-        uint64_t base = 0;
-        if (lane == 0) {
-            base = tile_base(t, nullptr);
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&mbar[b])),
-                         "r"(a.T * (uint32_t)sizeof(T2))
-                         : "memory");
-        }
-        base = __shfl_sync(0xffffffffu, base, 0);
-        const T2* g = a.psi + base;
-        const uint32_t dst0 = smem_addr(buf[b]);
-        for (uint32_t r = lane; r < a.rows; r += 32)
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                    dst0 + r * row_bytes),
-                "l"(g + srow[r]), "r"(row_bytes), "r"(smem_addr(&mbar[b]))
-                : "memory");
-    };
-    uint32_t ph[2] = {0u, 0u};
-    bool pending[2] = {false, false};  // a load into the buffer has been issued and not yet waited for
-    bool aborted = false;
-    uint64_t t = blockIdx.x;
-    if (t < a.ntiles) {
-        if (warp == 0) issue_load(t, 0);
-        pending[0] = true;
-    }
-    for (int k = 0; t < a.ntiles; t += gridDim.x, ++k) {
-        const int b = k & 1;
-        const uint64_t tn = t + gridDim.x;
-        if (tn < a.ntiles) {
-            if (warp == 0) {
-                // buf[b ^ 1] was last written back by this warp's bulk stores
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-                __syncwarp();
-                issue_load(tn, b ^ 1);
-            }
-            pending[b ^ 1] = true;
-        }
-        const bool bad = !mbar_try_wait_bounded(smem_addr(&mbar[b]), ph[b]);
-        if (__syncthreads_or(bad)) {
-            aborted = true;
-            break;
-        }
-        ph[b] ^= 1u;
-        pending[b] = false;
-        if (tid == 0) (void)tile_base(t, odig);
-        __syncthreads();
-        apply_chunks<R, DMAX>(buf[b], a.chunks, a.nchunks, stage, odig);
-        // generic-proxy writes of the tile -> async proxy, then write it back
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (warp == 0) {
-            uint64_t base = lane == 0 ? tile_base(t, nullptr) : 0;
-            base = __shfl_sync(0xffffffffu, base, 0);
-            T2* g = a.psi + base;
-            const uint32_t src0 = smem_addr(buf[b]);
-            for (uint32_t r = lane; r < a.rows; r += 32)
-                asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(g + srow[r]),
-                             "r"(src0 + r * row_bytes), "r"(row_bytes)
-                             : "memory");
-            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-        }
-    }
-    if (aborted && tid == 0) {
-        // loads still in flight land in this CTA's shared memory: wait (bounded) before leaving
-        for (int i = 0; i < 2; ++i)
-            if (pending[i]) (void)mbar_try_wait_bounded(smem_addr(&mbar[i]), ph[i]);
-        atomicExch(a.status, QD_ERR_TIMEOUT);
-    }
-    if (warp == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-    __syncthreads();
 }
 
 // Tile pass whose chunks hold tensor-core blocks (complex64): k_fused_tile
@@ -912,7 +691,7 @@ cudaError_t launch_fused_tc(const FusedArgs<float>& a, int dmax, cudaStream_t s)
 
 template <typename R>
 size_t fused_smem(const FusedArgs<R>& a) {
-    return chunk_smem_max<R>() + fused_rows_bytes(a.rows) + sizeof(typename Cplx<R>::T2) * (size_t)a.T;
+    return (size_t)a.stage + fused_rows_bytes(a.rows) + sizeof(typename Cplx<R>::T2) * (size_t)a.T;
 }
 
 // dmax: largest single-wire dimension among the pass's gates (selects the
@@ -934,43 +713,6 @@ cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
         k_fused_tile<R, 3><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
     else
         k_fused_tile<R, 5><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
-    count_launch();
-    return cudaGetLastError();
-}
-
-// Shared memory of the persistent kernel (two tile buffers), and whether a
-// pass can use it: rows of whole 16-byte units and the buffers within the
-// 227 KB a CTA may use.
-template <typename R>
-size_t fused_pipe_smem(uint32_t T, uint32_t rows) {
-    return chunk_smem_max<R>() + fused_rows_bytes(rows) + 2 * sizeof(typename Cplx<R>::T2) * (size_t)T;
-}
-template <typename R>
-bool fused_pipe_ok(uint32_t T, uint32_t bL, uint32_t rows) {
-    return (bL * sizeof(typename Cplx<R>::T2)) % 16 == 0 && fused_pipe_smem<R>(T, rows) <= 220 * 1024;
-}
-
-template <typename R>
-cudaError_t launch_fused_pipe(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
-    static int attr_dev = -1, sms = 0;
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (attr_dev != dev) {
-        cudaError_t e = cudaFuncSetAttribute(k_fused_pipe<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             220 * 1024);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fused_pipe<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return e;
-        attr_dev = dev;
-    }
-    const uint64_t grid = a.ntiles < (uint64_t)sms ? a.ntiles : (uint64_t)sms;
-    if (grid == 0) return cudaSuccess;
-    const size_t smem = fused_pipe_smem<R>(a.T, a.rows);
-    if (dmax <= 3)
-        k_fused_pipe<R, 3><<<(unsigned)grid, 512, smem, s>>>(a);
-    else
-        k_fused_pipe<R, 5><<<(unsigned)grid, 512, smem, s>>>(a);
     count_launch();
     return cudaGetLastError();
 }
@@ -1075,7 +817,6 @@ FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     c.Tmax = (o && o->max_tile_amps > 0) ? o->max_tile_amps : (prec == QD_C64 ? 8192 : 4096);
     c.min_gates = (o && o->min_gates > 0) ? o->min_gates : 2;
     c.min_row = (o && o->min_row > 0) ? o->min_row : (prec == QD_C64 ? 16 : 8);
-    c.persistent = true;
     if (c.mode == QD_FUSE_BLOCK) {
         c.block_dim = (o && o->block_dim > 0) ? o->block_dim : (prec == QD_C64 ? 64 : 8);
         if (c.block_dim > 64) c.block_dim = 64;
@@ -1659,10 +1400,11 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
 // largest single-wire dimension (kernel instance).
 template <typename R>
 static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<BlockPlan>& blocks,
-                          Program& prog, uint32_t* nchunks, int* dmax, bool* has_tc = nullptr) {
+                          Program& prog, uint32_t* nchunks, int* dmax, bool* has_tc = nullptr,
+                          uint32_t* max_bytes = nullptr) {
     using T2 = typename Cplx<R>::T2;
     std::vector<char> buf;
-    uint32_t n = 0;
+    uint32_t n = 0, mb = 0;
     int dm = 2;
     size_t i = 0;
     while (i < blocks.size()) {
@@ -1689,6 +1431,7 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
         h.ngates = (uint32_t)fg.size();
         h.npool = (uint32_t)pool.size();
         h.bytes = (uint32_t)((chunk_bytes<R>(h.ngates, h.npool) + 15) & ~(size_t)15);
+        mb = h.bytes > mb ? h.bytes : mb;
         const size_t o = buf.size();
         buf.resize(o + h.bytes, 0);
         std::memcpy(buf.data() + o, &h, sizeof h);
@@ -1698,6 +1441,7 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
     }
     *nchunks = n;
     if (dmax) *dmax = dm;
+    if (max_bytes) *max_bytes = mb;
     return prog.put(buf.data(), buf.size());
 }
 
@@ -1858,7 +1602,6 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int 
     };
 }
 
-static double pass_arith(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg, const PassPlan& p);
 
 // Ops of a whole circuit on the state at psi (layout L): optional reset to
 // |0...0>, then the planned passes in order.
@@ -1894,7 +1637,8 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
         uint32_t nchunks = 0;
         int dmax = 2;
         bool has_tc = false;
-        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax, &has_tc);
+        uint32_t stage_bytes = 0;
+        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax, &has_tc, &stage_bytes);
         const size_t offR = prog.put(geo.rowoff.data(), sizeof(uint64_t) * geo.R);
         FusedArgs<R> a;
         std::memset(static_cast<void*>(&a), 0, sizeof a);
@@ -1914,20 +1658,8 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
             a.free_b[i] = geo.free_b[i];
         }
         a.status = tc_status_ptr();
-        // The persistent kernel (one CTA of 512 threads per SM, bulk copies
-        // overlapping the next tile's load with this tile's gates) wins on
-        // passes that are light on arithmetic (measured on the 26.9M-amplitude
-        // layout: 157 vs 214 us for two diagonal gates, 215 vs 244 us for one
-        // 16-dimensional block); on heavy passes (214 flop per amplitude and
-        // more) two independent 256-thread CTAs per SM, which overlap each
-        // other's per-gate barriers, win.  Bulk copies also need 16-byte
-        // aligned rows: the state itself 16-byte aligned too.  The server
-        // turns it off: a kernel holding every SM would serialise requests
-        // that otherwise overlap on their streams.
-        const double flops_per_amp = pass_arith(L, G, cfg, p) / (double)L.D;
-        const bool pipe = !has_tc && cfg.persistent && a.status != nullptr && flops_per_amp < kPipeMaxFlops &&
-                          reinterpret_cast<uintptr_t>(psi) % 16 == 0 && fused_pipe_ok<R>(a.T, a.bL, a.rows);
-        prog.ops.push_back([a, offC, offR, dmax, pipe, has_tc](cudaStream_t s, const char* base) {
+        a.stage = stage_bytes;
+        prog.ops.push_back([a, offC, offR, dmax, has_tc](cudaStream_t s, const char* base) {
             FusedArgs<R> b = a;
             b.chunks = base + offC;
             b.rowoff = reinterpret_cast<const uint64_t*>(base + offR);
@@ -1938,7 +1670,7 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
                     return launch_fused_tc(b, dmax, s);
                 }
             }
-            return pipe ? launch_fused_pipe<R>(b, dmax, s) : launch_fused<R>(b, dmax, s);
+            return launch_fused<R>(b, dmax, s);
         });
     }
 }

@@ -30,7 +30,6 @@ struct FuseCfg {
     int64_t min_row;
     int block_dim;  // largest composed block inside a pass (< 4: no composition)
     int tc_mode;    // QD_TC_*: complex64 blocks of 17..64 dimensions
-    bool persistent;  // light tile passes may use the persistent kernel (one CTA per SM, whole GPU)
 };
 
 int64_t tile_limit(int32_t prec);

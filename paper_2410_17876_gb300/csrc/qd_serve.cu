@@ -381,7 +381,6 @@ qd_status qd_server_create(int32_t prec, const qd_server_opts* opts, qd_server**
         qd_fusion_opts fo{};
         if (opts) fo = opts->fusion;
         s->cfg = fuse_cfg(&fo, prec);
-        s->cfg.persistent = false;  // requests overlap on their streams; keep kernels that share the GPU
         qd_status rc = check_cfg(s->cfg, prec);
         if (rc == QD_OK && s->small_max > tile_limit(prec))
             rc = fail(QD_ERR_UNSUPPORTED, "small-request tile above shared memory");

@@ -108,11 +108,11 @@ def test_tile_too_large_is_rejected(qb, gen):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64"])
-def test_light_passes_persistent_kernel(qb, gen, prec):
+def test_light_passes(qb, gen, prec):
     """Passes light on arithmetic (phase and permutation gates, a few
-    controlled) run on the persistent double-buffered tile kernel: 2.98M
-    amplitudes in tiles of at most 4096, so every CTA walks several tiles
-    through both buffers, with controls outside the tile evaluated per tile."""
+    controlled; monomial gates run through the dense class update): 2.98M
+    amplitudes in tiles of at most 4096, with controls outside the tile
+    evaluated per tile."""
     p = qb.QD_C64 if prec == "c64" else qb.QD_C128
     rng = np.random.Generator(np.random.PCG64(77))
     dims = (2,) * 12 + (3,) * 6
