@@ -274,27 +274,69 @@ __device__ __forceinline__ void tile_gate(typename Cplx<R>::T2* tile, const FGat
     }
 }
 
-// Apply one composed block (P <= PP) to the tile, one class per thread.  A
-// class's P members are gathered into registers (padded rows are masked
-// out); each output row is accumulated from the matrix row in the staged
-// pool, read by all threads at the same address (a broadcast) -- for
-// complex64 two adjacent entries per 16-byte load.  All inputs are in
-// registers before the first store.  Monomial blocks run as dense ones (see
-// class_math).  Measured alternatives that were slower on the benchmark
-// circuit's passes: a second class per thread (its registers cost more than
-// the matrix loads it shares); all rows of one or two classes accumulated as
-// outer products over the inputs (20-28% slower); monomial blocks gathered
-// from the tile by source address (register pressure of the whole kernel).
+// Dense (or monomial) composed block, one class per thread: the class's
+// members are gathered into registers (padded rows masked out) before the
+// first store; each output row is accumulated from the matrix row in the
+// staged pool, read by all threads at the same address (a broadcast) -- for
+// complex64 two adjacent entries per 16-byte load.
+template <typename R, int PP>
+__device__ __forceinline__ void block_dense(typename Cplx<R>::T2* tile, const FGate& G,
+                                            const typename Cplx<R>::T2* M, const uint32_t (&off)[PP]) {
+    using T2 = typename Cplx<R>::T2;
+    const uint32_t nc = G.nclasses, lmask = G.lmask, smask = G.smask;
+    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+        const uint32_t b = G.map.map(c);
+        T2 x[PP];
+#pragma unroll
+        for (int k = 0; k < PP; ++k) {
+            x[k].x = 0;
+            x[k].y = 0;
+            if (lmask >> k & 1u) x[k] = tile[b + off[k]];
+        }
+#pragma unroll
+        for (int r = 0; r < PP; ++r) {
+            if (!(smask >> r & 1u)) continue;
+            const T2* Mr = M + r * PP;
+            T2 a;
+            a.x = a.y = 0;
+            if constexpr (sizeof(R) == 4 && PP % 2 == 0) {
+#pragma unroll
+                for (int k = 0; k < PP; k += 2) {
+                    const float4 m2 = *reinterpret_cast<const float4*>(Mr + k);
+                    fcmac(a, make_float2(m2.x, m2.y), x[k]);
+                    fcmac(a, make_float2(m2.z, m2.w), x[k + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < PP; ++k) fcmac(a, Mr[k], x[k]);
+            }
+            tile[b + off[r]] = a;
+        }
+    }
+}
+
+// Apply one composed block (P <= PP) to the tile, one class per thread.
+// Dense and monomial blocks (the latter run as dense ones, see class_math)
+// through block_dense; diagonal blocks scale each member.  Measured
+// alternatives that were slower on the benchmark circuit's passes: two
+// classes per thread (their registers cost more than the matrix loads they
+// share: 8-dimensional blocks 53 vs 48 us per 26.9M amplitudes); all rows of
+// one or two classes accumulated as outer products over the inputs (20-28%
+// slower); monomial blocks gathered from the tile by source address
+// (register pressure of the whole kernel).
 template <typename R, int PP>
 __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGate& G,
                                            const typename Cplx<R>::T2* pool) {
     using T2 = typename Cplx<R>::T2;
     const uint32_t nc = G.nclasses, lmask = G.lmask, smask = G.smask;
-    const int kind = G.kind;
     uint32_t off[PP];
 #pragma unroll
     for (int r = 0; r < PP; ++r) off[r] = G.off[r];
     const T2* M = pool + G.u_off;
+    if (G.kind != kDiag) {
+        block_dense<R, PP>(tile, G, M, off);
+        return;
+    }
     for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
         const uint32_t b0 = G.map.map(c);
         T2 x0[PP];
@@ -304,31 +346,9 @@ __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGa
             x0[k].y = 0;
             if (lmask >> k & 1u) x0[k] = tile[b0 + off[k]];
         }
-        if (kind != kDiag) {  // dense, or monomial through the dense path
 #pragma unroll
-            for (int r = 0; r < PP; ++r) {
-                if (!(smask >> r & 1u)) continue;
-                const T2* Mr = M + r * PP;
-                T2 a0;
-                a0.x = a0.y = 0;
-                if constexpr (sizeof(R) == 4 && PP % 2 == 0) {
-#pragma unroll
-                    for (int k = 0; k < PP; k += 2) {
-                        const float4 m2 = *reinterpret_cast<const float4*>(Mr + k);
-                        fcmac(a0, make_float2(m2.x, m2.y), x0[k]);
-                        fcmac(a0, make_float2(m2.z, m2.w), x0[k + 1]);
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < PP; ++k) fcmac(a0, Mr[k], x0[k]);
-                }
-                tile[b0 + off[r]] = a0;
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < PP; ++r)
-                if (smask >> r & 1u) tile[b0 + off[r]] = fcmul(M[r * PP + r], x0[r]);
-        }
+        for (int r = 0; r < PP; ++r)
+            if (smask >> r & 1u) tile[b0 + off[r]] = fcmul(M[r * PP + r], x0[r]);
     }
 }
 
