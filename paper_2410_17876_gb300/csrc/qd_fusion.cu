@@ -129,6 +129,7 @@ struct FusedArgs {
     const uint64_t* rowoff;  // device, rows entries: offset of each row from the tile base
     int32_t* status;         // tensor-core kernel: QD_ERR_TIMEOUT if a bounded wait gave up
     uint32_t stage;          // bytes of the pass's largest chunk: k_fused_tile's shared-memory stage
+    uint32_t first_bytes;    // bytes of the first chunk (staged by k_fused_tile with the row offsets)
     const char* desc_base;   // the program's descriptors (tensor-core operands)
 };
 
@@ -481,16 +482,18 @@ __device__ bool tile_tc_block(float2* tile, const FGate& G, TcTileCtx& c) {
 
 // Apply a list of chunks to a tile in shared memory.  stage: shared memory
 // for one chunk; odig: digits of the wires outside the tile (fused passes);
-// tc: tensor-core context (TC = true: complex64 tiles with kTcBlock gates).
+// tc: tensor-core context (TC = true: complex64 tiles with kTcBlock gates);
+// first_staged: the caller has already staged the first chunk.
 // Returns false (the same on every thread) if a tensor-core wait gave up.
 template <typename R, int DMAX, bool TC = false>
 __device__ __forceinline__ bool apply_chunks(typename Cplx<R>::T2* tile, const char* chunk, int nchunks,
-                                             unsigned char* stage, const int32_t* odig, TcTileCtx* tc = nullptr) {
+                                             unsigned char* stage, const int32_t* odig, TcTileCtx* tc = nullptr,
+                                             bool first_staged = false) {
     using T2 = typename Cplx<R>::T2;
     for (int ci = 0; ci < nchunks; ++ci) {
         const ChunkHdr h = *reinterpret_cast<const ChunkHdr*>(chunk);
         __syncthreads();  // the previous chunk is done with the stage
-        {
+        if (!(first_staged && ci == 0)) {
             // every 16-byte piece in flight at once (cp.async), then wait
             const uint32_t d0 = static_cast<uint32_t>(__cvta_generic_to_shared(stage));
             for (uint32_t i = threadIdx.x; i < h.bytes / 16; i += blockDim.x)
@@ -576,10 +579,15 @@ __global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ F
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
     {
+        // the row offsets and the first chunk arrive together (cp.async)
+        // while thread 0 derives the tile's base and outside digits
         const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(srow));
         for (uint32_t r = threadIdx.x; r < a.rows; r += blockDim.x)
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s0 + 8u * r), "l"(a.rowoff + r));
-        asm volatile("cp.async.wait_all;" ::: "memory");
+        const uint32_t d0 = static_cast<uint32_t>(__cvta_generic_to_shared(stage));
+        if (a.nchunks > 0)
+            for (uint32_t i = threadIdx.x; i < a.first_bytes / 16; i += blockDim.x)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16u * i), "l"(a.chunks + 16u * i));
     }
     if (threadIdx.x == 0) {
         uint32_t rem = blockIdx.x;
@@ -593,10 +601,11 @@ __global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ F
         }
         sbase = base;
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     T2* g = a.psi + sbase;
     tile_load_async<R>(tile, g, srow, a);  // published by apply_chunks' first barrier
-    apply_chunks<R, DMAX>(tile, a.chunks, a.nchunks, stage, odig);
+    apply_chunks<R, DMAX>(tile, a.chunks, a.nchunks, stage, odig, nullptr, true);
     __syncthreads();
     if (a.vec2) {
         for (uint32_t e = 2 * threadIdx.x; e < a.T; e += 2 * blockDim.x) {
@@ -1459,7 +1468,7 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
 template <typename R>
 static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<BlockPlan>& blocks,
                           Program& prog, uint32_t* nchunks, int* dmax, bool* has_tc = nullptr,
-                          uint32_t* max_bytes = nullptr) {
+                          uint32_t* max_bytes = nullptr, uint32_t* first_bytes = nullptr) {
     using T2 = typename Cplx<R>::T2;
     std::vector<char> buf;
     uint32_t n = 0, mb = 0;
@@ -1490,6 +1499,7 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
         h.npool = (uint32_t)pool.size();
         h.bytes = (uint32_t)((chunk_bytes<R>(h.ngates, h.npool) + 15) & ~(size_t)15);
         mb = h.bytes > mb ? h.bytes : mb;
+        if (n == 0 && first_bytes) *first_bytes = h.bytes;
         const size_t o = buf.size();
         buf.resize(o + h.bytes, 0);
         std::memcpy(buf.data() + o, &h, sizeof h);
@@ -1695,8 +1705,8 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
         uint32_t nchunks = 0;
         int dmax = 2;
         bool has_tc = false;
-        uint32_t stage_bytes = 0;
-        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax, &has_tc, &stage_bytes);
+        uint32_t stage_bytes = 0, first_bytes = 0;
+        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax, &has_tc, &stage_bytes, &first_bytes);
         const size_t offR = prog.put(geo.rowoff.data(), sizeof(uint64_t) * geo.R);
         FusedArgs<R> a;
         std::memset(static_cast<void*>(&a), 0, sizeof a);
@@ -1717,6 +1727,7 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
         }
         a.status = tc_status_ptr();
         a.stage = stage_bytes;
+        a.first_bytes = first_bytes;
         prog.ops.push_back([a, offC, offR, dmax, has_tc](cudaStream_t s, const char* base) {
             FusedArgs<R> b = a;
             b.chunks = base + offC;
