@@ -72,6 +72,8 @@ struct __align__(16) LocalMap {
 constexpr int kMaxBlock = 16;       // largest composed block on CUDA cores (product of its wires' dimensions)
 constexpr int kMaxTcBlock = 32;     // complex64: blocks of 17..32 dimensions run on the tensor cores inside tiles
 constexpr uint8_t kTcBlock = 3;     // FGate kind of such a block
+constexpr uint8_t kRun = 4;         // FGate kind of a run of single-wire gates applied in registers
+constexpr int kMaxRunGates = 16;    // gates per run
 constexpr int kMaxChunkGates = 64;  // gate records per chunk
 constexpr int kPoolEntries = 2048;  // matrix entries per chunk (complex, in the state's precision)
 
@@ -87,12 +89,18 @@ struct __align__(16) FGate {
     uint32_t lst, step;
     uint32_t u_off;  // matrix: entries [u_off, u_off + PP * PP) of the chunk pool, row-major, PP columns
     uint8_t P, PP, kind, single;
-    uint8_t n_out, pure, unitary, pad0;
+    uint8_t n_out, pure, unitary, nsub;
     uint16_t lmask, smask;
     uint32_t op_off;  // kTcBlock: byte offset of the B operand (hi | lo, 32 KB) from the descriptor base
-    uint8_t perm[kMaxBlock];
     uint8_t out_w[8], out_v[8];  // controls outside the tile: global wire, value
     uint16_t off[kMaxTcBlock];
+    // kRun: the block's wire dimensions (shape id), and per gate the position
+    // of its target among the block's wires, the members it acts on (its
+    // in-block controls met) and its d x d matrix in the chunk pool
+    uint8_t shape, pad1[3];
+    uint8_t sub_pos[kMaxRunGates];
+    uint16_t sub_mask[kMaxRunGates];
+    uint16_t sub_u[kMaxRunGates];
 };
 
 // Chunk header; the chunk is [header][ngates FGate][npool matrix entries], 16-byte aligned.
@@ -353,6 +361,103 @@ __device__ __forceinline__ void block_gate(typename Cplx<R>::T2* tile, const FGa
     }
 }
 
+// Runs of single-wire gates applied in registers (complex64).  A class of
+// the block's wires (at most four, of dimension 2 or 3, at most 16 members)
+// is gathered once; each gate of the run then updates the members in
+// registers -- d x d products on the groups of members that differ only in
+// the gate's target digit, skipping groups its controls exclude -- and the
+// class is written back once.  One shared-memory sweep for the whole run,
+// and each gate's own arithmetic instead of the composed P x P product.
+// Member m of a class has digit (m / stride_j) % d_j on block wire j, the
+// first wire least significant.  Every register index is a compile-time
+// constant: the gate's position selects an instantiation.
+template <int D0, int D1, int D2, int D3>
+struct RunShape {
+    static constexpr int P = D0 * D1 * D2 * D3;
+    static constexpr int nw = 1 + (D1 > 1) + (D2 > 1) + (D3 > 1);
+    static constexpr int dim(int j) { return j == 0 ? D0 : j == 1 ? D1 : j == 2 ? D2 : D3; }
+    static constexpr int stride(int j) { return j == 0 ? 1 : j == 1 ? D0 : j == 2 ? D0 * D1 : D0 * D1 * D2; }
+};
+
+template <typename S, int J>
+__device__ __forceinline__ void run_apply(float2 (&x)[S::P], const float2* U, uint32_t mask) {
+    constexpr int D = S::dim(J), ST = S::stride(J);
+    float2 u[D * D];
+#pragma unroll
+    for (int i = 0; i < D * D; ++i) u[i] = U[i];
+#pragma unroll
+    for (int m = 0; m < S::P; ++m) {
+        if ((m / ST) % D != 0) continue;  // group base: target digit 0
+        uint32_t gm = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) gm |= 1u << (m + k * ST);
+        if (!(mask & gm)) continue;  // the gate's controls exclude this group (uniform across threads)
+        float2 y[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            float2 acc = fcmul(u[r * D], x[m]);
+#pragma unroll
+            for (int k = 1; k < D; ++k) fcmac(acc, u[r * D + k], x[m + k * ST]);
+            y[r] = acc;
+        }
+#pragma unroll
+        for (int r = 0; r < D; ++r) x[m + r * ST] = y[r];
+    }
+}
+
+template <typename S>
+__device__ __forceinline__ void run_block(float2* tile, const FGate& G, const float2* pool) {
+    const uint16_t* off = G.off;  // read from the staged record at each use: registers go to the class
+    const uint32_t nc = G.nclasses;
+    const int ns = G.nsub;
+    for (uint32_t c = threadIdx.x; c < nc; c += blockDim.x) {
+        const uint32_t b = G.map.map(c);
+        float2 x[S::P];
+#pragma unroll
+        for (int k = 0; k < S::P; ++k) x[k] = tile[b + off[k]];
+        for (int s = 0; s < ns; ++s) {
+            const float2* U = pool + G.sub_u[s];
+            const uint32_t mask = G.sub_mask[s];
+            switch (G.sub_pos[s]) {
+                case 0: run_apply<S, 0>(x, U, mask); break;
+                case 1:
+                    if constexpr (S::nw > 1) run_apply<S, 1>(x, U, mask);
+                    break;
+                case 2:
+                    if constexpr (S::nw > 2) run_apply<S, 2>(x, U, mask);
+                    break;
+                default:
+                    if constexpr (S::nw > 3) run_apply<S, 3>(x, U, mask);
+                    break;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < S::P; ++r) tile[b + off[r]] = x[r];
+    }
+}
+
+// Shape ids of runs (wire dimensions, first wire least significant).
+constexpr int kRunShapes = 9;
+__host__ __device__ constexpr int run_shape_dims(int id, int j) {
+    constexpr int t[kRunShapes][4] = {{2, 2, 1, 1}, {2, 3, 1, 1}, {3, 2, 1, 1}, {3, 3, 1, 1}, {2, 2, 2, 1},
+                                      {2, 2, 3, 1}, {2, 3, 2, 1}, {3, 2, 2, 1}, {2, 2, 2, 2}};
+    return t[id][j];
+}
+
+__device__ __forceinline__ void run_dispatch(float2* tile, const FGate& G, const float2* pool) {
+    switch (G.shape) {
+        case 0: run_block<RunShape<2, 2, 1, 1>>(tile, G, pool); break;
+        case 1: run_block<RunShape<2, 3, 1, 1>>(tile, G, pool); break;
+        case 2: run_block<RunShape<3, 2, 1, 1>>(tile, G, pool); break;
+        case 3: run_block<RunShape<3, 3, 1, 1>>(tile, G, pool); break;
+        case 4: run_block<RunShape<2, 2, 2, 1>>(tile, G, pool); break;
+        case 5: run_block<RunShape<2, 2, 3, 1>>(tile, G, pool); break;
+        case 6: run_block<RunShape<2, 3, 2, 1>>(tile, G, pool); break;
+        case 7: run_block<RunShape<3, 2, 2, 1>>(tile, G, pool); break;
+        default: run_block<RunShape<2, 2, 2, 2>>(tile, G, pool); break;
+    }
+}
+
 // Tensor-core blocks inside a tile (complex64, blocks of 17..32 dimensions).
 // For 128 classes at a time the block is the contraction
 //     Y (128 x 64) = X (128 x 64) . B^T,  B = [[Re U, -Im U], [Im U, Re U]]
@@ -514,6 +619,13 @@ __device__ __forceinline__ bool apply_chunks(typename Cplx<R>::T2* tile, const c
                 if (G.kind == kTcBlock) {
                     if (!tile_tc_block(reinterpret_cast<float2*>(tile), G, *tc)) return false;
                     continue;  // tile_tc_block ends with a barrier
+                }
+            }
+            if constexpr (sizeof(R) == 4) {
+                if (G.kind == kRun) {
+                    run_dispatch(reinterpret_cast<float2*>(tile), G, reinterpret_cast<const float2*>(pool));
+                    __syncthreads();
+                    continue;
                 }
             }
             if (G.single) {
@@ -844,6 +956,7 @@ FuseCfg fuse_cfg(const qd_fusion_opts* o, int32_t prec) {
     FuseCfg c;
     c.mode = o ? o->mode : QD_FUSE_OFF;
     c.tc_mode = o ? o->tc_mode : QD_TC_TF32X3;
+    c.runs = prec == QD_C64;
     c.Tmax = (o && o->max_tile_amps > 0) ? o->max_tile_amps : (prec == QD_C64 ? 8192 : 4096);
     c.min_gates = (o && o->min_gates > 0) ? o->min_gates : 2;
     c.min_row = (o && o->min_row > 0) ? o->min_row : (prec == QD_C64 ? 16 : 8);
@@ -1086,7 +1199,11 @@ struct BlockPlan {
     std::vector<int> gates;  // in application order
     uint64_t lw;             // local wires (bit i = local wire i)
     bool single;
+    bool run = false;        // applied gate by gate in registers (kRun), not composed
 };
+
+// Shape id of a run over the local wires lw (ascending), or -1.
+static int run_shape_of(const TileGeom& geo, uint64_t lw);
 
 static int padded_dim(int P) {
     static const int sizes[] = {4, 6, 8, 9, 12, 16};
@@ -1116,7 +1233,7 @@ static int64_t local_prod(const TileGeom& geo, uint64_t lw) {
 static double sweep_cost(int kind, int64_t P) { return kind == kDense && P > 2 ? (double)P : 2.5; }
 
 static void form_blocks(const TileGeom& geo, const std::vector<HGate>& G, const std::vector<int>& pg, int Pmax,
-                        std::vector<BlockPlan>& out, bool one_pass_each = false) {
+                        std::vector<BlockPlan>& out, bool one_pass_each = false, bool runs = false) {
     out.clear();
     // per gate (index into pg): local wire mask, and whether it can join a block
     const size_t n = pg.size();
@@ -1177,9 +1294,23 @@ static void form_blocks(const TileGeom& geo, const std::vector<HGate>& G, const 
             bool all_diag = true;
             for (size_t ij : sel) all_diag = all_diag && G[pg[ij]].diag;
             const double cost_block = sweep_cost(all_diag ? kDiag : kDense, PW);
+            // a run: one sweep plus each gate's own arithmetic (d units for a
+            // d x d gate, times the share of classes its controls admit)
+            double cost_run = 1e300;
+            if (runs && !one_pass_each && sel.size() <= (size_t)kMaxRunGates && run_shape_of(geo, W) >= 0) {
+                cost_run = 2.5;
+                for (size_t ij : sel) {
+                    const HGate& g = G[pg[ij]];
+                    double share = 1.0;
+                    for (int c = 0; c < g.nc; ++c) share /= geo.local.dims[geo.loc[g.cw[c]]];
+                    cost_run += g.plan.d * share;
+                }
+            }
+            const double best = cost_run < cost_block ? cost_run : cost_block;
             // one_pass_each: every block or gate costs one pass over the state
-            if (sel.size() > 1 && (one_pass_each || cost_block <= cost_single)) {
+            if (sel.size() > 1 && (one_pass_each || best <= cost_single)) {
                 bp.single = false;
+                bp.run = cost_run < cost_block;
                 bp.gates.clear();
                 for (size_t ij : sel) bp.gates.push_back(pg[ij]);
                 bp.lw = W;
@@ -1284,7 +1415,6 @@ static void fill_single(const TileGeom& geo, const HGate& h, FGate& f, std::vect
     f.lmask = (uint16_t)p.lmask;
     f.smask = (uint16_t)p.smask;
     f.pure = p.pure ? 1 : 0;
-    for (int r = 0; r < kMaxSmallD && r < kMaxBlock; ++r) f.perm[r] = (uint8_t)p.perm[r];
     f.u_off = (uint32_t)pool.size();
     for (int i = 0; i < p.d * p.d; ++i) {
         typename Cplx<R>::T2 v;
@@ -1412,7 +1542,6 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
         f.kind = kPerm;
         f.pure = 1;
         for (int r = 0; r < P; ++r) {
-            f.perm[r] = (uint8_t)src[r];
             if (!one(r, src[r])) f.pure = 0;
             if (src[r] != r || !one(r, src[r])) {
                 f.smask |= (uint16_t)(1u << r);
@@ -1462,6 +1591,98 @@ static void fill_block(const TileGeom& geo, const std::vector<HGate>& G, const B
     f.n_out = 0;
 }
 
+static int run_shape_of(const TileGeom& geo, uint64_t lw) {
+    int d[4] = {1, 1, 1, 1}, n = 0;
+    for (int i = 0; i < geo.ns; ++i)
+        if (lw >> i & 1) {
+            if (n == 4) return -1;
+            d[n++] = geo.local.dims[i];
+        }
+    for (int id = 0; id < kRunShapes; ++id) {
+        bool eq = true;
+        for (int j = 0; j < 4; ++j) eq = eq && run_shape_dims(id, j) == d[j];
+        if (eq) return id;
+    }
+    return -1;
+}
+
+// A run (kRun): the block's gates in order, each as its d x d matrix, target
+// position and member mask, applied in registers by run_block.
+template <typename R>
+static void fill_run(const TileGeom& geo, const std::vector<HGate>& G, const BlockPlan& bp, FGate& f,
+                     std::vector<typename Cplx<R>::T2>& pool) {
+    std::memset(static_cast<void*>(&f), 0, sizeof f);
+    std::vector<int> wl;
+    for (int i = 0; i < geo.ns; ++i)
+        if (bp.lw >> i & 1) wl.push_back(i);
+    const int shape = run_shape_of(geo, bp.lw);
+    int dm[4], st[4], P = 1;
+    for (int j = 0; j < 4; ++j) {
+        dm[j] = run_shape_dims(shape, j);
+        st[j] = P;
+        P *= dm[j];
+    }
+    auto pos = [&](int global_wire) {
+        const int lw = geo.loc[global_wire];
+        for (size_t j = 0; j < wl.size(); ++j)
+            if (wl[j] == lw) return (int)j;
+        return -1;
+    };
+    f.single = 0;
+    f.kind = kRun;
+    f.P = (uint8_t)P;
+    f.PP = (uint8_t)P;
+    f.lmask = f.smask = (uint16_t)((1u << P) - 1u);
+    f.shape = (uint8_t)shape;
+    f.nsub = (uint8_t)bp.gates.size();
+    bool unitary = true;
+    for (size_t s = 0; s < bp.gates.size(); ++s) {
+        const HGate& h = G[bp.gates[s]];
+        unitary = unitary && h.unitary;
+        f.sub_pos[s] = (uint8_t)pos(h.wires[0]);
+        uint32_t mask = 0;
+        for (int m = 0; m < P; ++m) {
+            bool ok = true;
+            for (int c = 0; c < h.nc; ++c) {
+                const int j = pos(h.cw[c]);
+                ok = ok && (m / st[j]) % dm[j] == h.cv[c];
+            }
+            if (ok) mask |= 1u << m;
+        }
+        f.sub_mask[s] = (uint16_t)mask;
+        f.sub_u[s] = (uint16_t)pool.size();
+        const int d = h.plan.d;
+        for (int i = 0; i < d * d; ++i) {
+            typename Cplx<R>::T2 v;
+            v.x = (R)h.U[2 * i];
+            v.y = (R)h.U[2 * i + 1];
+            pool.push_back(v);
+        }
+    }
+    f.unitary = unitary ? 1 : 0;
+    for (int r = 0; r < P; ++r) {
+        uint32_t o = 0;
+        for (size_t j = 0; j < wl.size(); ++j) o += (uint32_t)((r / st[j]) % dm[j]) * (uint32_t)geo.local.b[wl[j]];
+        f.off[r] = (uint16_t)o;
+    }
+    int32_t ins_w[kMaxLocalIns];
+    int64_t ins_v[kMaxLocalIns];
+    int m = 0;
+    for (int lw : wl) {
+        ins_w[m] = lw;
+        ins_v[m] = 0;
+        ++m;
+    }
+    IndexMap imap;
+    uint64_t classes;
+    build_map(geo.local, ins_w, ins_v, m, imap, classes);
+    f.map.m = imap.m;
+    f.map.fixed = (uint32_t)imap.fixed;
+    for (int i = 0; i < imap.m; ++i) f.map.seg[i].init((uint32_t)imap.seg[i].d);
+    for (int i = 0; i <= imap.m; ++i) f.map.off[i] = (uint32_t)imap.off[i];
+    f.nclasses = (uint32_t)classes;
+}
+
 // Chunks of a list of blocks, contiguous, appended to prog.desc (256-aligned
 // start).  Returns the first chunk's offset; *nchunks the count; *dmax the
 // largest single-wire dimension (kernel instance).
@@ -1480,13 +1701,19 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
         while (i < blocks.size() && fg.size() < (size_t)kMaxChunkGates) {
             const BlockPlan& bp = blocks[i];
             const int64_t Pb = bp.single ? 0 : local_prod(geo, bp.lw);
-            const size_t need = bp.single ? (size_t)G[bp.gates[0]].plan.d * G[bp.gates[0]].plan.d
-                                          : (Pb > kMaxBlock ? 0 : (size_t)padded_dim((int)Pb) * padded_dim((int)Pb));
+            size_t need = bp.single ? (size_t)G[bp.gates[0]].plan.d * G[bp.gates[0]].plan.d
+                                    : (Pb > kMaxBlock ? 0 : (size_t)padded_dim((int)Pb) * padded_dim((int)Pb));
+            if (bp.run) {
+                need = 0;
+                for (int idx : bp.gates) need += (size_t)G[idx].plan.d * G[idx].plan.d;
+            }
             if (pool.size() + need + 1 > (size_t)kPoolEntries && !fg.empty()) break;
             FGate f;
             if (bp.single) {
                 fill_single<R>(geo, G[bp.gates[0]], f, pool);
                 dm = G[bp.gates[0]].plan.d > dm ? G[bp.gates[0]].plan.d : dm;
+            } else if (bp.run) {
+                fill_run<R>(geo, G, bp, f, pool);
             } else {
                 fill_block<R>(geo, G, bp, f, pool, &prog);
                 if (f.kind == kTcBlock && has_tc) *has_tc = true;
@@ -1701,7 +1928,7 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
         TileGeom geo;
         tile_geometry(L, p.smask, cfg.min_row, geo);
         std::vector<BlockPlan> blocks;
-        form_blocks(geo, G, p.gates, cfg.block_dim, blocks);
+        form_blocks(geo, G, p.gates, cfg.block_dim, blocks, false, cfg.runs && sizeof(R) == 4);
         uint32_t nchunks = 0;
         int dmax = 2;
         bool has_tc = false;
@@ -1795,7 +2022,8 @@ size_t put_small_chunks(const Layout& L, const std::vector<HGate>& G, const Fuse
     for (size_t i = 0; i < G.size(); ++i) all[i] = (int)i;
     std::vector<BlockPlan> blocks;
     // one-CTA circuits apply chunks without tensor cores: blocks of at most 16 dimensions
-    form_blocks(geo, G, all, cfg.block_dim < kMaxBlock ? cfg.block_dim : kMaxBlock, blocks);
+    form_blocks(geo, G, all, cfg.block_dim < kMaxBlock ? cfg.block_dim : kMaxBlock, blocks, false,
+                cfg.runs && sizeof(R) == 4);
     return emit_chunks<R>(geo, G, blocks, prog, nchunks, nullptr);
 }
 
@@ -1831,12 +2059,21 @@ static double pass_arith(const Layout& L, const std::vector<HGate>& G, const Fus
     TileGeom geo;
     tile_geometry(L, p.smask, cfg.min_row, geo);
     std::vector<BlockPlan> blocks;
-    form_blocks(geo, G, p.gates, cfg.block_dim, blocks);
+    form_blocks(geo, G, p.gates, cfg.block_dim, blocks, false, cfg.runs);
     const double tiles = (double)(L.D / p.T);
     double f = 0.0;
     std::vector<typename Cplx<double>::T2> pool;
     for (const BlockPlan& bp : blocks) {
         FGate fg;
+        if (bp.run) {  // each gate's d x d product on the groups its controls admit
+            fill_run<double>(geo, G, bp, fg, pool);
+            for (int s = 0; s < fg.nsub; ++s) {
+                int pm = 0;
+                for (uint32_t m = fg.sub_mask[s]; m; m &= m - 1) ++pm;
+                f += tiles * (double)fg.nclasses * 8.0 * run_shape_dims(fg.shape, fg.sub_pos[s]) * pm;
+            }
+            continue;
+        }
         if (bp.single) fill_single<double>(geo, G[bp.gates[0]], fg, pool);
         else fill_block<double>(geo, G, bp, fg, pool);
         if (fg.kind == kTcBlock) f += tiles * 8.0 * fg.P * fg.P * (double)fg.nclasses;  // dense block

@@ -30,6 +30,7 @@ struct FuseCfg {
     int64_t min_row;
     int block_dim;  // largest composed block inside a pass (< 4: no composition)
     int tc_mode;    // QD_TC_*: complex64 blocks of 17..64 dimensions
+    bool runs;      // complex64 tile passes: runs of single-wire gates may be applied in registers
 };
 
 int64_t tile_limit(int32_t prec);
