@@ -260,7 +260,9 @@ qd_status qd_flush(qd_state* st);
  * the tile size of pass p (0 = a per-gate kernel pass), pass_flops[p] the
  * arithmetic of pass p over the whole state (real floating-point operations:
  * 8 P per amplitude for a dense P x P block or gate, 6 per changed amplitude
- * for a diagonal or phased-permutation one, 0 for a pure permutation), and
+ * for a diagonal or phased-permutation one, 0 for a pure permutation; for a
+ * complex64 run of gates applied one by one in registers, 8 d per amplitude
+ * of the classes each d x d gate's controls admit), and
  * *n_passes the number of passes.  Every array has n_gates entries;
  * pass_tile_amps and pass_flops may be NULL. */
 qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd_gate_desc* gates,
