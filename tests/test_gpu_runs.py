@@ -1,6 +1,7 @@
 """Runs of single-wire gates applied in registers inside complex64 tile passes
-(kRun): every supported block shape, gates with controls inside the block,
-diagonal and permutation gates among them; results against the FP64 oracle."""
+(kRun, qubit blocks of three and four wires) and composed blocks of the other
+shapes: gates with controls inside the block, diagonal and permutation gates
+among them; results against the FP64 oracle."""
 import numpy as np
 import pytest
 
