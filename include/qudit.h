@@ -279,11 +279,13 @@ qd_status qd_plan_circuit(const int32_t* dims, int32_t n, int32_t prec, const qd
  * may be far larger than 2^64 (the paper's keys are 64-bit): the wires'
  * bit widths ceil(log2 d) must sum to at most 128 and D must stay below
  * 2^128.  A whole circuit runs in one launch on one CTA with the
- * amplitudes in shared memory: at most QD_SPARSE_MAX_NNZ non-zero
- * amplitudes after every gate.
+ * amplitudes in shared memory while the support stays within
+ * QD_SPARSE_MAX_NNZ non-zero amplitudes after every gate; after
+ * qd_sparse_reserve, larger supports run gate by gate on the whole GPU.
  * --------------------------------------------------------------------- */
 #define QD_SPARSE_MAX_NNZ 512
 #define QD_SPARSE_MAX_WIRES 128
+#define QD_SPARSE_MAX_RESERVE (1 << 22)
 
 typedef struct qd_sparse qd_sparse;
 
@@ -293,10 +295,21 @@ typedef struct qd_sparse qd_sparse;
 qd_status qd_sparse_create(const int32_t* dims, int32_t n, void* stream, qd_sparse** out);
 qd_status qd_sparse_destroy(qd_sparse* s);
 
+/* Allow supports of up to max_nnz non-zero amplitudes (QD_SPARSE_MAX_NNZ <
+ * max_nnz <= QD_SPARSE_MAX_RESERVE; never shrinks).  Calls whose support
+ * stays within QD_SPARSE_MAX_NNZ keep running in one launch on one CTA;
+ * a call that goes beyond it runs gate by gate on the whole GPU: entries in
+ * global memory, dense gates through a global hash table of classes (about
+ * 300 bytes of device memory per entry of capacity).  QD_ERR_ARG for
+ * max_nnz out of range, QD_ERR_OOM if the buffers cannot be allocated (the
+ * state and its capacity unchanged). */
+qd_status qd_sparse_reserve(qd_sparse* s, int64_t max_nnz);
+
 /* Apply n_gates single-wire gates (qd_gate_desc with n_wires = 1, controls
  * allowed; matrices as in qd_apply_circuit) in order.  Synchronous.  Exact
  * zeros are dropped.  QD_ERR_UNSUPPORTED (state left as before the call)
- * if a gate has more than one wire or the support exceeds QD_SPARSE_MAX_NNZ. */
+ * if a gate has more than one wire or the support exceeds QD_SPARSE_MAX_NNZ
+ * (or the capacity set by qd_sparse_reserve). */
 qd_status qd_sparse_run(qd_sparse* s, const qd_gate_desc* gates, int32_t n_gates, const double* matrices);
 
 /* Number of stored (non-zero) amplitudes. */

@@ -104,6 +104,7 @@ _SIGS = {
     "qd_sparse_destroy": (ctypes.c_int32, [_vp]),
     "qd_sparse_run": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_gate_desc), ctypes.c_int32, _f64p]),
     "qd_sparse_nnz": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_int64)]),
+    "qd_sparse_reserve": (ctypes.c_int32, [_vp, ctypes.c_int64]),
     "qd_sparse_get": (ctypes.c_int32, [_vp, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64), _f64p,
                                        ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]),
     "qd_apply_controlled_scan": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p, _i32p, _i32p, ctypes.c_int32]),
@@ -400,6 +401,7 @@ def qd_apply_circuit(st: int, circuit, mode=QD_FUSE_OFF, max_tile_amps=0, min_ga
 
 
 QD_SPARSE_MAX_NNZ = 512
+QD_SPARSE_MAX_RESERVE = 1 << 22
 
 
 def qd_sparse_create(dims, stream=None) -> int:
@@ -416,6 +418,10 @@ def qd_sparse_destroy(s: int) -> None:
 def qd_sparse_run(s: int, circuit) -> None:
     descs, m = circuit_arrays(circuit)
     _check(_lib.qd_sparse_run(_vp(s), descs, len(circuit.gates), _p(m, _f64p)), "qd_sparse_run")
+
+
+def qd_sparse_reserve(s: int, max_nnz: int) -> None:
+    _check(_lib.qd_sparse_reserve(_vp(s), int(max_nnz)), "qd_sparse_reserve")
 
 
 def qd_sparse_nnz(s: int) -> int:

@@ -27,6 +27,13 @@
 // Exact zeros are dropped.  More than QD_SPARSE_MAX_NNZ entries after a gate stops
 // the circuit with QD_ERR_UNSUPPORTED (the state is left as it was before
 // the call).
+//
+// Larger supports (after qd_sparse_reserve) run gate by gate on the whole
+// GPU with the same steps: the entries in global memory, diagonal and
+// monomial gates in place, dense gates through a global hash table of
+// classes (clear, insert with the same first-entry CAS, emit one class per
+// thread, then fix the count).  The state is snapshotted first, so an
+// overflow of the reserved capacity also leaves it as before the call.
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
@@ -195,6 +202,98 @@ __global__ void __launch_bounds__(kSparseThreads, 1)
     }
 }
 
+// ---- grid tier: one gate at a time over the whole GPU ----
+// cnt[0] = entries, cnt[1] = entries emitted by the current gate, cnt[2] =
+// overflow flag (sticky until the call ends).
+constexpr int kGridThreads = 256;
+
+__global__ void __launch_bounds__(kGridThreads) kg_inplace(const SparseGate* gp, u128* keys, double2* amps,
+                                                           const int32_t* cnt) {
+    const SparseGate& g = *gp;
+    const int n = cnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const u128 k = keys[i];
+        if (!controls_met(g, k)) continue;
+        const int x = digit_of(k, g.pos, g.bits);
+        const int r = g.kind == kDiag ? x : g.rowof[x];
+        keys[i] = with_digit(k, g.pos, g.bits, r);
+        amps[i] = zmul(g.U[r * g.d + x], amps[i]);
+    }
+}
+
+__global__ void __launch_bounds__(kGridThreads) kg_clear(int32_t* slot, uint32_t* mask, int64_t H, int32_t* cnt) {
+    for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x) {
+        slot[h] = 0;
+        mask[h] = 0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt[1] = 0;
+}
+
+__global__ void __launch_bounds__(kGridThreads)
+    kg_insert(const SparseGate* gp, const u128* keys, const double2* amps, int32_t* cnt, u128* okeys,
+              double2* oamps, int32_t* slot, uint32_t* mask, double2* member, int64_t H, int64_t cap) {
+    const SparseGate& g = *gp;
+    const int n = cnt[0];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const u128 k = keys[i];
+        if (!controls_met(g, k)) {
+            const int o = atomicAdd(&cnt[1], 1);
+            if (o < cap) {
+                okeys[o] = k;
+                oamps[o] = amps[i];
+            }
+            continue;
+        }
+        const int x = digit_of(k, g.pos, g.bits);
+        const u128 ck = with_digit(k, g.pos, g.bits, 0);
+        uint64_t h = slot_hash(ck) & (uint64_t)(H - 1);
+        for (int64_t probe = 0; probe < H; ++probe) {  // at most H probes: H > n classes
+            const int old = atomicCAS(&slot[h], 0, i + 1);
+            if (old == 0) break;
+            if (with_digit(keys[old - 1], g.pos, g.bits, 0) == ck) break;
+            h = (h + 1) & (uint64_t)(H - 1);
+        }
+        member[h * kSparseMaxD + x] = amps[i];
+        atomicOr(&mask[h], 1u << x);
+    }
+}
+
+__global__ void __launch_bounds__(kGridThreads)
+    kg_emit(const SparseGate* gp, const u128* keys, int32_t* cnt, u128* okeys, double2* oamps, const int32_t* slot,
+            const uint32_t* mask, const double2* member, int64_t H, int64_t cap) {
+    const SparseGate& g = *gp;
+    for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < H; s += (int64_t)gridDim.x * blockDim.x) {
+        const int first = slot[s];
+        if (first == 0) continue;
+        const u128 ck = with_digit(keys[first - 1], g.pos, g.bits, 0);
+        const uint32_t m = mask[s];
+        for (int r = 0; r < g.d; ++r) {
+            double2 y = make_double2(0.0, 0.0);
+            for (int x = 0; x < g.d; ++x)
+                if (m >> x & 1u) {
+                    const double2 t = zmul(g.U[r * g.d + x], member[s * kSparseMaxD + x]);
+                    y.x += t.x;
+                    y.y += t.y;
+                }
+            if (y.x == 0.0 && y.y == 0.0) continue;
+            const int o = atomicAdd(&cnt[1], 1);
+            if (o < cap) {
+                okeys[o] = with_digit(ck, g.pos, g.bits, r);
+                oamps[o] = y;
+            }
+        }
+    }
+}
+
+__global__ void kg_finish(int32_t* cnt, int64_t cap) {
+    if (cnt[1] > cap) {
+        cnt[2] = 1;
+        cnt[0] = (int32_t)cap;
+    } else {
+        cnt[0] = cnt[1];
+    }
+}
+
 }  // namespace
 }  // namespace qd
 
@@ -212,11 +311,42 @@ struct qd_sparse {
     qd::SparseGate* gates;  // device, grown on demand
     size_t gates_cap;
     int32_t nnz_host;
+    // grid tier (qd_sparse_reserve): capacity, entries (two buffers and a
+    // snapshot), hash table of H slots, counters; grid = the state lives in
+    // gk[cur] / ga[cur] instead of keys / amps
+    int64_t cap, H;
+    u128* gk[3];
+    double2* ga[3];
+    int32_t* gslot;
+    uint32_t* gmask;
+    double2* gmember;
+    int32_t* gcnt;
+    int cur;
+    bool grid;
 };
 
 namespace {
 
 qd_status sparse_fail_cuda(cudaError_t e, const char* what) { return qd::cuda_fail(e, what); }
+
+void grid_free(qd_sparse* s) {
+    for (int b = 0; b < 3; ++b) {
+        if (s->gk[b]) cudaFree(s->gk[b]);
+        if (s->ga[b]) cudaFree(s->ga[b]);
+        s->gk[b] = nullptr;
+        s->ga[b] = nullptr;
+    }
+    if (s->gslot) cudaFree(s->gslot);
+    if (s->gmask) cudaFree(s->gmask);
+    if (s->gmember) cudaFree(s->gmember);
+    if (s->gcnt) cudaFree(s->gcnt);
+    s->gslot = nullptr;
+    s->gmask = nullptr;
+    s->gmember = nullptr;
+    s->gcnt = nullptr;
+    s->cap = 0;
+    s->H = 0;
+}
 
 void sparse_free(qd_sparse* s) {
     if (!s) return;
@@ -224,7 +354,99 @@ void sparse_free(qd_sparse* s) {
     if (s->amps) cudaFree(s->amps);
     if (s->dev_i) cudaFree(s->dev_i);
     if (s->gates) cudaFree(s->gates);
+    grid_free(s);
     delete s;
+}
+
+unsigned grid_blocks(int64_t work) {
+    const int64_t b = (work + qd::kGridThreads - 1) / qd::kGridThreads;
+    return (unsigned)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
+}
+
+// The entries move between the one-CTA buffers (keys / amps) and the grid
+// tier's current buffer; n entries, on the state's stream.
+cudaError_t to_grid(qd_sparse* s) {
+    const int32_t n = s->nnz_host;
+    cudaError_t e = cudaSuccess;
+    if (n > 0) e = cudaMemcpyAsync(s->gk[0], s->keys, sizeof(u128) * n, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(s->ga[0], s->amps, sizeof(double2) * n, cudaMemcpyDeviceToDevice, s->stream);
+    const int32_t c[3] = {n, 0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->gcnt, c, sizeof c, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) {
+        s->cur = 0;
+        s->grid = true;
+    }
+    return e;
+}
+
+cudaError_t from_grid(qd_sparse* s) {  // only when the support fits the one-CTA buffers
+    const int32_t n = s->nnz_host;
+    cudaError_t e = cudaSuccess;
+    if (n > 0)
+        e = cudaMemcpyAsync(s->keys, s->gk[s->cur], sizeof(u128) * n, cudaMemcpyDeviceToDevice, s->stream);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(s->amps, s->ga[s->cur], sizeof(double2) * n, cudaMemcpyDeviceToDevice, s->stream);
+    const int32_t c[2] = {n, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s->dev_i, c, sizeof c, cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) s->grid = false;
+    return e;
+}
+
+// All gates of a call on the grid tier (gates already on the device).
+qd_status grid_run(qd_sparse* s, int n_gates, const std::vector<qd::SparseGate>& hg) {
+    const int32_t n0 = s->nnz_host;
+    const unsigned be = grid_blocks(s->cap), bh = grid_blocks(s->H);
+    // snapshot (buffer 2) so that an overflow leaves the state as before the call
+    if (n0 > 0) {
+        QD_CUDA(cudaMemcpyAsync(s->gk[2], s->gk[s->cur], sizeof(u128) * n0, cudaMemcpyDeviceToDevice, s->stream),
+                "sparse snapshot");
+        QD_CUDA(cudaMemcpyAsync(s->ga[2], s->ga[s->cur], sizeof(double2) * n0, cudaMemcpyDeviceToDevice, s->stream),
+                "sparse snapshot");
+    }
+    const int32_t c0[3] = {n0, 0, 0};
+    QD_CUDA(cudaMemcpyAsync(s->gcnt, c0, sizeof c0, cudaMemcpyHostToDevice, s->stream), "sparse counters");
+    int cur = s->cur;
+    for (int gi = 0; gi < n_gates; ++gi) {
+        const qd::SparseGate* g = s->gates + gi;
+        if (hg[(size_t)gi].kind != qd::kDense) {
+            qd::kg_inplace<<<be, qd::kGridThreads, 0, s->stream>>>(g, s->gk[cur], s->ga[cur], s->gcnt);
+            qd::count_launch();
+            continue;
+        }
+        const int nxt = cur ^ 1;
+        qd::kg_clear<<<bh, qd::kGridThreads, 0, s->stream>>>(s->gslot, s->gmask, s->H, s->gcnt);
+        qd::kg_insert<<<be, qd::kGridThreads, 0, s->stream>>>(g, s->gk[cur], s->ga[cur], s->gcnt, s->gk[nxt],
+                                                                s->ga[nxt], s->gslot, s->gmask, s->gmember, s->H,
+                                                                s->cap);
+        qd::kg_emit<<<bh, qd::kGridThreads, 0, s->stream>>>(g, s->gk[cur], s->gcnt, s->gk[nxt], s->ga[nxt], s->gslot,
+                                                              s->gmask, s->gmember, s->H, s->cap);
+        qd::kg_finish<<<1, 1, 0, s->stream>>>(s->gcnt, s->cap);
+        for (int k = 0; k < 4; ++k) qd::count_launch();
+        cur = nxt;
+    }
+    QD_CUDA(cudaGetLastError(), "sparse grid launch");
+    int32_t h[3];
+    QD_CUDA(cudaMemcpyAsync(h, s->gcnt, sizeof h, cudaMemcpyDeviceToHost, s->stream), "sparse counters");
+    QD_CUDA(cudaStreamSynchronize(s->stream), "sparse grid sync");
+    if (h[2] != 0) {  // restore the snapshot
+        if (n0 > 0) {
+            QD_CUDA(cudaMemcpyAsync(s->gk[s->cur], s->gk[2], sizeof(u128) * n0, cudaMemcpyDeviceToDevice, s->stream),
+                    "sparse restore");
+            QD_CUDA(cudaMemcpyAsync(s->ga[s->cur], s->ga[2], sizeof(double2) * n0, cudaMemcpyDeviceToDevice, s->stream),
+                    "sparse restore");
+        }
+        const int32_t c[3] = {n0, 0, 0};
+        QD_CUDA(cudaMemcpyAsync(s->gcnt, c, sizeof c, cudaMemcpyHostToDevice, s->stream), "sparse restore");
+        QD_CUDA(cudaStreamSynchronize(s->stream), "sparse restore");
+        return qd::fail(QD_ERR_UNSUPPORTED, "sparse circuit: more than %lld non-zero amplitudes after a gate "
+                                            "(state unchanged)", (long long)s->cap);
+    }
+    s->cur = cur;
+    s->nnz_host = h[0];
+    return QD_OK;
 }
 
 }  // namespace
@@ -358,6 +580,11 @@ qd_status qd_sparse_run(qd_sparse* s, const qd_gate_desc* gates, int32_t n_gates
             s->gates_cap = hg.size();
         }
         QD_CUDA(cudaMemcpyAsync(s->gates, hg.data(), bytes, cudaMemcpyHostToDevice, s->stream), "sparse gates upload");
+        if (s->grid) {  // the support is beyond the one-CTA buffers
+            const qd_status rc = grid_run(s, n_gates, hg);
+            if (rc == QD_OK && s->nnz_host <= QD_SPARSE_MAX_NNZ) QD_CUDA(from_grid(s), "sparse tier change");
+            return rc;
+        }
         static int attr_dev = -1;
         int dev = 0;
         cudaGetDevice(&dev);
@@ -374,13 +601,73 @@ qd_status qd_sparse_run(qd_sparse* s, const qd_gate_desc* gates, int32_t n_gates
         int32_t h[2];
         QD_CUDA(cudaMemcpyAsync(h, s->dev_i, sizeof h, cudaMemcpyDeviceToHost, s->stream), "sparse status");
         QD_CUDA(cudaStreamSynchronize(s->stream), "sparse sync");
-        if (h[1] != 0)
-            return qd::fail(QD_ERR_UNSUPPORTED, "sparse circuit: more than %d non-zero amplitudes after a gate "
-                                                "(state unchanged)", QD_SPARSE_MAX_NNZ);
+        if (h[1] != 0) {
+            if (s->cap <= QD_SPARSE_MAX_NNZ)
+                return qd::fail(QD_ERR_UNSUPPORTED, "sparse circuit: more than %d non-zero amplitudes after a gate "
+                                                    "(state unchanged; qd_sparse_reserve allows more)",
+                                QD_SPARSE_MAX_NNZ);
+            // the one-CTA launch left the state as it was: run the call on the grid tier
+            QD_CUDA(to_grid(s), "sparse tier change");
+            const qd_status rc = grid_run(s, n_gates, hg);
+            if (rc == QD_OK && s->nnz_host <= QD_SPARSE_MAX_NNZ) QD_CUDA(from_grid(s), "sparse tier change");
+            if (rc != QD_OK && s->nnz_host <= QD_SPARSE_MAX_NNZ) (void)from_grid(s);
+            return rc;
+        }
         s->nnz_host = h[0];
         return QD_OK;
     } catch (...) {
         return qd::fail(QD_ERR_OOM, "host exception in qd_sparse_run");
+    }
+}
+
+qd_status qd_sparse_reserve(qd_sparse* s, int64_t max_nnz) {
+    try {
+        if (!s) return qd::fail(QD_ERR_ARG, "sparse state is NULL");
+        if (max_nnz <= QD_SPARSE_MAX_NNZ || max_nnz > QD_SPARSE_MAX_RESERVE)
+            return qd::fail(QD_ERR_ARG, "capacity %lld outside (%d, %d]", (long long)max_nnz, QD_SPARSE_MAX_NNZ,
+                            QD_SPARSE_MAX_RESERVE);
+        if (max_nnz <= s->cap) return QD_OK;
+        qd_sparse t{};  // the new buffers
+        t.cap = max_nnz;
+        t.H = 1024;
+        while (t.H < 2 * max_nnz) t.H <<= 1;
+        cudaError_t e = cudaSuccess;
+        for (int b = 0; b < 3 && e == cudaSuccess; ++b) {
+            e = cudaMalloc(&t.gk[b], sizeof(u128) * (size_t)t.cap);
+            if (e == cudaSuccess) e = cudaMalloc(&t.ga[b], sizeof(double2) * (size_t)t.cap);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&t.gslot, sizeof(int32_t) * (size_t)t.H);
+        if (e == cudaSuccess) e = cudaMalloc(&t.gmask, sizeof(uint32_t) * (size_t)t.H);
+        if (e == cudaSuccess) e = cudaMalloc(&t.gmember, sizeof(double2) * qd::kSparseMaxD * (size_t)t.H);
+        if (e == cudaSuccess) e = cudaMalloc(&t.gcnt, 4 * sizeof(int32_t));
+        if (e == cudaSuccess && s->grid && s->nnz_host > 0) {  // move the current entries over
+            e = cudaMemcpyAsync(t.gk[0], s->gk[s->cur], sizeof(u128) * s->nnz_host, cudaMemcpyDeviceToDevice, s->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(t.ga[0], s->ga[s->cur], sizeof(double2) * s->nnz_host, cudaMemcpyDeviceToDevice,
+                                    s->stream);
+        }
+        const int32_t c[4] = {s->nnz_host, 0, 0, 0};
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t.gcnt, c, sizeof c, cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) {
+            grid_free(&t);
+            return qd::fail(QD_ERR_OOM, "sparse capacity %lld: %s", (long long)max_nnz, cudaGetErrorString(e));
+        }
+        grid_free(s);
+        for (int b = 0; b < 3; ++b) {
+            s->gk[b] = t.gk[b];
+            s->ga[b] = t.ga[b];
+        }
+        s->gslot = t.gslot;
+        s->gmask = t.gmask;
+        s->gmember = t.gmember;
+        s->gcnt = t.gcnt;
+        s->cap = t.cap;
+        s->H = t.H;
+        s->cur = 0;
+        return QD_OK;
+    } catch (...) {
+        return qd::fail(QD_ERR_OOM, "host exception in qd_sparse_reserve");
     }
 }
 
@@ -399,9 +686,11 @@ qd_status qd_sparse_get(qd_sparse* s, uint64_t* index_lo, uint64_t* index_hi, do
         if (max < n) return qd::fail(QD_ERR_ARG, "room for %lld entries, %d stored", (long long)max, n);
         std::vector<u128> k((size_t)n);
         std::vector<double2> a((size_t)n);
+        const u128* dk = s->grid ? s->gk[s->cur] : s->keys;
+        const double2* da = s->grid ? s->ga[s->cur] : s->amps;
         if (n > 0) {
-            QD_CUDA(cudaMemcpyAsync(k.data(), s->keys, sizeof(u128) * n, cudaMemcpyDeviceToHost, s->stream), "sparse keys");
-            QD_CUDA(cudaMemcpyAsync(a.data(), s->amps, sizeof(double2) * n, cudaMemcpyDeviceToHost, s->stream), "sparse amps");
+            QD_CUDA(cudaMemcpyAsync(k.data(), dk, sizeof(u128) * n, cudaMemcpyDeviceToHost, s->stream), "sparse keys");
+            QD_CUDA(cudaMemcpyAsync(a.data(), da, sizeof(double2) * n, cudaMemcpyDeviceToHost, s->stream), "sparse amps");
         }
         QD_CUDA(cudaStreamSynchronize(s->stream), "sparse readout");
         std::vector<std::pair<u128, double2>> e((size_t)n);

@@ -122,3 +122,57 @@ def test_rejects_multi_wire_and_wide_dims(qb, gen):
         qb.qd_sparse_run(s, gen.Circuit((2, 2), [gen.Gate((0, 1), np.eye(4, dtype=complex))]))
     assert ei.value.status == qb.QD_ERR_UNSUPPORTED
     qb.qd_sparse_destroy(s)
+
+
+def test_grid_tier_matches_oracles(qb, gen):
+    """Supports beyond the one-CTA buffers (qd_sparse_reserve): about 83K
+    non-zero amplitudes on 16 wires, dense, controlled and permutation gates,
+    against the sparse oracle and the dense oracle."""
+    rng = np.random.Generator(np.random.PCG64(971))
+    dims = (2, 3, 2, 2, 3, 2, 2, 2, 3, 2, 2, 2, 2, 3, 2, 2)
+    gates = [gen.Gate((w,), gen.fourier(dims[w])) for w in range(0, 12)]
+    gates += random_single_wire_circuit(dims, 40, rng).gates
+    circ = gen.Circuit(dims, gates)
+    s = qb.qd_sparse_create(dims)
+    qb.qd_sparse_reserve(s, 1 << 18)
+    qb.qd_sparse_run(s, circ)
+    got = qb.qd_sparse_get(s)
+    qb.qd_sparse_destroy(s)
+    assert len(got) > qb.QD_SPARSE_MAX_NNZ
+    ref = sparse.run_circuit(circ)
+    assert set(got) == set(ref)
+    assert max(abs(got[k] - ref[k]) for k in ref) < 1e-12
+    dense = oracle.run_circuit(circ)
+    assert np.max(np.abs(sparse.to_dense(dims, got) - dense)) < 1e-12
+
+
+def test_grid_tier_round_trip_and_capacity(qb, gen):
+    """The support grows past the one-CTA buffers and shrinks back (the state
+    returns to the one-CTA path); an overflow of the reserved capacity leaves
+    the state as before the call; a larger reservation keeps the state."""
+    dims = (2,) * 14
+    h = 1 / math.sqrt(2.0)
+    H = np.array([[h, h], [h, -h]], dtype=np.complex128)  # exactly real: undoing it cancels exactly
+    s = qb.qd_sparse_create(dims)
+    qb.qd_sparse_reserve(s, 2048)
+    qb.qd_sparse_run(s, gen.Circuit(dims, [gen.Gate((w,), H) for w in range(10)]))  # 1024 entries
+    assert qb.qd_sparse_nnz(s) == 1024
+    before = qb.qd_sparse_get(s)
+    with pytest.raises(qb.QuditError) as ei:
+        qb.qd_sparse_run(s, gen.Circuit(dims, [gen.Gate((w,), H) for w in range(10, 12)]))  # 4096 > 2048
+    assert ei.value.status == qb.QD_ERR_UNSUPPORTED
+    assert qb.qd_sparse_get(s) == before
+    qb.qd_sparse_reserve(s, 8192)
+    assert qb.qd_sparse_get(s) == before
+    qb.qd_sparse_run(s, gen.Circuit(dims, [gen.Gate((w,), H) for w in range(10, 12)]))
+    assert qb.qd_sparse_nnz(s) == 4096
+    # undo all Hadamards: back to |0...0>, then a GHZ on the one-CTA path
+    qb.qd_sparse_run(s, gen.Circuit(dims, [gen.Gate((w,), H) for w in range(12)]))
+    got = qb.qd_sparse_get(s)
+    assert set(got) == {0} and abs(got[0] - 1.0) < 1e-12
+    qb.qd_sparse_run(s, gen.ghz_circuit(dims))
+    got = qb.qd_sparse_get(s)
+    assert set(got) == {0, 2 ** 14 - 1}
+    with pytest.raises(qb.QuditError):
+        qb.qd_sparse_reserve(s, 100)
+    qb.qd_sparse_destroy(s)
