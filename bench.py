@@ -413,6 +413,40 @@ def measure_sparse_ghz(qb, gen, reps=20):
                         "wire), complex128", "rows": rows}
 
 
+def measure_sparse_grid(qb, gen, reps=5):
+    """A sparse state beyond the one-CTA buffers (qd_sparse_reserve, grid tier):
+    Fourier gates on 12 of 16 wires, then 40 seeded single-wire gates (Haar,
+    shifts and phases, 40% controlled).  Wall time of the synchronous
+    qd_sparse_run, median of ``reps``."""
+    rng = np.random.Generator(np.random.PCG64(971))
+    dims = (2, 3, 2, 2, 3, 2, 2, 2, 3, 2, 2, 2, 2, 3, 2, 2)
+    gates = [gen.Gate((w,), gen.fourier(dims[w])) for w in range(0, 12)]
+    for _ in range(40):
+        t = int(rng.integers(0, len(dims)))
+        d = dims[t]
+        k = rng.random()
+        U = gen.haar(d, rng) if k < 0.2 else (gen.x_plus(d, 1) if k < 0.6 else gen.z_gen(d))
+        c = int(rng.integers(0, len(dims)))
+        if rng.random() < 0.4 and c != t:
+            gates.append(gen.Gate((t,), U, (c,), (int(rng.integers(0, dims[c])),)))
+        else:
+            gates.append(gen.Gate((t,), U))
+    circ = gen.Circuit(dims, gates)
+    ts, nnz = [], 0
+    for _ in range(reps + 1):
+        s = qb.qd_sparse_create(dims)
+        qb.qd_sparse_reserve(s, 1 << 18)
+        n0 = qb.qd_launch_count()
+        t0 = time.perf_counter()
+        qb.qd_sparse_run(s, circ)
+        ts.append(time.perf_counter() - t0)
+        launches = qb.qd_launch_count() - n0
+        nnz = qb.qd_sparse_nnz(s)
+        qb.qd_sparse_destroy(s)
+    return {"workload": "16 wires (12 qubits, 4 qutrits), 52 single-wire gates, complex128 sparse state",
+            "gates": len(circ.gates), "nnz": nnz, "ms": 1e3 * float(np.median(ts[1:])), "launches": launches}
+
+
 def measure_tile_costs(qb, gen, torch, stream, reps=5):
     """Marginal cost of one gate or composed block inside a shared-memory tile pass
     on the 12-qubit + 8-qutrit layout (complex64): the pass with N + 6 copies minus
@@ -840,6 +874,10 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         extra["many_controls"] = measure_many_controls(qb, gen, torch, stream)
         extra["sparse_ghz"] = measure_sparse_ghz(qb, gen)
+        try:
+            extra["sparse_grid"] = measure_sparse_grid(qb, gen)
+        except Exception as e:  # reported, never fatal to the bench line
+            extra["sparse_grid"] = {"error": str(e)[:200]}
         torch.cuda.empty_cache()
         extra["lazy_frame"] = measure_lazy(qb, gen, torch, stream)
         extra["tile_costs"] = measure_tile_costs(qb, gen, torch, stream)
