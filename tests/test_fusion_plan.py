@@ -92,3 +92,23 @@ def test_non_fusable_gates_run_alone():
     for g in (1, 2):
         p = pass_of[pos[g]]
         assert tiles[p] == 0
+
+
+def test_sparse_qubit_blocks_become_register_runs():
+    """Four qubits with one dense gate each and controlled shifts: the cost model
+    picks a run of gates applied in registers over the composed 16 x 16 block for
+    complex64 (each gate's own arithmetic: 96 flop per amplitude), while complex128,
+    which has no runs, composes it (128 flop per amplitude); the executed order is
+    still a valid reordering."""
+    rng = np.random.Generator(np.random.PCG64(950))
+    dims = (2, 2, 2, 2, 3, 2, 3)
+    gates = [gen.Gate((w,), gen.haar(2, rng)) for w in range(4)]
+    gates += [gen.Gate(((w + 1) % 4,), gen.x_plus(2, 1), (w,), (1,)) for w in range(4)]
+    circ = gen.Circuit(dims, gates)
+    f64 = qb.qd_plan_circuit(dims, qb.QD_C64, circ, mode=qb.QD_FUSE_TILE, max_tile_amps=1024, with_flops=True)[3]
+    f128 = qb.qd_plan_circuit(dims, qb.QD_C128, circ, mode=qb.QD_FUSE_TILE, max_tile_amps=1024, with_flops=True)[3]
+    assert sum(f64) / circ.D == pytest.approx(96.0)
+    assert sum(f128) / circ.D == pytest.approx(128.0)
+    order, _, _ = _check_plan(circ, qb.QD_C64, mode=qb.QD_FUSE_TILE, max_tile_amps=1024)
+    psi0 = gen.random_state(circ.D, rng)
+    assert np.max(np.abs(oracle.run_circuit(circ, psi0) - oracle.run_circuit(_reordered(circ, order), psi0))) < 1e-12
