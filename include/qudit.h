@@ -299,8 +299,9 @@ qd_status qd_sparse_destroy(qd_sparse* s);
  * max_nnz <= QD_SPARSE_MAX_RESERVE; never shrinks).  Calls whose support
  * stays within QD_SPARSE_MAX_NNZ keep running in one launch on one CTA;
  * a call that goes beyond it runs gate by gate on the whole GPU: entries in
- * global memory, dense gates through a global hash table of classes (about
- * 300 bytes of device memory per entry of capacity).  QD_ERR_ARG for
+ * global memory, dense gates through a global hash table of classes (370
+ * to 640 bytes of device memory per entry of capacity: three entry buffers
+ * and a table of 2 to 4 slots per entry).  QD_ERR_ARG for
  * max_nnz out of range, QD_ERR_OOM if the buffers cannot be allocated (the
  * state and its capacity unchanged). */
 qd_status qd_sparse_reserve(qd_sparse* s, int64_t max_nnz);
