@@ -49,14 +49,14 @@ typedef int32_t qd_status;
 #define QD_ERR_OOM 2         /* device or host allocation failed */
 #define QD_ERR_CUDA 3        /* a CUDA runtime call or kernel launch failed */
 #define QD_ERR_TIMEOUT 4     /* a bounded device-side wait gave up */
-#define QD_ERR_UNSUPPORTED 5 /* valid request outside this build's limits */
+#define QD_ERR_UNSUPPORTED 5 /* valid request outside the library's limits */
 #define QD_ERR_DEVICE 6      /* a kernel reported an error through its status word */
 
 /* Precision of the stored amplitudes. */
 #define QD_C64 0  /* complex64: binary32 re/im, binary32 arithmetic */
 #define QD_C128 1 /* complex128: binary64 re/im, binary64 arithmetic */
 
-/* Limits of this build. */
+/* Limits of the library. */
 #define QD_MAX_WIRES 48      /* wires per state */
 #define QD_MAX_DIM 64        /* dimension of one wire */
 #define QD_MAX_GATE_DIM 64   /* P = product of a gate's wire dimensions */
