@@ -1,18 +1,22 @@
 """Benchmark: block simulation of a mixed-radix state vector on GB300.
 
-Workload: 12 qubits + 8 qutrits in a seeded wire order (26,873,856
-amplitudes), 500 gates of a Clifford+T-like hybrid mix (qubit H/S/T/CNOT,
-qutrit F_3/Z_3/X_3/controlled-X_3).  One step = reset to |0...0>, apply the
-500 gates, read the norm.  Metric: amplitude-gate updates per second
-(sum over gates of D / prod d_controls).
+Workload: 18 qubits + 8 qutrits in a seeded wire order (1,719,926,784
+amplitudes, 13.76 GB in complex64), 200 gates: 70% Haar-random single-qudit
+unitaries, 30% controlled gates (Haar or X_{+1} target, random control wire
+and value).  One step = reset to |0...0>, apply the 200 gates (fusion
+settings from the autotuner), read the norm.  Metric: amplitude-gate updates
+per second (sum over gates of D / prod d_controls).  The 12-qubit + 8-qutrit
+Clifford+T-like circuit (500 gates) in complex64 and complex128 and the
+other rows of the path (batches, serving, sparse states, ...) are reported
+as extra keys of the same line.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec c64|c128] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
 Under torchrun (N > 1) every rank runs an independent replica of the
-workload on its own GPU (the per-gate path has no exchange step when each
-GPU holds a whole state); time is the max over ranks and the value sums the
-ranks' updates ("weak" scaling).  ``--impl reference`` times the FP64 CPU
-oracle on the host cores on a bounded sample of the same workload.
+workload on its own GPU (a whole state per GPU has no exchange step); time
+is the max over ranks and the value sums the ranks' updates ("weak"
+scaling).  ``--impl reference`` times the FP64 CPU oracle on the host cores
+on a bounded sample of the same workload (its 20-wire prefix).
 """
 from __future__ import annotations
 
@@ -33,10 +37,13 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WORKLOAD = "12 qubits + 8 qutrits (26,873,856 amplitudes), depth 500 hybrid Clifford+T-like mix, seed 1"
+WORKLOAD = ("18 qubits + 8 qutrits (1,719,926,784 amplitudes), depth 200: 70% Haar single-qudit, "
+            "30% controlled (Haar or X_{+1}), seed 2")
+BENCH_CIRCUIT = "12 qubits + 8 qutrits (26,873,856 amplitudes), depth 500 hybrid Clifford+T-like mix, seed 1"
 METRIC = "amp-gate updates/s"
 UNIT = "updates/s"
 L2_BYTES = 129e6
+PREFIX_WIRES = 20
 # FP32 / FP64 vector peaks of GB300 from unit counts and the maximum SM clock:
 # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz; FP64 from NVIDIA's 1.25 TFLOP/s figure.
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -73,6 +80,28 @@ def circuit_updates(circ) -> int:
 def algorithmic_bytes(plan: dict, amp_bytes: int) -> int:
     """Bytes a gate must read and write: every touched row of every visited class, once each way."""
     return 2 * amp_bytes * int(plan["classes"]) * int(plan["touched_rows"])
+
+
+def method_flops(plan: dict, U) -> float:
+    """Floating-point work of one gate as the method states it (a complex
+    multiply-add is 8 flops, a complex product 6): a dense P x P gate costs
+    8 P flops per amplitude of every visited class; a diagonal (phase) gate 6
+    per amplitude it changes; a permutation nothing when every non-zero is 1
+    (data movement only), else 6 per amplitude it changes.  ``plan`` is
+    ``qd_plan_gate``'s record (kind 0 dense, 1 diagonal, 2 permutation)."""
+    U = np.asarray(U)
+    P = U.shape[0]
+    classes, rows = float(plan["classes"]), float(plan["touched_rows"])
+    if plan["kind"] == 0:
+        return 8.0 * P * classes * P
+    if plan["kind"] == 2 and np.all(U[np.abs(U) != 0] == 1):
+        return 0.0
+    return 6.0 * classes * rows
+
+
+def circuit_method_flops(qb, circ, prec) -> float:
+    return sum(method_flops(qb.qd_plan_gate(circ.dims, prec, g.wires, g.U, g.controls or None,
+                                            g.values or None), g.U) for g in circ.gates)
 
 
 def aggregate(units_per_rank, seconds_per_rank):
@@ -249,20 +278,20 @@ def run_reference(args):
     from paper_2410_17876_gb300 import inputs as gen
 
     oracle.build()
-    circ = gen.config1_circuit()
+    pre = gen.prefix_circuit(gen.config2_circuit(), PREFIX_WIRES)
     nthreads = oracle.max_threads()
     per_step_budget = max(1.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample(circ, per_step_budget / 4, nthreads)
+        oracle_sample(pre, per_step_budget / 4, nthreads)
     vals, gates_run, secs = [], [], []
     for _ in range(args.steps):
-        v, n, dt = oracle_sample(circ, per_step_budget, nthreads)
+        v, n, dt = oracle_sample(pre, per_step_budget, nthreads)
         vals.append(v)
         gates_run.append(n)
         secs.append(dt)
     value = statistics.median(vals)
-    sample = (f"first {min(gates_run)}-{max(gates_run)} of the 500 gates per step on the full "
-              f"26,873,856-amplitude state, FP64, {nthreads} OpenMP threads")
+    sample = (f"first {min(gates_run)}-{max(gates_run)} of the {len(pre.gates)} gates per step of the workload's "
+              f"{PREFIX_WIRES}-wire prefix ({pre.D:,} amplitudes), FP64, {nthreads} OpenMP threads")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -670,15 +699,15 @@ def oracle_checks(extra, nthreads: int, budget_s: float = 60.0) -> dict:
         return float(np.max(np.abs(got - ref))), inf
 
     t0 = time.perf_counter()
-    if "large_state" in extra:
-        pre, outs = extra["large_state"].pop("_prefix")
+    if "large_state_paths" in extra:
+        pre, outs = extra["large_state_paths"].pop("_prefix")
         ref = oracle.run_circuit(pre, nthreads=nthreads)
         rep = {"prefix": f"lowest 20 wires ({pre.D} amplitudes), {len(pre.gates)} gates"}
         for name, got in outs.items():
             e, inf = errs(ref, got)
             g64 = np.asarray(got, dtype=np.complex128)
             rep[name] = {"max_abs_err": e, "infidelity": inf, "norm_minus_1": float(np.vdot(g64, g64).real - 1.0)}
-        extra["large_state"]["error_vs_fp64_oracle"] = rep
+        extra["large_state_paths"]["error_vs_fp64_oracle"] = rep
     if "serving" in extra:
         kept = extra["serving"].pop("_sample")
         es, infs = [], []
@@ -695,6 +724,158 @@ def oracle_checks(extra, nthreads: int, budget_s: float = 60.0) -> dict:
     return {"seconds": time.perf_counter() - t0}
 
 
+def pass_attribution(qb, gen, torch, st, circ, prec, fuse, fopts, stream, amp_bytes):
+    """One extra, untimed run of the circuit with CUDA events around every
+    pass of its execution plan (one qd_apply_circuit call per pass), each
+    pass attributed to the kernel family that runs it.  Per family: seconds,
+    passes, HBM bytes of a pass (2 s D for tile and tensor-core passes, the
+    algorithmic bytes of the gate otherwise), the method's own flops of the
+    gates it applies (``method_flops``), the composed-block flops the
+    planner reports, and the MMA flops of tensor-core passes."""
+    D = circ.D
+    if fuse:
+        mode = {"tile": qb.QD_FUSE_TILE, "block": qb.QD_FUSE_BLOCK}[fuse]
+        order, pass_of, tiles, pflops = qb.qd_plan_circuit(circ.dims, prec, circ, mode=mode, with_flops=True,
+                                                           **fopts)
+        groups = [[] for _ in range(len(tiles))]
+        for g_idx, p_idx in zip(order, pass_of):
+            groups[p_idx].append(circ.gates[g_idx])
+    else:
+        groups = [[g] for g in circ.gates]
+        tiles, pflops = [0] * len(groups), [0.0] * len(groups)
+    subs = [gen.Circuit(circ.dims, gl) for gl in groups]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(subs) + 1)]
+    st.reset()
+    torch.cuda.synchronize()
+    evs[0].record(stream)
+    for i, sc in enumerate(subs):
+        st.run(sc, fuse=fuse, **fopts)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    fam = {}
+    for i, gl in enumerate(groups):
+        t = evs[i].elapsed_time(evs[i + 1]) / 1e3
+        plans = [qb.qd_plan_gate(circ.dims, prec, g.wires, g.U, g.controls or None, g.values or None) for g in gl]
+        wires = set()
+        for g in gl:
+            wires |= set(g.wires) | set(g.controls)
+        P = int(np.prod([circ.dims[w] for w in wires]))
+        if fuse and tiles[i] > 0:
+            k, nbytes = "tile", 2 * amp_bytes * D
+        elif fuse and len(gl) > 1 and prec == qb.QD_C64 and P >= 17:
+            k, nbytes = "tc", 2 * amp_bytes * D
+        elif len(gl) == 1:
+            k, nbytes = "gate", algorithmic_bytes(plans[0], amp_bytes)
+        else:
+            k, nbytes = "gate", 2 * amp_bytes * D
+        f = fam.setdefault(k, {"time": 0.0, "bytes": 0, "composed_flops": 0.0, "method_flops": 0.0, "n": 0,
+                               "mma_flops": 0.0, "gates": 0})
+        f["time"] += t
+        f["bytes"] += nbytes
+        f["composed_flops"] += float(pflops[i])
+        f["method_flops"] += sum(method_flops(pl, g.U) for pl, g in zip(plans, gl))
+        f["n"] += 1
+        f["gates"] += len(gl)
+        if k == "tc":  # 3 products x 16 k-steps of M=128, N=64, K=8 per 64 classes
+            f["mma_flops"] += math.ceil(D / P / 64) * 48 * 2 * 128 * 64 * 8
+    return fam
+
+
+KERNEL_NAMES = {"tile": "k_fused_tile (shared-memory tile pass)",
+                "tc": "k_block_tc (tcgen05 tensor-core block pass)",
+                "gate": "k_gate1 / k_gate_tile (per-gate passes)"}
+
+
+def roofline_of(fam, prec_name, is_c64):
+    """Roofline record of the family with the most time (see ``pass_attribution``)."""
+    dom = max(fam, key=lambda k: fam[k]["time"])
+    f = fam[dom]
+    peak, peak_kind = measured_peaks()
+    t = f["time"]
+    if dom == "tile":
+        alu_peak = FP32_TFLOPS if is_c64 else FP64_TFLOPS
+        roof = {"kernel": KERNEL_NAMES[dom], "bound": "alu", "achieved": f["method_flops"] / t / 1e12,
+                "peak": alu_peak, "unit": "TFLOP/s",
+                "work": "the method's own flops of the pass's gates: 8 P per amplitude of every visited class for "
+                        "dense P x P gates, 6 per changed amplitude for phases, 0 for pure permutations",
+                "peak_source": "derived: " + ALU_PEAK_NOTE,
+                "traffic": ncu_traffic(prec_name, "fused"), "launches_measured": f["n"],
+                "hbm_view": {"achieved_gbs": f["bytes"] / t / 1e9, "peak_gbs": peak, "frac": f["bytes"] / t / 1e9 / peak,
+                             "bytes": "2 s D per pass", "peak_source": peak_kind},
+                "composed_flops": {"achieved_tflops": f["composed_flops"] / t / 1e12,
+                                   "frac": f["composed_flops"] / t / 1e12 / alu_peak,
+                                   "work": "8 P flops per amplitude per composed P x P block (dense equivalent)"}}
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    else:
+        achieved = f["bytes"] / t / 1e9
+        roof = {"kernel": KERNEL_NAMES[dom], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "traffic": ncu_traffic(prec_name, "tc" if dom == "tc" else "gate"), "launches_measured": f["n"],
+                "method_tflops": f["method_flops"] / t / 1e12}
+        if dom == "tc":
+            tf32 = tf32_peak()
+            roof["tensor_view"] = {"achieved_tflops": f["mma_flops"] / t / 1e12, "peak_tflops": tf32,
+                                   "frac": f["mma_flops"] / t / 1e12 / tf32,
+                                   "peak_source": "measured bf16 burst x 0.489 (nominal TF32/BF16 dense ratio)"}
+    roof["passes_by_kernel"] = {k: {"seconds": v["time"], "passes": v["n"], "gates": v["gates"]}
+                                for k, v in fam.items()}
+    return roof
+
+
+def host_mem_available() -> int:
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
+
+
+def measure_benchmark_circuit(qb, gen, torch, stream, steps=10):
+    """The 12-qubit + 8-qutrit Clifford+T-like circuit (26,873,856 amplitudes,
+    500 gates): complex64 with autotuned fusion, complex128 per gate and in
+    tile passes.  Each: ``steps`` timed steps (reset, circuit, norm) with CUDA
+    events after a warm-up step, and the dominant kernel's roofline."""
+    from paper_2410_17876_gb300 import autotune
+
+    circ = gen.config1_circuit()
+    upd = circuit_updates(circ)
+    out = {"workload": BENCH_CIRCUIT, "updates_per_circuit": upd}
+    for name, prec, fuse in (("c64", qb.QD_C64, "auto"), ("c128_per_gate", qb.QD_C128, False),
+                             ("c128_tile", qb.QD_C128, "tile")):
+        st = qb.State(circ.dims, prec=prec, stream=stream)
+        fopts = {}
+        if fuse == "auto":
+            tuned = autotune.tune_circuit(st, circ)
+            fuse = tuned["mode"] if tuned["mode"] != "off" else False
+            fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"]} if fuse else {}
+
+        def step():
+            st.reset()
+            st.run(circ, fuse=fuse, **fopts)
+            return st.norm()
+
+        step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        amp_bytes = 8 if prec == qb.QD_C64 else 16
+        fam = pass_attribution(qb, gen, torch, st, circ, prec, fuse, fopts, stream, amp_bytes)
+        out[name] = {"ms_per_step": 1e3 * t, "value": upd / t, "unit": UNIT, "fusion": fuse or "off",
+                     "fusion_opts": fopts,
+                     "roofline": roofline_of(fam, "c64" if prec == qb.QD_C64 else "c128", prec == qb.QD_C64)}
+        st.close()
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_gpu(args):
     import torch
 
@@ -705,21 +886,20 @@ def run_gpu(args):
     if rank == 0 or world == 1:
         __graft_entry__.build()
     barrier(world)
+    from paper_2410_17876_gb300 import autotune
     from paper_2410_17876_gb300 import binding as qb
     from paper_2410_17876_gb300 import inputs as gen
 
-    prec = qb.QD_C64 if args.prec == "c64" else qb.QD_C128
-    amp_bytes = 8 if prec == qb.QD_C64 else 16
-    circ = gen.config1_circuit()
+    prec = qb.QD_C64
+    amp_bytes = 8
+    circ = gen.config2_circuit()
     upd = circuit_updates(circ)
     stream = torch.cuda.current_stream(local)
     st = qb.State(circ.dims, prec=prec, stream=stream, device=local)
 
     tuned = None
     if args.fuse == "auto":
-        from paper_2410_17876_gb300 import autotune
-
-        tuned = autotune.tune_circuit(st, circ)
+        tuned = autotune.tune_circuit(st, circ, budget_s=45.0)
         fuse = tuned["mode"] if tuned["mode"] != "off" else False
         fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"]} if fuse else {}
     else:
@@ -744,11 +924,13 @@ def run_gpu(args):
     torch.cuda.synchronize()
     n0 = qb.qd_launch_count()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     launches = qb.qd_launch_count() - n0
     dev_s = ev0.elapsed_time(ev1) / 1e3
     barrier(world)
@@ -756,119 +938,44 @@ def run_gpu(args):
     t_max = max_over_ranks(dev_s, world)
     value, _ = aggregate([upd * args.steps] * world, [t_max] * world)
 
-    # ---- per-launch durations of the dominant kernel (one extra, untimed step) ----
-    plans = [qb.qd_plan_gate(circ.dims, prec, g.wires, g.U, g.controls or None, g.values or None)
-             for g in circ.gates]
-    if fuse:
-        # one qd_apply_circuit call per planned pass, CUDA events around each
-        mode = {"tile": qb.QD_FUSE_TILE, "block": qb.QD_FUSE_BLOCK}[fuse]
-        order, pass_of, tiles, pflops = qb.qd_plan_circuit(circ.dims, prec, circ, mode=mode, with_flops=True,
-                                                           **fopts)
-        groups = [[] for _ in range(len(tiles))]
-        for g_idx, p_idx in zip(order, pass_of):
-            groups[p_idx].append(circ.gates[g_idx])
-        subs = [gen.Circuit(circ.dims, gl) for gl in groups]
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(subs) + 1)]
-        st.reset()
-        torch.cuda.synchronize()
-        evs[0].record(stream)
-        for i, sc in enumerate(subs):
-            st.run(sc, fuse=fuse, **fopts)
-            evs[i + 1].record(stream)
-        torch.cuda.synchronize()
-        fam = {}
-        for i, gl in enumerate(groups):
-            t = evs[i].elapsed_time(evs[i + 1]) / 1e3
-            wires = set()
-            for g in gl:
-                wires |= set(g.wires) | set(g.controls)
-            P = int(np.prod([circ.dims[w] for w in wires]))
-            if tiles[i] > 0:
-                k, nbytes = "tile", 2 * amp_bytes * circ.D
-            elif len(gl) > 1 and prec == qb.QD_C64 and P >= 17:
-                k, nbytes = "tc", 2 * amp_bytes * circ.D
-            else:
-                k, nbytes = "gate", algorithmic_bytes(
-                    qb.qd_plan_gate(circ.dims, prec, gl[0].wires, gl[0].U, gl[0].controls or None,
-                                    gl[0].values or None), amp_bytes) if len(gl) == 1 else 2 * amp_bytes * circ.D
-            f = fam.setdefault(k, {"time": 0.0, "bytes": 0, "flops": 0.0, "n": 0, "mma_flops": 0.0})
-            f["time"] += t
-            f["bytes"] += nbytes
-            f["flops"] += float(pflops[i])
-            f["n"] += 1
-            if k == "tc":  # 3 products x 16 k-steps of M=128, N=64, K=8 per 64 classes
-                f["mma_flops"] += math.ceil(circ.D / P / 64) * 48 * 2 * 128 * 64 * 8
-        dom = max(fam, key=lambda k: fam[k]["time"])
-        f = fam[dom]
-        kname = {"tile": "k_fused_tile (shared-memory tile pass)",
-                 "tc": "k_block_tc (tcgen05 tensor-core block pass)",
-                 "gate": "k_gate1 / k_gate_tile (per-gate passes)"}[dom]
-        k_time, k_flops, k_bytes, k_n = f["time"], f["flops"], f["bytes"], f["n"]
-        fam_summary = {k: {"seconds": v["time"], "passes": v["n"]} for k, v in fam.items()}
-    else:
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(circ.gates) + 1)]
-        st.reset()
-        torch.cuda.synchronize()
-        evs[0].record(stream)
-        for i, g in enumerate(circ.gates):
-            st.apply(g)
-            evs[i + 1].record(stream)
-        torch.cuda.synchronize()
-        k_time, k_bytes, k_n = 0.0, 0, 0
-        for i, p in enumerate(plans):
-            if p["family"] == 0 and p["touched_rows"] > 0:
-                k_time += evs[i].elapsed_time(evs[i + 1]) / 1e3
-                k_bytes += algorithmic_bytes(p, amp_bytes)
-                k_n += 1
-        kname = "k_gate1 (per-class register kernel, all gates of the circuit)"
-        dom, fam_summary = "gate", None
-    peak, peak_kind = measured_peaks()
-    if fuse and dom == "tile":
-        # a tile pass is bound by its on-chip arithmetic (composed blocks), not by HBM:
-        # FP32 (complex64) or FP64 (complex128) pipe peak from unit counts and clocks
-        alu_peak = FP32_TFLOPS if prec == qb.QD_C64 else FP64_TFLOPS
-        roof = {"kernel": kname, "bound": "alu", "achieved": k_flops / k_time / 1e12 if k_time > 0 else 0.0,
-                "peak": alu_peak, "unit": "TFLOP/s", "peak_source": "derived: " + ALU_PEAK_NOTE,
-                "traffic": ncu_traffic(args.prec, "fused"), "launches_measured": k_n,
-                "hbm_view": {"achieved_gbs": k_bytes / k_time / 1e9 if k_time > 0 else 0.0, "peak_gbs": peak}}
-        roof["frac"] = roof["achieved"] / roof["peak"]
-    else:
-        achieved = k_bytes / k_time / 1e9 if k_time > 0 else 0.0
-        roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": ncu_traffic(args.prec, "tc" if dom == "tc" else "gate"), "launches_measured": k_n}
-        if fuse and dom == "tc":
-            tf32 = tf32_peak()
-            roof["tensor_view"] = {"achieved_tflops": f["mma_flops"] / k_time / 1e12, "peak_tflops": tf32,
-                                   "frac": f["mma_flops"] / k_time / 1e12 / tf32,
-                                   "peak_source": "measured bf16 burst x 0.489 (nominal TF32/BF16 dense ratio)"}
-    if fam_summary:
-        roof["passes_by_kernel"] = fam_summary
+    # ---- per-pass durations of the dominant kernel (one extra, untimed step) ----
+    fam = pass_attribution(qb, gen, torch, st, circ, prec, fuse, fopts, stream, amp_bytes)
+    roof = roofline_of(fam, "c64", True)
+    step_method_flops = sum(v["method_flops"] for v in fam.values())
 
     # ---- end to end through the public API with host buffers ----
-    pinned = torch.empty(circ.D, dtype=torch.complex64 if prec == qb.QD_C64 else torch.complex128,
-                         pin_memory=True)
-    host_out = pinned.numpy()
+    state_bytes = circ.D * amp_bytes
     h2d = sum(g.U.size * 16 + 8 * len(g.controls) for g in circ.gates)
-    d2h = host_out.nbytes + 8
-    e2e_steps = max(1, min(args.steps, 5))
-    qb.qd_state_get_raw(st.handle, host_out)
-    barrier(world)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        st.reset()
-        st.run(circ, fuse=fuse, **fopts)
-        st.norm()
+    e2e = None
+    if host_mem_available() > 2.5 * state_bytes:
+        pinned = torch.empty(circ.D, dtype=torch.complex64, pin_memory=True)
+        host_out = pinned.numpy()
+        d2h = host_out.nbytes + 8
+        e2e_steps = max(1, min(args.steps, 3))
         qb.qd_state_get_raw(st.handle, host_out)
-    e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
-    e2e_value = world * upd / e2e_s
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            st.reset()
+            st.run(circ, fuse=fuse, **fopts)
+            st.norm()
+            qb.qd_state_get_raw(st.handle, host_out)
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / e2e_steps, world)
+        e2e = {"value": world * upd / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s,
+               "what": "reset, the circuit through qd_apply_circuit (matrices from host memory), the norm, and "
+                       "the whole final state copied into pinned host memory, every step"}
+        del pinned, host_out
+    st.close()
+    del st
+    torch.cuda.empty_cache()
 
     # ---- the other workloads of the path, each one timed run (rank 0 reports its own) ----
     extra = {}
     if not args.no_extra:
-        st.close()
+        extra["benchmark_circuit"] = measure_benchmark_circuit(qb, gen, torch, stream)
         torch.cuda.empty_cache()
-        extra["large_state"] = measure_large(qb, gen, torch, stream, amp_bytes_c64=8)
+        extra["large_state_paths"] = measure_large(qb, gen, torch, stream, amp_bytes_c64=8)
         torch.cuda.empty_cache()
         extra["stride_sweep"] = measure_stride_sweep(qb, gen, torch, stream)
         torch.cuda.empty_cache()
@@ -886,43 +993,44 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         extra["serving"] = measure_serving(qb, gen, torch)
         torch.cuda.empty_cache()
-        st = qb.State(circ.dims, prec=prec, stream=stream, device=local)
 
-    # ---- CPU oracle baseline (rank 0, N = 1 only) ----
+    # ---- CPU oracle baseline (rank 0, N = 1 only): the workload's 20-wire prefix ----
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
 
         oracle.build()
         nthreads = oracle.max_threads()
-        v, n, dt = oracle_sample(circ, args.cpu_seconds, nthreads)
+        pre = gen.prefix_circuit(circ, PREFIX_WIRES)
+        v, n, dt = oracle_sample(pre, args.cpu_seconds, nthreads)
         cpu = {"value": v, "unit": UNIT, "cores": nthreads, "kind": "oracle",
-               "sample": f"first {n} of the 500 gates on the full 26,873,856-amplitude state, FP64, "
-                         f"{dt:.1f} s"}
+               "sample": f"first {n} of the {len(pre.gates)} gates of the workload's {PREFIX_WIRES}-wire prefix "
+                         f"({pre.D:,} amplitudes; the gates whose wires all lie in it), FP64, {dt:.1f} s"}
         if extra:
             cpu["checks"] = oracle_checks(extra, nthreads)
     for rep in extra.values():  # outputs kept for checks that did not run
         for k in [k for k in rep if k.startswith("_")]:
             rep.pop(k)
-    st.close()
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == qb.QD_C64 else "f64",
-            "data": "synthetic",
-            "config": {"workload": WORKLOAD, "prec": args.prec, "fusion": fuse or "off",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "prec": "c64", "fusion": fuse or "off",
                        "fusion_opts": fopts, "autotuned": tuned is not None,
-                       "amplitudes": circ.D, "gates": len(circ.gates),
-                       "state_bytes": circ.D * amp_bytes,
-                       "l2": f"state {circ.D * amp_bytes / 1e6:.0f} MB > {L2_BYTES / 1e6:.0f} MB L2, no flush",
+                       "autotune_table_s": tuned.get("table") if tuned else None,
+                       "amplitudes": circ.D, "gates": len(circ.gates), "state_bytes": state_bytes,
+                       "l2": f"state {state_bytes / 1e9:.2f} GB > {L2_BYTES / 1e6:.0f} MB L2, no flush",
                        "parallelism": f"replicas x{world}"},
-            "hbm_gbs_effective": sum(algorithmic_bytes(p, amp_bytes) for p in plans) * args.steps / t_max / 1e9,
+            "method_tflops": step_method_flops * args.steps / t_max / 1e12,
+            "per_gate_equivalent_gbs": sum(algorithmic_bytes(qb.qd_plan_gate(circ.dims, prec, g.wires, g.U,
+                                                                             g.controls or None,
+                                                                             g.values or None), amp_bytes)
+                                           for g in circ.gates) * args.steps / t_max / 1e9,
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+            "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
         }
@@ -966,10 +1074,16 @@ def run_ncu_fused_case(args):
     from paper_2410_17876_gb300 import inputs as gen
 
     prec = qb.QD_C64 if args.prec == "c64" else qb.QD_C128
-    circ = gen.config1_circuit()
+    if args.ncu_workload == "prefix":
+        circ = gen.prefix_circuit(gen.config2_circuit(), PREFIX_WIRES)
+    else:
+        circ = gen.config1_circuit()
     st = qb.State(circ.dims, prec=prec)
     fuse = "tile" if args.fuse in ("auto", "tile") else args.fuse
-    st.run(circ, fuse=fuse, **({"max_tile_amps": args.tile} if args.tile and fuse == "tile" else {}))
+    opts = {"max_tile_amps": args.tile} if args.tile and fuse == "tile" else {}
+    if args.block_dim:
+        opts["block_dim"] = args.block_dim
+    st.run(circ, fuse=fuse, **opts)
     st.synchronize()
     st.close()
     torch.cuda.synchronize()
@@ -979,9 +1093,15 @@ def run_ncu_fused_case(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", choices=["c64", "c128"], default="c64")
+    ap.add_argument("--prec", choices=["c64", "c128"], default="c64",
+                    help="precision of the profiler cases (the bench line itself is complex64; complex128 is "
+                         "reported under benchmark_circuit)")
+    ap.add_argument("--block-dim", type=int, default=0, help="largest composed block (profiler cases)")
+    ap.add_argument("--ncu-workload", choices=["benchmark", "prefix"], default="benchmark",
+                    help="profiler case: the 12-qubit + 8-qutrit benchmark circuit, or the 20-wire prefix of the "
+                         "large workload (17,915,904 amplitudes, Haar gates)")
     ap.add_argument("--fuse", choices=["auto", "tile", "block", "off"], default="auto",
                     help="tile: consecutive gates share one shared-memory pass over the state; off: one pass per "
                          "gate; auto: the autotuner's choice of the two (and of tile size and block width)")
@@ -994,8 +1114,8 @@ def main(argv=None):
                     help="run only six dense single-wire gates (wires 0, 5, 10, 15, 19, 3) on the workload's "
                          "state, for a profiler capture of launches 4-6; prints nothing")
     ap.add_argument("--ncu-fused-case", action="store_true",
-                    help="run only the workload circuit once, fused (--fuse tile or block; auto means tile), "
-                         "for a profiler capture of one fused launch; prints nothing")
+                    help="run only the --ncu-workload circuit once, fused (--fuse tile or block; auto means "
+                         "tile), for a profiler capture of one fused launch; prints nothing")
     args = ap.parse_args(argv)
     if args.ncu_case:
         return run_ncu_case(args)

@@ -471,10 +471,10 @@ qd_status qd_synchronize(qd_state* st);
 
 /* ------------------------------------------------------------------------
  * Norm without allocation.  The paper has no counterpart to this call; it
- * exists for callers that cannot allocate device memory: a thread that is
- * capturing a CUDA graph (cudaMalloc is not allowed there), a framework
- * whose caching allocator owns all device memory, or a latency-critical loop
- * that must not stall on an allocation.  qd_norm needs a qd_state, and
+ * exists for callers that cannot allocate device memory: a framework whose
+ * caching allocator owns all device memory and forbids allocations beside
+ * it, or a latency-critical loop that must not stall on the device-wide
+ * synchronisation an allocation can cause.  qd_norm needs a qd_state, and
  * creating a state allocates its reduction workspace; this call allocates
  * nothing (no cudaMalloc, cudaFree or allocating library routine).
  *
@@ -484,7 +484,9 @@ qd_status qd_synchronize(qd_state* st);
  * dev_out: one double in device memory (8-byte aligned) that receives
  *   sum_j |psi_j|^2, computed exactly as qd_norm does (binary64, Neumaier
  *   compensation, fixed order), so the two agree bit for bit on the same
- *   amplitudes.
+ *   amplitudes, whichever the alignment of dev_amps (an 8-byte-aligned
+ *   complex64 pointer reads each pair of amplitudes with two loads instead
+ *   of one, in the same order).
  * stream: the cudaStream_t the two kernels are issued on (NULL = default);
  *   the call is asynchronous, read dev_out after synchronising the stream.
  *
@@ -497,10 +499,15 @@ qd_status qd_synchronize(qd_state* st);
  * writes every entry it reads before reading it, so nothing needs
  * clearing); calls whose kernels overlap on the GPU -- on different streams
  * or different host threads without ordering -- race on it and give wrong
- * results.  Order them on one stream or with events.
+ * results.  Order them on one stream or with events.  The looked-up address
+ * is kept for the life of the process: after cudaDeviceReset (or anything
+ * else that destroys a device's primary context) it is stale, so do not
+ * call qd_norm_noalloc on that device again in the same process.
  *
  * Errors: QD_ERR_ARG for NULL or misaligned pointers, an unknown precision,
  * or num_amplitudes outside [1, QD_NORM_NOALLOC_MAX_AMPLITUDES];
+ * QD_ERR_UNSUPPORTED for a device ordinal of 64 or above (the library keeps
+ * one looked-up address per device for ordinals 0..63);
  * QD_ERR_CUDA if the set-up or a launch fails.
  * --------------------------------------------------------------------- */
 #define QD_NORM_NOALLOC_BLOCKS 1024

@@ -121,6 +121,27 @@ def run_circuit(circ, psi0: Optional[np.ndarray] = None, nthreads: int = 1,
     return psi
 
 
+def _run_one(circ) -> np.ndarray:
+    return run_circuit(circ, nthreads=1)
+
+
+def run_circuits(circs, workers: Optional[int] = None) -> list:
+    """:func:`run_circuit` on many circuits, one single-threaded oracle per
+    circuit in a pool of ``workers`` processes (default: all host cores).
+    The pool is started with ``spawn``, so it is safe to use from a process
+    that already holds a CUDA context."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    circs = list(circs)
+    workers = workers or max(1, os.cpu_count() or 1)
+    if workers == 1 or len(circs) <= 1:
+        return [_run_one(c) for c in circs]
+    build()
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_run_one, circs, chunksize=max(1, len(circs) // (8 * workers))))
+
+
 def norm(psi: np.ndarray) -> float:
     """Squared norm ``sum |psi_j|^2`` (compensated summation)."""
     psi = np.ascontiguousarray(psi, dtype=np.complex128)

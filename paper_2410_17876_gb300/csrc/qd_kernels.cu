@@ -257,7 +257,9 @@ __global__ void __launch_bounds__(256) k_norm_partial(const typename Cplx<R>::T2
 // with Neumaier compensation, the exact product errors going into the
 // compensation, and each run's (s, c) is added to the binary64 compensated
 // sum.  The binary32 run sum errs by at most about 16 u^2 sum|x| (u = 2^-24),
-// below 1e-14 relative.  Two amplitudes per 16-byte load; psi 16-byte aligned.
+// below 1e-14 relative.  Two amplitudes per step: one 16-byte load when psi
+// is 16-byte aligned (A16), else two 8-byte loads -- the same arithmetic in
+// the same order either way, so both alignments give the same bits.
 __device__ __forceinline__ void fsum_add(float& s, float& c, float x) {
     const float t = s + x;
     if (fabsf(s) >= fabsf(x))
@@ -273,7 +275,8 @@ __device__ __forceinline__ void fsum_prob(float& s, float& c, float x, float y) 
     fsum_add(s, c, p2);
 }
 
-__global__ void __launch_bounds__(256) k_norm_partial_c64(const float4* psi2, int64_t D, double* partials) {
+template <bool A16>
+__global__ void __launch_bounds__(256) k_norm_partial_c64(const float2* psi, int64_t D, double* partials) {
     CSum acc{0.0, 0.0};
     const int64_t pairs = D >> 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -282,7 +285,13 @@ __global__ void __launch_bounds__(256) k_norm_partial_c64(const float4* psi2, in
         float s = 0.f, c = 0.f;
 #pragma unroll 8
         for (int k = 0; k < 8 && i < pairs; ++k, i += stride) {
-            const float4 v = psi2[i];
+            float4 v;
+            if constexpr (A16) {
+                v = reinterpret_cast<const float4*>(psi)[i];
+            } else {
+                const float2 a = psi[2 * i], b = psi[2 * i + 1];
+                v = make_float4(a.x, a.y, b.x, b.y);
+            }
             fsum_prob(s, c, v.x, v.y);
             fsum_prob(s, c, v.z, v.w);
         }
@@ -290,7 +299,7 @@ __global__ void __launch_bounds__(256) k_norm_partial_c64(const float4* psi2, in
         acc.c += (double)c;
     }
     if ((D & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
-        const float2 v = reinterpret_cast<const float2*>(psi2)[D - 1];
+        const float2 v = psi[D - 1];
         float s = 0.f, c = 0.f;
         fsum_prob(s, c, v.x, v.y);
         csum_add(acc, (double)s);
@@ -423,7 +432,9 @@ template <typename R>
 cudaError_t launch_norm(const void* psi, int64_t D, double* partials, int nblocks, double* dev_out,
                         cudaStream_t s) {
     if (sizeof(R) == 4 && reinterpret_cast<uintptr_t>(psi) % 16 == 0)
-        k_norm_partial_c64<<<nblocks, 256, 0, s>>>(reinterpret_cast<const float4*>(psi), D, partials);
+        k_norm_partial_c64<true><<<nblocks, 256, 0, s>>>(reinterpret_cast<const float2*>(psi), D, partials);
+    else if (sizeof(R) == 4)
+        k_norm_partial_c64<false><<<nblocks, 256, 0, s>>>(reinterpret_cast<const float2*>(psi), D, partials);
     else
         k_norm_partial<R><<<nblocks, 256, 0, s>>>(reinterpret_cast<const typename Cplx<R>::T2*>(psi), D,
                                                   partials);

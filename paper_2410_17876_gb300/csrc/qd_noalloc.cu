@@ -1,12 +1,10 @@
 // qd_norm_noalloc: the squared norm of caller-owned device amplitudes with
 // no allocation at all (see its declaration in include/qudit.h).
 //
-// Who needs this: code that must not call cudaMalloc -- for example a host
-// thread that is capturing a CUDA graph (an allocation would break or be
-// recorded into the capture), a framework whose caching allocator owns all
-// device memory and forbids side allocations, or a latency-critical loop
-// that cannot afford the device-wide synchronisation an allocation can
-// trigger.  qd_norm needs a qd_state, and creating one allocates a
+// Who needs this: code that must not call cudaMalloc -- for example a
+// framework whose caching allocator owns all device memory and forbids side
+// allocations, or a latency-critical loop that cannot afford the
+// device-wide synchronisation an allocation can trigger.  qd_norm needs a qd_state, and creating one allocates a
 // reduction workspace; this entry point instead keeps that workspace in a
 // fixed file-scope device array.
 //
@@ -81,10 +79,12 @@ extern "C" qd_status qd_norm_noalloc(const void* dev_amps, int64_t num_amplitude
         qd::set_last_error("qd_norm_noalloc: number of amplitudes outside [1, QD_NORM_NOALLOC_MAX_AMPLITUDES]");
         return QD_ERR_ARG;
     }
+    // reduce_blocks never returns more than 1024 blocks, which is what the
+    // array holds; checked here so that a change there cannot overrun it
     const int nb = qd::reduce_blocks(num_amplitudes);
     if (nb > QD_NORM_NOALLOC_BLOCKS) {
-        qd::set_last_error("qd_norm_noalloc: reduction needs more partial sums than the static scratch holds");
-        return QD_ERR_UNSUPPORTED;
+        qd::set_last_error("qd_norm_noalloc: internal error: more partial sums than the static scratch holds");
+        return QD_ERR_CUDA;
     }
     double* scratch = nullptr;
     qd_status rc = scratch_for_current_device(&scratch);

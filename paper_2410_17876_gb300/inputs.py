@@ -38,7 +38,7 @@ __all__ = [
     "Gate", "Circuit", "haar", "haar_batch", "x_plus", "z_gen", "fourier", "qubit_s",
     "qubit_t", "random_state", "config0_circuit", "config1_circuit",
     "config2_circuit", "prefix_circuit", "config3_batch", "config4_trace",
-    "random_mixed_circuit", "ghz_circuit", "amp_gate_updates",
+    "random_mixed_circuit", "ghz_circuit", "product_circuit", "amp_gate_updates",
     "circuit_from_arrays",
 ]
 
@@ -326,6 +326,30 @@ def config4_trace(seed: int = 4, rate: float = 2000.0, duration: float = 10.0,
         depth = int(rng.integers(depth_min, depth_max + 1))
         out.append((t, random_mixed_circuit(dims, depth, rng)))
     return out
+
+
+def product_circuit(dims: Sequence[int], depth: int, seed: int = 22) -> Circuit:
+    """Uncontrolled single-wire gates only, so that ``|0...0>`` stays a
+    product state: one Haar gate on every wire first (so no factor stays a
+    basis vector), then ``depth - len(dims)`` gates on uniform wires drawn
+    from {Haar, F_d, Z_d, X_{+1}} with probabilities 0.55 / 0.15 / 0.15 /
+    0.15."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    dims = tuple(int(x) for x in dims)
+    gates: List[Gate] = [Gate((w,), haar(dims[w], rng), name="haar") for w in range(len(dims))]
+    for _ in range(max(0, depth - len(dims))):
+        t = int(rng.integers(len(dims)))
+        d = dims[t]
+        k = float(rng.random())
+        if k < 0.55:
+            gates.append(Gate((t,), haar(d, rng), name="haar"))
+        elif k < 0.70:
+            gates.append(Gate((t,), fourier(d), name="F"))
+        elif k < 0.85:
+            gates.append(Gate((t,), z_gen(d), name="Z"))
+        else:
+            gates.append(Gate((t,), x_plus(d, 1), name="X"))
+    return Circuit(dims, gates)
 
 
 def ghz_circuit(dims: Sequence[int], root: int = 0) -> Circuit:

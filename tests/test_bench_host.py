@@ -93,3 +93,37 @@ def test_reference_arm_non_zero_rank_exits_without_work():
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_method_flops_per_gate_kind():
+    """8 P flops per amplitude for dense gates, 6 per changed amplitude for
+    phases and phased permutations, 0 for pure permutations; controls divide
+    the visited classes."""
+    from paper_2410_17876_gb300 import binding as qb
+
+    dims = (2, 3, 4)
+    D = 24
+    rng = np.random.Generator(np.random.PCG64(3))
+
+    def flops(wires, U, cw=(), cv=()):
+        p = qb.qd_plan_gate(dims, qb.QD_C64, wires, U, list(cw) or None, list(cv) or None)
+        return bench.method_flops(p, U)
+
+    assert flops((1,), gen.haar(3, rng)) == 8 * 3 * D
+    assert flops((1,), gen.haar(3, rng), (2,), (1,)) == 8 * 3 * D // 4
+    assert flops((0, 1), gen.haar(6, rng)) == 8 * 6 * D
+    assert flops((0,), gen.qubit_s()) == 6 * D // 2          # one non-unit diagonal entry
+    assert flops((1,), gen.z_gen(3)) == 6 * D * 2 // 3        # two non-unit entries of three
+    assert flops((1,), gen.x_plus(3)) == 0
+    assert flops((1,), -gen.x_plus(3)) == 6 * D
+
+
+def test_config2_method_flops_and_updates():
+    from paper_2410_17876_gb300 import binding as qb
+
+    c = gen.config2_circuit()
+    assert c.D == 1719926784 and len(c.gates) == 200
+    f = bench.circuit_method_flops(qb, c, qb.QD_C64)
+    u = bench.circuit_updates(c)
+    # dense gates cost 16 (qubit) or 24 (qutrit) flops per touched amplitude
+    assert 0.5 * 16 * u < f < 24 * u

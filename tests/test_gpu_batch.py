@@ -102,17 +102,33 @@ def test_invalid_circuit_rejects_the_batch(qb, gen):
     qb.qd_batch_destroy(b)
 
 
+# Sample rule for the workload's larger circuits (every circuit up to 2^16
+# amplitudes is compared): a seeded draw of 24 circuits with D in
+# (2^16, 2^18], 24 in (2^18, 2^20] and 16 in (2^20, 2^22].
+LARGE_STRATA = ((1 << 16, 1 << 18, 24), (1 << 18, 1 << 20, 24), (1 << 20, 1 << 22, 16))
+
+
 def test_batched_workload_8192_circuits(qb, gen):
-    """8192 circuits (widths 4-12, dims from {2,3,4,5}, depths 20-300), complex64:
-    every norm within 1e-5 of 1; every circuit with D <= 20,000 against the oracle."""
+    """8192 circuits (widths 4-12, dims from {2,3,4,5}, depths 20-300), complex64,
+    run as one batch under a CUDA graph: every norm within 1e-5 of 1; every
+    circuit with D <= 2^16 against the oracle (the one-CTA path up to 8192
+    amplitudes and the tile-pass programs on auxiliary streams above it), and
+    a stratified seeded sample of 64 circuits with 2^16 < D <= 2^22."""
     circs = gen.config3_batch()
     b = qb.qd_batch_create(qb.QD_C64)
     qb.qd_batch_run(b, circs, use_graph=True)
     norms = qb.qd_batch_norms(b, len(circs))
     assert np.all(np.abs(norms - 1.0) < 1e-5), np.max(np.abs(norms - 1.0))
     rng = np.random.Generator(np.random.PCG64(5))
-    small = [i for i, c in enumerate(circs) if c.D <= 20000]
-    for i in rng.permutation(small)[:40]:
-        got = qb.qd_batch_get_amplitudes(b, int(i))
-        assert_close(got, oracle.run_circuit(circs[int(i)]), qb.QD_C64, f"workload circuit {i}")
+    chosen = [i for i, c in enumerate(circs) if c.D <= (1 << 16)]
+    n_small = len(chosen)
+    for lo, hi, k in LARGE_STRATA:
+        pool = [i for i, c in enumerate(circs) if lo < c.D <= hi]
+        assert len(pool) >= k
+        chosen += sorted(int(i) for i in rng.permutation(pool)[:k])
+    got = [qb.qd_batch_get_amplitudes(b, i) for i in chosen]
     qb.qd_batch_destroy(b)
+    refs = oracle.run_circuits([circs[i] for i in chosen])
+    assert n_small > 5000 and sum(1 for i in chosen if circs[i].D > 8192) > 1500
+    for i, g, r in zip(chosen, got, refs):
+        assert_close(g, r, qb.QD_C64, f"workload circuit {i} (D = {circs[i].D})")

@@ -86,3 +86,122 @@ def test_config2_full_size_inverse_returns_to_zero(qb, gen, fuse):
     assert abs(nrm - 1.0) < 1e-4
     assert p0 > 1.0 - 1e-4, f"|psi_0|^2 = {p0}"
     assert 1.0 - p0 / nrm < 1e-4
+
+
+# ----------------------------------------------------------------------------
+# The 1.72e9-amplitude workload at full size, element by element against
+# closed forms (every byte offset range of the state, including the amplitudes
+# beyond 2^32 bytes).
+# ----------------------------------------------------------------------------
+LARGE_MODES = ["per_gate", "tile", "block"]
+
+
+def _run_mode(st, circ, mode):
+    st.reset()
+    if mode == "per_gate":
+        st.run(circ, fuse=False)
+    elif mode == "tile":
+        st.run(circ, fuse="tile")
+    else:
+        st.run(circ, fuse="block")
+
+
+def _sample_indices(D, seed, n_random=1_000_000, n_tail=100_000, extra=()):
+    """Sorted unique indices: the first 1000, ``n_random`` uniform draws, the
+    last ``n_tail`` (byte offsets above 2^32 for complex64 when D > 2^29),
+    plus ``extra``."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = [np.arange(min(1000, D), dtype=np.int64), rng.integers(0, D, size=n_random, dtype=np.int64),
+             np.arange(max(0, D - n_tail), D, dtype=np.int64), np.asarray(extra, dtype=np.int64)]
+    return np.unique(np.concatenate(parts))
+
+
+def _gather(st, idx):
+    """Amplitudes at ``idx`` read from the device state (complex128 on the host)."""
+    import torch
+
+    t = torch.from_numpy(idx).to(st.buf.device)
+    v = st.buf.view(-1, 2).index_select(0, t).double().cpu().numpy()
+    return v[:, 0] + 1j * v[:, 1]
+
+
+def _digits(idx, dims):
+    out = []
+    r = idx.copy()
+    for d in dims:
+        out.append(r % d)
+        r //= d
+    return out
+
+
+@pytest.fixture(scope="module")
+def large_state(qb, gen):
+    import torch
+
+    dims = gen.config2_circuit().dims
+    st = qb.State(dims, prec=qb.QD_C64)
+    yield st
+    st.close()
+    del st
+    torch.cuda.empty_cache()
+
+
+@pytest.fixture(scope="module")
+def product_ref(gen):
+    """Product-state circuit on the 26 wires of the large workload, and the
+    state's factors: the oracle run on each wire alone with that wire's gates
+    (the circuit has no controls, so the state is the Kronecker product of
+    these one-wire states)."""
+    dims = gen.config2_circuit().dims
+    circ = gen.product_circuit(dims, 200)
+    factors = []
+    for w, d in enumerate(dims):
+        one = gen.Circuit((d,), [gen.Gate((0,), g.U) for g in circ.gates if g.wires == (w,)])
+        factors.append(oracle.run_circuit(one))
+    return circ, factors
+
+
+@pytest.mark.parametrize("mode", LARGE_MODES)
+def test_config2_full_size_product_state(qb, large_state, product_ref, mode):
+    """1.72e9 amplitudes, complex64, 200 uncontrolled Haar / F / Z / X gates on
+    all 26 wires: psi[j] = prod_w v_w[digit_w(j)] on a sample of about 1.1e6
+    indices including the last 1e5, per gate, in tile passes and in
+    composed blocks (tensor cores, TF32x3)."""
+    circ, factors = product_ref
+    st = large_state
+    _run_mode(st, circ, mode)
+    idx = _sample_indices(st.D, seed=31)
+    got = _gather(st, idx)
+    ref = np.ones(idx.size, dtype=np.complex128)
+    for f, dg in zip(factors, _digits(idx, circ.dims)):
+        ref *= f[dg]
+    err = np.abs(got - ref)
+    assert float(err.max()) <= 1e-5, f"{mode}: max |d amp| = {err.max():.3e}"
+    rel_l2 = float(np.sum(err ** 2) / np.sum(np.abs(ref) ** 2))
+    assert rel_l2 <= 1e-6, f"{mode}: sampled relative squared error {rel_l2:.3e}"
+    big = np.abs(ref) >= 1e-3 * np.abs(ref).max()
+    worst = float(np.max(err[big] / np.abs(ref[big])))
+    assert worst <= 1e-4, f"{mode}: worst relative error {worst:.3e}"
+    assert abs(st.norm() - 1.0) < 1e-5
+
+
+@pytest.mark.parametrize("mode", LARGE_MODES)
+def test_config2_full_size_ghz(qb, gen, large_state, mode):
+    """Mixed-radix GHZ on the 26 wires of the large workload, rooted at the
+    qubit wire 0: amplitude 1/sqrt(2) at index 0 and at sum_t b_t (the last
+    basis state whose digits are all 1), zero at every other sampled index."""
+    st = large_state
+    dims = gen.config2_circuit().dims
+    assert dims[0] == 2
+    circ = gen.ghz_circuit(dims, root=0)
+    _run_mode(st, circ, mode)
+    strides = np.cumprod((1,) + dims[:-1]).astype(np.int64)
+    ones = int(strides.sum())
+    idx = _sample_indices(st.D, seed=32, extra=(0, ones, ones - 1, ones + 1))
+    got = _gather(st, idx)
+    ref = np.zeros(idx.size, dtype=np.complex128)
+    ref[np.searchsorted(idx, 0)] = 2 ** -0.5
+    ref[np.searchsorted(idx, ones)] = 2 ** -0.5
+    err = np.abs(got - ref)
+    assert float(err.max()) <= 1e-6, f"{mode}: max |d amp| = {err.max():.3e} at {idx[np.argmax(err)]}"
+    assert abs(st.norm() - 1.0) < 1e-6
