@@ -905,6 +905,8 @@ def run_gpu(args):
     else:
         fuse = args.fuse if args.fuse != "off" else False
         fopts = {"max_tile_amps": args.tile} if fuse == "tile" and args.tile else {}
+        if fuse and args.block_dim:
+            fopts["block_dim"] = args.block_dim
 
     def step():
         st.reset()
@@ -1098,7 +1100,8 @@ def main(argv=None):
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64",
                     help="precision of the profiler cases (the bench line itself is complex64; complex128 is "
                          "reported under benchmark_circuit)")
-    ap.add_argument("--block-dim", type=int, default=0, help="largest composed block (profiler cases)")
+    ap.add_argument("--block-dim", type=int, default=0,
+                    help="largest composed block with --fuse tile|block (0 = library default)")
     ap.add_argument("--ncu-workload", choices=["benchmark", "prefix"], default="benchmark",
                     help="profiler case: the 12-qubit + 8-qutrit benchmark circuit, or the 20-wire prefix of the "
                          "large workload (17,915,904 amplitudes, Haar gates)")

@@ -545,6 +545,20 @@ qd_status qd_plan_gate(const int32_t* dims, int32_t n, int32_t prec, const int32
                        int32_t k, const double* U, const int32_t* ctrl_wires,
                        const int32_t* ctrl_vals, int32_t n_ctrl, qd_plan_info* out);
 
+/* Testing hook of the bounded waits in the tensor-core block kernel (complex64
+ * blocks of 17..64 dimensions: qd_apply_multi, QD_FUSE_BLOCK passes, deferred
+ * fusion).  The paper has no counterpart; it exists so that the timeout path
+ * can be exercised without a GPU fault.  Every mbarrier wait of that kernel
+ * gives up after spin_limit polls (0 = the default, 2^26); the kernel then
+ * records QD_ERR_TIMEOUT in its status word, issues no further work, writes
+ * no output, releases its tensor memory and returns, and the next readout
+ * of the state (qd_norm, qd_probabilities, ...) returns QD_ERR_TIMEOUT.
+ * stall_producers != 0 makes the kernel's producer warps publish nothing, so
+ * the first waits run out and the pass leaves the state as it was.  The
+ * setting is process-wide and applies to launches issued after the call;
+ * (0, 0) restores the defaults.  Always QD_OK. */
+qd_status qd_test_set_tc_wait(uint32_t spin_limit, int32_t stall_producers);
+
 /* Host self-test of the index arithmetic (division by invariant integers
  * and the class enumeration) against plain integer division on
  * `trials` random cases.  QD_OK if every case agrees. */

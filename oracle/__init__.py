@@ -121,6 +121,24 @@ def run_circuit(circ, psi0: Optional[np.ndarray] = None, nthreads: int = 1,
     return psi
 
 
+class _Gate:
+    """Plain gate record (what :func:`apply_gate` reads), picklable."""
+
+    def __init__(self, wires, U, controls, values, name):
+        self.wires, self.U, self.controls, self.values, self.name = wires, U, controls, values, name
+
+
+class _Circuit:
+    def __init__(self, dims, gates):
+        self.dims, self.gates = dims, gates
+
+
+def _plain(circ) -> _Circuit:
+    return _Circuit(tuple(int(d) for d in circ.dims),
+                    [_Gate(tuple(g.wires), np.asarray(g.U), tuple(g.controls), tuple(g.values),
+                           getattr(g, "name", "U")) for g in circ.gates])
+
+
 def _run_one(circ) -> np.ndarray:
     return run_circuit(circ, nthreads=1)
 
@@ -133,7 +151,7 @@ def run_circuits(circs, workers: Optional[int] = None) -> list:
     import concurrent.futures as cf
     import multiprocessing as mp
 
-    circs = list(circs)
+    circs = [_plain(c) for c in circs]  # only what the oracle reads crosses the process boundary
     workers = workers or max(1, os.cpu_count() or 1)
     if workers == 1 or len(circs) <= 1:
         return [_run_one(c) for c in circs]

@@ -116,6 +116,7 @@ _SIGS = {
     "qd_plan_gate": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _f64p,
                                       _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(qd_plan_info)]),
     "qd_selftest_host": (ctypes.c_int32, [ctypes.c_int32]),
+    "qd_test_set_tc_wait": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_int32]),
     "qd_batch_create": (ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
     "qd_batch_run": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_circuit), ctypes.c_int32, ctypes.POINTER(qd_batch_opts)]),
     "qd_batch_relaunch": (ctypes.c_int32, [_vp]),
@@ -332,6 +333,12 @@ def qd_plan_gate(dims, prec, wires, U, ctrl_wires=None, ctrl_vals=None) -> dict:
     _check(_lib.qd_plan_gate(_p(d, _i32p), len(d), prec, _p(w, _i32p), len(w), _p(_mat(U), _f64p), cw, cv, n,
                              ctypes.byref(info)), "qd_plan_gate")
     return {f: getattr(info, f) for f, _ in qd_plan_info._fields_}
+
+
+def qd_test_set_tc_wait(spin_limit: int = 0, stall_producers: bool = False) -> None:
+    """Testing hook: polls per bounded wait of the tensor-core block kernel (0 = default)
+    and whether its producers publish nothing (so that its waits run out)."""
+    _check(_lib.qd_test_set_tc_wait(int(spin_limit), 1 if stall_producers else 0), "qd_test_set_tc_wait")
 
 
 def qd_selftest_host(trials: int = 200) -> None:

@@ -67,6 +67,8 @@ struct TcArgs {
     uint64_t off[64];
     int32_t* status;      // set to QD_ERR_TIMEOUT on a bounded-wait timeout
     int32_t renorm;       // the block is unitary: give each output class its input's 2-norm
+    uint32_t spin_limit;  // polls of every bounded mbarrier wait
+    int32_t stall;        // testing: the producers publish nothing, so the first waits run out
 };
 
 
@@ -209,13 +211,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             for (uint64_t chunk = blockIdx.x; chunk < n_chunks; chunk += gs, ++i) {
                 const int st = i & 1;
                 if (i >= 2) {
-                    if (!mbar_wait(smem_u32(&mbar_dfree[st]), ph_df[st])) {
+                    if (!mbar_wait(smem_u32(&mbar_dfree[st]), ph_df[st], a.spin_limit)) {
                         atomicExch(&abort_flag, 1);
                         break;
                     }
                     ph_df[st] ^= 1u;
                 }
-                if (!mbar_wait(smem_u32(&mbar_full[st]), ph_full[st])) {
+                if (!mbar_wait(smem_u32(&mbar_full[st]), ph_full[st], a.spin_limit)) {
                     atomicExch(&abort_flag, 1);
                     break;
                 }
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             // before the tensor memory is released: every committed group has
             // completed (already true on the normal path; bounded on abort)
             for (int t = 0; t < 2; ++t)
-                if (issued[t] > 0) mbar_wait(smem_u32(&mbar_mma[t]), (uint32_t)((issued[t] - 1) & 1));
+                if (issued[t] > 0) mbar_wait(smem_u32(&mbar_mma[t]), (uint32_t)((issued[t] - 1) & 1), a.spin_limit);
         }
         __syncwarp();
     } else if (warp < PW) {
@@ -290,7 +292,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             const int st = i & 1;
             if (chunk + gs < n_chunks) load(nxt, chunk + gs);
             if (i >= 2) {
-                bool bad = !mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
+                bool bad = !mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st], a.spin_limit);
                 ph_mma[st] ^= 1u;
                 if (__any_sync(0xffffffffu, bad)) return false;  // the whole warp leaves together
             }
@@ -343,8 +345,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             return true;
         };
         float2 xa[MPT], xb[MPT];
-        uint64_t chunk = blockIdx.x;
-        load(xa, chunk);
+        uint64_t chunk = a.stall ? n_chunks : blockIdx.x;  // stalled: no load, no arrival
+        if (chunk < n_chunks) load(xa, chunk);
         for (int i = 0; chunk < n_chunks;) {
             if (!step(xa, xb, i, chunk)) break;
             chunk += gs;
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             const int st = i & 1;
             // wait (bounded) for this chunk's accumulator; the barrier also
             // means every consumer is done reading Y of the previous chunk
-            const bool timed_out = !mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st]);
+            const bool timed_out = !mbar_wait(smem_u32(&mbar_mma[st]), ph_mma[st], a.spin_limit);
             ph_mma[st] ^= 1u;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (consumer_sync_or<kCons>(timed_out)) {
@@ -451,6 +453,11 @@ __device__ int32_t g_tc_status;
 }  // namespace
 
 size_t block_tc_operand_bytes() { return 2 * (size_t)kABytes; }  // the larger of the two modes
+
+// Bounded waits of the tensor-core block kernel: polls per wait, and the
+// testing switch that keeps its producers from publishing (qd_test_set_tc_wait).
+static uint32_t g_tc_spin_limit = kSpinLimit;
+static int32_t g_tc_stall = 0;
 
 int32_t* tc_status_ptr() {
     static int32_t* ptr[64] = {nullptr};
@@ -592,6 +599,8 @@ cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool re
     for (int r = 0; r < 64; ++r) a.off[r] = r < P ? off[r] : 0;
     a.status = status;
     a.renorm = renorm ? 1 : 0;
+    a.spin_limit = g_tc_spin_limit;
+    a.stall = g_tc_stall;
     const uint64_t chunks = (n_classes + kTcN - 1) / kTcN;
     cudaError_t e = tc_mode == QD_TC_BF16X3 ? launch_tc_mode<1>(a, chunks, sm_count, s)
                                             : launch_tc_mode<0>(a, chunks, sm_count, s);
@@ -601,3 +610,9 @@ cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool re
 }
 
 }  // namespace qd
+
+extern "C" qd_status qd_test_set_tc_wait(uint32_t spin_limit, int32_t stall_producers) {
+    qd::g_tc_spin_limit = spin_limit == 0 ? qd::kSpinLimit : spin_limit;
+    qd::g_tc_stall = stall_producers ? 1 : 0;
+    return QD_OK;
+}

@@ -15,7 +15,7 @@ namespace {
 constexpr int kTcN = 64;   // MMA N: classes per chunk (block kernel) or outputs (tile kernel)
 constexpr int kTcK = 128;  // real K of a 64-dimensional block (64 members x re/im)
 constexpr int kTcM = 128;  // MMA M
-constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier polls
+constexpr uint32_t kSpinLimit = 1u << 26;  // bounded mbarrier polls (default)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -114,8 +114,8 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
           "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_t limit = kSpinLimit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred P;\n\t"

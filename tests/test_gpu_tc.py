@@ -197,3 +197,34 @@ def test_block_mode_config2_prefix(qb, config2_prefix, tc_mode):
     got = st.raw()
     st.close()
     assert_close(got, ref, qb.QD_C64, f"config2 prefix, block mode {tc_mode}")
+
+
+def test_tc_wait_timeout_is_reported_and_the_state_recovers(qb, gen):
+    """The timeout path of the tensor-core block kernel, without a GPU fault:
+    with its producers kept from publishing and a short poll limit, every
+    CTA's first bounded wait runs out; the kernel writes nothing, releases its
+    tensor memory and returns, and the next readout reports QD_ERR_TIMEOUT.
+    The state is unchanged, and the same gate applied afterwards with the
+    default limits matches the oracle."""
+    rng = np.random.Generator(np.random.PCG64(41))
+    dims = (2, 2, 2, 2, 2, 3, 3, 2, 2, 3, 2, 2)  # 5 qubit wires form a 32-dimensional gate
+    psi0 = gen.random_state(int(np.prod(dims)), rng)
+    g = gen.Gate((0, 1, 2, 3, 4), gen.haar(32, rng))
+    st = qb.State(dims, prec=qb.QD_C64)
+    st.set_fusion(1, "tf32x3")
+    st.set_amplitudes(psi0)
+    before = st.raw().copy()
+    try:
+        qb.qd_test_set_tc_wait(1 << 12, stall_producers=True)
+        st.apply(g)
+        with pytest.raises(qb.QuditError) as ei:
+            st.norm()
+        assert ei.value.status == qb.QD_ERR_TIMEOUT, ei.value
+    finally:
+        qb.qd_test_set_tc_wait(0, stall_producers=False)
+    assert np.array_equal(st.raw(), before)  # the stalled pass wrote nothing
+    st.apply(g)
+    got = st.amplitudes()
+    assert abs(st.norm() - 1.0) < 1e-5
+    st.close()
+    assert_close(got, oracle.apply_gate(dims, before.astype(np.complex128), g), qb.QD_C64, "after a timeout")
