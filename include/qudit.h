@@ -112,7 +112,25 @@ qd_status qd_state_get_amplitudes(qd_state* st, double* host_interleaved);
  * to host memory of `bytes` bytes.  Synchronous. */
 qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes);
 
+/* Data movement of the wire-swap exchange between the shards of a state
+ * partitioned over several GPUs by its most significant wires (the paper
+ * names distributed execution as future work, section "Conclusion").  With
+ * lo = b_wire, d = d_wire and hi = D / (lo d), amplitude (h d + y) lo + l of
+ * the state is amplitude (y hi + h) lo + l of the moved order: `wire`
+ * becomes the most significant digit and the other wires keep their order,
+ * so the d blocks that go to d different shards are contiguous.
+ * qd_state_wire_to_top writes the moved order to dev_out; qd_state_wire_from_top
+ * sets the state from dev_in holding the moved order (as
+ * qd_state_set_amplitudes does: queued gates are dropped).  The device
+ * buffer holds D amplitudes of the state's precision, is 16-byte aligned,
+ * owned by the caller and must not overlap the state.  Asynchronous on the
+ * state's stream.  QD_ERR_ARG for a NULL, misaligned or overlapping buffer
+ * or a wire out of range. */
+qd_status qd_state_wire_to_top(qd_state* st, int32_t wire, void* dev_out);
+qd_status qd_state_wire_from_top(qd_state* st, int32_t wire, const void* dev_in);
+
 /* ------------------------------------------------------------------------
+ * Gates./* ------------------------------------------------------------------------
  * Gates.
  * --------------------------------------------------------------------- */
 

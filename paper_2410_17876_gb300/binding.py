@@ -117,6 +117,8 @@ _SIGS = {
                                       _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(qd_plan_info)]),
     "qd_selftest_host": (ctypes.c_int32, [ctypes.c_int32]),
     "qd_test_set_tc_wait": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_int32]),
+    "qd_state_wire_to_top": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "qd_state_wire_from_top": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "qd_batch_create": (ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
     "qd_batch_run": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_circuit), ctypes.c_int32, ctypes.POINTER(qd_batch_opts)]),
     "qd_batch_relaunch": (ctypes.c_int32, [_vp]),
@@ -245,6 +247,14 @@ def qd_state_get_raw(st: int, out: Optional[np.ndarray] = None) -> np.ndarray:
         out = np.empty(D, dtype=dt)
     _check(_lib.qd_state_get_raw(_vp(st), _vp(out.ctypes.data), out.nbytes), "qd_state_get_raw")
     return out
+
+
+def qd_state_wire_to_top(st: int, wire: int, dev_out: int) -> None:
+    _check(_lib.qd_state_wire_to_top(_vp(st), int(wire), ctypes.c_void_p(dev_out)), "qd_state_wire_to_top")
+
+
+def qd_state_wire_from_top(st: int, wire: int, dev_in: int) -> None:
+    _check(_lib.qd_state_wire_from_top(_vp(st), int(wire), ctypes.c_void_p(dev_in)), "qd_state_wire_from_top")
 
 
 def qd_apply_gate(st: int, target: int, U) -> None:

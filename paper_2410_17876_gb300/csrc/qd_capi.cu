@@ -813,6 +813,45 @@ qd_status qd_state_get_amplitudes(qd_state* st, double* host) {
     QD_GUARD_END
 }
 
+static qd_status wire_move_args(qd_state* st, int32_t wire, const void* buf, int64_t& lo, int64_t& d, int64_t& hi) {
+    if (!st || !buf) return fail(QD_ERR_ARG, "state or device buffer is NULL");
+    if (wire < 0 || wire >= st->L.n) return fail(QD_ERR_ARG, "wire %d out of range [0, %d)", wire, st->L.n);
+    const uintptr_t b = reinterpret_cast<uintptr_t>(buf), p = reinterpret_cast<uintptr_t>(st->psi);
+    if (b % 16 != 0) return fail(QD_ERR_ARG, "device buffer is not 16-byte aligned");
+    if (b < p + st->bytes && p < b + st->bytes) return fail(QD_ERR_ARG, "device buffer overlaps the state");
+    lo = st->L.b[wire];
+    d = st->L.dims[wire];
+    hi = st->L.D / (lo * d);
+    return QD_OK;
+}
+
+qd_status qd_state_wire_to_top(qd_state* st, int32_t wire, void* dev_out) {
+    QD_GUARD_BEGIN
+    int64_t lo, d, hi;
+    qd_status rc = wire_move_args(st, wire, dev_out, lo, d, hi);
+    if (rc != QD_OK) return rc;
+    QD_MATERIALIZE(st);
+    cudaError_t e = st->prec == QD_C64 ? launch_wire_move<float>(st->psi, dev_out, lo, d, hi, true, st->stream)
+                                       : launch_wire_move<double>(st->psi, dev_out, lo, d, hi, true, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wire move kernel");
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_wire_from_top(qd_state* st, int32_t wire, const void* dev_in) {
+    QD_GUARD_BEGIN
+    int64_t lo, d, hi;
+    qd_status rc = wire_move_args(st, wire, dev_in, lo, d, hi);
+    if (rc != QD_OK) return rc;
+    drop_pending(st);  // the state is overwritten, as by qd_state_set_amplitudes
+    if (st->lazy) lazy_reset(*st->lazy, st->L);
+    cudaError_t e = st->prec == QD_C64 ? launch_wire_move<float>(dev_in, st->psi, lo, d, hi, false, st->stream)
+                                       : launch_wire_move<double>(dev_in, st->psi, lo, d, hi, false, st->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "wire move kernel");
+    return QD_OK;
+    QD_GUARD_END
+}
+
 qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");

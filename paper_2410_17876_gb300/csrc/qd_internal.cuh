@@ -181,6 +181,13 @@ constexpr int kTcMinP = 17;  // complex64 blocks of at least this dimension go t
 
 int reduce_blocks(int64_t D);
 
+// Move one wire to the most significant digit (to_top) or back: with lo =
+// b_w, d = d_w, hi = D / (lo d), index (h d + y) lo + l of the state is index
+// (y hi + h) lo + l of the moved copy.  Out of place (src != dst).
+template <typename R>
+cudaError_t launch_wire_move(const void* src, void* dst, int64_t lo, int64_t d, int64_t hi, bool to_top,
+                             cudaStream_t s);
+
 void count_launch(int n = 1);
 
 }  // namespace qd

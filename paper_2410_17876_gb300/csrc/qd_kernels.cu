@@ -369,6 +369,28 @@ __global__ void __launch_bounds__(256) k_narrow(const double* in, int64_t D, typ
     }
 }
 
+// Wire move (the data movement of the wire-swap exchange between shards of a
+// partitioned state): thread -> element e of the moved order
+// (y, h, l) = digits of e over (d, hi, lo), l fastest; the natural index is
+// (h d + y) lo + l.  Consecutive threads touch consecutive l in both
+// layouts, so accesses coalesce in runs of lo.
+template <typename R>
+__global__ void __launch_bounds__(256) k_wire_move(const typename Cplx<R>::T2* __restrict__ src,
+                                                  typename Cplx<R>::T2* __restrict__ dst, uint64_t D,
+                                                  FastDiv lo_div, FastDiv hi_div, uint64_t d, bool to_top) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < D; e += stride) {
+        uint64_t q, l, y, h;
+        lo_div.divmod(e, q, l);
+        hi_div.divmod(q, y, h);
+        const uint64_t nat = (h * d + y) * lo_div.d + l;
+        if (to_top)
+            dst[e] = src[nat];
+        else
+            dst[nat] = src[e];
+    }
+}
+
 int grid_for(int64_t n, int per_block = 256, int cap = 152 * 16) {
     int64_t g = (n + per_block - 1) / per_block;
     if (g < 1) g = 1;
@@ -475,6 +497,19 @@ cudaError_t launch_narrow(const double* in, int64_t D, void* psi, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_wire_move(const void* src, void* dst, int64_t lo, int64_t d, int64_t hi, bool to_top,
+                             cudaStream_t s) {
+    const uint64_t D = (uint64_t)lo * (uint64_t)d * (uint64_t)hi;
+    if (D == 0) return cudaSuccess;
+    using T2 = typename Cplx<R>::T2;
+    k_wire_move<R><<<grid_for((int64_t)D), 256, 0, s>>>(reinterpret_cast<const T2*>(src), reinterpret_cast<T2*>(dst),
+                                                        D, FastDiv((uint64_t)lo), FastDiv((uint64_t)hi), (uint64_t)d,
+                                                        to_top);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // Explicit instantiations.
 #define QD_INST_GATE1(R, DT, VEC) \
     template cudaError_t launch_gate1<R, DT, VEC>(const Gate1Args<R, DT>&, cudaStream_t);
@@ -503,7 +538,8 @@ QD_INST_GATE1_ALL(8)
     template cudaError_t launch_marginal<R>(const void*, const IndexMap&, uint64_t, uint64_t, int,      \
                                             double*, int, double*, cudaStream_t);                       \
     template cudaError_t launch_widen<R>(const void*, int64_t, double*, cudaStream_t);                  \
-    template cudaError_t launch_narrow<R>(const double*, int64_t, void*, cudaStream_t);
+    template cudaError_t launch_narrow<R>(const double*, int64_t, void*, cudaStream_t);                 \
+    template cudaError_t launch_wire_move<R>(const void*, void*, int64_t, int64_t, int64_t, bool, cudaStream_t);
 QD_INST_R(float)
 QD_INST_R(double)
 
