@@ -245,6 +245,7 @@ static void free_state(qd_state* st) {
     }
     delete st->pend;
     delete st->lazy;
+    qd::circuit_cache_free(st->ccache);
     delete st;
 }
 

@@ -2344,6 +2344,90 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
 
 }  // extern "C"
 
+// The last circuit of qd_apply_circuit on a state.  Its key holds
+// everything the built program depends on besides the state itself (fusion
+// settings, every gate's wires, controls and matrix), compared byte for
+// byte.  A key seen for the second time in a row is built whole -- plan,
+// composed blocks, descriptors -- and its descriptors stay on the device;
+// from then on the same circuit only launches.
+struct qd::CircuitCache {
+    std::vector<char> key;
+    bool seen = false, built = false;
+    Program prog;
+    void* dev = nullptr;   // descriptors of prog
+    void* host = nullptr;  // pinned copy they were uploaded from
+    size_t cap = 0;
+    cudaEvent_t done{};    // after the last launch of prog
+    bool ev_live = false;
+};
+
+void qd::circuit_cache_free(CircuitCache* c) {
+    if (!c) return;
+    if (c->ev_live) {
+        cudaEventSynchronize(c->done);
+        cudaEventDestroy(c->done);
+    }
+    if (c->dev) cudaFree(c->dev);
+    if (c->host) cudaFreeHost(c->host);
+    delete c;
+}
+
+static void circuit_key(const FuseCfg& cfg, const std::vector<HGate>& G, std::vector<char>& key) {
+    key.clear();
+    auto put = [&](const void* p, size_t n) {
+        const char* c = static_cast<const char*>(p);
+        key.insert(key.end(), c, c + n);
+    };
+    put(&cfg, sizeof cfg);
+    const size_t n = G.size();
+    put(&n, sizeof n);
+    for (const HGate& h : G) {
+        put(&h.k, sizeof h.k);
+        put(&h.nc, sizeof h.nc);
+        put(h.wires, sizeof(int) * (size_t)h.k);
+        put(h.cw, sizeof(int) * (size_t)h.nc);
+        put(h.cv, sizeof(int) * (size_t)h.nc);
+        put(h.U, sizeof(double) * 2 * (size_t)h.P * (size_t)h.P);
+    }
+}
+
+// Build the whole circuit as one program, upload its descriptors to the
+// cache's own device buffer (after the previous program's launches have
+// finished with it) and mark it built.
+static qd_status cache_build(qd_state* st, CircuitCache& c, const std::vector<HGate>& G, const FuseCfg& cfg) {
+    Program prog;
+    std::vector<PassPlan> passes;
+    plan_passes(st->L, G, cfg, passes);
+    if (st->prec == QD_C64)
+        build_passes<float>(st->L, st->psi, G, cfg, passes, 0, passes.size(), prog);
+    else
+        build_passes<double>(st->L, st->psi, G, cfg, passes, 0, passes.size(), prog);
+    if (c.ev_live) QD_CUDA(cudaEventSynchronize(c.done), "circuit cache reuse");
+    const size_t n = prog.desc.size() > 0 ? prog.desc.size() : 16;
+    if (n > c.cap) {
+        if (c.dev) cudaFree(c.dev);
+        if (c.host) cudaFreeHost(c.host);
+        c.dev = c.host = nullptr;
+        c.cap = 0;
+        cudaError_t e = cudaMalloc(&c.dev, n);
+        if (e == cudaSuccess) e = cudaMallocHost(&c.host, n);
+        if (e != cudaSuccess) return fail(QD_ERR_OOM, "circuit cache (%zu bytes): %s", n, cudaGetErrorString(e));
+        c.cap = n;
+    }
+    if (!prog.desc.empty()) {
+        std::memcpy(c.host, prog.desc.data(), prog.desc.size());
+        QD_CUDA(cudaMemcpyAsync(c.dev, c.host, prog.desc.size(), cudaMemcpyHostToDevice, st->stream),
+                "circuit cache upload");
+    }
+    if (!c.ev_live) {
+        QD_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming), "circuit cache event");
+        c.ev_live = true;
+    }
+    c.prog = std::move(prog);
+    c.built = true;
+    return QD_OK;
+}
+
 qd_status qd::run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates, const double* matrices,
                           const qd_fusion_opts* opts) {
     try {
@@ -2354,6 +2438,23 @@ qd_status qd::run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gat
         const FuseCfg cfg = fuse_cfg(opts, st->prec);
         rc = check_cfg(cfg, st->prec);
         if (rc != QD_OK) return rc;
+        if (!st->ccache) st->ccache = new CircuitCache;
+        CircuitCache& cc = *st->ccache;
+        std::vector<char> key;
+        circuit_key(cfg, G, key);
+        if (cc.seen && key == cc.key) {
+            if (!cc.built) {
+                rc = cache_build(st, cc, G, cfg);
+                if (rc != QD_OK) return rc;
+            }
+            rc = issue(cc.prog, static_cast<const char*>(cc.dev), st->stream);
+            if (rc != QD_OK) return rc;
+            QD_CUDA(cudaEventRecord(cc.done, st->stream), "circuit cache event");
+            return QD_OK;
+        }
+        cc.key.swap(key);
+        cc.seen = true;
+        cc.built = false;
         // Build, upload and launch the passes in segments of 1, 2, 4, ...
         // passes: the host composes the next segment while the GPU runs the
         // previous one.  Two descriptor arenas alternate, so an upload only

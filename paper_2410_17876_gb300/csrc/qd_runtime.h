@@ -80,6 +80,10 @@ qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t
 
 }  // namespace qd
 
+namespace qd {
+struct CircuitCache;
+}
+
 static constexpr int kRingSlots = 8;
 
 struct qd_state {
@@ -104,9 +108,11 @@ struct qd_state {
     int32_t fuse_dim;    // deferred fusion: largest composed block (< 2: off)
     qd::Pending* pend;   // gates queued by deferred fusion
     qd::LazyFrame* lazy; // lazy permutations and phases (NULL: off)
+    qd::CircuitCache* ccache;  // the last circuit of qd_apply_circuit, built once when it repeats
 };
 
 namespace qd {
+void circuit_cache_free(CircuitCache* c);
 qd_status run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates, const double* matrices,
                       const qd_fusion_opts* opts);
 qd_status flush_pending(qd_state* st);

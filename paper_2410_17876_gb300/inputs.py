@@ -70,6 +70,16 @@ class Gate:
         U = np.ascontiguousarray(np.asarray(self.U, dtype=np.complex128))
         object.__setattr__(self, "U", U)
 
+    @classmethod
+    def _trusted(cls, wires: Tuple[int, ...], U: np.ndarray, controls: Tuple[int, ...] = (),
+                 values: Tuple[int, ...] = (), name: str = "U") -> "Gate":
+        """The same gate as ``Gate(...)`` from arguments that already have the
+        normalised types (tuples of ints, a C-contiguous complex128 matrix):
+        the generators build millions of gates, and the conversions dominate."""
+        g = object.__new__(cls)
+        g.__dict__.update(wires=wires, U=U, controls=controls, values=values, name=name)
+        return g
+
 
 @dataclasses.dataclass
 class Circuit:
@@ -184,28 +194,30 @@ def random_mixed_circuit(dims: Sequence[int], depth: int, rng: np.random.Generat
         mats.update(zip(idx.tolist(), haar_batch(d, len(idx), rng)))
     gates: List[Gate] = []
     fixed = {}
+    mk = Gate._trusted
+    tl, kl, k3l, cl, vl, xl = t.tolist(), kind.tolist(), k3.tolist(), craw.tolist(), vu.tolist(), xhalf.tolist()
     for i in range(depth):
-        ti = int(t[i])
+        ti = tl[i]
         d = dims[ti]
-        if kind[i] == 0:
-            gates.append(Gate((ti,), mats[i], name="haar"))
-        elif kind[i] == 1:
-            key = (d, int(k3[i]))
+        if kl[i] == 0:
+            gates.append(mk((ti,), mats[i], name="haar"))
+        elif kl[i] == 1:
+            key = (d, k3l[i])
             if key not in fixed:
                 fixed[key] = (x_plus(d, 1), z_gen(d), fourier(d))[key[1]]
-            gates.append(Gate((ti,), fixed[key], name=("X", "Z", "F")[key[1]]))
+            gates.append(mk((ti,), fixed[key], name=("X", "Z", "F")[key[1]]))
         else:
-            c = int(craw[i])
+            c = cl[i]
             if c >= ti:
                 c += 1
-            v = int(vu[i] * dims[c])
-            if xhalf[i]:
+            v = int(vl[i] * dims[c])
+            if xl[i]:
                 key = (d, "x")
                 if key not in fixed:
                     fixed[key] = x_plus(d, 1)
-                gates.append(Gate((ti,), fixed[key], (c,), (v,), name="CX"))
+                gates.append(mk((ti,), fixed[key], (c,), (v,), name="CX"))
             else:
-                gates.append(Gate((ti,), mats[i], (c,), (v,), name="CU"))
+                gates.append(mk((ti,), mats[i], (c,), (v,), name="CU"))
     return Circuit(dims, gates)
 
 

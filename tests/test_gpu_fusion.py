@@ -168,3 +168,38 @@ def test_tensor_core_tiles_on_benchmark_circuit(qb, gen):
     ref = oracle.run_circuit(circ, nthreads=max(1, oracle.max_threads()))
     assert_close(got, ref, qb.QD_C64, "benchmark circuit, tensor-core tiles")
     assert abs(nrm - 1.0) < 1e-5
+
+
+def test_repeated_circuit_is_built_once_and_stays_exact(qb, gen):
+    """A gate list repeated on the same state is planned, composed and
+    uploaded once (the second call) and only launched afterwards: every call
+    gives the same bits as the first, and changing one matrix entry, the
+    fusion settings or the gate order is seen as a different circuit."""
+    import oracle
+
+    rng = np.random.Generator(np.random.PCG64(515))
+    dims = (2, 3, 2, 2, 3, 2, 2, 2, 3, 2, 2, 2)
+    c1 = gen.random_mixed_circuit(dims, 120, rng)
+    c2 = gen.Circuit(dims, list(c1.gates))
+    g = c2.gates[7]
+    U = g.U.copy()
+    U[0, 0] *= -1.0  # no longer unitary, still a valid gate
+    c2.gates[7] = gen.Gate(g.wires, U, g.controls, g.values)
+    st = qb.State(dims, prec=qb.QD_C64)
+    outs = []
+    for c in (c1, c1, c1, c1, c2, c1, c2, c2, c2):
+        st.reset()
+        st.run(c, fuse="tile")
+        outs.append(st.raw().copy())
+    st.reset()
+    st.run(c1, fuse="tile", block_dim=4)
+    other_opts = st.raw().copy()
+    st.close()
+    for i in (1, 2, 3, 5):
+        assert np.array_equal(outs[i], outs[0])
+    for i in (6, 7, 8):
+        assert np.array_equal(outs[i], outs[4])
+    assert not np.array_equal(outs[4], outs[0])
+    assert_close(outs[0], oracle.run_circuit(c1), qb.QD_C64, "repeated circuit")
+    assert_close(outs[8], oracle.run_circuit(c2), qb.QD_C64, "changed matrix")
+    assert_close(other_opts, oracle.run_circuit(c1), qb.QD_C64, "other fusion settings")

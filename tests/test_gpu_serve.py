@@ -138,3 +138,32 @@ def test_request_larger_than_budget_is_rejected(qb, gen):
         qb.qd_server_submit(s, big)
     assert ei.value.status == qb.QD_ERR_UNSUPPORTED
     qb.qd_server_destroy(s)
+
+
+def test_large_requests_match_oracle_and_closed_forms(qb, gen):
+    """Requests above 2^20 amplitudes (the slot-stream path): two random
+    mixed circuits against the oracle, and a GHZ circuit on 15,925,248
+    amplitudes against its closed form, served together with small ones."""
+    import oracle
+
+    rng = np.random.Generator(np.random.PCG64(808))
+    big = [gen.random_mixed_circuit((2, 3, 4, 2, 3, 4, 2, 2, 3, 2, 2, 4, 3, 4), 60, rng),  # 1,327,104 amplitudes
+           gen.random_mixed_circuit((4, 3, 2, 2, 4, 3, 2, 4, 3, 2, 4, 2, 4, 3, 3), 50, rng)]  # 7,962,624
+    ghz_dims = (2, 2, 3, 4, 2, 3, 4, 4, 2, 3, 2, 4, 3, 2, 2, 2, 3)                    # 15,925,248
+    ghz = gen.ghz_circuit(ghz_dims, root=0)
+    small = [gen.random_mixed_circuit((2, 3, 2, 3), 80, rng) for _ in range(8)]
+    s = qb.qd_server_create(qb.QD_C64, hbm_budget_bytes=4 << 30)
+    ids = [qb.qd_server_submit(s, c, keep_state=True) for c in big + [ghz] + small]
+    qb.qd_server_drain(s, 600)
+    for i, c in enumerate(big):
+        got = qb.qd_server_get_amplitudes(s, ids[i], c.D)
+        assert_close(got, oracle.run_circuit(c, nthreads=oracle.max_threads()), qb.QD_C64, f"served dims={c.dims}")
+    got = qb.qd_server_get_amplitudes(s, ids[len(big)], ghz.D)
+    ones = int(np.sum(np.cumprod((1,) + ghz_dims[:-1])))
+    ref = np.zeros(ghz.D, dtype=np.complex128)
+    ref[0] = ref[ones] = 2 ** -0.5
+    assert float(np.max(np.abs(got - ref))) <= 1e-6
+    for j, c in enumerate(small):
+        got = qb.qd_server_get_amplitudes(s, ids[len(big) + 1 + j], c.D)
+        assert_close(got, oracle.run_circuit(c), qb.QD_C64, "small served request")
+    qb.qd_server_destroy(s)
