@@ -598,31 +598,41 @@ def measure_many_controls(qb, gen, torch, stream, reps=10):
     return out
 
 
-def measure_batched(qb, gen, torch, stream):
-    """8192 independent circuits (widths 4-12, dims {2,3,4,5}, depths 20-300), complex64,
-    captured in a CUDA graph: build+first run wall time, then relaunches timed with events."""
+def measure_batched(qb, gen, torch, stream, reps=3):
+    """8192 independent circuits (widths 4-12, dims {2,3,4,5}, depths 20-300),
+    complex64, captured in a CUDA graph, through each path of the larger
+    circuits: the device-side layer queue (one launch per pass position for
+    all of them) and one program per circuit on auxiliary streams.  Build
+    and first run: wall time; relaunches: CUDA events."""
     t0 = time.perf_counter()
     circs = gen.config3_batch()
     t_gen = time.perf_counter() - t0
     upd = sum(circuit_updates(c) for c in circs)
-    b = qb.qd_batch_create(qb.QD_C64, stream.cuda_stream)
-    t0 = time.perf_counter()
-    qb.qd_batch_run(b, circs, use_graph=True)
-    qb.qd_batch_synchronize(b)
-    t_first = time.perf_counter() - t0
-    reps = 3
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        qb.qd_batch_relaunch(b)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3 / reps
-    norms = qb.qd_batch_norms(b, len(circs))
-    qb.qd_batch_destroy(b)
-    return {"workload": "8192 circuits, widths 4-12, dims {2,3,4,5}, depths 20-300, complex64",
-            "circuits_per_s": len(circs) / t, "value": upd / t, "unit": UNIT, "seconds_per_batch": t,
-            "first_run_wall_s": t_first, "generate_s": t_gen, "max_norm_error": float(np.max(np.abs(norms - 1.0)))}
+    out = {"workload": "8192 circuits, widths 4-12, dims {2,3,4,5}, depths 20-300, complex64", "generate_s": t_gen}
+    for name, path in (("layer_queue", qb.QD_BATCH_LAYERS), ("stream_programs", qb.QD_BATCH_STREAMS)):
+        b = qb.qd_batch_create(qb.QD_C64, stream.cuda_stream)
+        t0 = time.perf_counter()
+        n0 = qb.qd_launch_count()
+        qb.qd_batch_run(b, circs, use_graph=True, path=path)
+        qb.qd_batch_synchronize(b)
+        t_first = time.perf_counter() - t0
+        launches = qb.qd_launch_count() - n0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            qb.qd_batch_relaunch(b)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / reps
+        norms = qb.qd_batch_norms(b, len(circs))
+        qb.qd_batch_destroy(b)
+        out[name] = {"circuits_per_s": len(circs) / t, "value": upd / t, "unit": UNIT, "seconds_per_batch": t,
+                     "first_run_wall_s": t_first, "launches_per_batch": launches,
+                     "max_norm_error": float(np.max(np.abs(norms - 1.0)))}
+        torch.cuda.empty_cache()
+    best = max(("layer_queue", "stream_programs"), key=lambda k: out[k]["circuits_per_s"])
+    out.update(circuits_per_s=out[best]["circuits_per_s"], value=out[best]["value"], unit=UNIT, best_path=best)
+    return out
 
 
 def measure_serving(qb, gen, torch, trace, plain_budget_s=6.0, capacity_s=2.0, in_flight=(16, 64, 256, 1024)):

@@ -370,7 +370,9 @@ typedef struct qd_batch_opts {
     int32_t small_max_amps;  /* 0 = default (8192 complex64, 4096 complex128) */
     int32_t n_streams;       /* 0 = default (8), at most 64 */
     int32_t use_graph;       /* capture the run in a CUDA graph */
-    int32_t reserved;
+    int32_t path;            /* 0 (default): circuits whose passes are all tile passes run through the
+                                device-side layer queue; 1: every such circuit as its own program on
+                                the auxiliary streams */
     qd_fusion_opts fusion;   /* for circuits outside the one-CTA path */
 } qd_batch_opts;
 

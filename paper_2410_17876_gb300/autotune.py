@@ -122,12 +122,13 @@ def tune_circuit(state, circuit, retune: bool = False, reps: int = 3, budget_s: 
 
 def tune_batch(circuits, prec: int, stream, retune: bool = False, sample: int = 512,
                small_caps: Sequence[int] = (2048, 4096, 8192), block_dims: Sequence[int] = (4, 8, 16),
-               reps: int = 2, budget_s: float = 30.0) -> dict:
-    """Best one-CTA threshold and block width for a batch of circuits, timed on
-    a seeded sample of the batch (graph relaunches)."""
+               paths: Sequence[int] = (0, 1), reps: int = 2, budget_s: float = 30.0) -> dict:
+    """Best one-CTA threshold, block width and path (0: device-side layer
+    queue, 1: one program per circuit on auxiliary streams) for a batch of
+    circuits, timed on a seeded sample of the batch (graph relaunches)."""
     from . import binding as qb
 
-    key = f"{gpu_name()}|batch|prec{prec}|n{len(circuits)}"
+    key = f"{gpu_name()}|batch2|prec{prec}|n{len(circuits)}"
     cache = _load()
     if not retune and key in cache:
         return cache[key]
@@ -135,14 +136,14 @@ def tune_batch(circuits, prec: int, stream, retune: bool = False, sample: int = 
     idx = rng.permutation(len(circuits))[:min(sample, len(circuits))]
     subset = [circuits[int(i)] for i in sorted(idx)]
     b = qb.qd_batch_create(prec, stream.cuda_stream)
-    cands = [(s, bd) for s in small_caps for bd in block_dims]
+    cands = [(s, bd, p) for p in paths for s in small_caps for bd in block_dims]
     if prec == qb.QD_C128:
         cands = [c for c in cands if c[0] <= 4096]
     state = {"c": None}
 
     def run(c):
         if state["c"] != c:
-            qb.qd_batch_run(b, subset, small_max_amps=c[0], block_dim=c[1], use_graph=True)
+            qb.qd_batch_run(b, subset, small_max_amps=c[0], block_dim=c[1], use_graph=True, path=c[2])
             state["c"] = c
         else:
             qb.qd_batch_relaunch(b)
@@ -150,8 +151,8 @@ def tune_batch(circuits, prec: int, stream, retune: bool = False, sample: int = 
     table = time_candidates(run, cands, stream, reps=reps, budget_s=budget_s)
     qb.qd_batch_destroy(b)
     best = min(table, key=table.get)
-    entry = {"small_max_amps": best[0], "block_dim": best[1], "seconds_sample": table[best],
-             "table": {f"{s}/{bd}": v for (s, bd), v in table.items()}}
+    entry = {"small_max_amps": best[0], "block_dim": best[1], "path": best[2], "seconds_sample": table[best],
+             "table": {f"{s}/{bd}/{p}": v for (s, bd, p), v in table.items()}}
     cache[key] = entry
     _save(cache)
     return entry

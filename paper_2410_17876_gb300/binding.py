@@ -63,7 +63,7 @@ class qd_circuit(ctypes.Structure):
 
 class qd_batch_opts(ctypes.Structure):
     _fields_ = [("small_max_amps", ctypes.c_int32), ("n_streams", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("fusion", qd_fusion_opts)]
+                ("path", ctypes.c_int32), ("fusion", qd_fusion_opts)]
 
 
 class qd_server_opts(ctypes.Structure):
@@ -499,8 +499,12 @@ def qd_batch_create(prec: int = QD_C64, stream: int = 0) -> int:
     return out.value
 
 
+QD_BATCH_LAYERS = 0   # eligible circuits through the device-side layer queue (default)
+QD_BATCH_STREAMS = 1  # one program per circuit on auxiliary streams
+
+
 def qd_batch_run(b: int, circuits, small_max_amps=0, n_streams=0, use_graph=False, fuse=True,
-                 max_tile_amps=0, min_gates=0, min_row=0, block_dim=0) -> None:
+                 max_tile_amps=0, min_gates=0, min_row=0, block_dim=0, path=QD_BATCH_LAYERS) -> None:
     """Run independent circuits (each from |0...0>) as one batch; asynchronous."""
     n = len(circuits)
     arr = (qd_circuit * max(1, n))()
@@ -514,7 +518,7 @@ def qd_batch_run(b: int, circuits, small_max_amps=0, n_streams=0, use_graph=Fals
         arr[i].n_gates = len(c.gates)
         arr[i].gates = descs
         arr[i].matrices = _p(m, _f64p)
-    opts = qd_batch_opts(int(small_max_amps), int(n_streams), 1 if use_graph else 0, 0,
+    opts = qd_batch_opts(int(small_max_amps), int(n_streams), 1 if use_graph else 0, int(path),
                          qd_fusion_opts(QD_FUSE_TILE if fuse else QD_FUSE_OFF, int(max_tile_amps), int(min_gates),
                                         int(min_row), int(block_dim), 0))
     _check(_lib.qd_batch_run(_vp(b), arr, n, ctypes.byref(opts)), "qd_batch_run")

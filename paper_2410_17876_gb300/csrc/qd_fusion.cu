@@ -141,6 +141,29 @@ struct FusedArgs {
     const char* desc_base;   // the program's descriptors (tensor-core operands)
 };
 
+// A tile pass of one circuit in a batch's device-side layer queue: the
+// fields of FusedArgs that a tile needs, with the descriptors given as byte
+// offsets into the batch's descriptor blob and at most kLayerMaxFree wires
+// outside the tile.
+constexpr int kLayerMaxFree = 16;
+template <typename R>
+struct LayerEntry {
+    using T2 = typename Cplx<R>::T2;
+    T2* psi;
+    uint64_t chunks_off, rows_off;
+    int32_t nchunks;
+    uint32_t T, bL, rows;
+    int32_t vec2;
+    FastDiv32 bLdiv;
+    uint64_t ntiles;
+    int32_t nfree;
+    int32_t free_w[kLayerMaxFree];
+    uint32_t free_d[kLayerMaxFree];
+    FastDiv32 free_div[kLayerMaxFree];
+    uint64_t free_b[kLayerMaxFree];
+    uint32_t stage, first_bytes;
+};
+
 
 namespace {
 
@@ -652,9 +675,9 @@ __device__ __forceinline__ bool apply_chunks(typename Cplx<R>::T2* tile, const c
 // cannot move past the next row-offset read (both are shared memory): one
 // load in flight per thread, the fixed cost of a pass.  The caller's next
 // barrier publishes the other threads' pieces.
-template <typename R>
+template <typename R, typename A>
 __device__ __forceinline__ void tile_load_async(typename Cplx<R>::T2* tile, const typename Cplx<R>::T2* g,
-                                                const uint64_t* srow, const FusedArgs<R>& a) {
+                                                const uint64_t* srow, const A& a) {
     constexpr uint32_t kEl = sizeof(typename Cplx<R>::T2);
     const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(tile));
     if (kEl == 16 || a.vec2) {
@@ -676,28 +699,31 @@ __device__ __forceinline__ void tile_load_async(typename Cplx<R>::T2* tile, cons
 
 __host__ __device__ inline size_t fused_rows_bytes(uint32_t rows) { return ((size_t)rows * 8 + 15) & ~(size_t)15; }
 
-template <typename R, int DMAX>
-__global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ FusedArgs<R> a) {
+// One tile of a pass: the row offsets and the first chunk are staged while
+// thread 0 derives the tile's base index and outside digits, the tile is
+// loaded, the pass's chunks are applied, the tile is stored.  `a` is the
+// pass's record (kernel parameters of k_fused_tile, or an entry of a
+// device-side layer queue); chunks / rowoff are its descriptors.
+template <typename R, int DMAX, typename A>
+__device__ __forceinline__ void tile_pass(const A& a, const char* chunks, const uint64_t* rowoff, uint32_t tile_idx,
+                                          unsigned char* smem_raw, int32_t* odig, uint64_t* sbase) {
     using T2 = typename Cplx<R>::T2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* stage = smem_raw;
     uint64_t* srow = reinterpret_cast<uint64_t*>(smem_raw + a.stage);
     T2* tile = reinterpret_cast<T2*>(smem_raw + a.stage + fused_rows_bytes(a.rows));
-    __shared__ int32_t odig[kMaxWires];
-    __shared__ uint64_t sbase;
     {
         // the row offsets and the first chunk arrive together (cp.async)
         // while thread 0 derives the tile's base and outside digits
         const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(srow));
         for (uint32_t r = threadIdx.x; r < a.rows; r += blockDim.x)
-            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s0 + 8u * r), "l"(a.rowoff + r));
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s0 + 8u * r), "l"(rowoff + r));
         const uint32_t d0 = static_cast<uint32_t>(__cvta_generic_to_shared(stage));
         if (a.nchunks > 0)
             for (uint32_t i = threadIdx.x; i < a.first_bytes / 16; i += blockDim.x)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16u * i), "l"(a.chunks + 16u * i));
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 16u * i), "l"(chunks + 16u * i));
     }
     if (threadIdx.x == 0) {
-        uint32_t rem = blockIdx.x;
+        uint32_t rem = tile_idx;
         uint64_t base = 0;
         for (int i = 0; i < a.nfree; ++i) {
             const uint32_t q = a.free_div[i].div(rem);
@@ -706,13 +732,13 @@ __global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ F
             base += (uint64_t)dig * a.free_b[i];
             rem = q;
         }
-        sbase = base;
+        *sbase = base;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    T2* g = a.psi + sbase;
+    T2* g = a.psi + *sbase;
     tile_load_async<R>(tile, g, srow, a);  // published by apply_chunks' first barrier
-    apply_chunks<R, DMAX>(tile, a.chunks, a.nchunks, stage, odig, nullptr, true);
+    apply_chunks<R, DMAX>(tile, chunks, a.nchunks, stage, odig, nullptr, true);
     __syncthreads();
     if (a.vec2) {
         for (uint32_t e = 2 * threadIdx.x; e < a.T; e += 2 * blockDim.x) {
@@ -725,6 +751,45 @@ __global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ F
             const uint32_t r = a.bLdiv.div(e);
             g[srow[r] + (e - r * a.bL)] = tile[e];
         }
+    }
+}
+
+template <typename R, int DMAX>
+__global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ FusedArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int32_t odig[kMaxWires];
+    __shared__ uint64_t sbase;
+    tile_pass<R, DMAX>(a, a.chunks, a.rowoff, blockIdx.x, smem_raw, odig, &sbase);
+}
+
+// Tile passes of many circuits in one launch (batches): the device-side
+// queue of one layer holds, for each circuit with a pass at that position,
+// the pass's record, and prefix[e] = tiles of the entries before e.  The
+// persistent CTAs walk the layer's tiles w = blockIdx.x, + gridDim.x, ...;
+// entry e of tile w is the last with prefix[e] <= w.  The queue is complete
+// before the launch, so no CTA ever waits on another.
+template <typename R, int DMAX>
+__global__ void __launch_bounds__(256, 3) k_fused_layer(const LayerEntry<R>* entries, const uint64_t* prefix,
+                                                         int32_t n, uint64_t total, const char* base) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int32_t odig[kMaxWires];
+    __shared__ uint64_t sbase;
+    __shared__ int32_t s_e;
+    for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
+        if (threadIdx.x == 0) {
+            int lo = 0, hi = n - 1;  // prefix[lo] <= w < prefix[n]
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (prefix[mid] <= w) lo = mid;
+                else hi = mid - 1;
+            }
+            s_e = lo;
+        }
+        __syncthreads();
+        const LayerEntry<R>& E = entries[s_e];
+        tile_pass<R, DMAX>(E, base + E.chunks_off, reinterpret_cast<const uint64_t*>(base + E.rows_off),
+                           (uint32_t)(w - prefix[s_e]), smem_raw, odig, &sbase);
+        __syncthreads();  // the next tile reuses shared memory
     }
 }
 
@@ -850,6 +915,34 @@ cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
         k_fused_tile<R, 3><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
     else
         k_fused_tile<R, 5><<<(unsigned)a.ntiles, 256, fused_smem<R>(a), s>>>(a);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// One layer of a batch's device-side queue: persistent CTAs, three per SM
+// (the occupancy of k_fused_tile), never more than the layer's tiles.
+template <typename R>
+cudaError_t launch_fused_layer(const LayerEntry<R>* entries, const uint64_t* prefix, int32_t n, uint64_t total,
+                               const char* base, int dmax, size_t smem, cudaStream_t s) {
+    if (n <= 0 || total == 0) return cudaSuccess;
+    static int attr_dev = -1, sms = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e = cudaFuncSetAttribute(k_fused_layer<R, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             220 * 1024);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fused_layer<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    const uint64_t cap = (uint64_t)(sms > 0 ? sms : 152) * 3;
+    const unsigned grid = (unsigned)(total < cap ? total : cap);
+    if (dmax <= 3)
+        k_fused_layer<R, 3><<<grid, 256, smem, s>>>(entries, prefix, n, total, base);
+    else
+        k_fused_layer<R, 5><<<grid, 256, smem, s>>>(entries, prefix, n, total, base);
     count_launch();
     return cudaGetLastError();
 }
@@ -1966,6 +2059,62 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
     }
 }
 
+// The passes of one circuit as entries of a batch's layer queue (entry k
+// goes to layer k), when every pass is a tile pass on CUDA cores with at
+// most kLayerMaxFree wires outside its tile; false otherwise (the circuit
+// then runs as its own program).  smem[k]: the dynamic shared memory of
+// entry k; dmax[k]: its largest single-wire dimension.
+template <typename R>
+static bool build_layer_entries(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
+                                const std::vector<PassPlan>& passes, Program& prog,
+                                std::vector<LayerEntry<R>>& out, std::vector<int>& dmax_out,
+                                std::vector<size_t>& smem) {
+    using T2 = typename Cplx<R>::T2;
+    out.clear();
+    dmax_out.clear();
+    smem.clear();
+    for (const PassPlan& p : passes)
+        if (!p.tile || p.block) return false;
+    for (const PassPlan& p : passes) {
+        TileGeom geo;
+        tile_geometry(L, p.smask, cfg.min_row, geo);
+        if (geo.nfree > kLayerMaxFree) return false;
+        std::vector<BlockPlan> blocks;
+        form_blocks(geo, G, p.gates, cfg.block_dim, blocks, false, cfg.runs && sizeof(R) == 4);
+        uint32_t nchunks = 0, stage_bytes = 0, first_bytes = 0;
+        int dmax = 2;
+        bool has_tc = false;
+        const size_t offC = emit_chunks<R>(geo, G, blocks, prog, &nchunks, &dmax, &has_tc, &stage_bytes, &first_bytes);
+        if (has_tc) return false;
+        const size_t offR = prog.put(geo.rowoff.data(), sizeof(uint64_t) * geo.R);
+        LayerEntry<R> e;
+        std::memset(static_cast<void*>(&e), 0, sizeof e);
+        e.psi = reinterpret_cast<T2*>(psi);
+        e.chunks_off = offC;
+        e.rows_off = offR;
+        e.nchunks = (int32_t)nchunks;
+        e.T = (uint32_t)p.T;
+        e.bL = geo.bL;
+        e.rows = geo.R;
+        e.vec2 = (sizeof(R) == 4 && geo.bL % 2 == 0) ? 1 : 0;
+        e.bLdiv.init(geo.bL);
+        e.ntiles = (uint64_t)(L.D / p.T);
+        e.nfree = geo.nfree;
+        for (int i = 0; i < geo.nfree; ++i) {
+            e.free_w[i] = geo.free_w[i];
+            e.free_d[i] = geo.free_d[i];
+            e.free_div[i].init(geo.free_d[i]);
+            e.free_b[i] = geo.free_b[i];
+        }
+        e.stage = stage_bytes;
+        e.first_bytes = first_bytes;
+        out.push_back(e);
+        dmax_out.push_back(dmax);
+        smem.push_back((size_t)stage_bytes + fused_rows_bytes(geo.R) + sizeof(T2) * (size_t)p.T);
+    }
+    return true;
+}
+
 template <typename R>
 void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, const FuseCfg& cfg,
                           bool reset_first, Program& prog) {
@@ -2112,6 +2261,8 @@ struct qd_batch {
     size_t norms_cap;
     double* partials;      // reduction scratch, one block per aux stream
     size_t partials_stride;
+    double* lpartials;     // reduction scratch of the batched norms (layer path)
+    size_t lpartials_cap;  // in doubles
     Arena arena;
     cudaGraph_t graph;
     cudaGraphExec_t graph_exec;
@@ -2140,6 +2291,7 @@ static void batch_free(qd_batch* b) {
     if (b->norms) cudaFree(b->norms);
     if (b->host_norms) cudaFreeHost(b->host_norms);
     if (b->partials) cudaFree(b->partials);
+    if (b->lpartials) cudaFree(b->lpartials);
     b->arena.release();
     delete b;
 }
@@ -2159,6 +2311,10 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
     int nstreams = (opts && opts->n_streams > 0) ? opts->n_streams : 8;
     if (nstreams > 64) nstreams = 64;
     const bool use_graph = opts && opts->use_graph;
+    // 0: circuits whose passes are all tile passes go through the layer queue
+    // (one launch per pass position for all of them); 1: one program per circuit
+    const int path = opts ? opts->path : 0;
+    if (path != 0 && path != 1) return fail(QD_ERR_ARG, "unknown batch path %d", path);
 
     // 1. validate every circuit and lay out the states
     std::vector<Layout> Ls((size_t)n);
@@ -2224,6 +2380,13 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
     uint32_t maxd3 = 1, maxd5 = 1;
     std::vector<Program> big;
     std::vector<int> big_idx;
+    std::vector<std::vector<LayerEntry<R>>> layers;
+    std::vector<int> layer_dmax;
+    std::vector<size_t> layer_smem;
+    std::vector<int> layered;  // circuits on the layer path
+    FuseCfg lcfg = cfg;
+    lcfg.min_gates = 1;  // a pass of one gate stays a tile pass
+    const bool try_layers = path == 0 && cfg.mode == QD_FUSE_TILE;
     for (int i = 0; i < n; ++i) {
         const Layout& L = Ls[i];
         bool fits = L.D <= small_max && (int)Gs[i].size() > 0;
@@ -2248,10 +2411,78 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
         } else {
             Program pg;
             pg.desc.swap(prog.desc);  // share one descriptor buffer: offsets stay global
+            if (try_layers) {
+                std::vector<PassPlan> passes;
+                plan_passes(L, Gs[i], lcfg, passes);
+                std::vector<LayerEntry<R>> ents;
+                std::vector<int> dms;
+                std::vector<size_t> sms;
+                const size_t mark = pg.desc.size();
+                if (build_layer_entries<R>(L, b->states + b->psi_off[i], Gs[i], lcfg, passes, pg, ents, dms, sms)) {
+                    prog.desc.swap(pg.desc);
+                    if (layers.size() < ents.size()) {
+                        layers.resize(ents.size());
+                        layer_dmax.resize(ents.size(), 2);
+                        layer_smem.resize(ents.size(), 0);
+                    }
+                    for (size_t k = 0; k < ents.size(); ++k) {
+                        layers[k].push_back(ents[k]);
+                        layer_dmax[k] = std::max(layer_dmax[k], dms[k]);
+                        layer_smem[k] = std::max(layer_smem[k], sms[k]);
+                    }
+                    layered.push_back(i);
+                    continue;
+                }
+                pg.desc.resize(mark);  // drop the descriptors of the attempt
+            }
             build_program<R>(L, b->states + b->psi_off[i], Gs[i], cfg, true, pg);
             prog.desc.swap(pg.desc);
             big.push_back(std::move(pg));
             big_idx.push_back(i);
+        }
+    }
+    // the layer queue: per layer its entries and the prefix of their tile
+    // counts; per layered circuit a norm / reset record with the prefix of
+    // its reduction blocks and of its reset chunks
+    std::vector<size_t> l_offE(layers.size()), l_offP(layers.size());
+    std::vector<uint64_t> l_total(layers.size());
+    for (size_t k = 0; k < layers.size(); ++k) {
+        std::vector<uint64_t> pre(layers[k].size() + 1, 0);
+        for (size_t e = 0; e < layers[k].size(); ++e) pre[e + 1] = pre[e] + layers[k][e].ntiles;
+        l_total[k] = pre.back();
+        l_offE[k] = prog.put(layers[k].data(), sizeof(LayerEntry<R>) * layers[k].size());
+        l_offP[k] = prog.put(pre.data(), sizeof(uint64_t) * pre.size());
+    }
+    size_t offN = 0, offNB = 0, offNC = 0;
+    uint64_t nblocks_total = 0, nchunks_total = 0;
+    if (!layered.empty()) {
+        std::vector<NormEntry> ne(layered.size());
+        std::vector<uint64_t> pb(layered.size() + 1, 0), pc(layered.size() + 1, 0);
+        for (size_t j = 0; j < layered.size(); ++j) {
+            const int i = layered[j];
+            NormEntry& e = ne[j];
+            std::memset(&e, 0, sizeof e);
+            e.psi = b->states + b->psi_off[i];
+            e.D = b->D[i];
+            e.nb = (uint32_t)reduce_blocks(b->D[i]);
+            e.a16 = 1;  // states are 256-byte aligned
+            e.part_off = pb[j];
+            e.out_index = (uint32_t)i;
+            pb[j + 1] = pb[j] + e.nb;
+            pc[j + 1] = pc[j] + (uint64_t)((b->D[i] + kBasisChunkAmps - 1) / kBasisChunkAmps);
+        }
+        nblocks_total = pb.back();
+        nchunks_total = pc.back();
+        offN = prog.put(ne.data(), sizeof(NormEntry) * ne.size());
+        offNB = prog.put(pb.data(), sizeof(uint64_t) * pb.size());
+        offNC = prog.put(pc.data(), sizeof(uint64_t) * pc.size());
+        if (2 * nblocks_total > b->lpartials_cap) {
+            if (b->lpartials) cudaFree(b->lpartials);
+            b->lpartials = nullptr;
+            b->lpartials_cap = 0;
+            cudaError_t e = cudaMalloc(&b->lpartials, sizeof(double) * 2 * nblocks_total);
+            if (e != cudaSuccess) return fail(QD_ERR_OOM, "batch norm scratch: %s", cudaGetErrorString(e));
+            b->lpartials_cap = 2 * nblocks_total;
         }
     }
     const size_t off3 = small3.empty() ? 0 : prog.put(small3.data(), sizeof(SmallTask) * small3.size());
@@ -2290,6 +2521,18 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
     if (e == cudaSuccess)
         e = launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + off5), (int)small5.size(), 5, maxd5,
                                   b->states, base, b->norms, ws);
+    if (e == cudaSuccess && !layered.empty()) {
+        const NormEntry* ne = reinterpret_cast<const NormEntry*>(base + offN);
+        e = launch_basis_batch<R>(ne, reinterpret_cast<const uint64_t*>(base + offNC), (int32_t)layered.size(),
+                                  nchunks_total, ws);
+        for (size_t k = 0; k < layers.size() && e == cudaSuccess; ++k)
+            e = launch_fused_layer<R>(reinterpret_cast<const LayerEntry<R>*>(base + l_offE[k]),
+                                      reinterpret_cast<const uint64_t*>(base + l_offP[k]), (int32_t)layers[k].size(),
+                                      l_total[k], base, layer_dmax[k], layer_smem[k], ws);
+        if (e == cudaSuccess)
+            e = launch_norm_batch<R>(ne, reinterpret_cast<const uint64_t*>(base + offNB), (int32_t)layered.size(),
+                                     nblocks_total, b->lpartials, b->norms, ws);
+    }
     if (e != cudaSuccess) {
         if (use_graph) {
             cudaGraph_t g;

@@ -181,6 +181,28 @@ constexpr int kTcMinP = 17;  // complex64 blocks of at least this dimension go t
 
 int reduce_blocks(int64_t D);
 
+// Norms of many states in two launches (batches), each state's result the
+// bits launch_norm gives it: nb = reduce_blocks(D) partial blocks starting
+// at partial pair part_off, the sum written to norms[out_index].
+struct NormEntry {
+    const void* psi;
+    int64_t D;
+    uint32_t nb;
+    uint32_t a16;        // complex64 amplitudes 16-byte aligned
+    uint64_t part_off;
+    uint32_t out_index;
+    uint32_t pad_;
+};
+template <typename R>
+cudaError_t launch_norm_batch(const NormEntry* entries, const uint64_t* block_prefix, int32_t n,
+                              uint64_t total_blocks, double* partials, double* norms, cudaStream_t s);
+// Set many states to |0...0> in one launch: chunk_prefix[e] = chunks of
+// kBasisChunkAmps amplitudes before entry e.
+constexpr int64_t kBasisChunkAmps = 1 << 16;
+template <typename R>
+cudaError_t launch_basis_batch(const NormEntry* entries, const uint64_t* chunk_prefix, int32_t n,
+                               uint64_t total_chunks, cudaStream_t s);
+
 // Move one wire to the most significant digit (to_top) or back: with lo =
 // b_w, d = d_w, hi = D / (lo d), index (h d + y) lo + l of the state is index
 // (y hi + h) lo + l of the moved copy.  Out of place (src != dst).

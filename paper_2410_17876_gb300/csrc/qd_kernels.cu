@@ -237,18 +237,26 @@ template <typename T2> __device__ __forceinline__ double prob(const T2& v) {
     return fma(re, re, im * im);
 }
 
+// Partial sum of block `blk` of `nblk` over psi[0, D): grid-stride from
+// blk * blockDim, then the fixed block tree; (s, c) written to out[0..1].
 template <typename R>
-__global__ void __launch_bounds__(256) k_norm_partial(const typename Cplx<R>::T2* psi, int64_t D,
-                                                       double* partials) {
+__device__ __forceinline__ void norm_partial_body(const typename Cplx<R>::T2* psi, int64_t D, uint32_t blk,
+                                                  uint32_t nblk, double* out) {
     CSum acc{0.0, 0.0};
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D; i += stride)
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    for (int64_t i = (int64_t)blk * blockDim.x + threadIdx.x; i < D; i += stride)
         csum_add(acc, prob(psi[i]));
     acc = block_reduce(acc);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = acc.s;
-        partials[2 * blockIdx.x + 1] = acc.c;
+        out[0] = acc.s;
+        out[1] = acc.c;
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_norm_partial(const typename Cplx<R>::T2* psi, int64_t D,
+                                                       double* partials) {
+    norm_partial_body<R>(psi, D, blockIdx.x, gridDim.x, partials + 2 * blockIdx.x);
 }
 
 // Complex64 norm with little binary64 work (binary64 is slow on this part):
@@ -276,11 +284,12 @@ __device__ __forceinline__ void fsum_prob(float& s, float& c, float x, float y) 
 }
 
 template <bool A16>
-__global__ void __launch_bounds__(256) k_norm_partial_c64(const float2* psi, int64_t D, double* partials) {
+__device__ __forceinline__ void norm_partial_c64_body(const float2* psi, int64_t D, uint32_t blk, uint32_t nblk,
+                                                      double* out) {
     CSum acc{0.0, 0.0};
     const int64_t pairs = D >> 1;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)nblk * blockDim.x;
+    int64_t i = (int64_t)blk * blockDim.x + threadIdx.x;
     while (i < pairs) {
         float s = 0.f, c = 0.f;
 #pragma unroll 8
@@ -298,7 +307,7 @@ __global__ void __launch_bounds__(256) k_norm_partial_c64(const float2* psi, int
         csum_add(acc, (double)s);
         acc.c += (double)c;
     }
-    if ((D & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    if ((D & 1) && blk == 0 && threadIdx.x == 0) {
         const float2 v = psi[D - 1];
         float s = 0.f, c = 0.f;
         fsum_prob(s, c, v.x, v.y);
@@ -307,21 +316,68 @@ __global__ void __launch_bounds__(256) k_norm_partial_c64(const float2* psi, int
     }
     acc = block_reduce(acc);
     if (threadIdx.x == 0) {
-        partials[2 * blockIdx.x] = acc.s;
-        partials[2 * blockIdx.x + 1] = acc.c;
+        out[0] = acc.s;
+        out[1] = acc.c;
     }
 }
 
-// Reduce rows of partials: out[row] = sum over nb (s, c) pairs of row `blockIdx.x`.
-__global__ void __launch_bounds__(256) k_reduce_final(const double* partials, int nb, double* out) {
-    const double* p = partials + (size_t)blockIdx.x * 2 * nb;
+template <bool A16>
+__global__ void __launch_bounds__(256) k_norm_partial_c64(const float2* psi, int64_t D, double* partials) {
+    norm_partial_c64_body<A16>(psi, D, blockIdx.x, gridDim.x, partials + 2 * blockIdx.x);
+}
+
+// Sum of nb (s, c) pairs at p, in a fixed order, into *out.
+__device__ __forceinline__ void reduce_final_body(const double* p, int nb, double* out) {
     CSum acc{0.0, 0.0};
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
         CSum w{p[2 * i], p[2 * i + 1]};
         acc = csum_merge(acc, w);
     }
     acc = block_reduce(acc);
-    if (threadIdx.x == 0) out[blockIdx.x] = acc.s + acc.c;
+    if (threadIdx.x == 0) *out = acc.s + acc.c;
+}
+
+// Reduce rows of partials: out[row] = sum over nb (s, c) pairs of row `blockIdx.x`.
+__global__ void __launch_bounds__(256) k_reduce_final(const double* partials, int nb, double* out) {
+    reduce_final_body(partials + (size_t)blockIdx.x * 2 * nb, nb, out + blockIdx.x);
+}
+
+// Norms of many states in two launches, each state's arithmetic exactly that
+// of its own launch_norm: block w of the first launch is block w - prefix[e]
+// of entry e's nb blocks (the last e with prefix[e] <= w).
+__device__ __forceinline__ int find_entry(const uint64_t* prefix, int n, uint64_t w) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= w) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_norm_partial_batch(const NormEntry* entries, const uint64_t* prefix,
+                                                             int32_t n, double* partials) {
+    __shared__ int s_e;
+    if (threadIdx.x == 0) s_e = find_entry(prefix, n, blockIdx.x);
+    __syncthreads();
+    const NormEntry& E = entries[s_e];
+    const uint32_t blk = (uint32_t)(blockIdx.x - prefix[s_e]);
+    double* out = partials + 2 * (E.part_off + blk);
+    if constexpr (sizeof(R) == 4) {
+        if (E.a16)
+            norm_partial_c64_body<true>(static_cast<const float2*>(E.psi), E.D, blk, E.nb, out);
+        else
+            norm_partial_c64_body<false>(static_cast<const float2*>(E.psi), E.D, blk, E.nb, out);
+    } else {
+        norm_partial_body<R>(static_cast<const typename Cplx<R>::T2*>(E.psi), E.D, blk, E.nb, out);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final_batch(const NormEntry* entries, double* partials,
+                                                            double* norms) {
+    const NormEntry& E = entries[blockIdx.x];
+    reduce_final_body(partials + 2 * E.part_off, (int)E.nb, norms + E.out_index);
 }
 
 template <typename R>
@@ -465,6 +521,48 @@ cudaError_t launch_norm(const void* psi, int64_t D, double* partials, int nblock
     return cudaGetLastError();
 }
 
+// |0...0> for many states: unit w of the launch zeroes chunk w - prefix[e]
+// (kBasisChunk amplitudes) of entry e's state; the unit that zeroed chunk 0
+// then sets amplitude 0 to 1.
+constexpr int64_t kBasisChunk = kBasisChunkAmps;
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_basis_batch(const NormEntry* entries, const uint64_t* prefix, int32_t n) {
+    using T2 = typename Cplx<R>::T2;
+    __shared__ int s_e;
+    if (threadIdx.x == 0) s_e = find_entry(prefix, n, blockIdx.x);
+    __syncthreads();
+    const NormEntry& E = entries[s_e];
+    const int64_t c = (int64_t)(blockIdx.x - prefix[s_e]);
+    const int64_t lo = c * kBasisChunk, hi = lo + kBasisChunk < E.D ? lo + kBasisChunk : E.D;
+    T2* psi = static_cast<T2*>(const_cast<void*>(E.psi));
+    T2 z;
+    z.x = 0;
+    z.y = 0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) psi[i] = z;
+    __syncthreads();
+    if (c == 0 && threadIdx.x == 0) psi[0].x = (R)1;
+}
+
+template <typename R>
+cudaError_t launch_basis_batch(const NormEntry* entries, const uint64_t* chunk_prefix, int32_t n,
+                               uint64_t total_chunks, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_basis_batch<R><<<(unsigned)total_chunks, 256, 0, s>>>(entries, chunk_prefix, n);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_norm_batch(const NormEntry* entries, const uint64_t* block_prefix, int32_t n,
+                              uint64_t total_blocks, double* partials, double* norms, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_norm_partial_batch<R><<<(unsigned)total_blocks, 256, 0, s>>>(entries, block_prefix, n, partials);
+    k_reduce_final_batch<<<(unsigned)n, 256, 0, s>>>(entries, partials, norms);
+    count_launch(2);
+    return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_probs(const void* psi, int64_t D, double* out, cudaStream_t s) {
     k_probs<R><<<grid_for(D), 256, 0, s>>>(reinterpret_cast<const typename Cplx<R>::T2*>(psi), D, out);
@@ -534,6 +632,10 @@ QD_INST_GATE1_ALL(8)
     template size_t gate_tile_smem<R>(int, int);                                                        \
     template cudaError_t launch_set_basis<R>(void*, int64_t, int64_t, cudaStream_t);                    \
     template cudaError_t launch_norm<R>(const void*, int64_t, double*, int, double*, cudaStream_t);     \
+    template cudaError_t launch_norm_batch<R>(const NormEntry*, const uint64_t*, int32_t, uint64_t, double*,   \
+                                              double*, cudaStream_t);                                         \
+    template cudaError_t launch_basis_batch<R>(const NormEntry*, const uint64_t*, int32_t, uint64_t,          \
+                                               cudaStream_t);                                                 \
     template cudaError_t launch_probs<R>(const void*, int64_t, double*, cudaStream_t);                  \
     template cudaError_t launch_marginal<R>(const void*, const IndexMap&, uint64_t, uint64_t, int,      \
                                             double*, int, double*, cudaStream_t);                       \

@@ -132,3 +132,43 @@ def test_batched_workload_8192_circuits(qb, gen):
     assert n_small > 5000 and sum(1 for i in chosen if circs[i].D > 8192) > 1500
     for i, g, r in zip(chosen, got, refs):
         assert_close(g, r, qb.QD_C64, f"workload circuit {i} (D = {circs[i].D})")
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64"])
+def test_layer_queue_and_stream_paths_agree(qb, gen, prec):
+    """Larger circuits of a batch through the device-side layer queue (one
+    launch per pass position for all of them) and as programs on auxiliary
+    streams: both against the oracle, each circuit's norm exactly its
+    qd_norm, and the layer path's norms and states the same bits under a
+    CUDA graph relaunch."""
+    p = qb.QD_C128 if prec == "c128" else qb.QD_C64
+    rng = np.random.Generator(np.random.PCG64(31))
+    circs = []
+    for i in range(30):
+        w = int(rng.integers(6, 12))
+        dims = tuple(int(x) for x in rng.choice([2, 3, 4, 5], size=w))
+        circs.append(gen.random_mixed_circuit(dims, int(rng.integers(20, 200)), rng))
+    circs.append(gen.Circuit((2, 3, 2, 3, 2, 3, 2, 3), [gen.Gate((1, 0), gen.haar(6, rng))]))  # not tile-only
+    outs = {}
+    for path in (qb.QD_BATCH_LAYERS, qb.QD_BATCH_STREAMS):
+        b = qb.qd_batch_create(p)
+        qb.qd_batch_run(b, circs, small_max_amps=1024, use_graph=True, path=path)
+        st = [qb.qd_batch_get_amplitudes(b, i) for i in range(len(circs))]
+        nr = qb.qd_batch_norms(b, len(circs))
+        qb.qd_batch_relaunch(b)
+        assert all(np.array_equal(qb.qd_batch_get_amplitudes(b, i), st[i]) for i in range(len(circs)))
+        assert np.array_equal(qb.qd_batch_norms(b, len(circs)), nr)
+        qb.qd_batch_destroy(b)
+        outs[path] = (st, nr)
+    tol = 1e-12 if p == qb.QD_C128 else 1e-5
+    for i, c in enumerate(circs):
+        ref = oracle.run_circuit(c)
+        for path in outs:
+            st, nr = outs[path]
+            assert_close(st[i], ref, p, f"batch path {path} circuit {i} dims={c.dims}")
+            assert abs(nr[i] - oracle.norm(ref)) < tol
+        if c.D > 1024:  # outside the one-CTA path: each norm is the bits qd_norm gives the same amplitudes
+            s = qb.State(c.dims, prec=p)
+            s.set_amplitudes(outs[qb.QD_BATCH_LAYERS][0][i])
+            assert s.norm() == outs[qb.QD_BATCH_LAYERS][1][i]
+            s.close()
