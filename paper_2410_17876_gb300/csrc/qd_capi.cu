@@ -1,6 +1,7 @@
 // C ABI of libqudit.so (declared in include/qudit.h): state objects, exact
 // gate classification, planning of the class enumeration and kernel
 // dispatch.  Host code only; the kernels live in qd_kernels.cu.
+#include <nvtx3/nvToolsExt.h>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -21,6 +22,9 @@ static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 qd_status fail(qd_status st, const char* fmt, ...) {
     char buf[512];
@@ -865,6 +869,7 @@ qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes) {
 }
 
 qd_status qd_apply_gate(qd_state* st, int32_t target, const double* U) {
+    qd::NvtxRange nvtx_("qd_apply_gate");
     QD_GUARD_BEGIN
     return apply_any(st, &target, 1, U, nullptr, nullptr, 0);
     QD_GUARD_END
@@ -872,6 +877,7 @@ qd_status qd_apply_gate(qd_state* st, int32_t target, const double* U) {
 
 qd_status qd_apply_controlled(qd_state* st, int32_t target, const double* U, const int32_t* cw,
                               const int32_t* cv, int32_t nc) {
+    qd::NvtxRange nvtx_("qd_apply_controlled");
     QD_GUARD_BEGIN
     return apply_any(st, &target, 1, U, cw, cv, nc);
     QD_GUARD_END
@@ -879,12 +885,14 @@ qd_status qd_apply_controlled(qd_state* st, int32_t target, const double* U, con
 
 qd_status qd_apply_multi(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
                          const int32_t* cv, int32_t nc) {
+    qd::NvtxRange nvtx_("qd_apply_multi");
     QD_GUARD_BEGIN
     return apply_any(st, wires, k, U, cw, cv, nc);
     QD_GUARD_END
 }
 
 qd_status qd_norm(qd_state* st, double* out) {
+    qd::NvtxRange nvtx_("qd_norm");
     QD_GUARD_BEGIN
     if (!st || !out) return fail(QD_ERR_ARG, "state or out is NULL");
     QD_FLUSH(st);

@@ -497,8 +497,8 @@ struct TcTileCtx {
     uint32_t phase;   // its next phase parity
     float* sB;        // shared: B_hi | B_lo (2 x 64 x 64 floats)
     const char* desc; // the program's descriptors (global)
-    float* s_nin;     // shared [2][128]: input norms, two halves per class
-    float* s_nout;    // shared [2][128]
+    float2* s_nin;    // shared [2][128]: input squared norms (s, c parts), two halves per class
+    float2* s_nout;   // shared [2][128]
 };
 constexpr uint32_t kTileTcOpBytes = 2u * 64u * 64u * 4u;
 
@@ -519,7 +519,7 @@ __device__ bool tile_tc_block(float2* tile, const FGate& G, TcTileCtx& c) {
         const uint32_t cls = g0 + (uint32_t)row;
         const bool valid = cls < nc;
         const uint32_t base = valid ? G.map.map(cls) : 0u;
-        float pn = 0.f;
+        NormAcc pn;
         {
             float xr[16], xi[16], h[16], l[16];
 #pragma unroll
@@ -528,7 +528,8 @@ __device__ bool tile_tc_block(float2* tile, const FGate& G, TcTileCtx& c) {
                 const float2 v = (valid && r < P) ? tile[base + G.off[r]] : make_float2(0.f, 0.f);
                 xr[i] = v.x;
                 xi[i] = v.y;
-                pn = fmaf(v.x, v.x, fmaf(v.y, v.y, pn));
+                pn.add_sq(v.x);
+                pn.add_sq(v.y);
             }
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
@@ -545,7 +546,7 @@ __device__ bool tile_tc_block(float2* tile, const FGate& G, TcTileCtx& c) {
             tmem_st16(c.tm + lanes + 32u + 16u * half, h);
             tmem_st16(c.tm + lanes + 96u + 16u * half, l);
         }
-        c.s_nin[half * 128 + row] = pn;
+        c.s_nin[half * 128 + row] = make_float2(pn.s, pn.c);
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();  // every member gathered before any output is written back
@@ -574,20 +575,22 @@ __device__ bool tile_tc_block(float2* tile, const FGate& G, TcTileCtx& c) {
         float yr[16], yi[16];
         tmem_ld16(c.tm + lanes + 128u + 16u * half, yr);
         tmem_ld16(c.tm + lanes + 160u + 16u * half, yi);
-        float po = 0.f;
+        NormAcc po;
 #pragma unroll
-        for (int i = 0; i < 16; ++i) po = fmaf(yr[i], yr[i], fmaf(yi[i], yi[i], po));
-        c.s_nout[half * 128 + row] = po;
+        for (int i = 0; i < 16; ++i) {
+            po.add_sq(yr[i]);
+            po.add_sq(yi[i]);
+        }
+        c.s_nout[half * 128 + row] = make_float2(po.s, po.c);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         float cc = 0.f;
         if (G.unitary) {
             // as in the whole-state kernel: y <- y (1 + c), c = sqrt(ni / no) - 1
-            const float ni = c.s_nin[row] + c.s_nin[128 + row], no = c.s_nout[row] + c.s_nout[128 + row];
-            if (ni > 0.f && no > 0.f) {
-                const float sn = sqrtf(no);
-                cc = (ni - no) / (sn * (sqrtf(ni) + sn));
-            }
+            const float2 a0 = c.s_nin[row], a1 = c.s_nin[128 + row];
+            const float2 b0 = c.s_nout[row], b1 = c.s_nout[128 + row];
+            cc = norm_fix((double)a0.x + (double)a0.y + (double)a1.x + (double)a1.y,
+                          (double)b0.x + (double)b0.y + (double)b1.x + (double)b1.y);
         }
         if (valid) {
 #pragma unroll
@@ -765,9 +768,13 @@ __global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ F
 // Tile passes of many circuits in one launch (batches): the device-side
 // queue of one layer holds, for each circuit with a pass at that position,
 // the pass's record, and prefix[e] = tiles of the entries before e.  The
-// persistent CTAs walk the layer's tiles w = blockIdx.x, + gridDim.x, ...;
-// entry e of tile w is the last with prefix[e] <= w.  The queue is complete
-// before the launch, so no CTA ever waits on another.
+// persistent CTAs walk the layer's tiles in runs of kLayerRun consecutive
+// tiles, run r = blockIdx.x, + gridDim.x, ...; entry e of tile w is the
+// last with prefix[e] <= w, found by a binary search from the previous
+// tile's entry (tiles only move forward).  The queue is complete before the
+// launch, so no CTA ever waits on another.
+constexpr uint32_t kLayerRun = 4;
+
 template <typename R, int DMAX>
 __global__ void __launch_bounds__(256, 3) k_fused_layer(const LayerEntry<R>* entries, const uint64_t* prefix,
                                                          int32_t n, uint64_t total, const char* base) {
@@ -775,21 +782,28 @@ __global__ void __launch_bounds__(256, 3) k_fused_layer(const LayerEntry<R>* ent
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
     __shared__ int32_t s_e;
-    for (uint64_t w = blockIdx.x; w < total; w += gridDim.x) {
-        if (threadIdx.x == 0) {
-            int lo = 0, hi = n - 1;  // prefix[lo] <= w < prefix[n]
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (prefix[mid] <= w) lo = mid;
-                else hi = mid - 1;
+    int e = 0;  // entry of the previous tile (thread 0)
+    for (uint64_t r0 = (uint64_t)blockIdx.x * kLayerRun; r0 < total; r0 += (uint64_t)gridDim.x * kLayerRun) {
+        const uint64_t r1 = r0 + kLayerRun < total ? r0 + kLayerRun : total;
+        for (uint64_t w = r0; w < r1; ++w) {
+            if (threadIdx.x == 0) {
+                if (prefix[e + 1] <= w) {  // prefix[lo] <= w < prefix[n]
+                    int lo = e + 1, hi = n - 1;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (prefix[mid] <= w) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    e = lo;
+                }
+                s_e = e;
             }
-            s_e = lo;
+            __syncthreads();
+            const LayerEntry<R>& E = entries[s_e];
+            tile_pass<R, DMAX>(E, base + E.chunks_off, reinterpret_cast<const uint64_t*>(base + E.rows_off),
+                               (uint32_t)(w - prefix[s_e]), smem_raw, odig, &sbase);
+            __syncthreads();  // the next tile reuses shared memory
         }
-        __syncthreads();
-        const LayerEntry<R>& E = entries[s_e];
-        tile_pass<R, DMAX>(E, base + E.chunks_off, reinterpret_cast<const uint64_t*>(base + E.rows_off),
-                           (uint32_t)(w - prefix[s_e]), smem_raw, odig, &sbase);
-        __syncthreads();  // the next tile reuses shared memory
     }
 }
 
@@ -812,7 +826,7 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile_tc(const __grid_constant_
     __shared__ uint64_t sbase;
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_base;
-    __shared__ float s_nin[256], s_nout[256];
+    __shared__ float2 s_nin[256], s_nout[256];
     const int tid = threadIdx.x;
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
@@ -919,8 +933,9 @@ cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One layer of a batch's device-side queue: persistent CTAs, three per SM
-// (the occupancy of k_fused_tile), never more than the layer's tiles.
+// One group of a layer of a batch's device-side queue: persistent CTAs, as
+// many per SM as the group's shared memory lets reside (so that the whole
+// grid is resident), never more than the group's runs of tiles.
 template <typename R>
 cudaError_t launch_fused_layer(const LayerEntry<R>* entries, const uint64_t* prefix, int32_t n, uint64_t total,
                                const char* base, int dmax, size_t smem, cudaStream_t s) {
@@ -937,8 +952,14 @@ cudaError_t launch_fused_layer(const LayerEntry<R>* entries, const uint64_t* pre
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    const uint64_t cap = (uint64_t)(sms > 0 ? sms : 152) * 3;
-    const unsigned grid = (unsigned)(total < cap ? total : cap);
+    int per_sm = 0;
+    cudaError_t e = dmax <= 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_layer<R, 3>, 256, smem)
+                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_layer<R, 5>, 256, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    const uint64_t runs = (total + kLayerRun - 1) / kLayerRun;
+    const uint64_t cap = (uint64_t)(sms > 0 ? sms : 152) * (uint64_t)per_sm;
+    const unsigned grid = (unsigned)(runs < cap ? runs : cap);
     if (dmax <= 3)
         k_fused_layer<R, 3><<<grid, 256, smem, s>>>(entries, prefix, n, total, base);
     else
@@ -2129,6 +2150,7 @@ void build_program(const Layout& L, void* psi, const std::vector<HGate>& G, cons
 
 qd_status issue(const Program& prog, const char* base, cudaStream_t s) {
     for (const Op& op : prog.ops) {
+        NvtxRange r("pass");
         cudaError_t e = op(s, base);
         if (e != cudaSuccess) return cuda_fail(e, "circuit kernel launch");
     }
@@ -2381,8 +2403,8 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
     std::vector<Program> big;
     std::vector<int> big_idx;
     std::vector<std::vector<LayerEntry<R>>> layers;
-    std::vector<int> layer_dmax;
-    std::vector<size_t> layer_smem;
+    std::vector<std::vector<int>> layer_dmax;      // per entry
+    std::vector<std::vector<size_t>> layer_smem;   // per entry
     std::vector<int> layered;  // circuits on the layer path
     FuseCfg lcfg = cfg;
     lcfg.min_gates = 1;  // a pass of one gate stays a tile pass
@@ -2422,13 +2444,13 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
                     prog.desc.swap(pg.desc);
                     if (layers.size() < ents.size()) {
                         layers.resize(ents.size());
-                        layer_dmax.resize(ents.size(), 2);
-                        layer_smem.resize(ents.size(), 0);
+                        layer_dmax.resize(ents.size());
+                        layer_smem.resize(ents.size());
                     }
                     for (size_t k = 0; k < ents.size(); ++k) {
                         layers[k].push_back(ents[k]);
-                        layer_dmax[k] = std::max(layer_dmax[k], dms[k]);
-                        layer_smem[k] = std::max(layer_smem[k], sms[k]);
+                        layer_dmax[k].push_back(dms[k]);
+                        layer_smem[k].push_back(sms[k]);
                     }
                     layered.push_back(i);
                     continue;
@@ -2441,17 +2463,46 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
             big_idx.push_back(i);
         }
     }
-    // the layer queue: per layer its entries and the prefix of their tile
-    // counts; per layered circuit a norm / reset record with the prefix of
-    // its reduction blocks and of its reset chunks
-    std::vector<size_t> l_offE(layers.size()), l_offP(layers.size());
-    std::vector<uint64_t> l_total(layers.size());
+    // the layer queue: per layer, its entries in groups by shared memory per
+    // CTA (what lets 3, 2 or 1 CTAs reside on an SM, so that a group's grid
+    // is resident at the occupancy of its own passes), each group with the
+    // prefix of its entries' tile counts; per layered circuit a norm / reset
+    // record with the prefix of its reduction blocks and of its reset chunks
+    struct LaunchGroup {
+        size_t offE, offP;
+        int32_t n;
+        uint64_t total;
+        int dmax;
+        size_t smem;
+    };
+    std::vector<LaunchGroup> groups;
     for (size_t k = 0; k < layers.size(); ++k) {
-        std::vector<uint64_t> pre(layers[k].size() + 1, 0);
-        for (size_t e = 0; e < layers[k].size(); ++e) pre[e + 1] = pre[e] + layers[k][e].ntiles;
-        l_total[k] = pre.back();
-        l_offE[k] = prog.put(layers[k].data(), sizeof(LayerEntry<R>) * layers[k].size());
-        l_offP[k] = prog.put(pre.data(), sizeof(uint64_t) * pre.size());
+        const size_t bounds[3] = {72 * 1024, 110 * 1024, (size_t)1 << 40};
+        size_t lo = 0;
+        for (size_t hi : bounds) {
+            std::vector<LayerEntry<R>> ge;
+            std::vector<uint64_t> pre(1, 0);
+            int dm = 2;
+            size_t sm = 0;
+            for (size_t e = 0; e < layers[k].size(); ++e) {
+                const size_t x = layer_smem[k][e];
+                if (x <= lo || x > hi) continue;
+                ge.push_back(layers[k][e]);
+                pre.push_back(pre.back() + layers[k][e].ntiles);
+                dm = std::max(dm, layer_dmax[k][e]);
+                sm = std::max(sm, x);
+            }
+            lo = hi;
+            if (ge.empty()) continue;
+            LaunchGroup g;
+            g.offE = prog.put(ge.data(), sizeof(LayerEntry<R>) * ge.size());
+            g.offP = prog.put(pre.data(), sizeof(uint64_t) * pre.size());
+            g.n = (int32_t)ge.size();
+            g.total = pre.back();
+            g.dmax = dm;
+            g.smem = sm;
+            groups.push_back(g);
+        }
     }
     size_t offN = 0, offNB = 0, offNC = 0;
     uint64_t nblocks_total = 0, nchunks_total = 0;
@@ -2525,10 +2576,13 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
         const NormEntry* ne = reinterpret_cast<const NormEntry*>(base + offN);
         e = launch_basis_batch<R>(ne, reinterpret_cast<const uint64_t*>(base + offNC), (int32_t)layered.size(),
                                   nchunks_total, ws);
-        for (size_t k = 0; k < layers.size() && e == cudaSuccess; ++k)
-            e = launch_fused_layer<R>(reinterpret_cast<const LayerEntry<R>*>(base + l_offE[k]),
-                                      reinterpret_cast<const uint64_t*>(base + l_offP[k]), (int32_t)layers[k].size(),
-                                      l_total[k], base, layer_dmax[k], layer_smem[k], ws);
+        for (size_t k = 0; k < groups.size() && e == cudaSuccess; ++k) {
+            NvtxRange r("batch layer group");
+            const LaunchGroup& g = groups[k];
+            e = launch_fused_layer<R>(reinterpret_cast<const LayerEntry<R>*>(base + g.offE),
+                                      reinterpret_cast<const uint64_t*>(base + g.offP), g.n, g.total, base, g.dmax,
+                                      g.smem, ws);
+        }
         if (e == cudaSuccess)
             e = launch_norm_batch<R>(ne, reinterpret_cast<const uint64_t*>(base + offNB), (int32_t)layered.size(),
                                      nblocks_total, b->lpartials, b->norms, ws);
@@ -2578,6 +2632,7 @@ extern "C" {
 
 qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gates, const double* matrices,
                            const qd_fusion_opts* opts) {
+    NvtxRange nvtx_("qd_apply_circuit");
     if (!st) return fail(QD_ERR_ARG, "state is NULL");
     qd_status rc = flush_pending(st);
     if (rc == QD_OK) rc = materialize(st);
@@ -2782,6 +2837,7 @@ qd_status qd_batch_create(int32_t prec, void* stream, qd_batch** out) {
 }
 
 qd_status qd_batch_run(qd_batch* b, const qd_circuit* circuits, int32_t n, const qd_batch_opts* opts) {
+    NvtxRange nvtx_("qd_batch_run");
     try {
         if (!b) return fail(QD_ERR_ARG, "batch is NULL");
         if (n < 0 || (n > 0 && !circuits)) return fail(QD_ERR_ARG, "bad circuit list");

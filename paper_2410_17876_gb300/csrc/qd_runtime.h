@@ -24,6 +24,16 @@ void set_last_error(const char* msg);
 
 qd_status make_layout(const int32_t* dims, int32_t n, Layout& L);
 
+// NVTX range for the lifetime of the object (API calls, fused passes, batch
+// layers, served requests); costs one call through a function pointer when
+// no profiler is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Device buffer plus pinned staging for kernel descriptors.  upload() waits
 // until the previous upload from the staging buffer has completed before
 // overwriting it, grows both buffers when needed (after synchronising the

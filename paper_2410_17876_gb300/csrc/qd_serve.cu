@@ -165,6 +165,7 @@ void publish(qd_server* s, const std::shared_ptr<Request>& r) {
 
 template <typename R>
 bool issue_big(qd_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
+    NvtxRange nvtx_("served request");
     Program prog;
     build_program<R>(r->L, s->arena_dev + r->off, r->G, s->cfg, true, prog);
     if (sl.arena.upload(prog.desc.data(), prog.desc.size(), sl.stream) != QD_OK) return false;

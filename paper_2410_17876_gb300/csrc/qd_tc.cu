@@ -139,8 +139,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
     // per-class squared norms: inputs (partial over the GP producers of a
     // class, slot = chunk iteration mod kNinSlots) and outputs (over the GC
     // consumers)
-    __shared__ float s_nin[kNinSlots][GP][kTcN];
-    __shared__ float s_nout[GC][kTcN];
+    __shared__ float2 s_nin[kNinSlots][GP][kTcN];  // (s, c) parts
+    __shared__ float2 s_nout[GC][kTcN];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     if (tid == 0) {
@@ -298,10 +298,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             }
             unsigned char* b = sB + st * kStage;
             if (a.renorm) {
-                float pn = 0.f;
+                NormAcc pn;
 #pragma unroll
-                for (int e = 0; e < MPT; ++e) pn = fmaf(cur[e].x, cur[e].x, fmaf(cur[e].y, cur[e].y, pn));
-                s_nin[i % kNinSlots][q0][n] = pn;
+                for (int e = 0; e < MPT; ++e) {
+                    pn.add_sq(cur[e].x);
+                    pn.add_sq(cur[e].y);
+                }
+                s_nin[i % kNinSlots][q0][n] = make_float2(pn.s, pn.c);
             }
             if constexpr (kBf) {
 #pragma unroll
@@ -398,12 +401,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             consumer_sync<kCons>();
             // outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
             float2 y[OPT];
-            float po = 0.f;
+            NormAcc po;
 #pragma unroll
             for (int k = 0; k < OPT; ++k) {
                 const int r = h + GC * k;
                 y[k] = r < a.P ? make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]) : make_float2(0.f, 0.f);
-                po = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, po));
+                if (a.renorm) {
+                    po.add_sq(y[k].x);
+                    po.add_sq(y[k].y);
+                }
             }
             float cc = 0.f;
             if (a.renorm) {
@@ -415,17 +421,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
                 // c is applied by one FMA: a factor 1 + c rounded to binary32
                 // would be off by up to half an ulp of 1 in the same direction
                 // for every class (the bias is nearly uniform), a drift of its own.
-                s_nout[h][n] = po;
+                // ni and no are compensated binary32 sums of exact squares
+                // (NormAcc), combined and turned into c in binary64.
+                s_nout[h][n] = make_float2(po.s, po.c);
                 consumer_sync<kCons>();
-                float ni = 0.f, no = 0.f;
+                double ni = 0.0, no = 0.0;  // the parts combined, and c formed, in binary64
 #pragma unroll
-                for (int g = 0; g < GP; ++g) ni += s_nin[i % kNinSlots][g][n];
-#pragma unroll
-                for (int g = 0; g < GC; ++g) no += s_nout[g][n];
-                if (ni > 0.f && no > 0.f) {
-                    const float sn = sqrtf(no);
-                    cc = (ni - no) / (sn * (sqrtf(ni) + sn));
+                for (int g = 0; g < GP; ++g) {
+                    const float2 v = s_nin[i % kNinSlots][g][n];
+                    ni += (double)v.x + (double)v.y;
                 }
+#pragma unroll
+                for (int g = 0; g < GC; ++g) {
+                    const float2 v = s_nout[g][n];
+                    no += (double)v.x + (double)v.y;
+                }
+                cc = norm_fix(ni, no);
             }
             const uint64_t g = chunk * kTcN + (uint64_t)n;
             if (g < a.n_classes) {

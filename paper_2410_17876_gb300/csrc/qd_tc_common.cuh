@@ -60,6 +60,31 @@ __host__ __device__ __forceinline__ uint32_t tf32_rne_bits(uint32_t u) {
 }
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(tf32_rne_bits(__float_as_uint(x))); }
 
+// Squared 2-norm of a class's members for the norm restoration of unitary
+// blocks, accumulated without loss: each x^2 is split exactly into p + e
+// (p = x*x, e = fma(x, x, -p), the TwoProduct of Dekker / Ogita-Rump-Oishi)
+// and added to a binary32 Neumaier sum (s, c) whose compensation also
+// collects the e's; the parts are later combined in binary64.
+struct NormAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_sq(float x) {
+        const float p = x * x;
+        c += fmaf(x, x, -p);
+        const float t = s + p;
+        c += fabsf(s) >= fabsf(p) ? (s - t) + p : (p - t) + s;
+        s = t;
+    }
+};
+
+// Restoration factor c = sqrt(ni / no) - 1 in binary64 (ni, no: squared
+// norms of a class before and after the block, each given as binary32
+// parts); the output is then y + y c, one binary32 FMA per component.
+__device__ __forceinline__ float norm_fix(double ni, double no) {
+    if (!(ni > 0.0) || !(no > 0.0)) return 0.f;
+    const double sn = sqrt(no);
+    return (float)((ni - no) / (sn * (sqrt(ni) + sn)));
+}
+
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
