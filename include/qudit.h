@@ -112,7 +112,19 @@ qd_status qd_state_get_amplitudes(qd_state* st, double* host_interleaved);
  * to host memory of `bytes` bytes.  Synchronous. */
 qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes);
 
-/* Data movement of the wire-swap exchange between the shards of a state
+/* Checkpoint and resume (the paper has no counterpart).  qd_state_save
+ * writes the state (after any queued gates and the lazy frame) to a file:
+ * a 64-byte header (magic "QDSTATE1", precision, number of wires, D), the
+ * wire dimensions as int32, then the raw amplitudes; qd_state_load reads
+ * such a file into a state of the same dims and precision (QD_ERR_ARG
+ * otherwise, the state unchanged if the header does not match).  Both copy
+ * through a pinned staging buffer of at most 256 MiB and are synchronous.
+ * QD_ERR_ARG for a path that cannot be opened or a short file; QD_ERR_OOM
+ * if the staging buffer cannot be allocated. */
+qd_status qd_state_save(qd_state* st, const char* path);
+qd_status qd_state_load(qd_state* st, const char* path);
+
+/* Data movement of the wire-swap exchange/* Data movement of the wire-swap exchange between the shards of a state
  * partitioned over several GPUs by its most significant wires (the paper
  * names distributed execution as future work, section "Conclusion").  With
  * lo = b_wire, d = d_wire and hi = D / (lo d), amplitude (h d + y) lo + l of

@@ -118,6 +118,8 @@ _SIGS = {
     "qd_selftest_host": (ctypes.c_int32, [ctypes.c_int32]),
     "qd_test_set_tc_wait": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_int32]),
     "qd_state_wire_to_top": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "qd_state_save": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p]),
+    "qd_state_load": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p]),
     "qd_state_wire_from_top": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "qd_batch_create": (ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
     "qd_batch_run": (ctypes.c_int32, [_vp, ctypes.POINTER(qd_circuit), ctypes.c_int32, ctypes.POINTER(qd_batch_opts)]),
@@ -247,6 +249,14 @@ def qd_state_get_raw(st: int, out: Optional[np.ndarray] = None) -> np.ndarray:
         out = np.empty(D, dtype=dt)
     _check(_lib.qd_state_get_raw(_vp(st), _vp(out.ctypes.data), out.nbytes), "qd_state_get_raw")
     return out
+
+
+def qd_state_save(st: int, path: str) -> None:
+    _check(_lib.qd_state_save(_vp(st), str(path).encode()), "qd_state_save")
+
+
+def qd_state_load(st: int, path: str) -> None:
+    _check(_lib.qd_state_load(_vp(st), str(path).encode()), "qd_state_load")
 
 
 def qd_state_wire_to_top(st: int, wire: int, dev_out: int) -> None:

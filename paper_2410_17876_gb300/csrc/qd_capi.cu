@@ -857,6 +857,82 @@ qd_status qd_state_wire_from_top(qd_state* st, int32_t wire, const void* dev_in)
     QD_GUARD_END
 }
 
+// Checkpoint file: a 64-byte header (magic "QDSTATE1", precision, number of
+// wires, the dims as int32 after it, then D), then the raw amplitudes.
+// Copies go through a pinned staging buffer of at most 256 MiB, so no
+// host buffer of the state's size is needed.
+static constexpr char kCkptMagic[8] = {'Q', 'D', 'S', 'T', 'A', 'T', 'E', '1'};
+static constexpr size_t kCkptChunk = (size_t)256 << 20;
+
+qd_status qd_state_save(qd_state* st, const char* path) {
+    QD_GUARD_BEGIN
+    if (!st || !path) return fail(QD_ERR_ARG, "state or path is NULL");
+    QD_MATERIALIZE(st);
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(QD_ERR_ARG, "cannot open %s for writing", path);
+    int64_t hdr[8] = {0};
+    std::memcpy(hdr, kCkptMagic, 8);
+    hdr[1] = st->prec;
+    hdr[2] = st->L.n;
+    hdr[3] = st->L.D;
+    bool ok = std::fwrite(hdr, sizeof hdr, 1, f) == 1 &&
+              std::fwrite(st->L.dims, sizeof(int32_t), (size_t)st->L.n, f) == (size_t)st->L.n;
+    void* stage = nullptr;
+    const size_t chunk = st->bytes < kCkptChunk ? st->bytes : kCkptChunk;
+    if (ok && cudaMallocHost(&stage, chunk) != cudaSuccess) {
+        std::fclose(f);
+        return fail(QD_ERR_OOM, "checkpoint staging buffer");
+    }
+    for (size_t o = 0; ok && o < st->bytes; o += chunk) {
+        const size_t n = st->bytes - o < chunk ? st->bytes - o : chunk;
+        ok = cudaMemcpyAsync(stage, static_cast<char*>(st->psi) + o, n, cudaMemcpyDeviceToHost, st->stream) ==
+                 cudaSuccess &&
+             cudaStreamSynchronize(st->stream) == cudaSuccess && std::fwrite(stage, 1, n, f) == n;
+    }
+    if (stage) cudaFreeHost(stage);
+    ok = (std::fclose(f) == 0) && ok;
+    if (!ok) return fail(QD_ERR_CUDA, "checkpoint of the state to %s failed", path);
+    return QD_OK;
+    QD_GUARD_END
+}
+
+qd_status qd_state_load(qd_state* st, const char* path) {
+    QD_GUARD_BEGIN
+    if (!st || !path) return fail(QD_ERR_ARG, "state or path is NULL");
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(QD_ERR_ARG, "cannot open %s", path);
+    int64_t hdr[8];
+    std::vector<int32_t> dims((size_t)st->L.n);
+    bool ok = std::fread(hdr, sizeof hdr, 1, f) == 1 && std::memcmp(hdr, kCkptMagic, 8) == 0 &&
+              hdr[1] == st->prec && hdr[2] == st->L.n && hdr[3] == st->L.D &&
+              std::fread(dims.data(), sizeof(int32_t), dims.size(), f) == dims.size() &&
+              std::memcmp(dims.data(), st->L.dims, sizeof(int32_t) * dims.size()) == 0;
+    if (!ok) {
+        std::fclose(f);
+        return fail(QD_ERR_ARG, "%s is not a checkpoint of a state with these dims and precision", path);
+    }
+    drop_pending(st);  // the state is overwritten, as by qd_state_set_amplitudes
+    if (st->lazy) lazy_reset(*st->lazy, st->L);
+    void* stage = nullptr;
+    const size_t chunk = st->bytes < kCkptChunk ? st->bytes : kCkptChunk;
+    if (cudaMallocHost(&stage, chunk) != cudaSuccess) {
+        std::fclose(f);
+        return fail(QD_ERR_OOM, "checkpoint staging buffer");
+    }
+    for (size_t o = 0; ok && o < st->bytes; o += chunk) {
+        const size_t n = st->bytes - o < chunk ? st->bytes - o : chunk;
+        ok = cudaStreamSynchronize(st->stream) == cudaSuccess && std::fread(stage, 1, n, f) == n &&
+             cudaMemcpyAsync(static_cast<char*>(st->psi) + o, stage, n, cudaMemcpyHostToDevice, st->stream) ==
+                 cudaSuccess;
+    }
+    ok = cudaStreamSynchronize(st->stream) == cudaSuccess && ok;
+    cudaFreeHost(stage);
+    std::fclose(f);
+    if (!ok) return fail(QD_ERR_ARG, "reading the checkpoint %s failed (short file or copy error)", path);
+    return QD_OK;
+    QD_GUARD_END
+}
+
 qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes) {
     QD_GUARD_BEGIN
     if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");

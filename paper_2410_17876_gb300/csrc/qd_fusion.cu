@@ -147,7 +147,7 @@ struct FusedArgs {
 // outside the tile.
 constexpr int kLayerMaxFree = 16;
 template <typename R>
-struct LayerEntry {
+struct __align__(16) LayerEntry {
     using T2 = typename Cplx<R>::T2;
     T2* psi;
     uint64_t chunks_off, rows_off;
@@ -782,7 +782,12 @@ __global__ void __launch_bounds__(256, 3) k_fused_layer(const LayerEntry<R>* ent
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
     __shared__ int32_t s_e;
+    // the current entry, staged in shared memory: read from global memory,
+    // its fields would be reloaded after every store of the tile to global
+    // memory (the compiler cannot rule out that the two alias)
+    __shared__ __align__(16) LayerEntry<R> sE;
     int e = 0;  // entry of the previous tile (thread 0)
+    int staged = -1;
     for (uint64_t r0 = (uint64_t)blockIdx.x * kLayerRun; r0 < total; r0 += (uint64_t)gridDim.x * kLayerRun) {
         const uint64_t r1 = r0 + kLayerRun < total ? r0 + kLayerRun : total;
         for (uint64_t w = r0; w < r1; ++w) {
@@ -799,9 +804,16 @@ __global__ void __launch_bounds__(256, 3) k_fused_layer(const LayerEntry<R>* ent
                 s_e = e;
             }
             __syncthreads();
-            const LayerEntry<R>& E = entries[s_e];
-            tile_pass<R, DMAX>(E, base + E.chunks_off, reinterpret_cast<const uint64_t*>(base + E.rows_off),
-                               (uint32_t)(w - prefix[s_e]), smem_raw, odig, &sbase);
+            const int ce = s_e;
+            if (ce != staged) {
+                const uint4* src = reinterpret_cast<const uint4*>(entries + ce);
+                uint4* dst = reinterpret_cast<uint4*>(&sE);
+                for (int i = threadIdx.x; i < (int)(sizeof(LayerEntry<R>) / 16); i += blockDim.x) dst[i] = src[i];
+                staged = ce;
+                __syncthreads();
+            }
+            tile_pass<R, DMAX>(sE, base + sE.chunks_off, reinterpret_cast<const uint64_t*>(base + sE.rows_off),
+                               (uint32_t)(w - prefix[ce]), smem_raw, odig, &sbase);
             __syncthreads();  // the next tile reuses shared memory
         }
     }
