@@ -1158,6 +1158,26 @@ def run_ncu_fused_case(args):
     return 0
 
 
+def run_ncu_batch_case(args):
+    """The first 1024 circuits of the 8192-circuit workload, once through the
+    device-side layer queue (a profiler capture of k_fused_layer)."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2410_17876_gb300 import binding as qb
+    from paper_2410_17876_gb300 import inputs as gen
+
+    circs = gen.config3_batch(n_circuits=1024)
+    b = qb.qd_batch_create(qb.QD_C64)
+    qb.qd_batch_run(b, circs, path=qb.QD_BATCH_LAYERS)
+    qb.qd_batch_synchronize(b)
+    qb.qd_batch_destroy(b)
+    torch.cuda.synchronize()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -1185,7 +1205,12 @@ def main(argv=None):
     ap.add_argument("--ncu-fused-case", action="store_true",
                     help="run only the --ncu-workload circuit once, fused (--fuse tile or block; auto means "
                          "tile), for a profiler capture of one fused launch; prints nothing")
+    ap.add_argument("--ncu-batch-case", action="store_true",
+                    help="run only 1024 circuits of the batched workload once through the layer queue, for a "
+                         "profiler capture of the layer kernel; prints nothing")
     args = ap.parse_args(argv)
+    if args.ncu_batch_case:
+        return run_ncu_batch_case(args)
     if args.ncu_case:
         return run_ncu_case(args)
     if args.ncu_fused_case:

@@ -2414,10 +2414,10 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
     uint32_t maxd3 = 1, maxd5 = 1;
     std::vector<Program> big;
     std::vector<int> big_idx;
-    std::vector<std::vector<LayerEntry<R>>> layers;
-    std::vector<std::vector<int>> layer_dmax;      // per entry
-    std::vector<std::vector<size_t>> layer_smem;   // per entry
-    std::vector<int> layered;  // circuits on the layer path
+    std::vector<int> layered;  // circuits on the layer path, and per such circuit its passes' entries
+    std::vector<std::vector<LayerEntry<R>>> c_ents;
+    std::vector<std::vector<int>> c_dmax;
+    std::vector<std::vector<size_t>> c_smem;
     FuseCfg lcfg = cfg;
     lcfg.min_gates = 1;  // a pass of one gate stays a tile pass
     const bool try_layers = path == 0 && cfg.mode == QD_FUSE_TILE;
@@ -2454,16 +2454,9 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
                 const size_t mark = pg.desc.size();
                 if (build_layer_entries<R>(L, b->states + b->psi_off[i], Gs[i], lcfg, passes, pg, ents, dms, sms)) {
                     prog.desc.swap(pg.desc);
-                    if (layers.size() < ents.size()) {
-                        layers.resize(ents.size());
-                        layer_dmax.resize(ents.size());
-                        layer_smem.resize(ents.size());
-                    }
-                    for (size_t k = 0; k < ents.size(); ++k) {
-                        layers[k].push_back(ents[k]);
-                        layer_dmax[k].push_back(dms[k]);
-                        layer_smem[k].push_back(sms[k]);
-                    }
+                    c_ents.push_back(std::move(ents));
+                    c_dmax.push_back(std::move(dms));
+                    c_smem.push_back(std::move(sms));
                     layered.push_back(i);
                     continue;
                 }
@@ -2475,11 +2468,16 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
             big_idx.push_back(i);
         }
     }
-    // the layer queue: per layer, its entries in groups by shared memory per
-    // CTA (what lets 3, 2 or 1 CTAs reside on an SM, so that a group's grid
-    // is resident at the occupancy of its own passes), each group with the
-    // prefix of its entries' tile counts; per layered circuit a norm / reset
-    // record with the prefix of its reduction blocks and of its reset chunks
+    // The layer queue.  The layered circuits are taken in groups of
+    // consecutive circuits whose states together fit in a third of the L2
+    // (a larger circuit is a group of its own): a group's layers run back to
+    // back, so its states stay in L2 from one pass to the next.  Within a
+    // group, layer k holds pass k of each of its circuits, split by shared
+    // memory per CTA (what lets 3, 2 or 1 CTAs reside on an SM, so that each
+    // launch's grid is resident at the occupancy of its own passes); each
+    // launch has the prefix of its entries' tile counts.  Per layered circuit
+    // a norm / reset record with the prefix of its reduction blocks and of
+    // its reset chunks.
     struct LaunchGroup {
         size_t offE, offP;
         int32_t n;
@@ -2488,33 +2486,45 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
         size_t smem;
     };
     std::vector<LaunchGroup> groups;
-    for (size_t k = 0; k < layers.size(); ++k) {
-        const size_t bounds[3] = {72 * 1024, 110 * 1024, (size_t)1 << 40};
-        size_t lo = 0;
-        for (size_t hi : bounds) {
-            std::vector<LayerEntry<R>> ge;
-            std::vector<uint64_t> pre(1, 0);
-            int dm = 2;
-            size_t sm = 0;
-            for (size_t e = 0; e < layers[k].size(); ++e) {
-                const size_t x = layer_smem[k][e];
-                if (x <= lo || x > hi) continue;
-                ge.push_back(layers[k][e]);
-                pre.push_back(pre.back() + layers[k][e].ntiles);
-                dm = std::max(dm, layer_dmax[k][e]);
-                sm = std::max(sm, x);
-            }
-            lo = hi;
-            if (ge.empty()) continue;
-            LaunchGroup g;
-            g.offE = prog.put(ge.data(), sizeof(LayerEntry<R>) * ge.size());
-            g.offP = prog.put(pre.data(), sizeof(uint64_t) * pre.size());
-            g.n = (int32_t)ge.size();
-            g.total = pre.back();
-            g.dmax = dm;
-            g.smem = sm;
-            groups.push_back(g);
+    constexpr size_t kL2Group = (size_t)44 << 20;
+    for (size_t j0 = 0; j0 < layered.size();) {
+        size_t j1 = j0, bytes = 0, nl = 0;
+        while (j1 < layered.size() &&
+               (j1 == j0 || bytes + (size_t)b->D[layered[j1]] * ab <= kL2Group)) {
+            bytes += (size_t)b->D[layered[j1]] * ab;
+            nl = std::max(nl, c_ents[j1].size());
+            ++j1;
         }
+        for (size_t k = 0; k < nl; ++k) {
+            const size_t bounds[3] = {72 * 1024, 110 * 1024, (size_t)1 << 40};
+            size_t lo = 0;
+            for (size_t hi : bounds) {
+                std::vector<LayerEntry<R>> ge;
+                std::vector<uint64_t> pre(1, 0);
+                int dm = 2;
+                size_t sm = 0;
+                for (size_t j = j0; j < j1; ++j) {
+                    if (k >= c_ents[j].size()) continue;
+                    const size_t x = c_smem[j][k];
+                    if (x <= lo || x > hi) continue;
+                    ge.push_back(c_ents[j][k]);
+                    pre.push_back(pre.back() + c_ents[j][k].ntiles);
+                    dm = std::max(dm, c_dmax[j][k]);
+                    sm = std::max(sm, x);
+                }
+                lo = hi;
+                if (ge.empty()) continue;
+                LaunchGroup g;
+                g.offE = prog.put(ge.data(), sizeof(LayerEntry<R>) * ge.size());
+                g.offP = prog.put(pre.data(), sizeof(uint64_t) * pre.size());
+                g.n = (int32_t)ge.size();
+                g.total = pre.back();
+                g.dmax = dm;
+                g.smem = sm;
+                groups.push_back(g);
+            }
+        }
+        j0 = j1;
     }
     size_t offN = 0, offNB = 0, offNC = 0;
     uint64_t nblocks_total = 0, nchunks_total = 0;
