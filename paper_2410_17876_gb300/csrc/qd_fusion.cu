@@ -589,8 +589,12 @@ __device__ bool tile_tc_block(float2* tile, const FGate& G, TcTileCtx& c) {
             // as in the whole-state kernel: y <- y (1 + c), c = sqrt(ni / no) - 1
             const float2 a0 = c.s_nin[row], a1 = c.s_nin[128 + row];
             const float2 b0 = c.s_nout[row], b1 = c.s_nout[128 + row];
-            cc = norm_fix((double)a0.x + (double)a0.y + (double)a1.x + (double)a1.y,
-                          (double)b0.x + (double)b0.y + (double)b1.x + (double)b1.y);
+            NormFF ni, no;
+            ni.add(a0.x, a0.y);
+            ni.add(a1.x, a1.y);
+            no.add(b0.x, b0.y);
+            no.add(b1.x, b1.y);
+            cc = norm_fix(ni, no);
         }
         if (valid) {
 #pragma unroll
@@ -767,56 +771,43 @@ __global__ void __launch_bounds__(256, 3) k_fused_tile(const __grid_constant__ F
 
 // Tile passes of many circuits in one launch (batches): the device-side
 // queue of one layer holds, for each circuit with a pass at that position,
-// the pass's record, and prefix[e] = tiles of the entries before e.  The
-// persistent CTAs walk the layer's tiles in runs of kLayerRun consecutive
-// tiles, run r = blockIdx.x, + gridDim.x, ...; entry e of tile w is the
-// last with prefix[e] <= w, found by a binary search from the previous
-// tile's entry (tiles only move forward).  The queue is complete before the
-// launch, so no CTA ever waits on another.
-constexpr uint32_t kLayerRun = 4;
-
+// the pass's record, and prefix[e] = tiles of the entries before e.  CTA w
+// applies tile w of the layer: its entry e is the last with prefix[e] <= w
+// (binary search by one thread), staged in shared memory.  One CTA per
+// tile, as k_fused_tile: the hardware scheduler balances tiles of unequal
+// cost.  The queue is complete before the launch, so no CTA ever waits on
+// another.
 template <typename R, int DMAX>
 __global__ void __launch_bounds__(256, 3) k_fused_layer(const LayerEntry<R>* entries, const uint64_t* prefix,
-                                                         int32_t n, uint64_t total, const char* base) {
+                                                         int32_t n, const char* base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int32_t odig[kMaxWires];
     __shared__ uint64_t sbase;
     __shared__ int32_t s_e;
-    // the current entry, staged in shared memory: read from global memory,
-    // its fields would be reloaded after every store of the tile to global
-    // memory (the compiler cannot rule out that the two alias)
+    // the entry, staged in shared memory: read from global memory, its fields
+    // would be reloaded after every store of the tile to global memory (the
+    // compiler cannot rule out that the two alias)
     __shared__ __align__(16) LayerEntry<R> sE;
-    int e = 0;  // entry of the previous tile (thread 0)
-    int staged = -1;
-    for (uint64_t r0 = (uint64_t)blockIdx.x * kLayerRun; r0 < total; r0 += (uint64_t)gridDim.x * kLayerRun) {
-        const uint64_t r1 = r0 + kLayerRun < total ? r0 + kLayerRun : total;
-        for (uint64_t w = r0; w < r1; ++w) {
-            if (threadIdx.x == 0) {
-                if (prefix[e + 1] <= w) {  // prefix[lo] <= w < prefix[n]
-                    int lo = e + 1, hi = n - 1;
-                    while (lo < hi) {
-                        const int mid = (lo + hi + 1) >> 1;
-                        if (prefix[mid] <= w) lo = mid;
-                        else hi = mid - 1;
-                    }
-                    e = lo;
-                }
-                s_e = e;
-            }
-            __syncthreads();
-            const int ce = s_e;
-            if (ce != staged) {
-                const uint4* src = reinterpret_cast<const uint4*>(entries + ce);
-                uint4* dst = reinterpret_cast<uint4*>(&sE);
-                for (int i = threadIdx.x; i < (int)(sizeof(LayerEntry<R>) / 16); i += blockDim.x) dst[i] = src[i];
-                staged = ce;
-                __syncthreads();
-            }
-            tile_pass<R, DMAX>(sE, base + sE.chunks_off, reinterpret_cast<const uint64_t*>(base + sE.rows_off),
-                               (uint32_t)(w - prefix[ce]), smem_raw, odig, &sbase);
-            __syncthreads();  // the next tile reuses shared memory
+    const uint64_t w = blockIdx.x;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n - 1;  // prefix[lo] <= w < prefix[n]
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= w) lo = mid;
+            else hi = mid - 1;
         }
+        s_e = lo;
     }
+    __syncthreads();
+    const int e = s_e;
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(entries + e);
+        uint4* dst = reinterpret_cast<uint4*>(&sE);
+        for (int i = threadIdx.x; i < (int)(sizeof(LayerEntry<R>) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+    tile_pass<R, DMAX>(sE, base + sE.chunks_off, reinterpret_cast<const uint64_t*>(base + sE.rows_off),
+                       (uint32_t)(w - prefix[e]), smem_raw, odig, &sbase);
 }
 
 // Tile pass whose chunks hold tensor-core blocks (complex64): k_fused_tile
@@ -945,14 +936,13 @@ cudaError_t launch_fused(const FusedArgs<R>& a, int dmax, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// One group of a layer of a batch's device-side queue: persistent CTAs, as
-// many per SM as the group's shared memory lets reside (so that the whole
-// grid is resident), never more than the group's runs of tiles.
+// One group of a layer of a batch's device-side queue: one CTA per tile.
 template <typename R>
 cudaError_t launch_fused_layer(const LayerEntry<R>* entries, const uint64_t* prefix, int32_t n, uint64_t total,
                                const char* base, int dmax, size_t smem, cudaStream_t s) {
     if (n <= 0 || total == 0) return cudaSuccess;
-    static int attr_dev = -1, sms = 0;
+    if (total >= ((uint64_t)1 << 31)) return cudaErrorInvalidConfiguration;
+    static int attr_dev = -1;
     int dev = 0;
     cudaGetDevice(&dev);
     if (attr_dev != dev) {
@@ -960,22 +950,13 @@ cudaError_t launch_fused_layer(const LayerEntry<R>* entries, const uint64_t* pre
                                              220 * 1024);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_fused_layer<R, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         attr_dev = dev;
     }
-    int per_sm = 0;
-    cudaError_t e = dmax <= 3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_layer<R, 3>, 256, smem)
-                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_fused_layer<R, 5>, 256, smem);
-    if (e != cudaSuccess) return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const uint64_t runs = (total + kLayerRun - 1) / kLayerRun;
-    const uint64_t cap = (uint64_t)(sms > 0 ? sms : 152) * (uint64_t)per_sm;
-    const unsigned grid = (unsigned)(runs < cap ? runs : cap);
     if (dmax <= 3)
-        k_fused_layer<R, 3><<<grid, 256, smem, s>>>(entries, prefix, n, total, base);
+        k_fused_layer<R, 3><<<(unsigned)total, 256, smem, s>>>(entries, prefix, n, base);
     else
-        k_fused_layer<R, 5><<<grid, 256, smem, s>>>(entries, prefix, n, total, base);
+        k_fused_layer<R, 5><<<(unsigned)total, 256, smem, s>>>(entries, prefix, n, base);
     count_launch();
     return cudaGetLastError();
 }
@@ -2468,16 +2449,15 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
             big_idx.push_back(i);
         }
     }
-    // The layer queue.  The layered circuits are taken in groups of
-    // consecutive circuits whose states together fit in a third of the L2
-    // (a larger circuit is a group of its own): a group's layers run back to
-    // back, so its states stay in L2 from one pass to the next.  Within a
-    // group, layer k holds pass k of each of its circuits, split by shared
-    // memory per CTA (what lets 3, 2 or 1 CTAs reside on an SM, so that each
-    // launch's grid is resident at the occupancy of its own passes); each
-    // launch has the prefix of its entries' tile counts.  Per layered circuit
-    // a norm / reset record with the prefix of its reduction blocks and of
-    // its reset chunks.
+    // The layer queue: layer k holds pass k of every layered circuit, split
+    // by shared memory per CTA (so that a launch's CTAs reside at the
+    // occupancy of its own passes) and by the largest wire dimension (the
+    // kernel instance); each launch has the prefix of its entries' tile
+    // counts.  (Measured: grouping the circuits so that each group's states
+    // fit in L2 and running a group's layers back to back was slower, 1.27 s
+    // against 0.65 s for the 8192-circuit workload: many small launches.)
+    // Per layered circuit a norm / reset record with the prefix of its
+    // reduction blocks and of its reset chunks.
     struct LaunchGroup {
         size_t offE, offP;
         int32_t n;
@@ -2486,19 +2466,17 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
         size_t smem;
     };
     std::vector<LaunchGroup> groups;
-    constexpr size_t kL2Group = (size_t)44 << 20;
     for (size_t j0 = 0; j0 < layered.size();) {
-        size_t j1 = j0, bytes = 0, nl = 0;
-        while (j1 < layered.size() &&
-               (j1 == j0 || bytes + (size_t)b->D[layered[j1]] * ab <= kL2Group)) {
-            bytes += (size_t)b->D[layered[j1]] * ab;
-            nl = std::max(nl, c_ents[j1].size());
-            ++j1;
-        }
+        const size_t j1 = layered.size();
+        size_t nl = 0;
+        for (size_t j = j0; j < j1; ++j) nl = std::max(nl, c_ents[j].size());
         for (size_t k = 0; k < nl; ++k) {
-            const size_t bounds[3] = {72 * 1024, 110 * 1024, (size_t)1 << 40};
+            const size_t bounds[6] = {72 * 1024, 110 * 1024, (size_t)1 << 40, 72 * 1024, 110 * 1024, (size_t)1 << 40};
             size_t lo = 0;
-            for (size_t hi : bounds) {
+            for (int bi = 0; bi < 6; ++bi) {
+                const size_t hi = bounds[bi];
+                const bool want5 = bi >= 3;  // first the passes of wires up to dimension 3, then up to 5
+                if (bi == 3) lo = 0;
                 std::vector<LayerEntry<R>> ge;
                 std::vector<uint64_t> pre(1, 0);
                 int dm = 2;
@@ -2506,7 +2484,7 @@ static qd_status batch_run_impl(qd_batch* b, const qd_circuit* circuits, int32_t
                 for (size_t j = j0; j < j1; ++j) {
                     if (k >= c_ents[j].size()) continue;
                     const size_t x = c_smem[j][k];
-                    if (x <= lo || x > hi) continue;
+                    if (x <= lo || x > hi || (c_dmax[j][k] > 3) != want5) continue;
                     ge.push_back(c_ents[j][k]);
                     pre.push_back(pre.back() + c_ents[j][k].ntiles);
                     dm = std::max(dm, c_dmax[j][k]);

@@ -422,19 +422,19 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
                 // would be off by up to half an ulp of 1 in the same direction
                 // for every class (the bias is nearly uniform), a drift of its own.
                 // ni and no are compensated binary32 sums of exact squares
-                // (NormAcc), combined and turned into c in binary64.
+                // (NormAcc), combined in double-binary32 (NormFF).
                 s_nout[h][n] = make_float2(po.s, po.c);
                 consumer_sync<kCons>();
-                double ni = 0.0, no = 0.0;  // the parts combined, and c formed, in binary64
+                NormFF ni, no;
 #pragma unroll
                 for (int g = 0; g < GP; ++g) {
                     const float2 v = s_nin[i % kNinSlots][g][n];
-                    ni += (double)v.x + (double)v.y;
+                    ni.add(v.x, v.y);
                 }
 #pragma unroll
                 for (int g = 0; g < GC; ++g) {
                     const float2 v = s_nout[g][n];
-                    no += (double)v.x + (double)v.y;
+                    no.add(v.x, v.y);
                 }
                 cc = norm_fix(ni, no);
             }

@@ -64,7 +64,7 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(tf32_
 // blocks, accumulated without loss: each x^2 is split exactly into p + e
 // (p = x*x, e = fma(x, x, -p), the TwoProduct of Dekker / Ogita-Rump-Oishi)
 // and added to a binary32 Neumaier sum (s, c) whose compensation also
-// collects the e's; the parts are later combined in binary64.
+// collects the e's; the parts of a class are then combined by NormFF.
 struct NormAcc {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add_sq(float x) {
@@ -76,13 +76,33 @@ struct NormAcc {
     }
 };
 
-// Restoration factor c = sqrt(ni / no) - 1 in binary64 (ni, no: squared
-// norms of a class before and after the block, each given as binary32
-// parts); the output is then y + y c, one binary32 FMA per component.
-__device__ __forceinline__ float norm_fix(double ni, double no) {
-    if (!(ni > 0.0) || !(no > 0.0)) return 0.f;
-    const double sn = sqrt(no);
-    return (float)((ni - no) / (sn * (sqrt(ni) + sn)));
+// A squared norm held as an unevaluated sum hi + lo of binary32 values
+// (double-binary32): the partial sums (s, c) of the threads of a class are
+// added with Knuth's TwoSum, so the total keeps about twice the binary32
+// significand -- as accurate as binary64 for these sums, without the
+// binary64 pipe (1/64 of the FP32 rate on this part).
+struct NormFF {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float s, float c) {
+        const float t = hi + s;
+        const float bb = t - hi;
+        lo += ((hi - (t - bb)) + (s - bb)) + c;
+        hi = t;
+    }
+};
+
+// Restoration factor c = sqrt(ni / no) - 1 of a class with squared norms ni
+// (input) and no (output).  The difference ni - no carries the whole
+// information and is formed from the double-binary32 sums without loss
+// (ni.hi - no.hi is exact when the two are within a factor 2); delta =
+// (ni - no) / no is then needed to binary32 precision only, and
+// sqrt(1 + delta) - 1 = delta / 2 - delta^2 / 8 + O(delta^3) (|delta| is
+// about 1e-6 for the tensor cores' accumulation bias).
+__device__ __forceinline__ float norm_fix(const NormFF& ni, const NormFF& no) {
+    if (!(ni.hi > 0.f) || !(no.hi > 0.f)) return 0.f;
+    const float delta = ((ni.hi - no.hi) + (ni.lo - no.lo)) / no.hi;
+    if (fabsf(delta) > 1e-2f) return sqrtf(1.f + delta) - 1.f;
+    return delta * fmaf(-0.125f, delta, 0.5f);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
