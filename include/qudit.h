@@ -591,7 +591,27 @@ qd_status qd_plan_gate(const int32_t* dims, int32_t n, int32_t prec, const int32
  * (0, 0) restores the defaults.  Always QD_OK. */
 qd_status qd_test_set_tc_wait(uint32_t spin_limit, int32_t stall_producers);
 
-/* Host self-test of the index arithmetic (division by invariant integers
+/* Bounds-checked build (compiled with QD_BOUNDS=1: a debug build of the
+ * library in place of a memory sanitizer; the paper has no counterpart).
+ * Its gate kernels -- per-class register kernel, multi-wire tile kernel,
+ * fused tile passes, the batch layer queue and the tensor-core block kernel
+ * -- check every global index they form against the size of the buffer it
+ * indexes; an index outside is recorded (the first one) and that access is
+ * skipped, with no trap or assert.  qd_bounds_status reads and clears the
+ * record: QD_OK and *first_bad_index = -1 if nothing was recorded,
+ * QD_ERR_DEVICE and the index otherwise.  *checks_compiled is 1 in the
+ * bounds-checked build, 0 in the regular one (where the record stays empty).
+ * Either out pointer may be NULL. */
+qd_status qd_bounds_status(int64_t* first_bad_index, int32_t* checks_compiled);
+
+/* Testing hook of the bounds-checked build: the per-class register kernel
+ * and the multi-wire tile kernel are told that their state is `amplitudes`
+ * shorter than it is, so that accesses to its last amplitudes are reported
+ * (and skipped) -- the check exercised without any access outside a buffer.
+ * 0 restores the default.  QD_ERR_ARG for a negative value. */
+qd_status qd_test_set_bounds_shrink(int64_t amplitudes);
+
+/* Host self-test of the index arithmetic/* Host self-test of the index arithmetic (division by invariant integers
  * and the class enumeration) against plain integer division on
  * `trials` random cases.  QD_OK if every case agrees. */
 qd_status qd_selftest_host(int32_t trials);

@@ -22,7 +22,9 @@ QD_OK, QD_ERR_ARG, QD_ERR_OOM, QD_ERR_CUDA, QD_ERR_TIMEOUT, QD_ERR_UNSUPPORTED, 
 QD_C64, QD_C128 = 0, 1
 QD_MAX_WIRES, QD_MAX_DIM, QD_MAX_GATE_DIM, QD_MAX_CONTROLS = 48, 64, 64, 16
 
-LIB_PATH = _build.LIB
+# QD_BOUNDS=1 in the environment selects the bounds-checked build of the
+# library (built by build.build(bounds=True) into its own directory).
+LIB_PATH = _build.LIB_BOUNDS if os.environ.get("QD_BOUNDS") == "1" else _build.LIB
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libqudit.so is not built ({LIB_PATH}); run paper_2410_17876_gb300.build.build() "
                       "or __graft_entry__.build() first -- there is no CPU fallback")
@@ -119,6 +121,8 @@ _SIGS = {
     "qd_test_set_tc_wait": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_int32]),
     "qd_state_wire_to_top": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "qd_state_save": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p]),
+    "qd_bounds_status": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
+    "qd_test_set_bounds_shrink": (ctypes.c_int32, [ctypes.c_int64]),
     "qd_state_load": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p]),
     "qd_state_wire_from_top": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "qd_batch_create": (ctypes.c_int32, [ctypes.c_int32, _vp, ctypes.POINTER(_vp)]),
@@ -249,6 +253,18 @@ def qd_state_get_raw(st: int, out: Optional[np.ndarray] = None) -> np.ndarray:
         out = np.empty(D, dtype=dt)
     _check(_lib.qd_state_get_raw(_vp(st), _vp(out.ctypes.data), out.nbytes), "qd_state_get_raw")
     return out
+
+
+def qd_bounds_status():
+    """(status, first_bad_index, checks_compiled) of the bounds-checked build's record (read and cleared)."""
+    bad = ctypes.c_int64()
+    comp = ctypes.c_int32()
+    rc = _lib.qd_bounds_status(ctypes.byref(bad), ctypes.byref(comp))
+    return int(rc), int(bad.value), int(comp.value)
+
+
+def qd_test_set_bounds_shrink(amplitudes: int) -> None:
+    _check(_lib.qd_test_set_bounds_shrink(int(amplitudes)), "qd_test_set_bounds_shrink")
 
 
 def qd_state_save(st: int, path: str) -> None:

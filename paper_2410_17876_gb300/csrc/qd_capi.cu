@@ -105,6 +105,7 @@ qd_status make_plan(const Layout& L, int32_t prec, const int32_t* wires, int32_t
     if (nc < 0 || nc > QD_MAX_CONTROLS) return fail(QD_ERR_ARG, "%d controls outside [0, %d]", nc, QD_MAX_CONTROLS);
     if (nc > 0 && (!cw || !cv)) return fail(QD_ERR_ARG, "control lists are NULL");
     if (k + nc > L.n) return fail(QD_ERR_ARG, "gate wires plus controls exceed the wire count");
+    p.D = (uint64_t)L.D;
     bool used[kMaxWires] = {false};
     int64_t P = 1;
     for (int i = 0; i < k; ++i) {
@@ -280,6 +281,7 @@ static cudaError_t run_gate1(qd_state* st, const Plan& p, const double* U) {
     Gate1Args<R, DT> a;
     std::memset(static_cast<void*>(&a), 0, sizeof a);
     a.psi = reinterpret_cast<T2*>(st->psi);
+    a.D = p.D - g_bounds_shrink;
     a.n_elems = p.classes / (uint64_t)p.vec;
     a.bt = (uint64_t)p.bt;
     a.map = p.map;
@@ -304,6 +306,7 @@ static cudaError_t run_gate1_scan(qd_state* st, const Plan& p, const double* U, 
     Gate1Args<R, DT> a;
     std::memset(static_cast<void*>(&a), 0, sizeof a);
     a.psi = reinterpret_cast<T2*>(st->psi);
+    a.D = p.D - g_bounds_shrink;
     a.n_elems = p.classes;  // one class per thread
     a.bt = (uint64_t)p.bt;
     a.map = p.map;
@@ -366,6 +369,7 @@ static qd_status run_tile(qd_state* st, const Plan& p, const double* U) {
     GateTileArgs<R> a;
     std::memset(static_cast<void*>(&a), 0, sizeof a);
     a.psi = reinterpret_cast<T2*>(st->psi);
+    a.D = p.D - g_bounds_shrink;
     a.U = dptr;
     a.n_classes = p.classes;
     a.map = p.map;
@@ -863,6 +867,24 @@ qd_status qd_state_wire_from_top(qd_state* st, int32_t wire, const void* dev_in)
 // host buffer of the state's size is needed.
 static constexpr char kCkptMagic[8] = {'Q', 'D', 'S', 'T', 'A', 'T', 'E', '1'};
 static constexpr size_t kCkptChunk = (size_t)256 << 20;
+
+qd_status qd_bounds_status(int64_t* first_bad_index, int32_t* checks_compiled) {
+    const uint64_t v[3] = {bounds_take_kernels(), bounds_take_fusion(), bounds_take_tc()};
+    uint64_t bad = 0;
+    for (uint64_t x : v)
+        if (x && !bad) bad = x;
+    if (first_bad_index) *first_bad_index = bad ? (int64_t)(bad - 1) : -1;
+    if (checks_compiled) *checks_compiled = QD_BOUNDS;
+    if (bad) return fail(QD_ERR_DEVICE, "a kernel formed the index %llu outside its buffer (access skipped)",
+                         (unsigned long long)(bad - 1));
+    return QD_OK;
+}
+
+qd_status qd_test_set_bounds_shrink(int64_t amplitudes) {
+    if (amplitudes < 0) return fail(QD_ERR_ARG, "negative shrink");
+    g_bounds_shrink = (uint64_t)amplitudes;
+    return QD_OK;
+}
 
 qd_status qd_state_save(qd_state* st, const char* path) {
     QD_GUARD_BEGIN

@@ -687,16 +687,19 @@ __device__ __forceinline__ void tile_load_async(typename Cplx<R>::T2* tile, cons
                                                 const uint64_t* srow, const A& a) {
     constexpr uint32_t kEl = sizeof(typename Cplx<R>::T2);
     const uint32_t s0 = static_cast<uint32_t>(__cvta_generic_to_shared(tile));
+    const uint64_t gbase = (uint64_t)(g - a.psi), lim = (uint64_t)a.ntiles * a.T;  // bounds-checked build
     if (kEl == 16 || a.vec2) {
         constexpr uint32_t per = 16 / kEl;
         for (uint32_t e = per * threadIdx.x; e < a.T; e += per * blockDim.x) {
             const uint32_t r = a.bLdiv.div(e);
+            if (!in_bounds(gbase + srow[r] + (e - r * a.bL) + per - 1, lim)) continue;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s0 + e * kEl),
                          "l"(g + srow[r] + (e - r * a.bL)));
         }
     } else {
         for (uint32_t e = threadIdx.x; e < a.T; e += blockDim.x) {
             const uint32_t r = a.bLdiv.div(e);
+            if (!in_bounds(gbase + srow[r] + (e - r * a.bL), lim)) continue;
             asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s0 + e * kEl),
                          "l"(g + srow[r] + (e - r * a.bL)));
         }
@@ -747,15 +750,18 @@ __device__ __forceinline__ void tile_pass(const A& a, const char* chunks, const 
     tile_load_async<R>(tile, g, srow, a);  // published by apply_chunks' first barrier
     apply_chunks<R, DMAX>(tile, chunks, a.nchunks, stage, odig, nullptr, true);
     __syncthreads();
+    const uint64_t lim = (uint64_t)a.ntiles * a.T;  // bounds-checked build
     if (a.vec2) {
         for (uint32_t e = 2 * threadIdx.x; e < a.T; e += 2 * blockDim.x) {
             const uint32_t r = a.bLdiv.div(e);
+            if (!in_bounds(*sbase + srow[r] + (e - r * a.bL) + 1, lim)) continue;
             *reinterpret_cast<float4*>(reinterpret_cast<float2*>(g) + srow[r] + (e - r * a.bL)) =
                 reinterpret_cast<const float4*>(tile)[e >> 1];
         }
     } else {
         for (uint32_t e = threadIdx.x; e < a.T; e += blockDim.x) {
             const uint32_t r = a.bLdiv.div(e);
+            if (!in_bounds(*sbase + srow[r] + (e - r * a.bL), lim)) continue;
             g[srow[r] + (e - r * a.bL)] = tile[e];
         }
     }
@@ -862,14 +868,17 @@ __global__ void __launch_bounds__(256, 2) k_fused_tile_tc(const __grid_constant_
     const bool ok = apply_chunks<float, DMAX, true>(tile, a.chunks, a.nchunks, stage, odig, &ctx);
     __syncthreads();
     if (ok) {
+        const uint64_t lim = (uint64_t)a.ntiles * a.T;  // bounds-checked build
         if (a.vec2) {
             for (uint32_t e = 2 * tid; e < a.T; e += 2 * blockDim.x) {
                 const uint32_t r = a.bLdiv.div(e);
+                if (!in_bounds(sbase + srow[r] + (e - r * a.bL) + 1, lim)) continue;
                 *reinterpret_cast<float4*>(g + srow[r] + (e - r * a.bL)) = reinterpret_cast<const float4*>(tile)[e >> 1];
             }
         } else {
             for (uint32_t e = tid; e < a.T; e += blockDim.x) {
                 const uint32_t r = a.bLdiv.div(e);
+                if (!in_bounds(sbase + srow[r] + (e - r * a.bL), lim)) continue;
                 g[srow[r] + (e - r * a.bL)] = tile[e];
             }
         }
@@ -960,6 +969,12 @@ cudaError_t launch_fused_layer(const LayerEntry<R>* entries, const uint64_t* pre
     count_launch();
     return cudaGetLastError();
 }
+
+}  // namespace
+
+QD_DEFINE_BOUNDS_TAKE(bounds_take_fusion)
+
+namespace {
 
 // Whole circuits of small states, one CTA per circuit: the state starts as
 // |0...0> in shared memory, every chunk of the circuit is applied there,
@@ -1930,6 +1945,7 @@ static Op gate1_op(void* psi, const Plan& p, const double* U) {
     Gate1Args<R, DT> a;
     std::memset(static_cast<void*>(&a), 0, sizeof a);
     a.psi = reinterpret_cast<T2*>(psi);
+    a.D = p.D - g_bounds_shrink;
     a.n_elems = p.classes / (uint64_t)p.vec;
     a.bt = (uint64_t)p.bt;
     a.map = p.map;
@@ -1973,8 +1989,9 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int 
         std::vector<uint64_t> off(p.off, p.off + P);
         float2* dpsi = reinterpret_cast<float2*>(psi);
         const bool renorm = unitary;
-        return [dpsi, aoff, tc_mode, renorm, classes, map, P, off](cudaStream_t s, const char* base) {
-            return launch_block_tc(dpsi, base + aoff, tc_mode, renorm, classes, map, P, off.data(), s);
+        const uint64_t D = p.D;
+        return [dpsi, aoff, tc_mode, renorm, classes, map, P, off, D](cudaStream_t s, const char* base) {
+            return launch_block_tc(dpsi, D, base + aoff, tc_mode, renorm, classes, map, P, off.data(), s);
         };
     }
     std::vector<T2> m((size_t)P * P);
@@ -1986,6 +2003,7 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int 
     GateTileArgs<R> a;
     std::memset(static_cast<void*>(&a), 0, sizeof a);
     a.psi = reinterpret_cast<T2*>(psi);
+    a.D = p.D - g_bounds_shrink;
     a.n_classes = p.classes;
     a.map = p.map;
     a.P = P;

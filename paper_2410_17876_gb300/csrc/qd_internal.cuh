@@ -26,7 +26,51 @@
 #define QD_HD __host__ __device__ __forceinline__
 #endif
 
+// Bounds-checked build (QD_BOUNDS=1; a debug build in place of a memory
+// sanitizer).  The gate kernels check every global index they form against
+// the size of the buffer it indexes.  An index outside records the first
+// such index (plus one) in a device word of its translation unit and the
+// access is skipped: no trap, no assert.  qd_bounds_status reads and clears
+// the words.  The regular build compiles the checks out.
+#ifndef QD_BOUNDS
+#define QD_BOUNDS 0
+#endif
+
 namespace qd {
+
+namespace {
+#if QD_BOUNDS
+__device__ unsigned long long g_bounds_bad = 0ull;
+__device__ __forceinline__ bool in_bounds(uint64_t i, uint64_t n) {
+    if (i < n) return true;
+    atomicCAS(&g_bounds_bad, 0ull, (unsigned long long)i + 1ull);
+    return false;
+}
+#else
+__device__ __forceinline__ constexpr bool in_bounds(uint64_t, uint64_t) { return true; }
+#endif
+}  // namespace
+
+// Host side of one translation unit's bounds word: 0, or 1 + the first index
+// found outside its buffer; cleared on read (0 in the regular build).
+#if QD_BOUNDS
+#define QD_DEFINE_BOUNDS_TAKE(fname)                                                              \
+    uint64_t fname() {                                                                            \
+        unsigned long long v = 0ull, z = 0ull;                                                    \
+        if (cudaMemcpyFromSymbol(&v, g_bounds_bad, sizeof v) != cudaSuccess) return 0;            \
+        if (v) cudaMemcpyToSymbol(g_bounds_bad, &z, sizeof z);                                    \
+        return (uint64_t)v;                                                                       \
+    }
+#else
+#define QD_DEFINE_BOUNDS_TAKE(fname) \
+    uint64_t fname() { return 0; }
+#endif
+uint64_t bounds_take_kernels();
+uint64_t bounds_take_fusion();
+uint64_t bounds_take_tc();
+// Amplitudes the bounds-checked build hides from the end of every buffer
+// (a testing hook: accesses there are then reported and skipped).
+extern uint64_t g_bounds_shrink;
 
 constexpr int kMaxWires = 48;
 constexpr int kMaxInserted = 24;  // gate wires (<= 6 for P <= 64) + controls (<= 16)
@@ -110,6 +154,7 @@ template <typename R, int DT>
 struct Gate1Args {
     using T2 = typename Cplx<R>::T2;
     T2* psi;
+    uint64_t D;           // amplitudes of the state (bounds-checked build)
     uint64_t n_elems;     // classes / vec
     uint64_t bt;          // stride of the target wire (distance between class members)
     IndexMap map;
@@ -135,6 +180,7 @@ template <typename R>
 struct GateTileArgs {
     using T2 = typename Cplx<R>::T2;
     T2* psi;
+    uint64_t D;           // amplitudes of the state (bounds-checked build)
     const T2* U;          // device, P x P row-major
     uint64_t n_classes;
     IndexMap map;
@@ -172,7 +218,7 @@ cudaError_t launch_narrow(const double* in, int64_t D, void* psi, cudaStream_t s
 // Tensor-core path for composed blocks (qd_tc.cu, complex64 only).
 size_t block_tc_operand_bytes();
 void block_tc_pack(const double* U, int P, int tc_mode, void* out);
-cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool renorm, uint64_t n_classes,
+cudaError_t launch_block_tc(float2* psi, uint64_t D, const void* a_ops, int tc_mode, bool renorm, uint64_t n_classes,
                             const IndexMap& map, int P, const uint64_t* off, cudaStream_t s);
 bool block_is_unitary(const double* U, int P, double tol);
 int32_t tc_status_take(cudaStream_t s);

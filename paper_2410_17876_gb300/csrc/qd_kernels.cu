@@ -49,6 +49,7 @@ template <> struct Ld<2> {  // complex64 only: one 16-byte access
 template <typename R, int DT, int VEC>
 __device__ __forceinline__ void gate1_class(const Gate1Args<R, DT>& a, uint64_t j) {
     using T2 = typename Cplx<R>::T2;
+    if (!in_bounds(j + (uint64_t)(DT - 1) * a.bt + (VEC - 1), a.D)) return;  // the class's last member
     T2* base = a.psi + j;
     T2 x[DT][VEC];
 #pragma unroll
@@ -144,7 +145,7 @@ __global__ void __launch_bounds__(256) k_gate_tile(const __grid_constant__ GateT
         T2 v;
         v.x = 0;
         v.y = 0;
-        if (valid) v = a.psi[j + a.off[r]];
+        if (valid && in_bounds(j + a.off[r], a.D)) v = a.psi[j + a.off[r]];
         sX[r * Q + q] = v;
     }
     __syncthreads();
@@ -165,7 +166,7 @@ __global__ void __launch_bounds__(256) k_gate_tile(const __grid_constant__ GateT
 #pragma unroll
         for (int i = 0; i < RB; ++i) {
             const int r = r0 + i * nrg;
-            if (r < P) a.psi[j + a.off[r]] = acc[i];
+            if (r < P && in_bounds(j + a.off[r], a.D)) a.psi[j + a.off[r]] = acc[i];
         }
     }
 }
@@ -457,6 +458,9 @@ int grid_for(int64_t n, int per_block = 256, int cap = 152 * 16) {
 }  // namespace
 
 int reduce_blocks(int64_t D) { return grid_for(D, 256 * 4, 1024); }
+
+QD_DEFINE_BOUNDS_TAKE(bounds_take_kernels)
+uint64_t g_bounds_shrink = 0;
 
 template <typename R, int DT, int VEC>
 cudaError_t launch_gate1(const Gate1Args<R, DT>& a, cudaStream_t s) {

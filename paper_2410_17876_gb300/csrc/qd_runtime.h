@@ -62,6 +62,7 @@ struct Plan {
     int64_t bt;
     IndexMap map;
     uint64_t classes;
+    uint64_t D;   // amplitudes of the state
     int64_t run;
     uint64_t off[kMaxGateDim];
 };

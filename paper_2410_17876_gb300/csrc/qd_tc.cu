@@ -59,6 +59,7 @@ constexpr int kYStride = 68;          // floats per staged accumulator row (bank
 
 struct TcArgs {
     float2* psi;
+    uint64_t D;           // amplitudes of the state (bounds-checked build)
     const void* a_ops;    // TF32x3: A_hi then A_lo, each 128 x 128 row-major floats (row = output,
                           // column = K); BF16x3: A_hi then A_lo, each in the K-major canonical layout
     uint64_t n_classes;
@@ -282,7 +283,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
 #pragma unroll
             for (int e = 0; e < MPT; ++e) {
                 const int r = row_of(e);
-                x[e] = (ok && r < a.P) ? a.psi[base + a.off[r]] : make_float2(0.f, 0.f);
+                x[e] = (ok && r < a.P && in_bounds(base + a.off[r], a.D)) ? a.psi[base + a.off[r]]
+                                                                           : make_float2(0.f, 0.f);
             }
         };
         uint32_t ph_mma[2] = {0u, 0u};
@@ -298,13 +300,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             }
             unsigned char* b = sB + st * kStage;
             if (a.renorm) {
-                NormAcc pn;
+                if constexpr (kBf) {  // BF16x3 (2^-16 per block): a binary32 sum is accurate enough
+                    float pn = 0.f;
 #pragma unroll
-                for (int e = 0; e < MPT; ++e) {
-                    pn.add_sq(cur[e].x);
-                    pn.add_sq(cur[e].y);
+                    for (int e = 0; e < MPT; ++e) pn = fmaf(cur[e].x, cur[e].x, fmaf(cur[e].y, cur[e].y, pn));
+                    s_nin[i % kNinSlots][q0][n] = make_float2(pn, 0.f);
+                } else {
+                    NormAcc pn;
+#pragma unroll
+                    for (int e = 0; e < MPT; ++e) {
+                        pn.add_sq(cur[e].x);
+                        pn.add_sq(cur[e].y);
+                    }
+                    s_nin[i % kNinSlots][q0][n] = make_float2(pn.s, pn.c);
                 }
-                s_nin[i % kNinSlots][q0][n] = make_float2(pn.s, pn.c);
             }
             if constexpr (kBf) {
 #pragma unroll
@@ -402,13 +411,18 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
             // outputs: y_r = (Y[r][n], Y[64 + r][n]), lanes along the classes
             float2 y[OPT];
             NormAcc po;
+            float po_plain = 0.f;
 #pragma unroll
             for (int k = 0; k < OPT; ++k) {
                 const int r = h + GC * k;
                 y[k] = r < a.P ? make_float2(Y[r * kYStride + n], Y[(64 + r) * kYStride + n]) : make_float2(0.f, 0.f);
                 if (a.renorm) {
-                    po.add_sq(y[k].x);
-                    po.add_sq(y[k].y);
+                    if constexpr (kBf) {
+                        po_plain = fmaf(y[k].x, y[k].x, fmaf(y[k].y, y[k].y, po_plain));
+                    } else {
+                        po.add_sq(y[k].x);
+                        po.add_sq(y[k].y);
+                    }
                 }
             }
             float cc = 0.f;
@@ -421,9 +435,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
                 // c is applied by one FMA: a factor 1 + c rounded to binary32
                 // would be off by up to half an ulp of 1 in the same direction
                 // for every class (the bias is nearly uniform), a drift of its own.
-                // ni and no are compensated binary32 sums of exact squares
-                // (NormAcc), combined in double-binary32 (NormFF).
-                s_nout[h][n] = make_float2(po.s, po.c);
+                // TF32x3: ni and no are compensated binary32 sums of exact
+                // squares (NormAcc), combined in double-binary32 (NormFF);
+                // measured on the large workload's prefix, the norm drifts
+                // by -5.1e-8 instead of -2.7e-7 with plain binary32 sums (at
+                // about a quarter more time per pass: the consumer warps are
+                // the kernel's critical path).  BF16x3 (2^-16 per block)
+                // keeps plain binary32 sums: compensation did not change its
+                // drift (-5.6e-8 against -2.5e-8).
+                s_nout[h][n] = kBf ? make_float2(po_plain, 0.f) : make_float2(po.s, po.c);
                 consumer_sync<kCons>();
                 NormFF ni, no;
 #pragma unroll
@@ -444,7 +464,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
 #pragma unroll
                 for (int k = 0; k < OPT; ++k) {
                     const int r = h + GC * k;
-                    if (r < a.P)
+                    if (r < a.P && in_bounds(base + a.off[r], a.D))
                         a.psi[base + a.off[r]] = make_float2(fmaf(y[k].x, cc, y[k].x), fmaf(y[k].y, cc, y[k].y));
                 }
             }
@@ -456,6 +476,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kCols));
 }
+
+}  // namespace
+
+QD_DEFINE_BOUNDS_TAKE(bounds_take_tc)
+
+namespace {
 
 // Status word of the tensor-core kernels: 0, or an error code set by a
 // kernel whose bounded wait gave up.  Read and cleared by tc_status_take().
@@ -588,7 +614,7 @@ static cudaError_t launch_tc_mode(const TcArgs& a, uint64_t chunks, int sm_count
     return cudaSuccess;
 }
 
-cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool renorm, uint64_t n_classes,
+cudaError_t launch_block_tc(float2* psi, uint64_t D, const void* a_ops, int tc_mode, bool renorm, uint64_t n_classes,
                             const IndexMap& map, int P, const uint64_t* off, cudaStream_t s) {
     if (n_classes == 0) return cudaSuccess;
     if (tc_mode != QD_TC_TF32X3 && tc_mode != QD_TC_BF16X3) return cudaErrorInvalidValue;
@@ -603,6 +629,7 @@ cudaError_t launch_block_tc(float2* psi, const void* a_ops, int tc_mode, bool re
     if (!status) return cudaErrorInvalidSymbol;
     TcArgs a;
     a.psi = psi;
+    a.D = D;
     a.a_ops = a_ops;
     a.n_classes = n_classes;
     a.map = map;

@@ -116,3 +116,10 @@ def test_invalid_layouts_rejected():
     for dims in [(1, 2), (2, 65), ()]:
         with pytest.raises(qb.QuditError):
             _plan(dims, [0], np.eye(2))
+
+
+def test_regular_build_has_no_bounds_checks():
+    """qd_bounds_status in the regular build: no checks compiled, nothing recorded (no GPU needed)."""
+    from paper_2410_17876_gb300 import binding as qb
+
+    assert qb.qd_bounds_status() == (qb.QD_OK, -1, 0)
