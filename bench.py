@@ -181,8 +181,8 @@ def measured_peaks():
 
 KERNEL_SOURCES = {
     "gate": ("qd_kernels.cu", "qd_internal.cuh"),
-    "fused": ("qd_fusion.cu", "qd_internal.cuh", "qd_program.h"),
-    "tc": ("qd_tc.cu", "qd_internal.cuh"),
+    "fused": ("qd_fusion.cu", "qd_internal.cuh", "qd_program.h", "qd_tc_common.cuh"),
+    "tc": ("qd_tc.cu", "qd_internal.cuh", "qd_tc_common.cuh"),
 }
 TRAFFIC_FILES = {"gate": "gate_kernel_traffic.json", "fused": "fused_kernel_traffic.json",
                  "tc": "tc_kernel_traffic.json"}
