@@ -7,10 +7,14 @@
 // kernels depend only on its own circuit, so its result is the same alone
 // and in any mix.
 //
-// One worker thread owns every CUDA call of the server: it releases timed
+// One worker thread owns the server's streams: it releases timed
 // submissions, admits requests in arrival order (first-fit allocation in one
 // device arena of the byte budget), issues their programs, polls completion
-// events and publishes results.
+// events and publishes results.  The programs themselves (pass planning,
+// block composition, descriptors: about half a millisecond of host time for
+// a 277-gate request) are built by a pool of builder threads as soon as a
+// request is admitted, so that one host thread's planning does not cap the
+// number of requests served per second.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -89,6 +93,8 @@ struct Request {
     double t_admit, t_done;
     double norm;
     int32_t status;
+    Program prog;                // built by a builder thread after admission
+    std::atomic<int> built{0};   // 0 pending, 1 built, 2 failed
 };
 
 struct Slot {  // runs one non-small request at a time
@@ -99,6 +105,17 @@ struct Slot {  // runs one non-small request at a time
     double* dnorm;
     double* hnorm;  // pinned
     std::shared_ptr<Request> req;
+    bool issued = false;
+};
+
+// The one-CTA program of a group of small requests, built by a builder thread.
+struct GroupBuild {
+    std::vector<std::shared_ptr<Request>> reqs;
+    Program prog;
+    size_t o3 = 0, o5 = 0;
+    int n3 = 0, n5 = 0;
+    uint32_t m3 = 1, m5 = 1;
+    std::atomic<int> built{0};  // 0 pending, 1 built, 2 failed
 };
 
 struct Lane {  // runs one group of small requests at a time
@@ -108,6 +125,14 @@ struct Lane {  // runs one group of small requests at a time
     double* dnorms;
     double* hnorms;  // pinned
     std::vector<std::shared_ptr<Request>> reqs;
+    std::shared_ptr<GroupBuild> gb;
+    bool issued = false;
+};
+
+// A build task: a non-small request's program, or a small-request group's.
+struct BuildTask {
+    std::shared_ptr<Request> req;
+    std::shared_ptr<GroupBuild> group;
 };
 
 constexpr int kLanes = 4;
@@ -137,6 +162,12 @@ struct qd_server {
     std::atomic<bool> stop{false};
     std::thread worker;
 
+    std::mutex bmu;  // builder pool
+    std::condition_variable bcv;
+    std::deque<BuildTask> bq;
+    bool bstop = false;
+    std::vector<std::thread> builders;
+
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
 };
 
@@ -163,11 +194,67 @@ void publish(qd_server* s, const std::shared_ptr<Request>& r) {
     s->cv.notify_all();
 }
 
+// Builder thread: host-side construction of programs (no stream work).
+template <typename R>
+void builder_loop(qd_server* s) {
+    cudaSetDevice(s->device);
+    while (true) {
+        BuildTask t;
+        {
+            std::unique_lock<std::mutex> lk(s->bmu);
+            s->bcv.wait(lk, [&] { return s->bstop || !s->bq.empty(); });
+            if (s->bq.empty()) return;  // stopping and nothing left
+            t = std::move(s->bq.front());
+            s->bq.pop_front();
+        }
+        int ok = 1;
+        try {
+            if (t.req) {
+                Request& r = *t.req;
+                build_program<R>(r.L, s->arena_dev + r.off, r.G, s->cfg, true, r.prog);
+            } else {
+                GroupBuild& g = *t.group;
+                std::vector<SmallTask> t3, t5;
+                for (size_t i = 0; i < g.reqs.size(); ++i) {
+                    const Request& r = *g.reqs[i];
+                    SmallTask st{};
+                    st.psi_off = r.off;
+                    st.D = (uint32_t)r.L.D;
+                    st.norm_index = (uint32_t)i;
+                    st.chunk_off = put_small_chunks<R>(r.L, r.G, s->cfg, g.prog, &st.nchunks);
+                    if (r.dmax <= 3) {
+                        t3.push_back(st);
+                        g.m3 = std::max(g.m3, st.D);
+                    } else {
+                        t5.push_back(st);
+                        g.m5 = std::max(g.m5, st.D);
+                    }
+                }
+                g.o3 = t3.empty() ? 0 : g.prog.put(t3.data(), sizeof(SmallTask) * t3.size());
+                g.o5 = t5.empty() ? 0 : g.prog.put(t5.data(), sizeof(SmallTask) * t5.size());
+                g.n3 = (int)t3.size();
+                g.n5 = (int)t5.size();
+            }
+        } catch (...) {
+            ok = 2;
+        }
+        if (t.req) t.req->built.store(ok, std::memory_order_release);
+        else t.group->built.store(ok, std::memory_order_release);
+    }
+}
+
+void enqueue_build(qd_server* s, BuildTask t) {
+    {
+        std::lock_guard<std::mutex> lk(s->bmu);
+        s->bq.push_back(std::move(t));
+    }
+    s->bcv.notify_one();
+}
+
 template <typename R>
 bool issue_big(qd_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
     NvtxRange nvtx_("served request");
-    Program prog;
-    build_program<R>(r->L, s->arena_dev + r->off, r->G, s->cfg, true, prog);
+    const Program& prog = r->prog;
     if (sl.arena.upload(prog.desc.data(), prog.desc.size(), sl.stream) != QD_OK) return false;
     if (issue(prog, static_cast<const char*>(sl.arena.dev), sl.stream) != QD_OK) return false;
     if (launch_norm<R>(s->arena_dev + r->off, r->L.D, sl.partials, reduce_blocks(r->L.D), sl.dnorm, sl.stream) !=
@@ -180,33 +267,15 @@ bool issue_big(qd_server* s, Slot& sl, const std::shared_ptr<Request>& r) {
 
 template <typename R>
 bool issue_small(qd_server* s, Lane& ln) {
-    Program prog;
-    std::vector<SmallTask> t3, t5;
-    uint32_t m3 = 1, m5 = 1;
-    for (size_t i = 0; i < ln.reqs.size(); ++i) {
-        const Request& r = *ln.reqs[i];
-        SmallTask t{};
-        t.psi_off = r.off;
-        t.D = (uint32_t)r.L.D;
-        t.norm_index = (uint32_t)i;
-        t.chunk_off = put_small_chunks<R>(r.L, r.G, s->cfg, prog, &t.nchunks);
-        if (r.dmax <= 3) {
-            t3.push_back(t);
-            m3 = std::max(m3, t.D);
-        } else {
-            t5.push_back(t);
-            m5 = std::max(m5, t.D);
-        }
-    }
-    const size_t o3 = t3.empty() ? 0 : prog.put(t3.data(), sizeof(SmallTask) * t3.size());
-    const size_t o5 = t5.empty() ? 0 : prog.put(t5.data(), sizeof(SmallTask) * t5.size());
-    if (ln.arena.upload(prog.desc.data(), prog.desc.size(), ln.stream) != QD_OK) return false;
+    NvtxRange nvtx_("served small-request group");
+    const GroupBuild& g = *ln.gb;
+    if (ln.arena.upload(g.prog.desc.data(), g.prog.desc.size(), ln.stream) != QD_OK) return false;
     const char* base = static_cast<const char*>(ln.arena.dev);
-    if (launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + o3), (int)t3.size(), 3, m3, s->arena_dev,
-                              base, ln.dnorms, ln.stream) != cudaSuccess)
+    if (launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + g.o3), g.n3, 3, g.m3, s->arena_dev, base,
+                              ln.dnorms, ln.stream) != cudaSuccess)
         return false;
-    if (launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + o5), (int)t5.size(), 5, m5, s->arena_dev,
-                              base, ln.dnorms, ln.stream) != cudaSuccess)
+    if (launch_batch_small<R>(reinterpret_cast<const SmallTask*>(base + g.o5), g.n5, 5, g.m5, s->arena_dev, base,
+                              ln.dnorms, ln.stream) != cudaSuccess)
         return false;
     if (cudaMemcpyAsync(ln.hnorms, ln.dnorms, sizeof(double) * ln.reqs.size(), cudaMemcpyDeviceToHost,
                         ln.stream) != cudaSuccess)
@@ -276,23 +345,50 @@ void worker_loop(qd_server* s) {
             } else {
                 Slot& sl = s->slots[(size_t)slot];
                 sl.req = r;
-                if (!issue_big<R>(s, sl, r)) {
-                    cudaGetLastError();
-                    r->status = QD_ERR_CUDA;
-                }
+                sl.issued = false;
+                enqueue_build(s, BuildTask{r, nullptr});
             }
         }
         if (!group.empty()) {
             Lane& ln = s->lanes[free_lane];
             ln.reqs = group;
-            if (!issue_small<R>(s, ln)) {
+            ln.gb = std::make_shared<GroupBuild>();
+            ln.gb->reqs = group;
+            ln.issued = false;
+            enqueue_build(s, BuildTask{nullptr, ln.gb});
+        }
+        // issue what the builders have finished
+        for (Slot& sl : s->slots) {
+            if (!sl.req || sl.issued) continue;
+            const int b = sl.req->built.load(std::memory_order_acquire);
+            if (b == 0) continue;
+            sl.issued = true;
+            progressed = true;
+            if (b == 2) {
+                sl.req->status = QD_ERR_OOM;  // host failure while building
+            } else if (!issue_big<R>(s, sl, sl.req)) {
+                cudaGetLastError();
+                sl.req->status = QD_ERR_CUDA;
+            }
+            sl.req->prog = Program();  // descriptors uploaded, launches issued
+        }
+        for (Lane& ln : s->lanes) {
+            if (ln.reqs.empty() || ln.issued) continue;
+            const int b = ln.gb->built.load(std::memory_order_acquire);
+            if (b == 0) continue;
+            ln.issued = true;
+            progressed = true;
+            if (b == 2) {
+                for (auto& r : ln.reqs) r->status = QD_ERR_OOM;
+            } else if (!issue_small<R>(s, ln)) {
                 cudaGetLastError();
                 for (auto& r : ln.reqs) r->status = QD_ERR_CUDA;
             }
+            ln.gb.reset();
         }
         // completions
         for (Slot& sl : s->slots) {
-            if (!sl.req) continue;
+            if (!sl.req || !sl.issued) continue;
             const cudaError_t q = sl.req->status == QD_OK ? cudaEventQuery(sl.done) : cudaSuccess;
             if (q == cudaErrorNotReady) continue;
             std::shared_ptr<Request> r = sl.req;
@@ -305,7 +401,7 @@ void worker_loop(qd_server* s) {
             progressed = true;
         }
         for (Lane& ln : s->lanes) {
-            if (ln.reqs.empty()) continue;
+            if (ln.reqs.empty() || !ln.issued) continue;
             const bool failed = ln.reqs[0]->status != QD_OK;
             const cudaError_t q = failed ? cudaSuccess : cudaEventQuery(ln.done);
             if (q == cudaErrorNotReady) continue;
@@ -344,6 +440,13 @@ void destroy_server(qd_server* s) {
         s->cv.notify_all();
         s->worker.join();
     }
+    {
+        std::lock_guard<std::mutex> lk(s->bmu);
+        s->bstop = true;
+    }
+    s->bcv.notify_all();
+    for (std::thread& t : s->builders)
+        if (t.joinable()) t.join();
     cudaDeviceSynchronize();
     for (Slot& sl : s->slots) {
         if (sl.stream) cudaStreamDestroy(sl.stream);
@@ -419,6 +522,12 @@ qd_status qd_server_create(int32_t prec, const qd_server_opts* opts, qd_server**
             destroy_server(s);
             return fail(QD_ERR_CUDA, "server set-up: %s", cudaGetErrorString(e));
         }
+        tc_status_ptr();  // resolved once here, before builder threads may ask for it
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int nb = (int)std::max(1u, std::min(8u, hw > 2 ? hw - 2 : 1u));
+        for (int i = 0; i < nb; ++i)
+            s->builders.emplace_back(prec == QD_C64 ? std::thread(builder_loop<float>, s)
+                                                    : std::thread(builder_loop<double>, s));
         s->worker = prec == QD_C64 ? std::thread(worker_loop<float>, s) : std::thread(worker_loop<double>, s);
         *out = s;
         return QD_OK;
