@@ -231,7 +231,9 @@ typedef struct qd_gate_desc {
  * The tensor-core modes split both operands, a = a_hi + a_lo, and accumulate
  * A_hi X_hi + A_hi X_lo + A_lo X_hi in FP32 in tensor memory. */
 #define QD_TC_TF32X3 0 /* tensor cores, TF32 parts (about 2^-21 relative per block); the default */
-#define QD_TC_BF16X3 1 /* tensor cores, BF16 parts (about 2^-16 relative per block) */
+#define QD_TC_BF16X3 1 /* tensor cores, BF16 parts (about 2^-16 relative per block); blocks without
+                          controls stream the state through a ring of shared-memory tiles (the
+                          classes of a tile as tensor-memory rows of the MMA's A operand) */
 #define QD_TC_OFF 2    /* FP32 CUDA cores (binary32 FMA, no split) */
 
 typedef struct qd_fusion_opts {
@@ -577,19 +579,24 @@ qd_status qd_plan_gate(const int32_t* dims, int32_t n, int32_t prec, const int32
                        int32_t k, const double* U, const int32_t* ctrl_wires,
                        const int32_t* ctrl_vals, int32_t n_ctrl, qd_plan_info* out);
 
-/* Testing hook of the bounded waits in the tensor-core block kernel (complex64
+/* Testing hook of the bounded waits in the tensor-core block kernels (complex64
  * blocks of 17..64 dimensions: qd_apply_multi, QD_FUSE_BLOCK passes, deferred
- * fusion).  The paper has no counterpart; it exists so that the timeout path
+ * fusion; the register-staged kernel and the BF16x3 tile-ring kernel).  The paper has no counterpart; it exists so that the timeout path
  * can be exercised without a GPU fault.  Every mbarrier wait of that kernel
  * gives up after spin_limit polls (0 = the default, 2^26); the kernel then
  * records QD_ERR_TIMEOUT in its status word, issues no further work, writes
  * no output, releases its tensor memory and returns, and the next readout
  * of the state (qd_norm, qd_probabilities, ...) returns QD_ERR_TIMEOUT.
- * stall_producers != 0 makes the kernel's producer warps publish nothing, so
- * the first waits run out and the pass leaves the state as it was.  The
+ * stall_producers != 0 makes the kernel's producer (or loader) warps publish
+ * nothing, so the first waits run out and the pass leaves the state as it was.  The
  * setting is process-wide and applies to launches issued after the call;
  * (0, 0) restores the defaults.  Always QD_OK. */
 qd_status qd_test_set_tc_wait(uint32_t spin_limit, int32_t stall_producers);
+
+/* Testing hook: launches of the BF16x3 tile-ring kernel since the library was
+ * loaded (process-wide), so that a test can tell which tensor-core kernel
+ * ran a block.  Always QD_OK; out may not be NULL. */
+qd_status qd_test_tc_ring_launches(int64_t* out);
 
 /* Bounds-checked build (compiled with QD_BOUNDS=1: a debug build of the
  * library in place of a memory sanitizer; the paper has no counterpart).
@@ -611,7 +618,7 @@ qd_status qd_bounds_status(int64_t* first_bad_index, int32_t* checks_compiled);
  * 0 restores the default.  QD_ERR_ARG for a negative value. */
 qd_status qd_test_set_bounds_shrink(int64_t amplitudes);
 
-/* Host self-test of the index arithmetic/* Host self-test of the index arithmetic (division by invariant integers
+/* Host self-test of the index arithmetic (division by invariant integers
  * and the class enumeration) against plain integer division on
  * `trials` random cases.  QD_OK if every case agrees. */
 qd_status qd_selftest_host(int32_t trials);

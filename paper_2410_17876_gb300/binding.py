@@ -119,6 +119,7 @@ _SIGS = {
                                       _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(qd_plan_info)]),
     "qd_selftest_host": (ctypes.c_int32, [ctypes.c_int32]),
     "qd_test_set_tc_wait": (ctypes.c_int32, [ctypes.c_uint32, ctypes.c_int32]),
+    "qd_test_tc_ring_launches": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int64)]),
     "qd_state_wire_to_top": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "qd_state_save": (ctypes.c_int32, [ctypes.c_void_p, ctypes.c_char_p]),
     "qd_bounds_status": (ctypes.c_int32, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]),
@@ -375,6 +376,13 @@ def qd_test_set_tc_wait(spin_limit: int = 0, stall_producers: bool = False) -> N
     """Testing hook: polls per bounded wait of the tensor-core block kernel (0 = default)
     and whether its producers publish nothing (so that its waits run out)."""
     _check(_lib.qd_test_set_tc_wait(int(spin_limit), 1 if stall_producers else 0), "qd_test_set_tc_wait")
+
+
+def qd_test_tc_ring_launches() -> int:
+    """Launches of the BF16x3 tile-ring kernel since the library was loaded."""
+    out = ctypes.c_int64(0)
+    _check(_lib.qd_test_tc_ring_launches(ctypes.byref(out)), "qd_test_tc_ring_launches")
+    return int(out.value)
 
 
 def qd_selftest_host(trials: int = 200) -> None:

@@ -25,25 +25,6 @@
 
 namespace qd {
 
-// ---------------------------------------------------------------------------
-// 32-bit division by invariant integers (same method as FastDiv, N = 32).
-// ---------------------------------------------------------------------------
-struct FastDiv32 {
-    uint32_t d, mul, s1, s2;
-    __host__ void init(uint32_t div) {
-        d = div;
-        int l = 0;
-        while (l < 32 && ((uint64_t)1 << l) < div) ++l;
-        mul = (uint32_t)(((((uint64_t)1 << l) - div) << 32) / div + 1);
-        s1 = l < 1 ? l : 1;
-        s2 = l > 1 ? l - 1 : 0;
-    }
-    __device__ __forceinline__ uint32_t div(uint32_t n) const {
-        const uint32_t t = __umulhi(mul, n);
-        return (t + ((n - t) >> s1)) >> s2;
-    }
-};
-
 constexpr int kMaxFusedD = 5;      // single-wire gates up to this dimension join fused passes
 constexpr int kMaxTileCtrl = 7;    // controls of a fused gate (inside or outside the tile)
 constexpr int kMaxLocalIns = 1 + kMaxTileCtrl;
@@ -1965,7 +1946,8 @@ static Op gate1_op(void* psi, const Plan& p, const double* U) {
 
 // The op of one gate for the per-gate kernels (no fusion).
 template <typename R>
-static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int tc_mode, bool unitary) {
+static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int tc_mode, bool unitary,
+                  const Layout& L, const int32_t* wires, int nwires, int ncontrols) {
     using T2 = typename Cplx<R>::T2;
     if (p.family == 0) {
         switch (p.d) {
@@ -1979,6 +1961,16 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int 
         }
     }
     const int P = p.P;
+    if (sizeof(R) == 4 && P >= kTcMinP && tc_mode == QD_TC_BF16X3 && ncontrols == 0) {
+        // BF16x3 through the ring of tiles, where the block suits it
+        std::vector<unsigned char> bops;
+        std::shared_ptr<const BlockRing> ring = block_ring_prepare(L, reinterpret_cast<float2*>(psi), wires, nwires, P,
+                                                                   U, unitary, bops);
+        if (ring) {
+            const size_t boff = prog.put(bops.data(), bops.size());
+            return [ring, boff](cudaStream_t s, const char* base) { return launch_block_ring(*ring, base + boff, s); };
+        }
+    }
     if (sizeof(R) == 4 && P >= kTcMinP && tc_mode != QD_TC_OFF) {
         // complex64 block of 17..64 dimensions: tensor cores
         std::vector<float> A(block_tc_operand_bytes() / sizeof(float));
@@ -2035,14 +2027,16 @@ static void build_passes(const Layout& L, void* psi, const std::vector<HGate>& G
             if (q.family == 0 && q.smask == 0) continue;  // identity
             bool unitary = true;
             for (int idx : p.gates) unitary = unitary && G[idx].unitary;
-            prog.ops.push_back(gate_op<R>(psi, q, M.data(), prog, cfg.tc_mode, unitary));
+            std::vector<int32_t> w32(wl.begin(), wl.end());
+            prog.ops.push_back(gate_op<R>(psi, q, M.data(), prog, cfg.tc_mode, unitary, L, w32.data(),
+                                          (int)w32.size(), 0));
             continue;
         }
         if (!p.tile) {
             const HGate& h = G[p.gates[0]];
             if (h.plan.family == 0 && h.plan.smask == 0) continue;  // identity
             if (h.plan.classes == 0) continue;
-            prog.ops.push_back(gate_op<R>(psi, h.plan, h.U, prog, cfg.tc_mode, h.unitary));
+            prog.ops.push_back(gate_op<R>(psi, h.plan, h.U, prog, cfg.tc_mode, h.unitary, L, h.wires, h.k, h.nc));
             continue;
         }
         TileGeom geo;

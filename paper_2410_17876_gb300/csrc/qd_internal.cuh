@@ -22,6 +22,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <memory>
+#include <vector>
+
 #ifndef QD_HD
 #define QD_HD __host__ __device__ __forceinline__
 #endif
@@ -111,6 +114,23 @@ struct FastDiv {
     QD_HD void divmod(uint64_t n, uint64_t& q, uint64_t& r) const {
         q = div(n);
         r = n - q * d;
+    }
+};
+
+// Unsigned 32-bit division by an invariant divisor (same method, N = 32).
+struct FastDiv32 {
+    uint32_t d, mul, s1, s2;
+    __host__ void init(uint32_t div) {
+        d = div;
+        int l = 0;
+        while (l < 32 && ((uint64_t)1 << l) < div) ++l;
+        mul = (uint32_t)(((((uint64_t)1 << l) - div) << 32) / div + 1);
+        s1 = l < 1 ? l : 1;
+        s2 = l > 1 ? l - 1 : 0;
+    }
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        const uint32_t t = __umulhi(mul, n);
+        return (t + ((n - t) >> s1)) >> s2;
     }
 };
 
@@ -221,6 +241,15 @@ void block_tc_pack(const double* U, int P, int tc_mode, void* out);
 cudaError_t launch_block_tc(float2* psi, uint64_t D, const void* a_ops, int tc_mode, bool renorm, uint64_t n_classes,
                             const IndexMap& map, int P, const uint64_t* off, cudaStream_t s);
 bool block_is_unitary(const double* U, int P, double tol);
+// BF16x3 blocks without controls through the ring of tiles: the kernel's
+// arguments for a block on `wires` (k wires, the gate's order) with the
+// P x P matrix U, and its B operand (to be uploaded); nullptr where the
+// block does not suit that kernel (the register-staged one then runs).
+struct BlockRing;
+std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi, const int32_t* wires, int k,
+                                                    int P, const double* U, bool renorm,
+                                                    std::vector<unsigned char>& b_ops);
+cudaError_t launch_block_ring(const BlockRing& r, const void* b_ops, cudaStream_t s);
 int32_t tc_status_take(cudaStream_t s);
 int32_t* tc_status_ptr();  // device status word shared by the kernels with bounded waits
 constexpr int kTcMinP = 17;  // complex64 blocks of at least this dimension go to the tensor cores

@@ -34,8 +34,11 @@
 // word, stops issuing work, releases its tensor memory and returns.
 #include <cuda_bf16.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstring>
+#include <memory>
+#include <vector>
 
 #include "qd_internal.cuh"
 #include "qd_tc_common.cuh"
@@ -477,6 +480,424 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(kCols));
 }
 
+
+// ---------------------------------------------------------------------------
+// BF16x3 blocks over a ring of tiles (complex64, 17..64 dimensions, no
+// controls).
+//
+// The state is cut into tiles: a tile holds the Q x P amplitudes whose
+// digits outside S = W + C are fixed, W the block's wires and C the lowest
+// wires not in W (Q = the product of C's dimensions, at most 128 classes).
+// Every wire below the highest wire of C is in S, so a tile is R rows of bL
+// contiguous amplitudes (the run of the lowest wires) at row offsets set by
+// the digits of the block's wires above the run; in shared memory the tile
+// keeps that order, and member r of class c sits at cl[c] + ml[r] in it and
+// at base + cl[c] + gofs[r] in the state.  Per tile the block is the
+// contraction
+//     Y (128 x 2Ph) = X (128 x 2Ph) . B,  B = [[Re M^T, Im M^T], [-Im M^T, Re M^T]],
+// rows of X = the tile's classes, columns Re x_0 .. Re x_{Ph-1}, Im x_0 ..
+// (Ph = P rounded up to a multiple of 8, zero-padded).  X sits in tensor
+// memory (lane = class), B in shared memory (K-major), so each class's
+// outputs come back to one thread.
+// Roles, meeting only at mbarriers (every wait bounded):
+//   loader (warp 17): bulk copies of tile i's rows into ring slot i mod
+//     nslots, completing on the slot's mbarrier by their byte count (rows of
+//     fewer than 16 amplitudes or an unaligned state: cp.async pieces and
+//     cp.async.mbarrier.arrive.noinc); the tile's base offset with them;
+//   converters (warps 0..7: half h = w / 4 of the members, TMEM lanes
+//     32 (w mod 4) ..): gather each class's members from the slot, split
+//     them into bf16 hi / lo parts and write A_hi, A_lo of TMEM stage
+//     i mod 2 (tcgen05.st), partial input norms to shared memory; the slot
+//     goes back to the loader as soon as it is read;
+//   MMA (warp 16, one thread): 3 x Ph / 8 MMAs (M = 128, N = 2Ph, K = 16),
+//     A_hi B_hi + A_hi B_lo + A_lo B_hi, into the stage's accumulator;
+//   epilogue (warps 8..15, halves and lane quarters as the converters):
+//     read the half's outputs (tcgen05.ld, lane = class), hand the stage
+//     back, combine the two halves' output norms (named barrier per pair),
+//     restore each class's norm and store the outputs to global memory
+//     (lanes along the classes).
+// A slot is held only from its copy to its conversion, so all but one of
+// the slots have copies in flight.  Tensor memory, per stage (256 columns):
+// A_hi [0, 64), A_lo [64, 128), accumulator [128, 128 + 2Ph).
+constexpr int kRingMaxSlots = 6;
+constexpr int kRingMaxQ = 128;
+constexpr int kRingMaxRows = 64;
+constexpr int kRingConvWarps = 8;                 // warps 0..7
+constexpr int kRingEpiWarps = 8;                  // warps 8..15
+constexpr int kRingMmaWarp = kRingConvWarps + kRingEpiWarps;
+constexpr int kRingLoadWarp = kRingMmaWarp + 1;
+constexpr int kRingThreads = 32 * (kRingLoadWarp + 1);
+constexpr uint32_t kRingStageCols = 256;
+
+struct RingArgs {
+    float2* psi;
+    uint64_t D;                  // amplitudes of the state (bounds-checked build)
+    const unsigned char* b_ops;  // B_hi | B_lo: bf16, K-major canonical layout, 2Ph x 2Ph each
+    int32_t* status;             // set to QD_ERR_TIMEOUT on a bounded-wait timeout
+    uint32_t spin_limit;
+    int32_t stall;               // testing: the loader copies nothing, so the first waits run out
+    int32_t renorm;              // the block is unitary: give each output class its input's 2-norm
+    int32_t vec2;                // 16-byte copies (even rows, 16-byte aligned state)
+    int32_t bulk;                // rows by bulk copies (rows of a multiple of 16 bytes, aligned)
+    uint32_t P, Q, T, bL, R, nslots;
+    FastDiv32 bLdiv;
+    uint32_t ntiles;
+    int32_t nfree;               // wires outside S, ascending: tile index digits
+    uint32_t free_d[kMaxWires];
+    FastDiv32 free_div[kMaxWires];
+    uint64_t free_b[kMaxWires];
+    uint64_t srow[kRingMaxRows];  // offset of each row from the tile's base
+    uint64_t gofs[kMaxGateDim];   // member r -> offset from its class's amplitude in the state
+    uint16_t cl[kRingMaxQ];       // class c -> offset in the tile (and from the tile's base)
+    uint16_t ml[kMaxGateDim];     // member r -> offset from its class in the tile
+};
+
+__device__ __forceinline__ uint64_t ring_tile_base(const RingArgs& a, uint32_t t) {
+    uint64_t base = 0;
+    uint32_t rem = t;
+    for (int i = 0; i < a.nfree; ++i) {
+        const uint32_t q = a.free_div[i].div(rem);
+        base += (uint64_t)(rem - q * a.free_d[i]) * a.free_b[i];
+        rem = q;
+    }
+    return base;
+}
+
+// Eight accumulator columns into registers, without waiting; the caller
+// waits (tcgen05.wait::ld) and passes the registers through reg_after_wait.
+__device__ __forceinline__ void tmem_ld8_issue(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+// An empty asm ordered after the wait (volatile asm keeps its order) that
+// redefines x, so that no use of x moves above the wait.
+__device__ __forceinline__ void reg_after_wait(float& x) { asm volatile("" : "+f"(x)); }
+
+// Barrier among the two warps of an epilogue pair (named barrier 1 + q,
+// 64 threads) that also ORs a flag over them.
+__device__ __forceinline__ bool pair_sync_or(uint32_t q, bool flag) {
+    uint32_t any;
+    asm volatile(
+        "{\n\t.reg .pred p, f;\n\t"
+        "setp.ne.u32 f, %1, 0;\n\t"
+        "bar.red.or.pred p, %2, 64, f;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(any)
+        : "r"((uint32_t)flag), "r"(1u + q)
+        : "memory");
+    return any != 0;
+}
+__device__ __forceinline__ void pair_sync(uint32_t q) { asm volatile("bar.sync %0, 64;" ::"r"(1u + q) : "memory"); }
+
+template <int PH>
+__global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_constant__ RingArgs a) {
+    static_assert(PH % 8 == 0 && PH >= 8 && PH <= 64, "Ph: a multiple of 8 up to 64");
+    constexpr uint32_t N2 = 2 * PH;
+    constexpr uint32_t NP = PH / 8;            // pieces of eight members
+    constexpr uint32_t NPH = (NP + 1) / 2;     // pieces of half 0 (half 1: NP / 2)
+    constexpr uint32_t bhalf = N2 * N2 * 2;    // bytes of one of B_hi / B_lo
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const uint32_t T = a.T;
+    unsigned char* sB = smem;
+    float2* ring = reinterpret_cast<float2*>(smem + 2 * bhalf);
+    __shared__ __align__(8) uint64_t m_full[kRingMaxSlots], m_empty[kRingMaxSlots];
+    __shared__ __align__(8) uint64_t m_conv[2], m_mma[2], m_dfree[2];
+    __shared__ uint64_t s_row[kRingMaxRows];
+    __shared__ uint64_t s_gofs[kMaxGateDim];
+    __shared__ uint64_t s_tbase[kRingMaxSlots];  // base of the tile in each slot (loader -> converters)
+    __shared__ uint64_t s_sbase[2];               // base of the tile in each TMEM stage (converters -> epilogue)
+    __shared__ uint32_t s_cl[kRingMaxQ];
+    __shared__ uint32_t s_ml[kMaxGateDim];
+    __shared__ float s_nin[2][2][kRingMaxQ];     // [stage][half][class]
+    __shared__ float s_nout[2][2][kRingMaxQ];
+    __shared__ uint32_t tmem_base;
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    if (tid == 0) {
+        abort_flag = 0;
+        for (uint32_t s = 0; s < a.nslots; ++s) {
+            // bulk: the loader's expect_tx arrival; cp.async: one arrival per
+            // loader lane when its copies land, plus lane 0's after the base
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_full[s])), "r"(a.bulk ? 1 : 33));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_empty[s])), "r"(kRingConvWarps));
+        }
+        for (int i = 0; i < 2; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_conv[i])), "r"(kRingConvWarps));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_mma[i])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_dfree[i])), "r"(kRingEpiWarps));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    for (uint32_t i = tid; i < kRingMaxRows; i += kRingThreads) s_row[i] = i < a.R ? a.srow[i] : 0;
+    for (uint32_t i = tid; i < kRingMaxQ; i += kRingThreads) s_cl[i] = i < a.Q ? a.cl[i] : 0;
+    for (uint32_t i = tid; i < kMaxGateDim; i += kRingThreads) {
+        s_ml[i] = i < a.P ? a.ml[i] : 0;
+        s_gofs[i] = i < a.P ? a.gofs[i] : 0;
+    }
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.b_ops);
+        uint4* dst = reinterpret_cast<uint4*>(sB);
+        for (uint32_t i = tid; i < 2 * bhalf / 16; i += kRingThreads) dst[i] = src[i];
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // B is read by the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tm = tmem_base;
+    const uint32_t G = gridDim.x;
+
+    if (warp == kRingLoadWarp) {
+        // ---------------- loader ----------------
+        uint32_t fills[kRingMaxSlots] = {0, 0, 0, 0, 0, 0};
+        uint32_t i = 0;
+        for (uint32_t t = a.stall ? a.ntiles : blockIdx.x; t < a.ntiles; t += G, ++i) {
+            const uint32_t s = i % a.nslots;
+            if (i >= a.nslots) {
+                const bool bad = !mbar_wait_sleep(smem_u32(&m_empty[s]), ((i / a.nslots) - 1u) & 1u, a.spin_limit);
+                if (__any_sync(0xffffffffu, bad)) {
+                    if (lane == 0) atomicExch(&abort_flag, 1);
+                    break;
+                }
+            }
+            const uint64_t base = ring_tile_base(a, t);
+            const uint32_t d0 = smem_u32(ring + (size_t)s * T);
+            const uint32_t fb = smem_u32(&m_full[s]);
+            ++fills[s];
+            if (lane == 0) s_tbase[s] = base;  // published by lane 0's arrival below
+            if (a.bulk) {
+                // one bulk copy per row; the slot's mbarrier expects the tile's bytes
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(T * 8u)
+                                 : "memory");
+                __syncwarp();
+                for (uint32_t r = lane; r < a.R; r += 32) {
+                    const uint64_t g = base + s_row[r];
+                    if (!in_bounds(g + a.bL - 1, a.D)) continue;
+                    asm volatile(
+                        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                            d0 + 8u * r * a.bL),
+                        "l"(a.psi + g), "r"(8u * a.bL), "r"(fb)
+                        : "memory");
+                }
+                continue;
+            }
+            if (a.vec2) {
+                for (uint32_t e = 2 * (uint32_t)lane; e < T; e += 64) {
+                    const uint32_t r = a.bLdiv.div(e);
+                    const uint64_t g = base + s_row[r] + (e - r * a.bL);
+                    if (!in_bounds(g + 1, a.D)) continue;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d0 + 8u * e), "l"(a.psi + g)
+                                 : "memory");
+                }
+            } else {
+                for (uint32_t e = (uint32_t)lane; e < T; e += 32) {
+                    const uint32_t r = a.bLdiv.div(e);
+                    const uint64_t g = base + s_row[r] + (e - r * a.bL);
+                    if (!in_bounds(g, a.D)) continue;
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d0 + 8u * e), "l"(a.psi + g)
+                                 : "memory");
+                }
+            }
+            // one arrival per lane when its copies have landed, and lane 0's now
+            asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(fb) : "memory");
+            if (lane == 0) mbar_arrive(fb);
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        // no copy may still be landing when the CTA ends (after an abort,
+        // issued slots can be left unconsumed)
+        if (a.bulk && lane == 0)
+            for (uint32_t u = 0; u < a.nslots; ++u)
+                if (fills[u] > 0) mbar_wait_sleep(smem_u32(&m_full[u]), (fills[u] - 1u) & 1u, a.spin_limit);
+    } else if (warp < kRingConvWarps) {
+        // ---------------- converters: warp = (half, quarter) ----------------
+        const uint32_t q = (uint32_t)warp & 3u, h = (uint32_t)warp >> 2;
+        const uint32_t L = 32u * q + (uint32_t)lane;
+        const uint32_t cb = s_cl[L];  // 0 beyond Q: those rows are computed and never stored
+        const uint32_t lanes = (32u * q) << 16;
+        uint32_t i = 0;
+        for (uint32_t t = blockIdx.x; t < a.ntiles; t += G, ++i) {
+            const uint32_t s = i % a.nslots, st = i & 1u;
+            bool bad = !mbar_wait_sleep(smem_u32(&m_full[s]), (i / a.nslots) & 1u, a.spin_limit);
+            if (!bad && i >= 2) bad = !mbar_wait_sleep(smem_u32(&m_dfree[st]), ((i >> 1) - 1u) & 1u, a.spin_limit);
+            if (__any_sync(0xffffffffu, bad)) {
+                if (lane == 0) atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const float2* x = ring + (size_t)s * T + cb;
+            const uint32_t ta = tm + lanes + st * kRingStageCols;
+            float nin = 0.f;
+#pragma unroll 1
+            for (uint32_t j = h; j < NP; j += 2) {
+                const uint32_t r0 = 8u * j;
+                float xr[8], xi[8];
+                if (r0 + 8u <= a.P) {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float2 v = x[s_ml[r0 + k]];
+                        xr[k] = v.x;
+                        xi[k] = v.y;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const float2 v = r0 + k < a.P ? x[s_ml[r0 + k]] : make_float2(0.f, 0.f);
+                        xr[k] = v.x;
+                        xi[k] = v.y;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) nin = fmaf(xr[k], xr[k], fmaf(xi[k], xi[k], nin));
+                uint32_t hr[4], lr[4], hi_[4], li[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    bf16_split2(xr[2 * k], xr[2 * k + 1], hr[k], lr[k]);
+                    bf16_split2(xi[2 * k], xi[2 * k + 1], hi_[k], li[k]);
+                }
+                tmem_st4u(ta + r0 / 2, hr[0], hr[1], hr[2], hr[3]);
+                tmem_st4u(ta + 64u + r0 / 2, lr[0], lr[1], lr[2], lr[3]);
+                tmem_st4u(ta + (PH + r0) / 2, hi_[0], hi_[1], hi_[2], hi_[3]);
+                tmem_st4u(ta + 64u + (PH + r0) / 2, li[0], li[1], li[2], li[3]);
+            }
+            // the slot is read: back to the loader
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&m_empty[s]));
+            s_nin[st][h][L] = nin;
+            if (warp == 0 && lane == 0) s_sbase[st] = s_tbase[s];
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&m_conv[st]));
+        }
+    } else if (warp < kRingConvWarps + kRingEpiWarps) {
+        // ---------------- epilogue: warp = (half, quarter) ----------------
+        const uint32_t e = (uint32_t)warp - kRingConvWarps;
+        const uint32_t q = e & 3u, h = e >> 2;
+        const uint32_t L = 32u * q + (uint32_t)lane;
+        const bool valid = L < a.Q;
+        const uint64_t cb = s_cl[L];
+        const uint32_t lanes = (32u * q) << 16;
+        uint32_t i = 0;
+        for (uint32_t t = blockIdx.x; t < a.ntiles; t += G, ++i) {
+            const uint32_t st = i & 1u;
+            // the converters' arrival also publishes the tile's base and input norms
+            bool bad = !mbar_wait_sleep(smem_u32(&m_conv[st]), (i >> 1) & 1u, a.spin_limit);
+            if (!bad) bad = !mbar_wait_sleep(smem_u32(&m_mma[st]), (i >> 1) & 1u, a.spin_limit);
+            if (pair_sync_or(q, bad)) {  // both warps of the pair leave together
+                if (lane == 0) atomicExch(&abort_flag, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ta = tm + lanes + st * kRingStageCols + 128u;
+            // this half's members: pieces j = 2 jj + h
+            float yr[8 * NPH], yi[8 * NPH];
+#pragma unroll
+            for (uint32_t jj = 0; jj < NPH; ++jj) {
+                const uint32_t j = 2u * jj + h;
+                if (j < NP) {
+                    tmem_ld8_issue(ta + 8u * j, yr + 8 * jj);
+                    tmem_ld8_issue(ta + PH + 8u * j, yi + 8 * jj);
+                }
+            }
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float no = 0.f;
+#pragma unroll
+            for (uint32_t c = 0; c < 8 * NPH; ++c) {
+                reg_after_wait(yr[c]);
+                reg_after_wait(yi[c]);
+                if (2u * (c / 8) + h < NP) no = fmaf(yr[c], yr[c], fmaf(yi[c], yi[c], no));
+            }
+            const uint64_t base = s_sbase[st] + cb;
+            const float ni = s_nin[st][0][L] + s_nin[st][1][L];
+            s_nout[st][h][L] = no;
+            // the accumulator is in registers: the stage goes back to the converters
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&m_dfree[st]));
+            pair_sync(q);  // both halves' output norms are in shared memory
+            float cc = 0.f;
+            if (a.renorm) {
+                // the tensor cores' FP32 accumulation is biased toward zero; a
+                // unitary block keeps each class's 2-norm: y <- y (1 + c),
+                // c = sqrt(ni / no) - 1 (binary32 sums: BF16x3 is good to 2^-16)
+                NormFF ni_, no_;
+                ni_.add(ni, 0.f);
+                no_.add(s_nout[st][0][L] + s_nout[st][1][L], 0.f);
+                cc = norm_fix(ni_, no_);
+            }
+            if (valid) {
+                float2* dst = a.psi + base;
+                const uint64_t lim = a.D - base;  // bounds-checked build
+#pragma unroll
+                for (uint32_t jj = 0; jj < NPH; ++jj) {
+                    const uint32_t j = 2u * jj + h;
+#pragma unroll
+                    for (uint32_t k = 0; k < 8; ++k) {
+                        const uint32_t r = 8u * j + k;
+                        if (j < NP && r < a.P) {
+                            const uint64_t o = s_gofs[r];
+                            if (in_bounds(o, lim))
+                                dst[o] = make_float2(fmaf(yr[8 * jj + k], cc, yr[8 * jj + k]),
+                                                     fmaf(yi[8 * jj + k], cc, yi[8 * jj + k]));
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == kRingMmaWarp) {
+        // ---------------- MMA warp ----------------
+        if (lane == 0) {
+            constexpr uint32_t idesc = tc_idesc_n(1u, N2);
+            const uint64_t bd0 = smem_desc(smem_u32(sB), (N2 / 8) * 128, 128);
+            constexpr uint64_t kStepB = 2 * (N2 / 8) * 128 / 16;  // one k-step: two core matrices along K
+            constexpr uint64_t bLo = bhalf >> 4;
+            int issued[2] = {0, 0};
+            uint32_t i = 0;
+            for (uint32_t t = blockIdx.x; t < a.ntiles; t += G, ++i) {
+                const uint32_t st = i & 1u;
+                if (!mbar_wait_sleep(smem_u32(&m_conv[st]), (i >> 1) & 1u, a.spin_limit)) {
+                    atomicExch(&abort_flag, 1);
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sb = tm + st * kRingStageCols;
+#pragma unroll
+                for (int term = 0; term < 3; ++term) {
+                    const uint32_t a0 = sb + (term == 2 ? 64u : 0u);       // A_lo for the third product
+                    const uint64_t b0 = bd0 + (term == 1 ? bLo : 0ull);    // B_lo for the second
+#pragma unroll
+                    for (uint32_t ks = 0; ks < (uint32_t)PH / 8; ++ks)
+                        mma_bf16_ta(sb + 128u, a0 + 8u * ks, b0 + (uint64_t)ks * kStepB, idesc,
+                                    (term != 0 || ks != 0) ? 1u : 0u);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_u32(&m_mma[st]))
+                             : "memory");
+                ++issued[st];
+            }
+            // before the tensor memory is released: every committed group has completed
+            for (int u = 0; u < 2; ++u)
+                if (issued[u] > 0) mbar_wait_sleep(smem_u32(&m_mma[u]), (uint32_t)((issued[u] - 1) & 1), a.spin_limit);
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicExch(a.status, QD_ERR_TIMEOUT);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tm), "r"(512));
+}
+
 }  // namespace
 
 QD_DEFINE_BOUNDS_TAKE(bounds_take_tc)
@@ -647,7 +1068,214 @@ cudaError_t launch_block_tc(float2* psi, uint64_t D, const void* a_ops, int tc_m
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Host side of the ring kernel.
+// ---------------------------------------------------------------------------
+struct BlockRing {
+    RingArgs a;
+    size_t smem;
+    int ph;  // P rounded up to a multiple of 8: the kernel's instantiation
+};
+
+static std::atomic<int64_t> g_ring_launches{0};
+
+// Dynamic shared memory of the ring kernel (the B operand and the slots).
+constexpr size_t kRingSmemCap = 216 * 1024;
+constexpr size_t kRingMinSmem = 120 * 1024;  // > 228 KB / 2
+
+std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi, const int32_t* wires, int k,
+                                                    int P, const double* U, bool renorm,
+                                                    std::vector<unsigned char>& b_ops) {
+    if (k < 1 || P < kTcMinP || P > kMaxGateDim) return nullptr;
+    uint64_t W = 0;
+    int64_t Pw = 1;
+    for (int i = 0; i < k; ++i) {
+        if (wires[i] < 0 || wires[i] >= L.n || wires[i] >= 64) return nullptr;
+        W |= 1ull << wires[i];
+        Pw *= L.dims[wires[i]];
+    }
+    if (Pw != P) return nullptr;
+    const uint32_t Ph = (uint32_t)((P + 7) & ~7), N2 = 2 * Ph;
+    const size_t bbytes = (size_t)2 * N2 * N2 * 2;
+    const size_t avail = kRingSmemCap - bbytes;
+    uint64_t qcap = avail / (4 * (size_t)P * 8);  // at least four slots (copies in flight)
+    if (qcap > (uint64_t)kRingMaxQ) qcap = kRingMaxQ;
+    // C: the lowest wires outside W while the classes of a tile stay within qcap
+    uint64_t S = W, Q = 1;
+    int nC = 0;
+    int Cw[kMaxWires];
+    for (int w = 0; w < L.n; ++w) {
+        if (W >> w & 1) continue;
+        if (Q * (uint64_t)L.dims[w] > qcap) break;
+        S |= 1ull << w;
+        Q *= (uint64_t)L.dims[w];
+        Cw[nC++] = w;
+    }
+    // a tile of few classes leaves most MMA rows idle: the register-staged kernel instead
+    if (Q < 32 && (uint64_t)L.D / (uint64_t)P > Q) return nullptr;
+    int L0 = 0;
+    while (L0 < L.n && (S >> L0 & 1)) ++L0;
+    const uint64_t bL = (uint64_t)L.b[L0];
+    int rw[kMaxWires], nr = 0;
+    uint64_t R = 1;
+    for (int w = L0; w < L.n; ++w)
+        if (W >> w & 1) {
+            rw[nr++] = w;
+            R *= (uint64_t)L.dims[w];
+        }
+    const uint64_t T = Q * (uint64_t)P;
+    if (bL * R != T || R > (uint64_t)kRingMaxRows || T > 65535) return nullptr;
+    const uint64_t ntiles = (uint64_t)L.D / T;
+    if (ntiles * T != (uint64_t)L.D || ntiles >= (1ull << 32)) return nullptr;
+    uint64_t nslots = avail / (T * 8);
+    if (nslots > (uint64_t)kRingMaxSlots) nslots = kRingMaxSlots;
+    if (nslots < 2) return nullptr;
+
+    auto sp = std::make_shared<BlockRing>();
+    RingArgs& a = sp->a;
+    std::memset(static_cast<void*>(&a), 0, sizeof a);
+    a.psi = psi;
+    a.D = (uint64_t)L.D - g_bounds_shrink;
+    a.renorm = renorm ? 1 : 0;
+    a.vec2 = (bL % 2 == 0 && (reinterpret_cast<uintptr_t>(psi) & 15u) == 0) ? 1 : 0;
+    // rows of at least 128 bytes go by bulk copies (16-byte aligned: the rows
+    // start at multiples of bL, and bL is even)
+    a.bulk = (a.vec2 && bL >= 16) ? 1 : 0;
+    a.P = (uint32_t)P;
+    sp->ph = (int)Ph;
+    a.Q = (uint32_t)Q;
+    a.T = (uint32_t)T;
+    a.bL = (uint32_t)bL;
+    a.R = (uint32_t)R;
+    a.nslots = (uint32_t)nslots;
+    a.bLdiv.init((uint32_t)bL);
+    a.ntiles = (uint32_t)ntiles;
+    // offsets inside a tile: the run's wires keep their strides, row wires
+    // count rows of bL amplitudes
+    int64_t ls[kMaxWires];
+    for (int w = 0; w < L0; ++w) ls[w] = L.b[w];
+    {
+        int64_t m = (int64_t)bL;
+        for (int j = 0; j < nr; ++j) {
+            ls[rw[j]] = m;
+            m *= L.dims[rw[j]];
+        }
+    }
+    for (uint64_t r = 0; r < R; ++r) {
+        uint64_t rem = r, off = 0;
+        for (int j = 0; j < nr; ++j) {
+            off += (rem % (uint64_t)L.dims[rw[j]]) * (uint64_t)L.b[rw[j]];
+            rem /= (uint64_t)L.dims[rw[j]];
+        }
+        a.srow[r] = off;
+    }
+    for (int r = 0; r < P; ++r) {  // member r: digits over the gate's wires, the first least significant
+        int64_t rem = r, off = 0, goff = 0;
+        for (int i = 0; i < k; ++i) {
+            const int64_t dg = rem % L.dims[wires[i]];
+            off += dg * ls[wires[i]];
+            goff += dg * L.b[wires[i]];
+            rem /= L.dims[wires[i]];
+        }
+        a.ml[r] = (uint16_t)off;
+        a.gofs[r] = (uint64_t)goff;
+    }
+    for (uint64_t c = 0; c < Q; ++c) {
+        uint64_t rem = c, off = 0;
+        for (int j = 0; j < nC; ++j) {
+            off += (rem % (uint64_t)L.dims[Cw[j]]) * (uint64_t)L.b[Cw[j]];
+            rem /= (uint64_t)L.dims[Cw[j]];
+        }
+        a.cl[c] = (uint16_t)off;
+    }
+    a.nfree = 0;
+    for (int w = 0; w < L.n; ++w)
+        if (!(S >> w & 1)) {
+            a.free_d[a.nfree] = (uint32_t)L.dims[w];
+            a.free_div[a.nfree].init((uint32_t)L.dims[w]);
+            a.free_b[a.nfree] = (uint64_t)L.b[w];
+            ++a.nfree;
+        }
+    sp->smem = bbytes + (size_t)nslots * (size_t)T * 8;
+    // one CTA per SM: each allocates all 512 tensor-memory columns
+    if (sp->smem < kRingMinSmem) sp->smem = kRingMinSmem;
+    // B = [[Re M^T, Im M^T], [-Im M^T, Re M^T]] (K = inputs, N = outputs),
+    // split into bf16 hi | lo, K-major canonical layout with N2 rows
+    b_ops.assign(bbytes, 0);
+    unsigned char* hi = b_ops.data();
+    unsigned char* lo = hi + bbytes / 2;
+    auto put = [&](uint32_t n, uint32_t kk, double v) {
+        const uint16_t h = bf16_bits_rne((float)v);
+        const uint16_t l = bf16_bits_rne((float)(v - (double)bf16_value(h)));
+        const uint32_t o = kmajor_off_h(n, kk, N2);
+        std::memcpy(hi + o, &h, 2);
+        std::memcpy(lo + o, &l, 2);
+    };
+    for (int j = 0; j < P; ++j)
+        for (int r = 0; r < P; ++r) {
+            const double re = U[2 * (j * P + r)], im = U[2 * (j * P + r) + 1];
+            put((uint32_t)j, (uint32_t)r, re);
+            put((uint32_t)j, Ph + (uint32_t)r, -im);
+            put(Ph + (uint32_t)j, (uint32_t)r, im);
+            put(Ph + (uint32_t)j, Ph + (uint32_t)r, re);
+        }
+    return sp;
+}
+
+template <int PH>
+static cudaError_t launch_ring_ph(const RingArgs& a, size_t smem, unsigned grid, cudaStream_t s) {
+    static int attr_dev = -1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (attr_dev != dev) {
+        cudaError_t e =
+            cudaFuncSetAttribute(k_block_tc_ring<PH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRingSmemCap);
+        if (e != cudaSuccess) return e;
+        attr_dev = dev;
+    }
+    k_block_tc_ring<PH><<<grid, kRingThreads, smem, s>>>(a);
+    return cudaSuccess;
+}
+
+cudaError_t launch_block_ring(const BlockRing& r, const void* b_ops, cudaStream_t s) {
+    static int sm_count = 0;
+    if (sm_count == 0) {
+        int dv = 0;
+        cudaGetDevice(&dv);
+        cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dv);
+        if (sm_count <= 0) sm_count = 148;
+    }
+    int32_t* status = tc_status_ptr();
+    if (!status) return cudaErrorInvalidSymbol;
+    RingArgs a = r.a;
+    a.b_ops = static_cast<const unsigned char*>(b_ops);
+    a.status = status;
+    a.spin_limit = g_tc_spin_limit;
+    a.stall = g_tc_stall;
+    const unsigned grid = (unsigned)(a.ntiles < (uint32_t)sm_count ? a.ntiles : (uint32_t)sm_count);
+    cudaError_t e;
+    switch (r.ph) {
+        case 24: e = launch_ring_ph<24>(a, r.smem, grid, s); break;
+        case 32: e = launch_ring_ph<32>(a, r.smem, grid, s); break;
+        case 40: e = launch_ring_ph<40>(a, r.smem, grid, s); break;
+        case 48: e = launch_ring_ph<48>(a, r.smem, grid, s); break;
+        case 56: e = launch_ring_ph<56>(a, r.smem, grid, s); break;
+        case 64: e = launch_ring_ph<64>(a, r.smem, grid, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (e != cudaSuccess) return e;
+    count_launch();
+    g_ring_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
 }  // namespace qd
+
+extern "C" qd_status qd_test_tc_ring_launches(int64_t* out) {
+    if (!out) return QD_ERR_ARG;
+    *out = qd::g_ring_launches.load(std::memory_order_relaxed);
+    return QD_OK;
+}
 
 extern "C" qd_status qd_test_set_tc_wait(uint32_t spin_limit, int32_t stall_producers) {
     qd::g_tc_spin_limit = spin_limit == 0 ? qd::kSpinLimit : spin_limit;

@@ -39,6 +39,11 @@ __host__ __device__ constexpr uint32_t tc_idesc(uint32_t fmt) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTcN >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
 }
 
+// The same with an explicit N (a multiple of 16, 16 <= N <= 256).
+__host__ __device__ constexpr uint32_t tc_idesc_n(uint32_t fmt, uint32_t n) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
+
 // Byte offset of element (row, k) in a K-major no-swizzle operand with `rows`
 // rows: 4-byte elements (4 per core-matrix row) ...
 __host__ __device__ __forceinline__ uint32_t kmajor_off(uint32_t row, uint32_t k, uint32_t rows) {
@@ -115,19 +120,21 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         : "r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
-// bf16 hi / lo parts of four floats, packed two per 32-bit word (element k in
-// the low half, k + 1 in the high half).
+// bf16 hi / lo parts of two floats, packed in one 32-bit word each (x0 in
+// the low half): hi = bf16(x) and lo = bf16(x - hi), both rounded to
+// nearest even, two values per conversion instruction.
+__device__ __forceinline__ void bf16_split2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - hf.x, x1 - hf.y);
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// ... and of four floats (element k in the low half, k + 1 in the high half).
 __device__ __forceinline__ void bf16_split4(float x0, float x1, float x2, float x3, uint2& hi, uint2& lo) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
-    const __nv_bfloat16 h2 = __float2bfloat16_rn(x2), h3 = __float2bfloat16_rn(x3);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
-    const __nv_bfloat16 l2 = __float2bfloat16_rn(x2 - __bfloat162float(h2));
-    const __nv_bfloat16 l3 = __float2bfloat16_rn(x3 - __bfloat162float(h3));
-    hi.x = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-    hi.y = (uint32_t)__bfloat16_as_ushort(h2) | ((uint32_t)__bfloat16_as_ushort(h3) << 16);
-    lo.x = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-    lo.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
+    bf16_split2(x0, x1, hi.x, lo.x);
+    bf16_split2(x2, x3, hi.y, lo.y);
 }
 
 __device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
@@ -138,6 +145,23 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t tmem_d, uint32_t tmem_a, ui
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
         :
         : "r"(tmem_d), "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// BF16 MMA with the A operand in tensor memory (lane = row of A, 32-bit
+// column = two consecutive K elements, the lower K index in the low half).
+__device__ __forceinline__ void mma_bf16_ta(uint32_t tmem_d, uint32_t tmem_a, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
+        :
+        : "r"(tmem_d), "r"(tmem_a), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void tmem_st4u(uint32_t taddr, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v0), "r"(v1),
+                 "r"(v2), "r"(v3));
 }
 
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float* v) {
@@ -168,6 +192,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, uint32_
             "selp.b32 %0, 1, 0, P;\n\t}"
             : "=r"(done)
             : "r"(mbar), "r"(phase));
+        if (done) return true;
+    }
+    return false;
+}
+
+// Bounded wait whose polls suspend the thread (up to hint_ns per poll) until
+// the phase completes, instead of spinning on the issue slots.
+__device__ __forceinline__ bool mbar_wait_sleep(uint32_t mbar, uint32_t phase, uint32_t limit,
+                                                uint32_t hint_ns = 1000) {
+    for (uint32_t it = 0; it < limit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred P;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2, %3;\n\t"
+            "selp.b32 %0, 1, 0, P;\n\t}"
+            : "=r"(done)
+            : "r"(mbar), "r"(phase), "r"(hint_ns));
         if (done) return true;
     }
     return false;
