@@ -507,10 +507,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
 //   converters (warps 0..7: half h = w / 4 of the members, TMEM lanes
 //     32 (w mod 4) ..): gather each class's members from the slot, split
 //     them into bf16 hi / lo parts and write A_hi, A_lo of TMEM stage
-//     i mod 2 (tcgen05.st), partial input norms to shared memory; the slot
-//     goes back to the loader as soon as it is read;
-//   MMA (warp 16, one thread): 3 x Ph / 8 MMAs (M = 128, N = 2Ph, K = 16),
-//     A_hi B_hi + A_hi B_lo + A_lo B_hi, into the stage's accumulator;
+//     i mod 2 (tcgen05.st) once the MMAs of tile i - 2 have read them,
+//     partial input norms to shared memory; the slot goes back to the
+//     loader as soon as it is read;
+//   MMA (warp 16, one thread): once the epilogue has read the stage's
+//     accumulator (tile i - 2), 3 x Ph / 8 MMAs (M = 128, N = 2Ph, K = 16),
+//     A_hi B_hi + A_hi B_lo + A_lo B_hi, into it;
 //   epilogue (warps 8..15, halves and lane quarters as the converters):
 //     read the half's outputs (tcgen05.ld, lane = class), hand the stage
 //     back, combine the two halves' output norms (named barrier per pair),
@@ -521,6 +523,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
 // A_hi [0, 64), A_lo [64, 128), accumulator [128, 128 + 2Ph).
 constexpr int kRingMaxSlots = 6;
 constexpr int kRingMaxQ = 128;
+constexpr int kRingMaxK = 64;
 constexpr int kRingMaxRows = 64;
 constexpr int kRingConvWarps = 8;                 // warps 0..7
 constexpr int kRingEpiWarps = 8;                  // warps 8..15
@@ -539,7 +542,7 @@ struct RingArgs {
     int32_t renorm;              // the block is unitary: give each output class its input's 2-norm
     int32_t vec2;                // 16-byte copies (even rows, 16-byte aligned state)
     int32_t bulk;                // rows by bulk copies (rows of a multiple of 16 bytes, aligned)
-    uint32_t P, Q, T, bL, R, nslots;
+    uint32_t P, Q, K, T, bL, R, nslots;  // Q classes per chunk (MMA rows), K chunks per tile
     FastDiv32 bLdiv;
     uint32_t ntiles;
     int32_t nfree;               // wires outside S, ascending: tile index digits
@@ -548,7 +551,8 @@ struct RingArgs {
     uint64_t free_b[kMaxWires];
     uint64_t srow[kRingMaxRows];  // offset of each row from the tile's base
     uint64_t gofs[kMaxGateDim];   // member r -> offset from its class's amplitude in the state
-    uint16_t cl[kRingMaxQ];       // class c -> offset in the tile (and from the tile's base)
+    uint16_t cl[kRingMaxQ];       // class c of a chunk -> offset from the chunk's first class
+    uint16_t chk[kRingMaxK];      // chunk k -> offset of its first class in the tile (and from the tile's base)
     uint16_t ml[kMaxGateDim];     // member r -> offset from its class in the tile
 };
 
@@ -606,13 +610,15 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
     float2* ring = reinterpret_cast<float2*>(smem + 2 * bhalf);
     __shared__ __align__(8) uint64_t m_full[kRingMaxSlots], m_empty[kRingMaxSlots];
     __shared__ __align__(8) uint64_t m_conv[2], m_mma[2], m_dfree[2];
+    __shared__ __align__(8) uint64_t m_meta[4];  // tile i's base and input norms, at i mod 4
     __shared__ uint64_t s_row[kRingMaxRows];
     __shared__ uint64_t s_gofs[kMaxGateDim];
     __shared__ uint64_t s_tbase[kRingMaxSlots];  // base of the tile in each slot (loader -> converters)
-    __shared__ uint64_t s_sbase[2];               // base of the tile in each TMEM stage (converters -> epilogue)
+    __shared__ uint64_t s_sbase[4];               // base of tile i at i mod 4 (converters -> epilogue)
     __shared__ uint32_t s_cl[kRingMaxQ];
+    __shared__ uint32_t s_chk[kRingMaxK];
     __shared__ uint32_t s_ml[kMaxGateDim];
-    __shared__ float s_nin[2][2][kRingMaxQ];     // [stage][half][class]
+    __shared__ float s_nin[4][2][kRingMaxQ];     // [tile mod 4][half][class]
     __shared__ float s_nout[2][2][kRingMaxQ];
     __shared__ uint32_t tmem_base;
     __shared__ int abort_flag;
@@ -631,6 +637,8 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_mma[i])), "r"(1));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_dfree[i])), "r"(kRingEpiWarps));
         }
+        for (int i = 0; i < 4; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&m_meta[i])), "r"(kRingConvWarps));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -640,6 +648,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
     }
     for (uint32_t i = tid; i < kRingMaxRows; i += kRingThreads) s_row[i] = i < a.R ? a.srow[i] : 0;
     for (uint32_t i = tid; i < kRingMaxQ; i += kRingThreads) s_cl[i] = i < a.Q ? a.cl[i] : 0;
+    for (uint32_t i = tid; i < kRingMaxK; i += kRingThreads) s_chk[i] = i < a.K ? a.chk[i] : 0;
     for (uint32_t i = tid; i < kMaxGateDim; i += kRingThreads) {
         s_ml[i] = i < a.P ? a.ml[i] : 0;
         s_gofs[i] = i < a.P ? a.gofs[i] : 0;
@@ -655,6 +664,8 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tm = tmem_base;
     const uint32_t G = gridDim.x;
+    // chunks this CTA runs: K per tile of tiles blockIdx.x, + G, ...
+    const uint32_t n_chunks = (blockIdx.x < a.ntiles ? (a.ntiles - blockIdx.x + G - 1) / G : 0u) * a.K;
 
     if (warp == kRingLoadWarp) {
         // ---------------- loader ----------------
@@ -724,60 +735,73 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
         const uint32_t L = 32u * q + (uint32_t)lane;
         const uint32_t cb = s_cl[L];  // 0 beyond Q: those rows are computed and never stored
         const uint32_t lanes = (32u * q) << 16;
-        uint32_t i = 0;
-        for (uint32_t t = blockIdx.x; t < a.ntiles; t += G, ++i) {
-            const uint32_t s = i % a.nslots, st = i & 1u;
-            bool bad = !mbar_wait_sleep(smem_u32(&m_full[s]), (i / a.nslots) & 1u, a.spin_limit);
-            if (!bad && i >= 2) bad = !mbar_wait_sleep(smem_u32(&m_dfree[st]), ((i >> 1) - 1u) & 1u, a.spin_limit);
+        uint32_t i = 0, ic = 0;  // tile, chunk counters
+        bool quit = false;
+        for (uint32_t t = blockIdx.x; t < a.ntiles && !quit; t += G, ++i) {
+            const uint32_t s = i % a.nslots;
+            const bool bad = !mbar_wait_sleep(smem_u32(&m_full[s]), (i / a.nslots) & 1u, a.spin_limit);
             if (__any_sync(0xffffffffu, bad)) {
                 if (lane == 0) atomicExch(&abort_flag, 1);
                 break;
             }
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const float2* x = ring + (size_t)s * T + cb;
-            const uint32_t ta = tm + lanes + st * kRingStageCols;
-            float nin = 0.f;
+            for (uint32_t k = 0; k < a.K; ++k, ++ic) {
+                const uint32_t st = ic & 1u;
+                // A of this stage is free once the chunk two back has been multiplied
+                const bool bad2 = ic >= 2 && !mbar_wait_sleep(smem_u32(&m_mma[st]), ((ic >> 1) - 1u) & 1u, a.spin_limit);
+                if (__any_sync(0xffffffffu, bad2)) {
+                    if (lane == 0) atomicExch(&abort_flag, 1);
+                    quit = true;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const float2* x = ring + (size_t)s * T + s_chk[k] + cb;
+                const uint32_t ta = tm + lanes + st * kRingStageCols;
+                float nin = 0.f;
 #pragma unroll 1
-            for (uint32_t j = h; j < NP; j += 2) {
-                const uint32_t r0 = 8u * j;
-                float xr[8], xi[8];
-                if (r0 + 8u <= a.P) {
+                for (uint32_t j = h; j < NP; j += 2) {
+                    const uint32_t r0 = 8u * j;
+                    float xr[8], xi[8];
+                    if (r0 + 8u <= a.P) {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const float2 v = x[s_ml[r0 + k]];
-                        xr[k] = v.x;
-                        xi[k] = v.y;
+                        for (int m = 0; m < 8; ++m) {
+                            const float2 v = x[s_ml[r0 + m]];
+                            xr[m] = v.x;
+                            xi[m] = v.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) {
+                            const float2 v = r0 + m < a.P ? x[s_ml[r0 + m]] : make_float2(0.f, 0.f);
+                            xr[m] = v.x;
+                            xi[m] = v.y;
+                        }
                     }
-                } else {
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        const float2 v = r0 + k < a.P ? x[s_ml[r0 + k]] : make_float2(0.f, 0.f);
-                        xr[k] = v.x;
-                        xi[k] = v.y;
+                    for (int m = 0; m < 8; ++m) nin = fmaf(xr[m], xr[m], fmaf(xi[m], xi[m], nin));
+                    uint32_t hr[4], lr[4], hi_[4], li[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        bf16_split2(xr[2 * m], xr[2 * m + 1], hr[m], lr[m]);
+                        bf16_split2(xi[2 * m], xi[2 * m + 1], hi_[m], li[m]);
                     }
+                    tmem_st4u(ta + r0 / 2, hr[0], hr[1], hr[2], hr[3]);
+                    tmem_st4u(ta + 64u + r0 / 2, lr[0], lr[1], lr[2], lr[3]);
+                    tmem_st4u(ta + (PH + r0) / 2, hi_[0], hi_[1], hi_[2], hi_[3]);
+                    tmem_st4u(ta + 64u + (PH + r0) / 2, li[0], li[1], li[2], li[3]);
                 }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) nin = fmaf(xr[k], xr[k], fmaf(xi[k], xi[k], nin));
-                uint32_t hr[4], lr[4], hi_[4], li[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    bf16_split2(xr[2 * k], xr[2 * k + 1], hr[k], lr[k]);
-                    bf16_split2(xi[2 * k], xi[2 * k + 1], hi_[k], li[k]);
-                }
-                tmem_st4u(ta + r0 / 2, hr[0], hr[1], hr[2], hr[3]);
-                tmem_st4u(ta + 64u + r0 / 2, lr[0], lr[1], lr[2], lr[3]);
-                tmem_st4u(ta + (PH + r0) / 2, hi_[0], hi_[1], hi_[2], hi_[3]);
-                tmem_st4u(ta + 64u + (PH + r0) / 2, li[0], li[1], li[2], li[3]);
+                s_nin[ic & 3u][h][L] = nin;
+                if (warp == 0 && lane == 0) s_sbase[ic & 3u] = s_tbase[s] + s_chk[k];
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&m_meta[ic & 3u]));
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&m_conv[st]));
             }
-            // the slot is read: back to the loader
+            if (quit) break;
+            // every chunk of the slot is read: back to the loader
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&m_empty[s]));
-            s_nin[st][h][L] = nin;
-            if (warp == 0 && lane == 0) s_sbase[st] = s_tbase[s];
-            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&m_conv[st]));
         }
     } else if (warp < kRingConvWarps + kRingEpiWarps) {
         // ---------------- epilogue: warp = (half, quarter) ----------------
@@ -787,11 +811,11 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
         const bool valid = L < a.Q;
         const uint64_t cb = s_cl[L];
         const uint32_t lanes = (32u * q) << 16;
-        uint32_t i = 0;
-        for (uint32_t t = blockIdx.x; t < a.ntiles; t += G, ++i) {
+        for (uint32_t i = 0; i < n_chunks; ++i) {
             const uint32_t st = i & 1u;
-            // the converters' arrival also publishes the tile's base and input norms
-            bool bad = !mbar_wait_sleep(smem_u32(&m_conv[st]), (i >> 1) & 1u, a.spin_limit);
+            // the chunk's base and input norms (m_meta), then its products: the
+            // converters' stage barrier may already be a phase further on
+            bool bad = !mbar_wait_sleep(smem_u32(&m_meta[i & 3u]), (i >> 2) & 1u, a.spin_limit);
             if (!bad) bad = !mbar_wait_sleep(smem_u32(&m_mma[st]), (i >> 1) & 1u, a.spin_limit);
             if (pair_sync_or(q, bad)) {  // both warps of the pair leave together
                 if (lane == 0) atomicExch(&abort_flag, 1);
@@ -817,8 +841,8 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
                 reg_after_wait(yi[c]);
                 if (2u * (c / 8) + h < NP) no = fmaf(yr[c], yr[c], fmaf(yi[c], yi[c], no));
             }
-            const uint64_t base = s_sbase[st] + cb;
-            const float ni = s_nin[st][0][L] + s_nin[st][1][L];
+            const uint64_t base = s_sbase[i & 3u] + cb;
+            const float ni = s_nin[i & 3u][0][L] + s_nin[i & 3u][1][L];
             s_nout[st][h][L] = no;
             // the accumulator is in registers: the stage goes back to the converters
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -862,10 +886,12 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
             constexpr uint64_t kStepB = 2 * (N2 / 8) * 128 / 16;  // one k-step: two core matrices along K
             constexpr uint64_t bLo = bhalf >> 4;
             int issued[2] = {0, 0};
-            uint32_t i = 0;
-            for (uint32_t t = blockIdx.x; t < a.ntiles; t += G, ++i) {
+            for (uint32_t i = 0; i < n_chunks; ++i) {
                 const uint32_t st = i & 1u;
-                if (!mbar_wait_sleep(smem_u32(&m_conv[st]), (i >> 1) & 1u, a.spin_limit)) {
+                // the accumulator of this stage is free once the epilogue has read the chunk two back
+                bool ok = i < 2 || mbar_wait_sleep(smem_u32(&m_dfree[st]), ((i >> 1) - 1u) & 1u, a.spin_limit);
+                ok = ok && mbar_wait_sleep(smem_u32(&m_conv[st]), (i >> 1) & 1u, a.spin_limit);
+                if (!ok) {
                     atomicExch(&abort_flag, 1);
                     break;
                 }
@@ -1098,21 +1124,32 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
     const uint32_t Ph = (uint32_t)((P + 7) & ~7), N2 = 2 * Ph;
     const size_t bbytes = (size_t)2 * N2 * N2 * 2;
     const size_t avail = kRingSmemCap - bbytes;
-    uint64_t qcap = avail / (4 * (size_t)P * 8);  // at least four slots (copies in flight)
-    if (qcap > (uint64_t)kRingMaxQ) qcap = kRingMaxQ;
-    // C: the lowest wires outside W while the classes of a tile stay within qcap
-    uint64_t S = W, Q = 1;
-    int nC = 0;
-    int Cw[kMaxWires];
-    for (int w = 0; w < L.n; ++w) {
+    // Classes: the lowest wires outside W.  A chunk takes as many as the MMA
+    // has rows (per-chunk costs are fixed; measured on 2^27 amplitudes and a
+    // 64-dimensional block, 128 classes per tile take 0.40 ms per pass, 64
+    // 0.77 ms); the tile then takes further such wires as whole chunks while
+    // two slots still fit, so that its rows grow (a bulk copy of a short row
+    // costs about as much as one of a long one).
+    uint64_t S = W, Q = 1, K = 1;
+    int nC = 0, nK = 0;
+    int Cw[kMaxWires], Kw[kMaxWires];
+    int w = 0;
+    for (; w < L.n; ++w) {
         if (W >> w & 1) continue;
-        if (Q * (uint64_t)L.dims[w] > qcap) break;
+        if (Q * (uint64_t)L.dims[w] > (uint64_t)kRingMaxQ || 2 * Q * (uint64_t)L.dims[w] * P * 8 > avail) break;
         S |= 1ull << w;
         Q *= (uint64_t)L.dims[w];
         Cw[nC++] = w;
     }
+    for (; w < L.n; ++w) {
+        if (W >> w & 1) continue;
+        if (K * (uint64_t)L.dims[w] > (uint64_t)kRingMaxK || 2 * Q * K * (uint64_t)L.dims[w] * P * 8 > avail) break;
+        S |= 1ull << w;
+        K *= (uint64_t)L.dims[w];
+        Kw[nK++] = w;
+    }
     // a tile of few classes leaves most MMA rows idle: the register-staged kernel instead
-    if (Q < 32 && (uint64_t)L.D / (uint64_t)P > Q) return nullptr;
+    if (Q < 32 && (uint64_t)L.D / (uint64_t)P > Q * K) return nullptr;
     int L0 = 0;
     while (L0 < L.n && (S >> L0 & 1)) ++L0;
     const uint64_t bL = (uint64_t)L.b[L0];
@@ -1123,7 +1160,7 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
             rw[nr++] = w;
             R *= (uint64_t)L.dims[w];
         }
-    const uint64_t T = Q * (uint64_t)P;
+    const uint64_t T = Q * K * (uint64_t)P;
     if (bL * R != T || R > (uint64_t)kRingMaxRows || T > 65535) return nullptr;
     const uint64_t ntiles = (uint64_t)L.D / T;
     if (ntiles * T != (uint64_t)L.D || ntiles >= (1ull << 32)) return nullptr;
@@ -1144,6 +1181,7 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
     a.P = (uint32_t)P;
     sp->ph = (int)Ph;
     a.Q = (uint32_t)Q;
+    a.K = (uint32_t)K;
     a.T = (uint32_t)T;
     a.bL = (uint32_t)bL;
     a.R = (uint32_t)R;
@@ -1187,6 +1225,14 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
             rem /= (uint64_t)L.dims[Cw[j]];
         }
         a.cl[c] = (uint16_t)off;
+    }
+    for (uint64_t c = 0; c < K; ++c) {
+        uint64_t rem = c, off = 0;
+        for (int j = 0; j < nK; ++j) {
+            off += (rem % (uint64_t)L.dims[Kw[j]]) * (uint64_t)L.b[Kw[j]];
+            rem /= (uint64_t)L.dims[Kw[j]];
+        }
+        a.chk[c] = (uint16_t)off;
     }
     a.nfree = 0;
     for (int w = 0; w < L.n; ++w)
