@@ -542,6 +542,7 @@ struct RingArgs {
     int32_t renorm;              // the block is unitary: give each output class its input's 2-norm
     int32_t vec2;                // 16-byte copies (even rows, 16-byte aligned state)
     int32_t bulk;                // rows by bulk copies (rows of a multiple of 16 bytes, aligned)
+    int32_t pair16;              // members r, r + 1 (r even) adjacent and 16-byte aligned: paired stores
     uint32_t P, Q, K, T, bL, R, nslots;  // Q classes per chunk (MMA rows), K chunks per tile
     FastDiv32 bLdiv;
     uint32_t ntiles;
@@ -866,13 +867,21 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
                 for (uint32_t jj = 0; jj < NPH; ++jj) {
                     const uint32_t j = 2u * jj + h;
 #pragma unroll
-                    for (uint32_t k = 0; k < 8; ++k) {
+                    for (uint32_t k = 0; k < 8; k += 2) {
                         const uint32_t r = 8u * j + k;
-                        if (j < NP && r < a.P) {
+                        if (j >= NP || r >= a.P) continue;
+                        const uint32_t c0 = 8 * jj + k;
+                        const float2 y0 = make_float2(fmaf(yr[c0], cc, yr[c0]), fmaf(yi[c0], cc, yi[c0]));
+                        const float2 y1 = make_float2(fmaf(yr[c0 + 1], cc, yr[c0 + 1]), fmaf(yi[c0 + 1], cc, yi[c0 + 1]));
+                        if (a.pair16) {
+                            // wire 0 (even dimension) is the gate's first wire: members r, r + 1
+                            // (r even) are adjacent amplitudes, one 16-byte store
                             const uint64_t o = s_gofs[r];
-                            if (in_bounds(o, lim))
-                                dst[o] = make_float2(fmaf(yr[8 * jj + k], cc, yr[8 * jj + k]),
-                                                     fmaf(yi[8 * jj + k], cc, yi[8 * jj + k]));
+                            if (in_bounds(o + 1, lim))
+                                *reinterpret_cast<float4*>(dst + o) = make_float4(y0.x, y0.y, y1.x, y1.y);
+                        } else {
+                            if (in_bounds(s_gofs[r], lim)) dst[s_gofs[r]] = y0;
+                            if (r + 1 < a.P && in_bounds(s_gofs[r + 1], lim)) dst[s_gofs[r + 1]] = y1;
                         }
                     }
                 }
@@ -1178,6 +1187,10 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
     // rows of at least 128 bytes go by bulk copies (16-byte aligned: the rows
     // start at multiples of bL, and bL is even)
     a.bulk = (a.vec2 && bL >= 16) ? 1 : 0;
+    // 16-byte output stores of members r, r + 1 (r even): wire 0 of even
+    // dimension is the gate's first wire, so the two are adjacent and every
+    // pair starts at an even index (the other wires' strides are even)
+    a.pair16 = ((reinterpret_cast<uintptr_t>(psi) & 15u) == 0 && L.dims[0] % 2 == 0 && wires[0] == 0) ? 1 : 0;
     a.P = (uint32_t)P;
     sp->ph = (int)Ph;
     a.Q = (uint32_t)Q;
