@@ -51,6 +51,15 @@ FP64_TFLOPS = 1.25
 ALU_PEAK_NOTE = "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz = 80.5 TFLOP/s (FP64: 1.25 TFLOP/s nominal)"
 
 
+def bf16_peak() -> float:
+    """Dense BF16 tensor peak in TFLOP/s: the measured burst figure (fallback 1900)."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("bf16_tflops", 1900.0))
+    return 1900.0
+
+
 def tf32_peak() -> float:
     """Dense TF32 tensor peak in TFLOP/s: the measured bf16 burst figure times the
     nominal TF32/BF16 ratio (1.1 / 2.25)."""
@@ -795,8 +804,9 @@ def pass_attribution(qb, gen, torch, st, circ, prec, fuse, fopts, stream, amp_by
     D = circ.D
     if fuse:
         mode = {"tile": qb.QD_FUSE_TILE, "block": qb.QD_FUSE_BLOCK}[fuse]
+        popts = {k: v for k, v in fopts.items() if k != "tc_mode"}  # the plan does not depend on it
         order, pass_of, tiles, pflops = qb.qd_plan_circuit(circ.dims, prec, circ, mode=mode, with_flops=True,
-                                                           **fopts)
+                                                           **popts)
         groups = [[] for _ in range(len(tiles))]
         for g_idx, p_idx in zip(order, pass_of):
             groups[p_idx].append(circ.gates[g_idx])
@@ -823,7 +833,9 @@ def pass_attribution(qb, gen, torch, st, circ, prec, fuse, fopts, stream, amp_by
         if fuse and tiles[i] > 0:
             k, nbytes = "tile", 2 * amp_bytes * D
         elif fuse and len(gl) > 1 and prec == qb.QD_C64 and P >= 17:
-            k, nbytes = "tc", 2 * amp_bytes * D
+            # BF16x3 composed blocks (no controls) stream through the tile ring
+            k = "ring" if fopts.get("tc_mode") == "bf16x3" else "tc"
+            nbytes = 2 * amp_bytes * D
         elif len(gl) == 1:
             k, nbytes = "gate", algorithmic_bytes(plans[0], amp_bytes)
         else:
@@ -838,11 +850,14 @@ def pass_attribution(qb, gen, torch, st, circ, prec, fuse, fopts, stream, amp_by
         f["gates"] += len(gl)
         if k == "tc":  # 3 products x 16 k-steps of M=128, N=64, K=8 per 64 classes
             f["mma_flops"] += math.ceil(D / P / 64) * 48 * 2 * 128 * 64 * 8
+        elif k == "ring":  # useful products: 3 x 2 (2P)^2 per class, D / P classes
+            f["mma_flops"] += 24.0 * P * D
     return fam
 
 
 KERNEL_NAMES = {"tile": "k_fused_tile (shared-memory tile pass)",
-                "tc": "k_block_tc (tcgen05 tensor-core block pass)",
+                "tc": "k_block_tc (tcgen05 tensor-core block pass, TF32x3)",
+                "ring": "k_block_tc_ring (tcgen05 block pass over a ring of bulk-copied tiles, BF16x3)",
                 "gate": "k_gate1 / k_gate_tile (per-gate passes)"}
 
 
@@ -871,8 +886,13 @@ def roofline_of(fam, traffic_key, is_c64):
         achieved = f["bytes"] / t / 1e9
         roof = {"kernel": KERNEL_NAMES[dom], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_kind,
-                "traffic": ncu_traffic(traffic_key, "tc" if dom == "tc" else "gate"), "launches_measured": f["n"],
-                "method_tflops": f["method_flops"] / t / 1e12}
+                "traffic": ncu_traffic(traffic_key, "tc" if dom in ("tc", "ring") else "gate"),
+                "launches_measured": f["n"], "method_tflops": f["method_flops"] / t / 1e12}
+        if dom == "ring":
+            roof["tensor_view"] = {"achieved_tflops": f["mma_flops"] / t / 1e12, "peak_tflops": bf16_peak(),
+                                   "frac": f["mma_flops"] / t / 1e12 / bf16_peak(),
+                                   "work": "the three BF16 products of each class's real 2P x 2P embedding",
+                                   "peak_source": "measured bf16 burst"}
         if dom == "tc":
             tf32 = tf32_peak()
             roof["tensor_view"] = {"achieved_tflops": f["mma_flops"] / t / 1e12, "peak_tflops": tf32,
@@ -911,7 +931,8 @@ def measure_benchmark_circuit(qb, gen, torch, stream, steps=10):
         if fuse == "auto":
             tuned = autotune.tune_circuit(st, circ)
             fuse = tuned["mode"] if tuned["mode"] != "off" else False
-            fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"]} if fuse else {}
+            fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"],
+                     "tc_mode": tuned["tc_mode"]} if fuse else {}
 
         def step():
             st.reset()
@@ -969,12 +990,15 @@ def run_gpu(args):
     if args.fuse == "auto":
         tuned = autotune.tune_circuit(st, circ, budget_s=45.0)
         fuse = tuned["mode"] if tuned["mode"] != "off" else False
-        fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"]} if fuse else {}
+        fopts = {"max_tile_amps": tuned["max_tile_amps"], "block_dim": tuned["block_dim"],
+                 "tc_mode": tuned["tc_mode"]} if fuse else {}
     else:
         fuse = args.fuse if args.fuse != "off" else False
         fopts = {"max_tile_amps": args.tile} if fuse == "tile" and args.tile else {}
         if fuse and args.block_dim:
             fopts["block_dim"] = args.block_dim
+        if fuse:
+            fopts["tc_mode"] = args.tc_mode
 
     def step():
         st.reset()
@@ -1159,6 +1183,8 @@ def run_ncu_fused_case(args):
     opts = {"max_tile_amps": args.tile} if args.tile and fuse == "tile" else {}
     if args.block_dim:
         opts["block_dim"] = args.block_dim
+    if fuse == "block":
+        opts["tc_mode"] = args.tc_mode
     st.run(circ, fuse=fuse, **opts)
     st.synchronize()
     st.close()
@@ -1194,6 +1220,8 @@ def main(argv=None):
     ap.add_argument("--prec", choices=["c64", "c128"], default="c64",
                     help="precision of the profiler cases (the bench line itself is complex64; complex128 is "
                          "reported under benchmark_circuit)")
+    ap.add_argument("--tc-mode", default="tf32x3", choices=["tf32x3", "bf16x3", "fp32"],
+                    help="arithmetic of complex64 blocks of 17..64 dimensions when --fuse is not auto")
     ap.add_argument("--block-dim", type=int, default=0,
                     help="largest composed block with --fuse tile|block (0 = library default)")
     ap.add_argument("--ncu-workload", choices=["benchmark", "prefix"], default="benchmark",

@@ -19,15 +19,19 @@ from typing import Callable, Dict, Iterable, Optional, Sequence, Tuple
 
 import numpy as np
 
-# (mode, max_tile_amps, block_dim): mode 0 = one kernel pass per gate,
-# 1 = shared-memory tile passes, 2 = whole-state composed blocks
+# (mode, max_tile_amps, block_dim, tc_mode): mode 0 = one kernel pass per
+# gate, 1 = shared-memory tile passes, 2 = whole-state composed blocks;
+# tc_mode = the arithmetic of complex64 blocks of 17..64 dimensions
+# (0 TF32x3, 1 BF16x3).  Whole-state block candidates come first, so that a
+# spent time budget cuts tile candidates, not them.
 FUSION_CANDIDATES = {
-    0: [(0, 0, 0)] + [(1, t, b) for t in (2048, 4096, 8192, 16384) for b in (1, 4, 8, 16)]
-       + [(1, t, b) for t in (4096, 8192) for b in (24, 32)]  # blocks of 17..32 dims on tensor cores in tiles
-       + [(2, 0, b) for b in (32, 64)],
-    1: [(0, 0, 0)] + [(1, t, b) for t in (1024, 2048, 4096, 8192) for b in (1, 4, 8, 16)]
-       + [(2, 0, b) for b in (4, 8)],
+    0: [(0, 0, 0, 0)] + [(2, 0, b, tc) for tc in (1, 0) for b in (64, 32)]
+       + [(1, t, b, 0) for t in (2048, 4096, 8192, 16384) for b in (1, 4, 8, 16)]
+       + [(1, t, b, 0) for t in (4096, 8192) for b in (24, 32)],  # blocks of 17..32 dims on tensor cores in tiles
+    1: [(0, 0, 0, 0)] + [(1, t, b, 0) for t in (1024, 2048, 4096, 8192) for b in (1, 4, 8, 16)]
+       + [(2, 0, b, 0) for b in (4, 8)],
 }
+TC_NAMES = {0: "tf32x3", 1: "bf16x3"}
 MODE_NAMES = {0: "off", 1: "tile", 2: "block"}
 
 
@@ -71,8 +75,8 @@ def shape_key(kind: str, prec: int, dims: Sequence[int], n_gates: int) -> str:
             f"dmax{max(dims)}|g{int(round(math.log2(max(n_gates, 1))))}")
 
 
-def time_candidates(run: Callable[[Tuple[int, int]], None], candidates: Iterable[Tuple[int, int]],
-                    stream, reps: int = 3, budget_s: float = 30.0) -> Dict[Tuple[int, int], float]:
+def time_candidates(run: Callable[[tuple], None], candidates: Iterable[tuple],
+                    stream, reps: int = 3, budget_s: float = 30.0) -> Dict[tuple, float]:
     """Seconds per run of each candidate (one warm-up run, then ``reps`` timed
     with CUDA events on ``stream``); stops early when the budget is spent."""
     import torch
@@ -97,9 +101,9 @@ def time_candidates(run: Callable[[Tuple[int, int]], None], candidates: Iterable
 def tune_circuit(state, circuit, retune: bool = False, reps: int = 3, budget_s: float = 30.0) -> dict:
     """Best fusion settings for ``circuit`` on ``state`` (a ``binding.State`` of
     the circuit's dims).  Returns {"mode" ("off" / "tile" / "block"),
-    "max_tile_amps", "block_dim", "seconds", "table"}; the state is left in
-    an unspecified state."""
-    key = shape_key("circuit", state.prec, circuit.dims, len(circuit.gates))
+    "max_tile_amps", "block_dim", "tc_mode" ("tf32x3" / "bf16x3"), "seconds",
+    "table"}; the state is left in an unspecified state."""
+    key = shape_key("circuit2", state.prec, circuit.dims, len(circuit.gates))
     cache = _load()
     if not retune and key in cache:
         return cache[key]
@@ -109,12 +113,13 @@ def tune_circuit(state, circuit, retune: bool = False, reps: int = 3, budget_s: 
         if c[0] == 0:
             state.run(circuit, fuse=False)
         else:
-            state.run(circuit, fuse=MODE_NAMES[c[0]], max_tile_amps=c[1], block_dim=c[2])
+            state.run(circuit, fuse=MODE_NAMES[c[0]], max_tile_amps=c[1], block_dim=c[2], tc_mode=TC_NAMES[c[3]])
 
     table = time_candidates(run, FUSION_CANDIDATES[state.prec], state.stream, reps=reps, budget_s=budget_s)
     best = min(table, key=table.get)
-    entry = {"mode": MODE_NAMES[best[0]], "max_tile_amps": best[1], "block_dim": best[2], "seconds": table[best],
-             "table": {f"{MODE_NAMES[m]}/{t}/{b}": v for (m, t, b), v in table.items()}}
+    entry = {"mode": MODE_NAMES[best[0]], "max_tile_amps": best[1], "block_dim": best[2],
+             "tc_mode": TC_NAMES[best[3]], "seconds": table[best],
+             "table": {f"{MODE_NAMES[m]}/{t}/{b}/{TC_NAMES[tc]}": v for (m, t, b, tc), v in table.items()}}
     cache[key] = entry
     _save(cache)
     return entry

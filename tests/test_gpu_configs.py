@@ -93,7 +93,10 @@ def test_config2_full_size_inverse_returns_to_zero(qb, gen, fuse):
 # closed forms (every byte offset range of the state, including the amplitudes
 # beyond 2^32 bytes).
 # ----------------------------------------------------------------------------
-LARGE_MODES = ["per_gate", "tile", "block"]
+# block: composed blocks of up to 64 dimensions in TF32x3 (register-staged
+# kernel); block_bf16x3: the same in BF16x3 through the tile ring, the
+# configuration the benchmark's autotuner picks for this workload
+LARGE_MODES = ["per_gate", "tile", "block", "block_bf16x3"]
 
 
 def _run_mode(st, circ, mode):
@@ -102,8 +105,10 @@ def _run_mode(st, circ, mode):
         st.run(circ, fuse=False)
     elif mode == "tile":
         st.run(circ, fuse="tile")
-    else:
+    elif mode == "block":
         st.run(circ, fuse="block")
+    else:
+        st.run(circ, fuse="block", block_dim=64, tc_mode="bf16x3")
 
 
 def _sample_indices(D, seed, n_random=1_000_000, n_tail=100_000, extra=()):
@@ -166,7 +171,7 @@ def test_config2_full_size_product_state(qb, large_state, product_ref, mode):
     """1.72e9 amplitudes, complex64, 200 uncontrolled Haar / F / Z / X gates on
     all 26 wires: psi[j] = prod_w v_w[digit_w(j)] on a sample of about 1.1e6
     indices including the last 1e5, per gate, in tile passes and in
-    composed blocks (tensor cores, TF32x3)."""
+    composed blocks (tensor cores, TF32x3 and BF16x3)."""
     circ, factors = product_ref
     st = large_state
     _run_mode(st, circ, mode)
@@ -189,7 +194,9 @@ def test_config2_full_size_product_state(qb, large_state, product_ref, mode):
 def test_config2_full_size_ghz(qb, gen, large_state, mode):
     """Mixed-radix GHZ on the 26 wires of the large workload, rooted at the
     qubit wire 0: amplitude 1/sqrt(2) at index 0 and at sum_t b_t (the last
-    basis state whose digits are all 1), zero at every other sampled index."""
+    basis state whose digits are all 1), zero at every other sampled index.
+    BF16x3 blocks are held to the complex64 tolerance (1e-5): their products
+    are good to about 2^-16 relative per block, the others to 1e-6."""
     st = large_state
     dims = gen.config2_circuit().dims
     assert dims[0] == 2
@@ -203,5 +210,6 @@ def test_config2_full_size_ghz(qb, gen, large_state, mode):
     ref[np.searchsorted(idx, 0)] = 2 ** -0.5
     ref[np.searchsorted(idx, ones)] = 2 ** -0.5
     err = np.abs(got - ref)
-    assert float(err.max()) <= 1e-6, f"{mode}: max |d amp| = {err.max():.3e} at {idx[np.argmax(err)]}"
-    assert abs(st.norm() - 1.0) < 1e-6
+    tol = 1e-5 if mode == "block_bf16x3" else 1e-6
+    assert float(err.max()) <= tol, f"{mode}: max |d amp| = {err.max():.3e} at {idx[np.argmax(err)]}"
+    assert abs(st.norm() - 1.0) < tol
