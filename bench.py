@@ -1192,6 +1192,29 @@ def run_ncu_fused_case(args):
     return 0
 
 
+def run_ncu_block_case(args):
+    """One 64-dimensional Haar block (the six highest wires) on 2^27 qubit
+    amplitudes (1.07 GB complex64), applied twice in BF16x3: a case of the
+    tile-ring kernel small enough for a full profiler capture (the second
+    launch), larger than L2."""
+    import torch
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2410_17876_gb300 import binding as qb
+    from paper_2410_17876_gb300 import inputs as gen
+
+    st = qb.State((2,) * 27, prec=qb.QD_C64)
+    st.set_fusion(1, "bf16x3")
+    g = gen.Gate((21, 22, 23, 24, 25, 26), gen.haar(64, np.random.Generator(np.random.PCG64(1))))
+    st.apply(g)
+    st.apply(g)
+    torch.cuda.synchronize()
+    st.close()
+    return 0
+
+
 def run_ncu_batch_case(args):
     """The first 1024 circuits of the 8192-circuit workload, once through the
     device-side layer queue (a profiler capture of k_fused_layer)."""
@@ -1241,12 +1264,17 @@ def main(argv=None):
     ap.add_argument("--ncu-fused-case", action="store_true",
                     help="run only the --ncu-workload circuit once, fused (--fuse tile or block; auto means "
                          "tile), for a profiler capture of one fused launch; prints nothing")
+    ap.add_argument("--ncu-block-case", action="store_true",
+                    help="run only one 64-dimensional BF16x3 block twice on 2^27 amplitudes, for a profiler "
+                         "capture of the tile-ring kernel; prints nothing")
     ap.add_argument("--ncu-batch-case", action="store_true",
                     help="run only 1024 circuits of the batched workload once through the layer queue, for a "
                          "profiler capture of the layer kernel; prints nothing")
     args = ap.parse_args(argv)
     if args.ncu_batch_case:
         return run_ncu_batch_case(args)
+    if args.ncu_block_case:
+        return run_ncu_block_case(args)
     if args.ncu_case:
         return run_ncu_case(args)
     if args.ncu_fused_case:
