@@ -694,7 +694,13 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
                 __syncwarp();
                 for (uint32_t r = lane; r < a.R; r += 32) {
                     const uint64_t g = base + s_row[r];
-                    if (!in_bounds(g + a.bL - 1, a.D)) continue;
+                    if (!in_bounds(g + a.bL - 1, a.D)) {
+                        // bounds-checked build: the row is skipped, its bytes counted as landed
+                        asm volatile("mbarrier.complete_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(fb),
+                                     "r"(8u * a.bL)
+                                     : "memory");
+                        continue;
+                    }
                     asm volatile(
                         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                             d0 + 8u * r * a.bL),

@@ -1,7 +1,8 @@
 """The bounds-checked debug build (QD_BOUNDS=1), which stands in for a memory
 sanitizer: built in its own directory and loaded in a fresh interpreter, it
 runs circuits through every gate path (per gate in both precisions, tile
-passes, tensor-core blocks, a multi-wire gate, a batch through the layer
+passes, tensor-core blocks in TF32x3 and through the BF16x3 tile ring, a
+multi-wire gate, a batch through the layer
 queue and through stream programs) against the oracle with no index
 recorded outside its buffer; then the testing hook that hides the last
 amplitudes of the state from the per-gate kernels shows that such an index
@@ -36,9 +37,16 @@ SCRIPT = textwrap.dedent("""
     circ.gates.insert(40, gen.Gate((1, 3, 0), gen.haar(24, rng)))      # multi-wire, tensor cores in complex64
     ref = oracle.run_circuit(circ)
     for prec in (qb.QD_C128, qb.QD_C64):
-        for fuse in (False, "tile", "block"):
+        for fuse in (False, "tile", "block", "block_bf16x3"):
+            if fuse == "block_bf16x3" and prec != qb.QD_C64:
+                continue
             st = qb.State(dims, prec=prec)
-            st.run(circ, fuse=fuse)
+            if fuse == "block_bf16x3":   # tensor-core blocks through the tile ring
+                n0 = qb.qd_test_tc_ring_launches()
+                st.run(circ, fuse="block", tc_mode="bf16x3")
+                assert qb.qd_test_tc_ring_launches() > n0
+            else:
+                st.run(circ, fuse=fuse)
             assert_close(st.amplitudes(), ref, prec, f"bounds build prec={{prec}} fuse={{fuse}}")
             st.close()
     circs = [gen.random_mixed_circuit(tuple(int(x) for x in rng.choice([2, 3, 4], size=int(rng.integers(5, 11)))),
