@@ -522,8 +522,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
 // the slots have copies in flight.  Tensor memory, per stage (256 columns):
 // A_hi [0, 64), A_lo [64, 128), accumulator [128, 128 + 2Ph).
 constexpr int kRingMaxSlots = 6;
-constexpr int kRingMaxQ = 128;
-constexpr int kRingMaxK = 64;
+constexpr int kRingMaxQ = 128;     // classes per chunk: the MMA's rows
+constexpr int kRingMaxCls = 512;   // classes per tile
 constexpr int kRingMaxRows = 64;
 constexpr int kRingConvWarps = 8;                 // warps 0..7
 constexpr int kRingEpiWarps = 8;                  // warps 8..15
@@ -543,7 +543,7 @@ struct RingArgs {
     int32_t vec2;                // 16-byte copies (even rows, 16-byte aligned state)
     int32_t bulk;                // rows by bulk copies (rows of a multiple of 16 bytes, aligned)
     int32_t pair16;              // members r, r + 1 (r even) adjacent and 16-byte aligned: paired stores
-    uint32_t P, Q, K, T, bL, R, nslots;  // Q classes per chunk (MMA rows), K chunks per tile
+    uint32_t P, Q, K, T, bL, R, nslots;  // Q classes per tile, K = ceil(Q / 128) chunks of up to 128
     FastDiv32 bLdiv;
     uint32_t ntiles;
     int32_t nfree;               // wires outside S, ascending: tile index digits
@@ -552,8 +552,7 @@ struct RingArgs {
     uint64_t free_b[kMaxWires];
     uint64_t srow[kRingMaxRows];  // offset of each row from the tile's base
     uint64_t gofs[kMaxGateDim];   // member r -> offset from its class's amplitude in the state
-    uint16_t cl[kRingMaxQ];       // class c of a chunk -> offset from the chunk's first class
-    uint16_t chk[kRingMaxK];      // chunk k -> offset of its first class in the tile (and from the tile's base)
+    uint16_t cl[kRingMaxCls];     // class c of a tile -> offset in the tile (and from the tile's base)
     uint16_t ml[kMaxGateDim];     // member r -> offset from its class in the tile
 };
 
@@ -616,8 +615,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
     __shared__ uint64_t s_gofs[kMaxGateDim];
     __shared__ uint64_t s_tbase[kRingMaxSlots];  // base of the tile in each slot (loader -> converters)
     __shared__ uint64_t s_sbase[4];               // base of tile i at i mod 4 (converters -> epilogue)
-    __shared__ uint32_t s_cl[kRingMaxQ];
-    __shared__ uint32_t s_chk[kRingMaxK];
+    __shared__ uint16_t s_cl[kRingMaxCls];
     __shared__ uint32_t s_ml[kMaxGateDim];
     __shared__ float s_nin[4][2][kRingMaxQ];     // [tile mod 4][half][class]
     __shared__ float s_nout[2][2][kRingMaxQ];
@@ -648,8 +646,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     for (uint32_t i = tid; i < kRingMaxRows; i += kRingThreads) s_row[i] = i < a.R ? a.srow[i] : 0;
-    for (uint32_t i = tid; i < kRingMaxQ; i += kRingThreads) s_cl[i] = i < a.Q ? a.cl[i] : 0;
-    for (uint32_t i = tid; i < kRingMaxK; i += kRingThreads) s_chk[i] = i < a.K ? a.chk[i] : 0;
+    for (uint32_t i = tid; i < kRingMaxCls; i += kRingThreads) s_cl[i] = i < a.Q ? a.cl[i] : 0;
     for (uint32_t i = tid; i < kMaxGateDim; i += kRingThreads) {
         s_ml[i] = i < a.P ? a.ml[i] : 0;
         s_gofs[i] = i < a.P ? a.gofs[i] : 0;
@@ -740,7 +737,6 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
         // ---------------- converters: warp = (half, quarter) ----------------
         const uint32_t q = (uint32_t)warp & 3u, h = (uint32_t)warp >> 2;
         const uint32_t L = 32u * q + (uint32_t)lane;
-        const uint32_t cb = s_cl[L];  // 0 beyond Q: those rows are computed and never stored
         const uint32_t lanes = (32u * q) << 16;
         uint32_t i = 0, ic = 0;  // tile, chunk counters
         bool quit = false;
@@ -761,7 +757,9 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const float2* x = ring + (size_t)s * T + s_chk[k] + cb;
+                // class 128 k + L of the tile (beyond Q: row computed, never stored)
+                const uint32_t c = 128u * k + L;
+                const float2* x = ring + (size_t)s * T + (c < a.Q ? s_cl[c] : 0u);
                 const uint32_t ta = tm + lanes + st * kRingStageCols;
                 float nin = 0.f;
 #pragma unroll 1
@@ -797,7 +795,7 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
                     tmem_st4u(ta + 64u + (PH + r0) / 2, li[0], li[1], li[2], li[3]);
                 }
                 s_nin[ic & 3u][h][L] = nin;
-                if (warp == 0 && lane == 0) s_sbase[ic & 3u] = s_tbase[s] + s_chk[k];
+                if (warp == 0 && lane == 0) s_sbase[ic & 3u] = s_tbase[s];
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_u32(&m_meta[ic & 3u]));
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -815,8 +813,6 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
         const uint32_t e = (uint32_t)warp - kRingConvWarps;
         const uint32_t q = e & 3u, h = e >> 2;
         const uint32_t L = 32u * q + (uint32_t)lane;
-        const bool valid = L < a.Q;
-        const uint64_t cb = s_cl[L];
         const uint32_t lanes = (32u * q) << 16;
         for (uint32_t i = 0; i < n_chunks; ++i) {
             const uint32_t st = i & 1u;
@@ -848,7 +844,9 @@ __global__ void __launch_bounds__(kRingThreads, 1) k_block_tc_ring(const __grid_
                 reg_after_wait(yi[c]);
                 if (2u * (c / 8) + h < NP) no = fmaf(yr[c], yr[c], fmaf(yi[c], yi[c], no));
             }
-            const uint64_t base = s_sbase[i & 3u] + cb;
+            const uint32_t cls = 128u * (i % a.K) + L;  // the tile's class of this lane in this chunk
+            const bool valid = cls < a.Q;
+            const uint64_t base = s_sbase[i & 3u] + (valid ? s_cl[cls] : 0u);
             const float ni = s_nin[i & 3u][0][L] + s_nin[i & 3u][1][L];
             s_nout[st][h][L] = no;
             // the accumulator is in registers: the stage goes back to the converters
@@ -1139,32 +1137,28 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
     const uint32_t Ph = (uint32_t)((P + 7) & ~7), N2 = 2 * Ph;
     const size_t bbytes = (size_t)2 * N2 * N2 * 2;
     const size_t avail = kRingSmemCap - bbytes;
-    // Classes: the lowest wires outside W.  A chunk takes as many as the MMA
-    // has rows (per-chunk costs are fixed; measured on 2^27 amplitudes and a
-    // 64-dimensional block, 128 classes per tile take 0.40 ms per pass, 64
-    // 0.77 ms); the tile then takes further such wires as whole chunks while
-    // two slots still fit, so that its rows grow (a bulk copy of a short row
-    // costs about as much as one of a long one).
-    uint64_t S = W, Q = 1, K = 1;
-    int nC = 0, nK = 0;
-    int Cw[kMaxWires], Kw[kMaxWires];
-    int w = 0;
-    for (; w < L.n; ++w) {
+    // Classes: the lowest wires outside W, as many as two ring slots hold
+    // (at most kRingMaxCls).  Every wire below the highest of them is in the
+    // tile, so its rows are as long as they can be (a bulk copy of a short
+    // row costs about as much as one of a long one).  The tile's classes are
+    // cut into chunks of 128, the MMA's rows (the last chunk partial): the
+    // per-chunk costs are fixed (measured on 2^27 amplitudes and a
+    // 64-dimensional block, chunks of 128 classes take 0.40 ms per pass, of
+    // 64 0.77 ms), and a flat cut fills more rows than a product of wires
+    // (216 classes: 2 chunks, not 3 of 72).
+    uint64_t S = W, Q = 1;
+    int nC = 0;
+    int Cw[kMaxWires];
+    for (int w = 0; w < L.n; ++w) {
         if (W >> w & 1) continue;
-        if (Q * (uint64_t)L.dims[w] > (uint64_t)kRingMaxQ || 2 * Q * (uint64_t)L.dims[w] * P * 8 > avail) break;
+        if (Q * (uint64_t)L.dims[w] > (uint64_t)kRingMaxCls || 2 * Q * (uint64_t)L.dims[w] * P * 8 > avail) break;
         S |= 1ull << w;
         Q *= (uint64_t)L.dims[w];
         Cw[nC++] = w;
     }
-    for (; w < L.n; ++w) {
-        if (W >> w & 1) continue;
-        if (K * (uint64_t)L.dims[w] > (uint64_t)kRingMaxK || 2 * Q * K * (uint64_t)L.dims[w] * P * 8 > avail) break;
-        S |= 1ull << w;
-        K *= (uint64_t)L.dims[w];
-        Kw[nK++] = w;
-    }
+    const uint64_t K = (Q + kRingMaxQ - 1) / kRingMaxQ;
     // a tile of few classes leaves most MMA rows idle: the register-staged kernel instead
-    if (Q < 32 && (uint64_t)L.D / (uint64_t)P > Q * K) return nullptr;
+    if (Q < 32 && (uint64_t)L.D / (uint64_t)P > Q) return nullptr;
     int L0 = 0;
     while (L0 < L.n && (S >> L0 & 1)) ++L0;
     const uint64_t bL = (uint64_t)L.b[L0];
@@ -1175,7 +1169,7 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
             rw[nr++] = w;
             R *= (uint64_t)L.dims[w];
         }
-    const uint64_t T = Q * K * (uint64_t)P;
+    const uint64_t T = Q * (uint64_t)P;
     if (bL * R != T || R > (uint64_t)kRingMaxRows || T > 65535) return nullptr;
     const uint64_t ntiles = (uint64_t)L.D / T;
     if (ntiles * T != (uint64_t)L.D || ntiles >= (1ull << 32)) return nullptr;
@@ -1245,14 +1239,7 @@ std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi
         }
         a.cl[c] = (uint16_t)off;
     }
-    for (uint64_t c = 0; c < K; ++c) {
-        uint64_t rem = c, off = 0;
-        for (int j = 0; j < nK; ++j) {
-            off += (rem % (uint64_t)L.dims[Kw[j]]) * (uint64_t)L.b[Kw[j]];
-            rem /= (uint64_t)L.dims[Kw[j]];
-        }
-        a.chk[c] = (uint16_t)off;
-    }
+
     a.nfree = 0;
     for (int w = 0; w < L.n; ++w)
         if (!(S >> w & 1)) {

@@ -1,6 +1,7 @@
 """GPU parity of the BF16x3 tile-ring kernel (complex64 blocks of 17..64
-dimensions without controls) against the oracle: chunks of up to 128
-classes, one to four chunks per tile, two to six ring slots, odd row lengths (8-byte copies instead
+dimensions without controls) against the oracle: tiles of up to 512
+classes cut into chunks of 128 (the last one partial: 243, 216 and 144
+classes), one to four chunks per tile, two to six ring slots, odd row lengths (8-byte copies instead
 of bulk copies), a single tile holding the whole state, several tiles per
 CTA with a ragged last round, blocks whose wires sit inside and above the
 contiguous run, padded block dimensions, the launch counter that tells the
@@ -65,7 +66,7 @@ CASES = [
     ((4, 4, 4, 2, 3), (0, 1, 2)),
     # P = 48 on wires 0..2, the classes above the block
     ((4, 3, 4, 2, 3, 2, 2, 2, 3), (0, 1, 2)),
-    # several chunks of classes per tile (128 x 4, 16 tiles; 96 x 4 with a qutrit among the chunk wires)
+    # several chunks of classes per tile (512 = 4 x 128, 16 tiles; 384 = 3 x 128 with qutrits among the class wires)
     ((2,) * 12 + (3, 4, 2, 2), (12, 13, 0)),
     ((2, 2, 2, 2, 2, 2, 2, 3, 2, 3, 2, 2, 2), (9, 12, 0, 1)),
 ]
@@ -85,8 +86,8 @@ def test_ring_block_matches_oracle(qb, gen, dims, wires):
 
 
 def test_ring_many_tiles_per_cta(qb, gen):
-    """2.65M amplitudes, a 64-dimensional block: 288 tiles of two chunks of
-    72 classes, several per CTA, a ragged last round over the SMs."""
+    """2.65M amplitudes, a 64-dimensional block: 288 tiles of 144 classes
+    (chunks of 128 and 16), several per CTA, a ragged last round over the SMs."""
     rng = np.random.Generator(np.random.PCG64(90))
     dims = (2, 3, 2, 2, 3, 2, 2, 2, 2, 3, 2, 2, 2, 2, 3, 2, 2, 2, 2)
     psi0 = gen.random_state(int(np.prod(dims)), rng)
