@@ -1839,14 +1839,122 @@ static size_t emit_chunks(const TileGeom& geo, const std::vector<HGate>& G, cons
 }
 
 // QD_FUSE_BLOCK: blocks over the whole state, one pass each.
+// Whole-state blocks (QD_FUSE_BLOCK), each one pass over the state.  A block
+// starts from the wires of the first remaining gate and takes every later
+// gate on its wires that commutes with the gates left behind before it; then,
+// one gate's wires at a time, the block adds the wires that let it take the
+// most gates (ties: the smaller block), while it stays within Pmax
+// dimensions and the addition takes more gates.  Its wires are then those of
+// the gates it took.  (Adding wires in gate order instead: 25 blocks for the
+// 200 gates of the 18-qubit + 8-qutrit workload at Pmax = 64, this 20.)
+static void form_whole_blocks(const TileGeom& geo, const std::vector<HGate>& G, int Pmax,
+                              std::vector<BlockPlan>& out) {
+    out.clear();
+    const size_t n = G.size();
+    std::vector<uint64_t> lwm(n);
+    std::vector<char> inside(n);
+    for (size_t i = 0; i < n; ++i) {
+        const HGate& h = G[i];
+        lwm[i] = local_mask(geo, h.tmask | h.cmask);
+        bool in = h.k == 1;
+        for (int c = 0; c < h.nc && in; ++c) in = geo.loc[h.cw[c]] >= 0;
+        inside[i] = in;
+    }
+    auto prod_of = [&](uint64_t m) {
+        int64_t p = 1;
+        while (m) {
+            p *= geo.local.dims[__builtin_ctzll(m)];
+            m &= m - 1;
+        }
+        return p;
+    };
+    std::vector<int> rem(n);
+    for (size_t i = 0; i < n; ++i) rem[i] = (int)i;
+    // the gates a block on wires S takes from the first kPlanWindow remaining
+    auto scan = [&](uint64_t S, std::vector<int>* sel) {
+        uint64_t BW = 0, BR = 0;
+        int cnt = 0;
+        const size_t m = rem.size() < kPlanWindow ? rem.size() : kPlanWindow;
+        for (size_t j = 0; j < m; ++j) {
+            const int gi = rem[j];
+            const HGate& g = G[gi];
+            const uint64_t Wg = g.diag ? 0 : g.tmask;
+            const uint64_t Rg = g.cmask | (g.diag ? g.tmask : 0);
+            const bool blocked = (Wg & (BW | BR)) || (Rg & BW);
+            if (!blocked && inside[gi] && (lwm[gi] & ~S) == 0) {
+                ++cnt;
+                if (sel) sel->push_back(gi);
+                continue;
+            }
+            BW |= Wg;
+            BR |= Rg;
+        }
+        return cnt;
+    };
+    std::vector<char> taken(n, 0);
+    std::vector<uint64_t> tried;
+    while (!rem.empty()) {
+        const int g0 = rem[0];
+        BlockPlan bp;
+        bp.single = true;
+        bp.gates = {g0};
+        bp.lw = lwm[g0];
+        if (Pmax >= 4 && inside[g0] && prod_of(lwm[g0]) <= Pmax) {
+            uint64_t S = lwm[g0];
+            int cur = scan(S, nullptr);
+            for (;;) {
+                uint64_t bestS = 0;
+                int bestN = cur;
+                int64_t bestP = 0;
+                tried.clear();
+                const size_t m = rem.size() < kPlanWindow ? rem.size() : kPlanWindow;
+                for (size_t j = 0; j < m; ++j) {
+                    const int gi = rem[j];
+                    if (!inside[gi]) continue;
+                    const uint64_t S2 = S | lwm[gi];
+                    if (S2 == S) continue;
+                    bool seen = false;
+                    for (uint64_t t : tried) seen = seen || t == S2;
+                    if (seen) continue;
+                    tried.push_back(S2);
+                    const int64_t P2 = prod_of(S2);
+                    if (P2 > Pmax) continue;
+                    const int c2 = scan(S2, nullptr);
+                    if (c2 > bestN || (c2 == bestN && bestS != 0 && P2 < bestP)) {
+                        bestS = S2;
+                        bestN = c2;
+                        bestP = P2;
+                    }
+                }
+                if (bestS == 0) break;  // no addition takes more gates
+                S = bestS;
+                cur = bestN;
+            }
+            std::vector<int> sel;
+            scan(S, &sel);
+            if (sel.size() > 1) {
+                bp.single = false;
+                bp.gates = sel;
+                bp.lw = 0;
+                for (int gi : sel) bp.lw |= lwm[gi];
+            }
+        }
+        out.push_back(bp);
+        for (int gi : bp.gates) taken[gi] = 1;
+        std::vector<int> rest;
+        rest.reserve(rem.size());
+        for (int gi : rem)
+            if (!taken[gi]) rest.push_back(gi);
+        rem.swap(rest);
+    }
+}
+
 static void plan_blocks(const Layout& L, const std::vector<HGate>& G, const FuseCfg& cfg,
                         std::vector<PassPlan>& passes) {
     TileGeom geo;
     tile_geometry(L, (L.n >= 64) ? ~0ull : ((1ull << L.n) - 1), 1, geo, false);
-    std::vector<int> all(G.size());
-    for (size_t i = 0; i < G.size(); ++i) all[i] = (int)i;
     std::vector<BlockPlan> blocks;
-    form_blocks(geo, G, all, cfg.block_dim, blocks, true);
+    form_whole_blocks(geo, G, cfg.block_dim, blocks);
     for (const BlockPlan& bp : blocks) {
         PassPlan p;
         p.tile = false;
