@@ -832,10 +832,11 @@ def pass_attribution(qb, gen, torch, st, circ, prec, fuse, fopts, stream, amp_by
         P = int(np.prod([circ.dims[w] for w in wires]))
         if fuse and tiles[i] > 0:
             k, nbytes = "tile", 2 * amp_bytes * D
+        elif fuse and len(gl) > 1 and prec == qb.QD_C64 and fopts.get("tc_mode") == "bf16x3" and P >= 9:
+            # BF16x3 composed blocks (no controls) of 9..64 dimensions stream through the tile ring
+            k, nbytes = "ring", 2 * amp_bytes * D
         elif fuse and len(gl) > 1 and prec == qb.QD_C64 and P >= 17:
-            # BF16x3 composed blocks (no controls) stream through the tile ring
-            k = "ring" if fopts.get("tc_mode") == "bf16x3" else "tc"
-            nbytes = 2 * amp_bytes * D
+            k, nbytes = "tc", 2 * amp_bytes * D
         elif len(gl) == 1:
             k, nbytes = "gate", algorithmic_bytes(plans[0], amp_bytes)
         else:

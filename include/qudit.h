@@ -223,17 +223,20 @@ typedef struct qd_gate_desc {
 #define QD_FUSE_BLOCK 2 /* the circuit is grouped into blocks of at most block_dim (default 64 for
                            complex64, 8 for complex128) dimensions, each composed in binary64 and
                            applied in one pass over the state; complex64 blocks of 17 or more
-                           dimensions run as set by tc_mode */
+                           dimensions (with QD_TC_BF16X3 and no controls: 9 or more) run as set
+                           by tc_mode */
 
-/* Arithmetic of complex64 blocks and multi-wire gates of 17..64 dimensions
+/* Arithmetic of complex64 blocks and multi-wire gates of 17..64 dimensions,
+ * and with QD_TC_BF16X3 of those of 9..16 dimensions without controls too
  * (qd_fusion_opts.tc_mode, qd_set_fusion).  The block is applied as the real
  * contraction [Re Y; Im Y] = [[Re M, -Im M], [Im M, Re M]] [Re X; Im X].
  * The tensor-core modes split both operands, a = a_hi + a_lo, and accumulate
  * A_hi X_hi + A_hi X_lo + A_lo X_hi in FP32 in tensor memory. */
 #define QD_TC_TF32X3 0 /* tensor cores, TF32 parts (about 2^-21 relative per block); the default */
 #define QD_TC_BF16X3 1 /* tensor cores, BF16 parts (about 2^-16 relative per block); blocks without
-                          controls stream the state through a ring of shared-memory tiles (the
-                          classes of a tile as tensor-memory rows of the MMA's A operand) */
+                          controls (9..64 dimensions) stream the state through a ring of
+                          shared-memory tiles (the classes of a tile as tensor-memory rows of
+                          the MMA's A operand) */
 #define QD_TC_OFF 2    /* FP32 CUDA cores (binary32 FMA, no split) */
 
 typedef struct qd_fusion_opts {
@@ -264,7 +267,7 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
  * qd_state_set_amplitudes and qd_state_reset discard the queue (the state
  * is overwritten).  max_block_dim <= 1 flushes and returns to one launch
  * per call; tc_mode also selects the arithmetic of unfused complex64
- * multi-wire gates of 17..64 dimensions.  QD_ERR_ARG for an unknown
+ * multi-wire gates of 17..64 dimensions (BF16X3 without controls: 9..64).  QD_ERR_ARG for an unknown
  * tc_mode. */
 qd_status qd_set_fusion(qd_state* st, int32_t max_block_dim, int32_t tc_mode);
 

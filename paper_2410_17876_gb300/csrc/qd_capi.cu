@@ -628,7 +628,8 @@ static qd_status apply_now(qd_state* st, const int32_t* wires, int32_t k, const 
         if (e != cudaSuccess) return cuda_fail(e, "gate kernel");
         return QD_OK;
     }
-    if (st->prec == QD_C64 && p.P >= kTcMinP && st->tc_mode != QD_TC_OFF) {
+    if (st->prec == QD_C64 && st->tc_mode != QD_TC_OFF &&
+        (p.P >= kTcMinP || (st->tc_mode == QD_TC_BF16X3 && nc == 0 && p.P >= kRingMinP))) {
         // tensor-core block: through the circuit path (descriptor upload + launch)
         qd_gate_desc g{};
         g.n_wires = k;

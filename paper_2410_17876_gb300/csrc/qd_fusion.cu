@@ -2069,7 +2069,7 @@ static Op gate_op(void* psi, const Plan& p, const double* U, Program& prog, int 
         }
     }
     const int P = p.P;
-    if (sizeof(R) == 4 && P >= kTcMinP && tc_mode == QD_TC_BF16X3 && ncontrols == 0) {
+    if (sizeof(R) == 4 && P >= kRingMinP && tc_mode == QD_TC_BF16X3 && ncontrols == 0) {
         // BF16x3 through the ring of tiles, where the block suits it
         std::vector<unsigned char> bops;
         std::shared_ptr<const BlockRing> ring = block_ring_prepare(L, reinterpret_cast<float2*>(psi), wires, nwires, P,

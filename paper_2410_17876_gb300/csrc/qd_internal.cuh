@@ -253,6 +253,7 @@ cudaError_t launch_block_ring(const BlockRing& r, const void* b_ops, cudaStream_
 int32_t tc_status_take(cudaStream_t s);
 int32_t* tc_status_ptr();  // device status word shared by the kernels with bounded waits
 constexpr int kTcMinP = 17;  // complex64 blocks of at least this dimension go to the tensor cores
+constexpr int kRingMinP = 9;  // BF16x3: blocks without controls of at least this dimension, through the tile ring
 
 int reduce_blocks(int64_t D);
 

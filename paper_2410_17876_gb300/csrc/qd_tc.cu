@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_block_tc(const __grid_constan
 
 
 // ---------------------------------------------------------------------------
-// BF16x3 blocks over a ring of tiles (complex64, 17..64 dimensions, no
+// BF16x3 blocks over a ring of tiles (complex64, 9..64 dimensions, no
 // controls).
 //
 // The state is cut into tiles: a tile holds the Q x P amplitudes whose
@@ -1125,7 +1125,7 @@ constexpr size_t kRingMinSmem = 120 * 1024;  // > 228 KB / 2
 std::shared_ptr<const BlockRing> block_ring_prepare(const Layout& L, float2* psi, const int32_t* wires, int k,
                                                     int P, const double* U, bool renorm,
                                                     std::vector<unsigned char>& b_ops) {
-    if (k < 1 || P < kTcMinP || P > kMaxGateDim) return nullptr;
+    if (k < 1 || P < kRingMinP || P > kMaxGateDim) return nullptr;
     uint64_t W = 0;
     int64_t Pw = 1;
     for (int i = 0; i < k; ++i) {
@@ -1307,6 +1307,7 @@ cudaError_t launch_block_ring(const BlockRing& r, const void* b_ops, cudaStream_
     const unsigned grid = (unsigned)(a.ntiles < (uint32_t)sm_count ? a.ntiles : (uint32_t)sm_count);
     cudaError_t e;
     switch (r.ph) {
+        case 16: e = launch_ring_ph<16>(a, r.smem, grid, s); break;
         case 24: e = launch_ring_ph<24>(a, r.smem, grid, s); break;
         case 32: e = launch_ring_ph<32>(a, r.smem, grid, s); break;
         case 40: e = launch_ring_ph<40>(a, r.smem, grid, s); break;

@@ -1,4 +1,4 @@
-"""GPU parity of the BF16x3 tile-ring kernel (complex64 blocks of 17..64
+"""GPU parity of the BF16x3 tile-ring kernel (complex64 blocks of 9..64
 dimensions without controls) against the oracle: tiles of up to 512
 classes cut into chunks of 128 (the last one partial: 243, 216 and 144
 classes), one to four chunks per tile, two to six ring slots, odd row lengths (8-byte copies instead
@@ -66,6 +66,9 @@ CASES = [
     ((4, 4, 4, 2, 3), (0, 1, 2)),
     # P = 48 on wires 0..2, the classes above the block
     ((4, 3, 4, 2, 3, 2, 2, 2, 3), (0, 1, 2)),
+    # P = 9 and P = 16 (padded to 16 rows of the operand)
+    ((2, 2, 3, 2, 2, 3, 2, 2, 2, 2, 2), (2, 5)),
+    ((2, 3, 2, 2, 4, 2, 2, 2, 2, 2, 3, 2, 2), (4, 8, 7)),
     # several chunks of classes per tile (512 = 4 x 128, 16 tiles; 384 = 3 x 128 with qutrits among the class wires)
     ((2,) * 12 + (3, 4, 2, 2), (12, 13, 0)),
     ((2, 2, 2, 2, 2, 2, 2, 3, 2, 3, 2, 2, 2), (9, 12, 0, 1)),
@@ -76,7 +79,7 @@ CASES = [
 def test_ring_block_matches_oracle(qb, gen, dims, wires):
     rng = np.random.Generator(np.random.PCG64(sum(dims) + 7 * len(wires)))
     P = int(np.prod([dims[w] for w in wires]))
-    assert 17 <= P <= 64
+    assert 9 <= P <= 64
     psi0 = gen.random_state(int(np.prod(dims)), rng)
     g = gen.Gate(wires, gen.haar(P, rng))
     got, ring = _apply(qb, dims, [g, g], psi0)
