@@ -1039,6 +1039,11 @@ def run_gpu(args):
     step_method_flops = sum(v["method_flops"] for v in fam.values())
 
     # ---- end to end through the public API with host buffers ----
+    # The serving trace's generation (host threads: Python and the linear
+    # algebra library) ends first: running beside the read-back it made the
+    # 13.76 GB copies alternate between ~92 and ~240 ms (71 ms alone).
+    if trace_thread is not None:
+        trace_thread.join()
     state_bytes = circ.D * amp_bytes
     h2d = sum(g.U.size * 16 + 8 * len(g.controls) for g in circ.gates)
     e2e = None
@@ -1057,8 +1062,7 @@ def run_gpu(args):
             st.norm()
             qb.qd_state_get_raw(st.handle, host_out)
             per_step.append(time.perf_counter() - t0)
-        # the median step: the 13.76 GB read-back varies from 71 to 330 ms between identical copies on
-        # this shared node (host-memory bandwidth), which the median keeps out of the value
+        # the median step (the read-back of 13.76 GB at the host link's ~193 GB/s is most of a step)
         e2e_s = max_over_ranks(statistics.median(per_step), world)
         e2e = {"value": world * upd / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s, "ms_per_step_mean": 1e3 * statistics.mean(per_step),
@@ -1091,7 +1095,6 @@ def run_gpu(args):
         torch.cuda.empty_cache()
         extra["batched"] = measure_batched(qb, gen, torch, stream)
         torch.cuda.empty_cache()
-        trace_thread.join()
         extra["serving"] = measure_serving(qb, gen, torch, trace_box[0])
         torch.cuda.empty_cache()
 
