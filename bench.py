@@ -1039,9 +1039,8 @@ def run_gpu(args):
     step_method_flops = sum(v["method_flops"] for v in fam.values())
 
     # ---- end to end through the public API with host buffers ----
-    # The serving trace's generation (host threads: Python and the linear
-    # algebra library) ends first: running beside the read-back it made the
-    # 13.76 GB copies alternate between ~92 and ~240 ms (71 ms alone).
+    # The serving trace's generation (host threads) ends first, so that the
+    # host is otherwise idle during these steps.
     if trace_thread is not None:
         trace_thread.join()
     state_bytes = circ.D * amp_bytes
