@@ -88,7 +88,9 @@ qd_status qd_state_wrap(void* dev_ptr, size_t bytes, const int32_t* dims, int32_
  * state's stream.  NULL is accepted. */
 qd_status qd_state_destroy(qd_state* st);
 
-/* Set the state to the basis state |0...0>. */
+/* Set the state to the basis state |0...0>.  Asynchronous: two kernels on
+ * the state's stream (a fill of every amplitude with zero, then the one set
+ * to 1), no runtime memset. */
 qd_status qd_state_reset(qd_state* st);
 
 /* Issue the state's later work on another cudaStream_t (NULL = default). */
@@ -111,6 +113,18 @@ qd_status qd_state_get_amplitudes(qd_state* st, double* host_interleaved);
 /* Copy the raw amplitudes (2*D floats for QD_C64, 2*D doubles for QD_C128)
  * to host memory of `bytes` bytes.  Synchronous. */
 qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes);
+
+/* The same copy, enqueued on the state's stream; the call returns without
+ * waiting for it.  Queued gates and the lazy frame are applied first, as
+ * for qd_state_get_raw.  The host buffer belongs to the caller and may be
+ * read after qd_synchronize on this state; it should be page-locked
+ * (cudaHostAlloc, or pinned by the caller's framework), since the CUDA
+ * runtime runs a copy into pageable memory through its own staging and
+ * returns only once it has landed.  With two states on two streams, one
+ * state's read-back then runs while the other state computes.  QD_ERR_ARG
+ * for NULL arguments or a buffer smaller than the state; QD_ERR_CUDA if the
+ * copy cannot be enqueued. */
+qd_status qd_state_get_raw_async(qd_state* st, void* host, size_t bytes);
 
 /* Checkpoint and resume (the paper has no counterpart).  qd_state_save
  * writes the state (after any queued gates and the lazy frame) to a file:

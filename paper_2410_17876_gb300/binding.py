@@ -92,6 +92,7 @@ _SIGS = {
     "qd_state_set_amplitudes": (ctypes.c_int32, [_vp, _f64p]),
     "qd_state_get_amplitudes": (ctypes.c_int32, [_vp, _f64p]),
     "qd_state_get_raw": (ctypes.c_int32, [_vp, _vp, ctypes.c_size_t]),
+    "qd_state_get_raw_async": (ctypes.c_int32, [_vp, _vp, ctypes.c_size_t]),
     "qd_apply_gate": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p]),
     "qd_apply_controlled": (ctypes.c_int32, [_vp, ctypes.c_int32, _f64p, _i32p, _i32p, ctypes.c_int32]),
     "qd_apply_multi": (ctypes.c_int32, [_vp, _i32p, ctypes.c_int32, _f64p, _i32p, _i32p, ctypes.c_int32]),
@@ -253,6 +254,16 @@ def qd_state_get_raw(st: int, out: Optional[np.ndarray] = None) -> np.ndarray:
     if out is None:
         out = np.empty(D, dtype=dt)
     _check(_lib.qd_state_get_raw(_vp(st), _vp(out.ctypes.data), out.nbytes), "qd_state_get_raw")
+    return out
+
+
+def qd_state_get_raw_async(st: int, out: np.ndarray) -> np.ndarray:
+    """Enqueue the copy of the native-precision amplitudes into ``out`` (a
+    contiguous array the caller keeps alive, ideally page-locked) on the
+    state's stream; read it after ``qd_synchronize``."""
+    if not out.flags.c_contiguous:
+        raise ValueError("out must be contiguous")
+    _check(_lib.qd_state_get_raw_async(_vp(st), _vp(out.ctypes.data), out.nbytes), "qd_state_get_raw_async")
     return out
 
 

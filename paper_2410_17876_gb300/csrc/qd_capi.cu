@@ -967,6 +967,16 @@ qd_status qd_state_get_raw(qd_state* st, void* host, size_t bytes) {
     QD_GUARD_END
 }
 
+qd_status qd_state_get_raw_async(qd_state* st, void* host, size_t bytes) {
+    QD_GUARD_BEGIN
+    if (!st || !host) return fail(QD_ERR_ARG, "state or host buffer is NULL");
+    QD_MATERIALIZE(st);
+    if (bytes < st->bytes) return fail(QD_ERR_ARG, "host buffer of %zu bytes < %zu", bytes, st->bytes);
+    QD_CUDA(cudaMemcpyAsync(host, st->psi, st->bytes, cudaMemcpyDeviceToHost, st->stream), "download");
+    return QD_OK;
+    QD_GUARD_END
+}
+
 qd_status qd_apply_gate(qd_state* st, int32_t target, const double* U) {
     qd::NvtxRange nvtx_("qd_apply_gate");
     QD_GUARD_BEGIN

@@ -8,6 +8,8 @@
 // tile column) owns one class and no synchronisation between classes is
 // needed -- the parallelism "across blocks as well as the repetitions of
 // the blocks" that the paper leaves as future scope.
+#include <algorithm>
+
 #include "qd_internal.cuh"
 
 namespace qd {
@@ -169,6 +171,17 @@ __global__ void __launch_bounds__(256) k_gate_tile(const __grid_constant__ GateT
             if (r < P && in_bounds(j + a.off[r], a.D)) a.psi[j + a.off[r]] = acc[i];
         }
     }
+}
+
+// Zero n words of the state (grid-stride); the reset's fill runs on the SMs
+// rather than as a runtime memset, which may be served by a copy engine and
+// then queue behind another stream's host copies.
+template <typename W>
+__global__ void k_zero_words(W* p, int64_t n) {
+    W z;
+    __builtin_memset(&z, 0, sizeof z);
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += step) p[i] = z;
 }
 
 template <typename R>
@@ -503,8 +516,30 @@ cudaError_t launch_gate1_scan(const Gate1Args<R, DT>& a, const ScanControls& c, 
 
 template <typename R>
 cudaError_t launch_set_basis(void* psi, int64_t D, int64_t index, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(psi, 0, (size_t)D * sizeof(typename Cplx<R>::T2), s);
-    if (e != cudaSuccess) return e;
+    // |index>: every amplitude zeroed (16-byte stores where the buffer allows,
+    // the state's size is a multiple of 8 bytes), then the one set to 1.
+    const int64_t bytes = D * (int64_t)sizeof(typename Cplx<R>::T2);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms <= 0)
+        sms = 152;
+    auto grid = [sms](int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 8); };
+    if (reinterpret_cast<uintptr_t>(psi) % 16 == 0) {
+        const int64_t n16 = bytes / 16;
+        if (n16 > 0) {
+            k_zero_words<ulonglong2><<<grid(n16), 256, 0, s>>>(reinterpret_cast<ulonglong2*>(psi), n16);
+            count_launch();
+        }
+        if (bytes % 16 != 0) {
+            k_zero_words<unsigned long long><<<1, 32, 0, s>>>(
+                reinterpret_cast<unsigned long long*>(psi) + 2 * n16, 1);
+            count_launch();
+        }
+    } else {
+        k_zero_words<unsigned long long><<<grid(bytes / 8), 256, 0, s>>>(
+            reinterpret_cast<unsigned long long*>(psi), bytes / 8);
+        count_launch();
+    }
     k_set_basis<R><<<1, 1, 0, s>>>(reinterpret_cast<typename Cplx<R>::T2*>(psi), index);
     count_launch();
     return cudaGetLastError();

@@ -287,6 +287,18 @@ def config2_circuit(seed: int = 2, depth: int = 200, n_qubits: int = 18,
     return Circuit(dims, gates)
 
 
+def redraw_haar(circ: Circuit, seed: int) -> Circuit:
+    """The same circuit with every gate named "haar" or "CU" given a fresh
+    Haar matrix of its size (seeded): the same wires, controls and gate kinds,
+    so the same work, with new matrices."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    gates = []
+    for g in circ.gates:
+        U = haar(g.U.shape[0], rng) if g.name in ("haar", "CU") else g.U
+        gates.append(Gate(g.wires, U, g.controls, g.values, name=g.name))
+    return Circuit(circ.dims, gates)
+
+
 def prefix_circuit(circ: Circuit, n_prefix: int) -> Circuit:
     """The gates of ``circ`` whose wires all lie in the lowest ``n_prefix`` wires."""
     keep = []
