@@ -1068,6 +1068,7 @@ def run_gpu(args):
             qb.qd_state_get_raw(s_.handle, o_)
         barrier(world)
         starts, norms = [], []
+        up0 = qb.qd_bytes_uploaded()
         t0 = time.perf_counter()
         for i in range(e2e_steps):
             s_, o_ = states[i % nbuf], outs[i % nbuf]
@@ -1082,11 +1083,13 @@ def run_gpu(args):
         for s_ in states:
             s_.synchronize()
         total = time.perf_counter() - t0
+        uploaded = (qb.qd_bytes_uploaded() - up0) // e2e_steps
         last = (e2e_steps - 1) % nbuf
         head = states[last].buf[:2000].cpu().numpy().view(np.complex64)
         readback_ok = bool(np.array_equal(outs[last][:1000], head))
         e2e_s = max_over_ranks(total / e2e_steps, world)
-        e2e = {"value": world * upd / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": world * upd / e2e_s, "unit": UNIT, "h2d_bytes_per_step": uploaded,
+               "gate_input_bytes_per_step": h2d,
                "d2h_bytes_per_step": outs[0].nbytes + 8, "steps": e2e_steps, "ms_per_step": 1e3 * e2e_s,
                "ms_total": 1e3 * total,
                "ms_between_step_starts": [round(1e3 * (b - a), 1) for a, b in zip(starts, starts[1:])],
@@ -1094,7 +1097,9 @@ def run_gpu(args):
                "readback_matches_device": readback_ok, "host_mem_available_gb": round(avail / 1e9, 1),
                "what": "every step a new circuit of the workload's shape (fresh Haar matrices from host "
                        "memory: planned, composed and uploaded by qd_apply_circuit), the norm read on the "
-                       "host, and the whole final state copied into pinned host memory (qd_state_get_raw_async)"
+                       "host, and the whole final state copied into pinned host memory (qd_state_get_raw_async); "
+                       "h2d_bytes_per_step: the descriptors, composed block matrices and tensor-core operands the "
+                       "library uploaded (qd_bytes_uploaded), built from gate_input_bytes_per_step of gate records"
                        + ("; two states on two streams alternate, so a step's read-back overlaps the next "
                           "step's compute; time from the first step's start to the last read-back's end"
                           if nbuf == 2 else "; one state, steps back to back")}

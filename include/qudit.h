@@ -576,6 +576,13 @@ const char* qd_last_error(void);
 /* Number of kernels this library has launched in the process so far. */
 uint64_t qd_launch_count(void);
 
+/* Bytes of gate data this library has copied from host to device memory in
+ * the process so far: circuit descriptors (with composed block matrices and
+ * tensor-core operands) and single-gate matrices.  Amplitude uploads
+ * (qd_state_set_amplitudes, qd_state_load) and the batch and sparse paths'
+ * own uploads are not counted. */
+uint64_t qd_bytes_uploaded(void);
+
 /* Library version string. */
 const char* qd_version(void);
 

@@ -115,6 +115,7 @@ _SIGS = {
     "qd_norm_noalloc": (ctypes.c_int32, [_vp, ctypes.c_int64, ctypes.c_int32, _vp, _vp]),
     "qd_last_error": (ctypes.c_char_p, []),
     "qd_launch_count": (ctypes.c_uint64, []),
+    "qd_bytes_uploaded": (ctypes.c_uint64, []),
     "qd_version": (ctypes.c_char_p, []),
     "qd_plan_gate": (ctypes.c_int32, [_i32p, ctypes.c_int32, ctypes.c_int32, _i32p, ctypes.c_int32, _f64p,
                                       _i32p, _i32p, ctypes.c_int32, ctypes.POINTER(qd_plan_info)]),
@@ -365,6 +366,10 @@ def qd_last_error() -> str:
 
 def qd_launch_count() -> int:
     return int(_lib.qd_launch_count())
+
+
+def qd_bytes_uploaded() -> int:
+    return int(_lib.qd_bytes_uploaded())
 
 
 def qd_version() -> str:

@@ -20,6 +20,8 @@ namespace qd {
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+static std::atomic<uint64_t> g_uploaded{0};
+void count_upload(size_t bytes) { g_uploaded.fetch_add((uint64_t)bytes, std::memory_order_relaxed); }
 
 static thread_local std::string g_err;
 
@@ -365,6 +367,7 @@ static qd_status run_tile(qd_state* st, const Plan& p, const double* U) {
         h[i].y = (R)U[2 * i + 1];
     }
     QD_CUDA(cudaMemcpyAsync(dptr, h, sizeof(T2) * P * P, cudaMemcpyHostToDevice, st->stream), "matrix upload");
+    count_upload(sizeof(T2) * P * P);
     QD_CUDA(cudaEventRecord(st->ring_ev[s], st->stream), "matrix ring record");
     GateTileArgs<R> a;
     std::memset(static_cast<void*>(&a), 0, sizeof a);
@@ -1146,6 +1149,8 @@ qd_status qd_flush(qd_state* st) {
 const char* qd_last_error(void) { return g_err.c_str(); }
 
 uint64_t qd_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+uint64_t qd_bytes_uploaded(void) { return g_uploaded.load(std::memory_order_relaxed); }
 
 const char* qd_version(void) { return "qudit-gb300 0.1 (sm_103a)"; }
 

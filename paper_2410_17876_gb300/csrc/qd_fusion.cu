@@ -2012,6 +2012,7 @@ qd_status Arena::upload(const void* bytes, size_t n, cudaStream_t s) {
     }
     std::memcpy(host, bytes, n);
     QD_CUDA(cudaMemcpyAsync(dev, host, n, cudaMemcpyHostToDevice, s), "descriptor upload");
+    count_upload(n);
     QD_CUDA(cudaEventRecord(ev, s), "descriptor event");
     return QD_OK;
 }
@@ -2836,6 +2837,7 @@ static qd_status cache_build(qd_state* st, CircuitCache& c, const std::vector<HG
         std::memcpy(c.host, prog.desc.data(), prog.desc.size());
         QD_CUDA(cudaMemcpyAsync(c.dev, c.host, prog.desc.size(), cudaMemcpyHostToDevice, st->stream),
                 "circuit cache upload");
+        count_upload(prog.desc.size());
     }
     if (!c.ev_live) {
         QD_CUDA(cudaEventCreateWithFlags(&c.done, cudaEventDisableTiming), "circuit cache event");

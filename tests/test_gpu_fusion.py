@@ -174,7 +174,9 @@ def test_repeated_circuit_is_built_once_and_stays_exact(qb, gen):
     """A gate list repeated on the same state is planned, composed and
     uploaded once (the second call) and only launched afterwards: every call
     gives the same bits as the first, and changing one matrix entry, the
-    fusion settings or the gate order is seen as a different circuit."""
+    fusion settings or the gate order is seen as a different circuit.  The
+    library's count of uploaded gate bytes shows the uploads: every call
+    uploads except a repeat of an already built circuit."""
     import oracle
 
     rng = np.random.Generator(np.random.PCG64(515))
@@ -186,11 +188,14 @@ def test_repeated_circuit_is_built_once_and_stays_exact(qb, gen):
     U[0, 0] *= -1.0  # no longer unitary, still a valid gate
     c2.gates[7] = gen.Gate(g.wires, U, g.controls, g.values)
     st = qb.State(dims, prec=qb.QD_C64)
-    outs = []
+    outs, uploaded = [], []
     for c in (c1, c1, c1, c1, c2, c1, c2, c2, c2):
         st.reset()
+        u0 = qb.qd_bytes_uploaded()
         st.run(c, fuse="tile")
+        uploaded.append(qb.qd_bytes_uploaded() - u0)
         outs.append(st.raw().copy())
+    assert [i for i, u in enumerate(uploaded) if u == 0] == [2, 3, 8], uploaded
     st.reset()
     st.run(c1, fuse="tile", block_dim=4)
     other_opts = st.raw().copy()
