@@ -127,3 +127,26 @@ def test_config2_method_flops_and_updates():
     u = bench.circuit_updates(c)
     # dense gates cost 16 (qubit) or 24 (qutrit) flops per touched amplitude
     assert 0.5 * 16 * u < f < 24 * u
+
+
+def test_end_to_end_circuits_keep_the_workload_shape():
+    """The end-to-end steps' circuits: the large workload's wires, controls
+    and gate kinds with fresh unitary Haar matrices (seeded), so each step
+    does the same updates and method flops on new inputs."""
+    from paper_2410_17876_gb300 import binding as qb
+
+    c = gen.config2_circuit()
+    a, b, a2 = gen.redraw_haar(c, 1000), gen.redraw_haar(c, 1001), gen.redraw_haar(c, 1000)
+    assert bench.circuit_updates(a) == bench.circuit_updates(c)
+    assert bench.circuit_method_flops(qb, a, qb.QD_C64) == bench.circuit_method_flops(qb, c, qb.QD_C64)
+    redrawn = 0
+    for g0, ga, gb, ga2 in zip(c.gates, a.gates, b.gates, a2.gates):
+        assert (ga.wires, ga.controls, ga.values, ga.name) == (g0.wires, g0.controls, g0.values, g0.name)
+        assert np.array_equal(ga.U, ga2.U)
+        assert np.allclose(ga.U @ ga.U.conj().T, np.eye(ga.U.shape[0]), atol=1e-12)
+        if g0.name in ("haar", "CU"):
+            assert not np.allclose(ga.U, g0.U) and not np.allclose(ga.U, gb.U)
+            redrawn += 1
+        else:
+            assert np.array_equal(ga.U, g0.U)
+    assert redrawn > 150
