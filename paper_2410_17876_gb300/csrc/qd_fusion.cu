@@ -2772,6 +2772,11 @@ qd_status qd_apply_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_ga
 struct qd::CircuitCache {
     std::vector<char> key;
     bool seen = false, built = false;
+    // the last whole-state block plan and its structure key (settings,
+    // every gate's wires, controls and diagonal flag; no matrix values):
+    // the plan depends on nothing else
+    std::vector<char> skey;
+    std::vector<PassPlan> splan;
     Program prog;
     void* dev = nullptr;   // descriptors of prog
     void* host = nullptr;  // pinned copy they were uploaded from
@@ -2810,13 +2815,48 @@ static void circuit_key(const FuseCfg& cfg, const std::vector<HGate>& G, std::ve
     }
 }
 
+// The pass plan of G; QD_FUSE_BLOCK plans are kept per structure, so a
+// circuit that differs from the last one only in its matrices is not
+// planned again.
+static void plan_cached(const qd_state* st, CircuitCache& c, const std::vector<HGate>& G, const FuseCfg& cfg,
+                        std::vector<PassPlan>& passes) {
+    if (cfg.mode != QD_FUSE_BLOCK) {
+        plan_passes(st->L, G, cfg, passes);
+        return;
+    }
+    std::vector<char> key;
+    auto put = [&](const void* p, size_t n) {
+        const char* b = static_cast<const char*>(p);
+        key.insert(key.end(), b, b + n);
+    };
+    put(&cfg, sizeof cfg);
+    const size_t n = G.size();
+    put(&n, sizeof n);
+    for (const HGate& h : G) {
+        put(&h.k, sizeof h.k);
+        put(&h.nc, sizeof h.nc);
+        put(h.wires, sizeof(int) * (size_t)h.k);
+        put(h.cw, sizeof(int) * (size_t)h.nc);
+        put(h.cv, sizeof(int) * (size_t)h.nc);
+        const char d = h.diag ? 1 : 0;
+        put(&d, 1);
+    }
+    if (!c.skey.empty() && key == c.skey) {
+        passes = c.splan;
+        return;
+    }
+    plan_passes(st->L, G, cfg, passes);
+    c.skey.swap(key);
+    c.splan = passes;
+}
+
 // Build the whole circuit as one program, upload its descriptors to the
 // cache's own device buffer (after the previous program's launches have
 // finished with it) and mark it built.
 static qd_status cache_build(qd_state* st, CircuitCache& c, const std::vector<HGate>& G, const FuseCfg& cfg) {
     Program prog;
     std::vector<PassPlan> passes;
-    plan_passes(st->L, G, cfg, passes);
+    plan_cached(st, c, G, cfg, passes);
     if (st->prec == QD_C64)
         build_passes<float>(st->L, st->psi, G, cfg, passes, 0, passes.size(), prog);
     else
@@ -2880,7 +2920,7 @@ qd_status qd::run_circuit(qd_state* st, const qd_gate_desc* gates, int32_t n_gat
         // previous one.  Two descriptor arenas alternate, so an upload only
         // waits for the copy two segments back.
         std::vector<PassPlan> passes;
-        plan_passes(st->L, G, cfg, passes);
+        plan_cached(st, cc, G, cfg, passes);
         if (!st->arena) st->arena = new Arena[2];
         size_t i = 0;
         for (int seg = 0; i < passes.size(); ++seg) {

@@ -112,3 +112,42 @@ def test_sparse_qubit_blocks_become_register_runs():
     order, _, _ = _check_plan(circ, qb.QD_C64, mode=qb.QD_FUSE_TILE, max_tile_amps=1024)
     psi0 = gen.random_state(circ.D, rng)
     assert np.max(np.abs(oracle.run_circuit(circ, psi0) - oracle.run_circuit(_reordered(circ, order), psi0))) < 1e-12
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("block_dim", [16, 64])
+def test_whole_state_blocks_preserve_the_result(seed, block_dim):
+    """QD_FUSE_BLOCK plans: every gate once, every block within block_dim
+    dimensions, and the executed order gives the same state."""
+    rng = np.random.Generator(np.random.PCG64(100 + seed))
+    dims = tuple(int(x) for x in rng.choice([2, 3, 4, 5], size=int(rng.integers(5, 9))))
+    circ = gen.random_mixed_circuit(dims, 150, rng)
+    extra = [gen.Gate((int(t),), gen.z_gen(dims[int(t)])) for t in rng.integers(len(dims), size=20)]
+    extra.append(gen.Gate((0, 1), gen.haar(dims[0] * dims[1], rng)))
+    circ = gen.Circuit(dims, circ.gates[:60] + extra + circ.gates[60:])
+    order, pass_of, _ = qb.qd_plan_circuit(dims, qb.QD_C64, circ, mode=qb.QD_FUSE_BLOCK, block_dim=block_dim)
+    n = len(circ.gates)
+    assert sorted(order.tolist()) == list(range(n))
+    assert np.all(np.diff(pass_of) >= 0)
+    for p in range(pass_of[-1] + 1):
+        gates = [circ.gates[order[i]] for i in np.nonzero(pass_of == p)[0]]
+        if len(gates) > 1:
+            wires = set()
+            for g in gates:
+                assert len(g.wires) == 1
+                wires |= set(g.wires) | set(g.controls)
+            assert np.prod([dims[w] for w in wires]) <= block_dim
+    psi0 = gen.random_state(circ.D, rng)
+    a = oracle.run_circuit(circ, psi0)
+    b = oracle.run_circuit(_reordered(circ, order), psi0)
+    assert np.max(np.abs(a - b)) < 1e-12
+
+
+def test_whole_state_block_pass_counts_of_the_workloads():
+    """Blocks of up to 64 dimensions grown by the wires that take the most
+    gates: 20 passes for the 200 gates of the 18-qubit + 8-qutrit workload
+    (adding wires in gate order: 25) and 39 for the 500 gates of the
+    12-qubit + 8-qutrit circuit."""
+    for circ, most in ((gen.config2_circuit(), 20), (gen.config1_circuit(), 39)):
+        _, pass_of, _ = qb.qd_plan_circuit(circ.dims, qb.QD_C64, circ, mode=qb.QD_FUSE_BLOCK, block_dim=64)
+        assert pass_of[-1] + 1 <= most, pass_of[-1] + 1
