@@ -287,7 +287,5 @@ cudaError_t launch_wire_move(const void* src, void* dst, int64_t lo, int64_t d, 
                              cudaStream_t s);
 
 void count_launch(int n = 1);
-// Host-to-device bytes of gate data (descriptors and matrices) copied so far.
-void count_upload(size_t bytes);
 
 }  // namespace qd

@@ -131,4 +131,6 @@ qd_status materialize(qd_state* st);  // apply the lazy frame to the device stat
 qd_status apply_any(qd_state* st, const int32_t* wires, int32_t k, const double* U, const int32_t* cw,
                     const int32_t* cv, int32_t nc);
 qd_status read_out(qd_state* st, int count, double* host);
+// Host-to-device bytes of gate data (descriptors and matrices) copied so far.
+void count_upload(size_t bytes);
 }  // namespace qd
